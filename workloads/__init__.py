@@ -1,0 +1,307 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+This module only draws random numbers and random relabelings.  It holds none
+of the batched-einsum arithmetic (no contraction, no canonicalization), so
+both the oracle under ``oracle/`` and the CUDA path may take their inputs
+from here without sharing any of the method's code.
+
+Every generator uses numpy's PCG64 with a fixed base seed per workload plus a
+per-tensor offset, so a given (workload, size) always yields the same arrays.
+
+Workload shapes follow the paper's FEM / DG / chemistry examples:
+  * FEM action  'ij,ej->ei', b=4, D 4x4 shared, E=4096 (Sec. "Batched
+    Einstein Summation", the hot-loop example, and the motivating
+    FEM operator of the introduction).
+  * DG local gradient split per derivative direction x, P4 tetrahedron
+    (35 dofs), E=262144 elements, u = sin(a)*b fused into the operand load
+    (Sec. "Batched einsums in DG-FEM Operators", local gradient tuple and
+    the gradient kernel pattern of Appendix C).
+  * Chemistry-style dense contraction 'abef,efij->abij' with v=128, o=32
+    (the cluster-operator form quoted in the introduction).
+  * An uneven mix drawn from twelve notations that appear in the paper.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+import string
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BASE_SEED = 1000
+
+# --------------------------------------------------------------------------
+# helpers
+# --------------------------------------------------------------------------
+
+
+def rng(workload: int, offset: int = 0) -> np.random.Generator:
+    """PCG64 stream for tensor ``offset`` of workload ``workload``."""
+    return np.random.Generator(np.random.PCG64([BASE_SEED + workload, offset]))
+
+
+def uniform(workload, offset, shape, lo=-1.0, hi=1.0):
+    return rng(workload, offset).uniform(lo, hi, size=shape)
+
+
+def normal(workload, offset, shape):
+    return rng(workload, offset).standard_normal(size=shape)
+
+
+def small_ints(workload, offset, shape, lo=-3, hi=3):
+    """Integer-valued float64 entries in [lo, hi]: products and sums of these
+    stay exact in FP64, so any correct evaluation order gives the same bits."""
+    return rng(workload, offset).integers(lo, hi + 1, size=shape).astype(np.float64)
+
+
+# --------------------------------------------------------------------------
+# Workload 1: FEM action 'ij,ej->ei'
+# --------------------------------------------------------------------------
+
+FEM_SPEC_NOTATION = "ij,ej->ei"
+
+
+def fem_action(E: int = 4096, ndof: int = 4, b: int = 4, ints: bool = False):
+    """Shared reference matrix D (ndof x ndof) and b field arrays u_k (E x ndof),
+    all uniform[-1, 1] (or small integers when ``ints``)."""
+    gen = small_ints if ints else uniform
+    D = gen(1, 0, (ndof, ndof))
+    us = [gen(1, 1 + k, (E, ndof)) for k in range(b)]
+    return D, us
+
+
+def fem_action_spec(E: int = 4096, ndof: int = 4, b: int = 4) -> str:
+    rows = " | ".join(f"D,u{k}" for k in range(b))
+    decls = " ; ".join([f"D:f64[{ndof},{ndof}]"] + [f"u{k}:f64[{E},{ndof}]" for k in range(b)])
+    return f"{FEM_SPEC_NOTATION} | {rows} ; {decls}"
+
+
+# --------------------------------------------------------------------------
+# Workload 2: DG local gradient with a functional field operand
+# --------------------------------------------------------------------------
+
+
+def dg_gradient(E: int = 262144, ndof: int = 35, dim: int = 3, ints: bool = False):
+    """D[r,i,j] (dim x ndof x ndof), geometric factors G[e,r,x] (E x dim x dim),
+    fields a, b (E x ndof); all N(0,1) in FP64 (small integers when ``ints``;
+    the fused producer then stays exact only if it has no transcendental)."""
+    if ints:
+        D = small_ints(2, 0, (dim, ndof, ndof))
+        G = small_ints(2, 1, (E, dim, dim))
+        a = small_ints(2, 2, (E, ndof))
+        b = small_ints(2, 3, (E, ndof))
+    else:
+        D = normal(2, 0, (dim, ndof, ndof))
+        G = normal(2, 1, (E, dim, dim))
+        a = normal(2, 2, (E, ndof))
+        b = normal(2, 3, (E, ndof))
+    return D, G, a, b
+
+
+def dg_gradient_spec(E: int = 262144, ndof: int = 35, dim: int = 3, producer: str = "sin(a[e,j])*b[e,j]") -> str:
+    """Text of the DG gradient batched einsum: row x computes
+    R_x[e,i] = sum_{r,j} D[r,i,j] * G[e,r,x] * U[e,j] with U the fused field."""
+    rows = " | ".join(f"D,G{x},U" for x in range(dim))
+    decls = [f"D:f64[{dim},{ndof},{ndof}]", f"G:f64[{E},{dim},{dim}]",
+             f"a:f64[{E},{ndof}]", f"b:f64[{E},{ndof}]"]
+    decls += [f"G{x}(e,r) := G[e,r,{x}]" for x in range(dim)]
+    decls += [f"U(e,j) := {producer}"]
+    return f"rij,er,ej->ei | {rows} ; " + " ; ".join(decls)
+
+
+# --------------------------------------------------------------------------
+# Workload 3: dense chemistry-style contraction 'abef,efij->abij'
+# --------------------------------------------------------------------------
+
+
+def _decay(n1, n2):
+    g1 = np.arange(n1)[:, None]
+    g2 = np.arange(n2)[None, :]
+    return np.abs(g1 - g2).astype(np.float64)
+
+
+def chem_dense(v: int = 128, o: int = 32, b: int = 4, ints: bool = False):
+    """A_k[a,b,e,f] = N(0,1)*exp(-(|a-e|+|b-f|)/8) (v^4 each, k=1..b) and the
+    shared T[e,f,i,j] = N(0,1)*exp(-(|e-i|+|f-j|)/8) (v^2 o^2).  "Index gap"
+    is read as the L1 distance between the paired indices.  With ``ints`` the
+    entries are small integers instead (exactly representable in FP16)."""
+    if ints:
+        As = [small_ints(3, 1 + k, (v, v, v, v)) for k in range(b)]
+        T = small_ints(3, 0, (v, v, o, o))
+        return As, T
+    dae = _decay(v, v)                      # |a-e|
+    w4 = np.exp(-(dae[:, None, :, None] + dae[None, :, None, :]) / 8.0)
+    As = []
+    for k in range(b):
+        A = normal(3, 1 + k, (v, v, v, v))
+        A *= w4
+        As.append(A)
+    dei = _decay(v, o)
+    wT = np.exp(-(dei[:, None, :, None] + dei[None, :, None, :]) / 8.0)
+    T = normal(3, 0, (v, v, o, o)) * wT
+    return As, T
+
+
+def chem_dense_spec(v: int = 128, o: int = 32, b: int = 4) -> str:
+    rows = " | ".join(f"A{k},T" for k in range(b))
+    decls = [f"A{k}:f64[{v},{v},{v},{v}]" for k in range(b)] + [f"T:f64[{v},{v},{o},{o}]"]
+    return f"abef,efij->abij | {rows} ; " + " ; ".join(decls)
+
+
+# --------------------------------------------------------------------------
+# Random relabelings (index renames, row permutations, operand swaps)
+# --------------------------------------------------------------------------
+
+
+@dataclass
+class Relabeled:
+    out: str
+    ins: list
+    rows: list
+    row_perm: list          # new row q is old row row_perm[q]
+    op_perm: list           # new operand p is old operand op_perm[p]
+    rename: dict            # old letter -> new letter
+
+
+def relabel(out: str, ins, rows, gen: np.random.Generator, arg_rename=None) -> Relabeled:
+    """Apply a random injective index rename into a..z, a random row
+    permutation and a random operand permutation (the same for all rows)."""
+    letters = sorted(set(out).union(*[set(s) for s in ins]))
+    targets = gen.permutation(list(string.ascii_lowercase))[: len(letters)]
+    rename = {c: str(t) for c, t in zip(letters, targets)}
+    b, n = len(rows), len(ins)
+    row_perm = [int(x) for x in gen.permutation(b)]
+    op_perm = [int(x) for x in gen.permutation(n)]
+    new_out = "".join(rename[c] for c in out)
+    new_ins = ["".join(rename[c] for c in ins[p]) for p in op_perm]
+    ar = arg_rename or (lambda a: a)
+    new_rows = [[ar(rows[q][p]) for p in op_perm] for q in row_perm]
+    return Relabeled(new_out, new_ins, new_rows, row_perm, op_perm, rename)
+
+
+# --------------------------------------------------------------------------
+# Notations of the uneven mix (all appear in the paper)
+# --------------------------------------------------------------------------
+
+# (name, notation).  Sources: matmul example; matvec of the transform-writer
+# listing; FEM action; DG gradient / divergence / face mass tuples; the
+# batched triple product; the Fig. 1 contraction; the canonical-form
+# example; the isomorphic-batched example; the two cluster contractions of
+# the introduction.
+MIX_NOTATIONS = [
+    ("matmul", "ik,kj->ij"),
+    ("matvec", "ij,j->i"),
+    ("fem_action", "ij,ej->ei"),
+    ("dg_gradient", "rij,er,ej->ei"),
+    ("dg_divergence", "xre,rij,xej->ei"),
+    ("face_mass", "fe,ifj,fej->ei"),
+    ("triple_product", "ik,kl,lj->ij"),
+    ("fig1", "mnj,mni,kli->ijkl"),
+    ("canon_example", "ij,ik->i"),
+    ("iso_example", "ijk,ik,ij,ij->i"),
+    ("cluster", "ijcd,cdab->ijab"),
+    ("tensor_train", "ij,kl,jl->ik"),
+]
+
+
+def _flops(out, ins, lens):
+    idx = set(out).union(*[set(s) for s in ins])
+    vol = 1
+    for c in idx:
+        vol *= lens[c]
+    return 2 * vol * max(1, len(ins) - 1) if len(ins) > 1 else vol
+
+
+@dataclass
+class Instance:
+    name: str
+    out: str
+    ins: list
+    rows: list
+    shapes: dict
+    dtype: str
+    lens: dict
+    row_perm: list = field(default_factory=list)
+    op_perm: list = field(default_factory=list)
+
+
+def mix_instance(gen: np.random.Generator, lo_exp=3.0, hi_exp=12.0,
+                 max_operand=1 << 22, max_flops=1 << 30, max_tries=1000) -> Instance:
+    """One instance of the uneven mix: a notation picked uniformly, index
+    lengths round(2^U(lo,hi)), resampled while an operand is too large or the
+    instance's flop count exceeds the cap; dtype f64 or f32 with p = 1/2;
+    b in {1..4} with the first operand shared by all rows; then a random
+    rename and row / operand permutation."""
+    name, notation = MIX_NOTATIONS[int(gen.integers(len(MIX_NOTATIONS)))]
+    lhs, out = notation.split("->")
+    ins = lhs.split(",")
+    letters = sorted(set(out).union(*[set(s) for s in ins]))
+    for _ in range(max_tries):
+        lens = {c: int(round(2.0 ** gen.uniform(lo_exp, hi_exp))) for c in letters}
+        sizes = [math.prod(lens[c] for c in s) for s in ins] + [math.prod(lens[c] for c in out)]
+        if max(sizes) <= max_operand and _flops(out, ins, lens) <= max_flops:
+            break
+    else:
+        raise RuntimeError("could not draw an instance under the caps")
+    dtype = "f64" if gen.random() < 0.5 else "f32"
+    b = int(gen.integers(1, 5))
+    rows = []
+    for q in range(b):
+        rows.append(["X0"] + [f"X{p}_{q}" for p in range(1, len(ins))])
+    r = relabel(out, ins, rows, gen)
+    shapes = {}
+    for row in r.rows:
+        for p, a in enumerate(row):
+            shapes[a] = tuple(lens[c] for c in _inv_letters(r.ins[p], r.rename))
+    new_lens = {r.rename[c]: lens[c] for c in letters}
+    return Instance(name, r.out, r.ins, r.rows, shapes, dtype, new_lens, r.row_perm, r.op_perm)
+
+
+def _inv_letters(s, rename):
+    inv = {v: k for k, v in rename.items()}
+    return [inv[c] for c in s]
+
+
+def instance_spec(inst: Instance) -> str:
+    rows = " | ".join(",".join(r) for r in inst.rows)
+    seen = []
+    for r in inst.rows:
+        for a in r:
+            if a not in seen:
+                seen.append(a)
+    decls = [f"{a}:{inst.dtype}[{','.join(str(x) for x in inst.shapes[a])}]" for a in seen]
+    return f"{','.join(inst.ins)}->{inst.out} | {rows} ; " + " ; ".join(decls)
+
+
+def instance_arrays(inst: Instance, gen: np.random.Generator, ints: bool = False):
+    """Arrays for every distinct argument of ``inst`` in first-appearance order."""
+    seen = []
+    for r in inst.rows:
+        for a in r:
+            if a not in seen:
+                seen.append(a)
+    out = {}
+    dt = np.float64 if inst.dtype == "f64" else np.float32
+    for a in seen:
+        if ints:
+            x = gen.integers(-2, 3, size=inst.shapes[a]).astype(dt)
+        else:
+            x = gen.uniform(-1.0, 1.0, size=inst.shapes[a]).astype(dt)
+        out[a] = x
+    return out
+
+
+def poisson_arrivals(rate: float, duration: float, seed_offset: int = 0):
+    """Arrival times (seconds) of a Poisson stream (workload 5)."""
+    g = rng(5, seed_offset)
+    t, ts = 0.0, []
+    while True:
+        t += g.exponential(1.0 / rate)
+        if t >= duration:
+            return np.asarray(ts)
+        ts.append(t)
+
+
+def all_permutations(n):
+    return list(itertools.permutations(range(n)))
