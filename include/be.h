@@ -1,0 +1,226 @@
+/*
+ * be.h -- C ABI of the B300 batched-einsum engine.
+ *
+ * A batched einsum (b, n, I_out, (I_in,j)_j, ((A^{i,j})_j)_i) is b einsums
+ * that share one Einstein notation and may share operands (paper, Sec.
+ * "Batched Einstein Summation", Def. of a batched einsum).  Its operands may
+ * be lambdas over buffers (Sec. "Integration of Optimized Batched Einsums
+ * into Practical Programs", Def. "Functional Batched Einstein Summation").
+ * The engine parses such a spec, maps it to a normal form (Sec. "A
+ * Canonical form for Batched Einsums", Alg. 1), looks a tuned configuration
+ * up under that form and transfers it to the caller's names (Alg. 2), and
+ * evaluates the batch on the GPU (Eq. (1) per row).
+ *
+ * Conventions for every call:
+ *   - Return value: BE_OK (0) or one of the BE_E* codes below.  No C++
+ *     exception crosses this boundary.  be_last_error() gives a message for
+ *     the calling thread's last failure.
+ *   - Handles (be_einsum, be_canon, be_ctx) are allocated by the library
+ *     and released by the matching be_free_* / be_ctx_destroy.
+ *   - Device memory passed in be_buf is owned by the caller and only
+ *     borrowed for the duration of the (asynchronous) work on the stream.
+ *   - Strings written into caller buffers are NUL-terminated; when the
+ *     buffer is too small the call writes nothing, stores the needed size
+ *     (including the NUL) in *needed and returns BE_EARG.
+ */
+#ifndef BE_H
+#define BE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define BE_OK 0
+#define BE_EPARSE 1        /* text does not follow the grammar of be_parse        */
+#define BE_EINVALID 2      /* violates a soundness rule of Eq. (1) (Sec. "Preliminaries") */
+#define BE_ESHAPE 3        /* inconsistent axis lengths / buffer shapes           */
+#define BE_EDTYPE 4        /* unknown or mismatching dtype                        */
+#define BE_ETOOMANY 5      /* beyond a stated limit (26 indices, 16 operands ...) */
+#define BE_ENOTFOUND 6     /* no tuning record under this normal form             */
+#define BE_EDB 7           /* tuning database file unreadable or corrupt          */
+#define BE_EBUDGET 8       /* request does not fit the HBM admission budget       */
+#define BE_ETIMEOUT 9      /* a bounded device-side wait ran out                  */
+#define BE_ECUDA 10        /* a CUDA runtime call failed                          */
+#define BE_EUNSUPPORTED 11 /* valid input the engine does not handle              */
+#define BE_EARG 12         /* bad argument (NULL handle, buffer too small, ...)   */
+
+/* ---- dtypes: the DtypeRank values of the induced-graph appendix; bfloat16 = 9 ---- */
+#define BE_I8 1
+#define BE_I32 2
+#define BE_I64 3
+#define BE_F16 4
+#define BE_F32 5
+#define BE_F64 6
+#define BE_C64 7
+#define BE_C128 8
+#define BE_BF16 9
+
+/* ---- evaluation strategies (be_config.strategy) ---- */
+#define BE_STRAT_AUTO 0        /* pick by pattern: ELEMENT, DENSE_SPLIT, else GENERIC   */
+#define BE_STRAT_GENERIC 1     /* one thread per output element, any notation           */
+#define BE_STRAT_ELEMENT 2     /* shared small operators x streamed per-element operands */
+#define BE_STRAT_DENSE_SPLIT 3 /* FP64 contraction as split FP16 products on tcgen05   */
+
+/* ---- precision modes (part of the tuning key, not of the normal form) ---- */
+#define BE_PREC_FP64 0         /* results within 1e-12 of the absolute contraction */
+#define BE_PREC_SPLIT 1        /* split-precision tensor-core products, within 1e-6 */
+
+/* ---- sigma kinds for be_canon_sigma ---- */
+#define BE_SIGMA_INDEX 0       /* canonical index letter k -> user index letter     */
+#define BE_SIGMA_ARG 1         /* canonical argument A<k> -> user argument name     */
+#define BE_SIGMA_ROW 2         /* canonical row k -> user row (decimal)             */
+#define BE_SIGMA_POS 3         /* canonical operand position k -> user position     */
+
+typedef struct be_ctx be_ctx;
+typedef struct be_einsum be_einsum;
+typedef struct be_canon be_canon;
+
+/* A tuned configuration, stated on the canonical form's names. */
+typedef struct {
+  int32_t strategy;    /* BE_STRAT_*                                          */
+  int32_t tile[4];     /* strategy tile sizes (0 = strategy default)          */
+  int32_t stages;      /* pipeline depth (0 = default)                        */
+  uint32_t stage_mask; /* bit k: keep canonical argument A<k> in shared memory */
+  int32_t vec;         /* elements per vector access (0 = default)            */
+  int32_t split;       /* split-precision product terms (0 = none)            */
+} be_config;
+
+/* A caller-owned array.  For be_execute ptr is a device pointer; for
+ * be_execute_host a host pointer.  strides: elements per step of each
+ * dimension (NULL: dense row-major).  dtype: BE_* above. */
+typedef struct {
+  void *ptr;
+  const int64_t *strides;
+  int32_t ndim;
+  int32_t dtype;
+} be_buf;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int be_version(void);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *be_last_error(void);
+
+/*
+ * be_parse -- text -> batched-einsum IR.
+ *   text:  "<notation> | <row> | <row> ... ; <decl> ; <decl> ..."
+ *          notation "ij,ej->ei" over letters a..z (Sec. "Preliminaries",
+ *          index grammar); each row lists one argument name per operand;
+ *          decl "name:dtype[d0,d1,..]" declares a buffer, and
+ *          "name(p,q,..)[:dtype[dims]] := expr" a lambda operand whose body
+ *          uses + - * / unary -, sin cos exp abs, numbers, $scalars,
+ *          buffer refs name[p,0,..] and "p==k ? x : y".
+ *   out:   new handle on success (free with be_free_einsum).
+ * Errors: BE_EPARSE (grammar), BE_EINVALID (soundness: Dim vs index list,
+ * output index not in any input, repeated output index, n = 0),
+ * BE_ESHAPE (unequal lengths of one index), BE_EDTYPE, BE_ETOOMANY
+ * (> 16 operands or > 4096 rows), BE_EUNSUPPORTED (0-dimensional operand).
+ */
+int be_parse(const char *text, be_einsum **out);
+void be_free_einsum(be_einsum *e);
+
+/* Sizes of a parsed einsum: rows b, operands n, declared buffers, distinct
+ * idealized arguments, runtime scalars, output rank and output dtype. */
+int be_einsum_info(const be_einsum *e, int32_t *b, int32_t *n, int32_t *n_buffers,
+                   int32_t *n_args, int32_t *n_scalars, int32_t *out_ndim, int32_t *out_dtype);
+/* Output shape (out_ndim entries). */
+int be_einsum_out_shape(const be_einsum *e, int64_t *shape);
+/* Declared buffer k (declaration order): name, dtype, rank and shape (up to 26 entries). */
+int be_einsum_buffer(const be_einsum *e, int32_t k, char *name, size_t len, size_t *needed,
+                     int32_t *dtype, int32_t *ndim, int64_t *shape);
+
+/*
+ * be_canonicalize -- Alg. 1: the normal form C(e) and the maps from its
+ * symbols to e's (sigma^I, sigma^A, and the row / operand orders).
+ * C(e) = C(e') iff e and e' are isomorphic batched einsums (Def. of a
+ * canonicalization function); our C is the lexicographically smallest
+ * token vector over operand and row orders with first-appearance naming.
+ */
+int be_canonicalize(const be_einsum *e, be_canon **out);
+void be_free_canon(be_canon *c);
+/* Printed normal form "be1:<b>;<n>;<out>-><ins>;<lengths>;<rows>;<dtypes>". */
+int be_canon_key(const be_canon *c, char *buf, size_t len, size_t *needed);
+/* Name in the user's einsum of canonical symbol canon_id of the given kind. */
+int be_canon_sigma(const be_canon *c, int32_t kind, int32_t canon_id, char *user_name, size_t len,
+                   size_t *needed);
+/* Token vector of C(e) (for tests); count in *n_tokens. */
+int be_canon_tokens(const be_canon *c, int64_t *tokens, size_t cap, size_t *n_tokens);
+
+/*
+ * Induced graph of Appendix B.1 (for tests).  colors: cap_nodes entries,
+ * 1..9; edges: cap_edges (from, to) pairs.  Sizes go to *n_nodes / *n_edges.
+ */
+int be_induced_graph(const be_einsum *e, int32_t *n_nodes, int32_t *colors, int32_t cap_nodes,
+                     int32_t *edges, int64_t cap_edges, int64_t *n_edges);
+/* Compliance conditions of Appendix B.2 on a caller graph: *failed = 0 if
+ * all hold, else the number k of the first failing condition (Ck). */
+int be_graph_check(int32_t n_nodes, const int32_t *colors, const int32_t *edges, int64_t n_edges,
+                   int32_t *failed);
+
+/*
+ * be_identify -- Alg. 2: express a stored reference einsum's names in a
+ * target einsum's names.  Both are canonicalized; if the normal forms
+ * differ the call returns BE_EINVALID (the algorithm's exception).
+ * Otherwise writes "ref=target;..." pairs for every index (letters) and
+ * argument (names) of ref.
+ */
+int be_identify(const be_einsum *ref, const be_einsum *target, char *buf, size_t len, size_t *needed);
+
+/*
+ * Tuning database keyed by (normal form, device name, precision mode),
+ * the paper's database of performance facts (Introduction, Fig. "The
+ * Feinsum approach").  db_path: append-only text file, created if missing;
+ * NULL keeps the database in memory.  device_name: the key's device field;
+ * NULL uses the CUDA name of `device`.  hbm_budget_bytes bounds device
+ * memory admitted by the serving loop (0 = unbounded).
+ * Errors: BE_EDB when the file exists but a record is malformed.
+ */
+int be_ctx_create(const char *db_path, const char *device_name, int32_t device,
+                  size_t hbm_budget_bytes, be_ctx **out);
+void be_ctx_destroy(be_ctx *x);
+/* Best stored config for c's normal form (BE_ENOTFOUND if none). */
+int be_lookup(be_ctx *x, const be_canon *c, int32_t precision, be_config *out, double *seconds);
+/* Store a measured config (appended to the file); the best per key wins. */
+int be_record(be_ctx *x, const be_canon *c, int32_t precision, const be_config *cfg, double seconds);
+/* Number of distinct keys held. */
+int be_db_size(be_ctx *x, int64_t *n);
+
+/*
+ * be_execute -- evaluate every row of e on `stream` (cudaStream_t; NULL =
+ * default stream), asynchronously.
+ *   bufs:    one be_buf per declared buffer of e, declaration order, device
+ *            pointers, dtype equal to the declaration; strides may be NULL.
+ *   outs:    one dense row-major device array per row (output shape, dtype
+ *            e's output dtype = highest-ranked argument dtype).
+ *   scalars: values of e's runtime scalars ($name), first-appearance order.
+ *   cfg:     NULL looks the config up in x's database under the normal form
+ *            and precision; without a record the strategy's defaults run.
+ * Errors: BE_EARG / BE_EDTYPE / BE_ESHAPE for mismatching buffers,
+ * BE_EUNSUPPORTED when a forced strategy does not fit e, BE_ECUDA.
+ */
+int be_execute(be_ctx *x, const be_einsum *e, const be_config *cfg, int32_t precision,
+               const be_buf *bufs, int32_t n_bufs, const be_buf *outs, int32_t n_outs,
+               const double *scalars, int32_t n_scalars, void *stream);
+
+/*
+ * be_execute_host -- as be_execute with HOST buffers: copies the inputs to
+ * device memory owned by x, evaluates, copies the outputs back and waits
+ * for the stream.  The staging memory is kept in x and reused.
+ */
+int be_execute_host(be_ctx *x, const be_einsum *e, const be_config *cfg, int32_t precision,
+                    const be_buf *bufs, int32_t n_bufs, const be_buf *outs, int32_t n_outs,
+                    const double *scalars, int32_t n_scalars, void *stream);
+
+/* Strategy the engine would run for e under cfg (after AUTO resolution). */
+int be_plan_strategy(be_ctx *x, const be_einsum *e, const be_config *cfg, int32_t precision,
+                     int32_t *strategy);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BE_H */

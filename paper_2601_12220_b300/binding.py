@@ -1,0 +1,341 @@
+"""Thin ctypes binding of the engine's C ABI (include/be.h).
+
+Argument marshalling only: every step (parse, canonicalize, lookup,
+evaluation) runs inside libbe.so.  Device buffers are torch tensors (torch
+provides device memory and streams); host buffers for ``execute_host`` are
+numpy arrays.  The library is loaded from this package's directory and an
+ImportError is raised if it has not been built -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbe.so")
+
+OK, EPARSE, EINVALID, ESHAPE, EDTYPE, ETOOMANY, ENOTFOUND, EDB, EBUDGET, ETIMEOUT, ECUDA, EUNSUPPORTED, EARG = range(13)
+I8, I32, I64, F16, F32, F64, C64, C128, BF16 = 1, 2, 3, 4, 5, 6, 7, 8, 9
+STRAT_AUTO, STRAT_GENERIC, STRAT_ELEMENT, STRAT_DENSE_SPLIT = 0, 1, 2, 3
+PREC_FP64, PREC_SPLIT = 0, 1
+SIGMA_INDEX, SIGMA_ARG, SIGMA_ROW, SIGMA_POS = 0, 1, 2, 3
+STATUS_NAMES = {0: "BE_OK", 1: "BE_EPARSE", 2: "BE_EINVALID", 3: "BE_ESHAPE", 4: "BE_EDTYPE",
+                5: "BE_ETOOMANY", 6: "BE_ENOTFOUND", 7: "BE_EDB", 8: "BE_EBUDGET", 9: "BE_ETIMEOUT",
+                10: "BE_ECUDA", 11: "BE_EUNSUPPORTED", 12: "BE_EARG"}
+
+# every symbol include/be.h declares
+EXPORTS = [
+    "be_version", "be_last_error", "be_parse", "be_free_einsum", "be_einsum_info", "be_einsum_out_shape",
+    "be_einsum_buffer", "be_canonicalize", "be_free_canon", "be_canon_key", "be_canon_sigma",
+    "be_canon_tokens", "be_induced_graph", "be_graph_check", "be_identify", "be_ctx_create",
+    "be_ctx_destroy", "be_lookup", "be_record", "be_db_size", "be_execute", "be_execute_host",
+    "be_plan_strategy",
+]
+
+
+class BEError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("strategy", ctypes.c_int32), ("tile", ctypes.c_int32 * 4), ("stages", ctypes.c_int32),
+                ("stage_mask", ctypes.c_uint32), ("vec", ctypes.c_int32), ("split", ctypes.c_int32)]
+
+    def as_tuple(self):
+        return (self.strategy, tuple(self.tile), self.stages, self.stage_mask, self.vec, self.split)
+
+
+def make_config(strategy=0, tile=(0, 0, 0, 0), stages=0, stage_mask=0, vec=0, split=0) -> Config:
+    c = Config()
+    c.strategy = strategy
+    for k in range(4):
+        c.tile[k] = tile[k] if k < len(tile) else 0
+    c.stages, c.stage_mask, c.vec, c.split = stages, stage_mask, vec, split
+    return c
+
+
+class Buf(ctypes.Structure):
+    _fields_ = [("ptr", ctypes.c_void_p), ("strides", ctypes.POINTER(ctypes.c_int64)),
+                ("ndim", ctypes.c_int32), ("dtype", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with python -m paper_2601_12220_b300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        P = ctypes.POINTER
+        sig = {
+            "be_version": (ctypes.c_int, []),
+            "be_last_error": (ctypes.c_char_p, []),
+            "be_parse": (ctypes.c_int, [ctypes.c_char_p, P(vp)]),
+            "be_free_einsum": (None, [vp]),
+            "be_einsum_info": (ctypes.c_int, [vp] + [P(i32)] * 7),
+            "be_einsum_out_shape": (ctypes.c_int, [vp, P(i64)]),
+            "be_einsum_buffer": (ctypes.c_int, [vp, i32, ctypes.c_char_p, sz, P(sz), P(i32), P(i32), P(i64)]),
+            "be_canonicalize": (ctypes.c_int, [vp, P(vp)]),
+            "be_free_canon": (None, [vp]),
+            "be_canon_key": (ctypes.c_int, [vp, ctypes.c_char_p, sz, P(sz)]),
+            "be_canon_sigma": (ctypes.c_int, [vp, i32, i32, ctypes.c_char_p, sz, P(sz)]),
+            "be_canon_tokens": (ctypes.c_int, [vp, P(i64), sz, P(sz)]),
+            "be_induced_graph": (ctypes.c_int, [vp, P(i32), P(i32), i32, P(i32), i64, P(i64)]),
+            "be_graph_check": (ctypes.c_int, [i32, P(i32), P(i32), i64, P(i32)]),
+            "be_identify": (ctypes.c_int, [vp, vp, ctypes.c_char_p, sz, P(sz)]),
+            "be_ctx_create": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_char_p, i32, sz, P(vp)]),
+            "be_ctx_destroy": (None, [vp]),
+            "be_lookup": (ctypes.c_int, [vp, vp, i32, P(Config), P(ctypes.c_double)]),
+            "be_record": (ctypes.c_int, [vp, vp, i32, P(Config), ctypes.c_double]),
+            "be_db_size": (ctypes.c_int, [vp, P(i64)]),
+            "be_execute": (ctypes.c_int, [vp, vp, P(Config), i32, P(Buf), i32, P(Buf), i32,
+                                          P(ctypes.c_double), i32, vp]),
+            "be_execute_host": (ctypes.c_int, [vp, vp, P(Config), i32, P(Buf), i32, P(Buf), i32,
+                                               P(ctypes.c_double), i32, vp]),
+            "be_plan_strategy": (ctypes.c_int, [vp, vp, P(Config), i32, P(i32)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(code):
+    if code != OK:
+        raise BEError(code, lib().be_last_error().decode())
+
+
+def _string(fn, *args):
+    need = ctypes.c_size_t(0)
+    fn(*args, None, 0, ctypes.byref(need))
+    buf = ctypes.create_string_buffer(need.value)
+    check(fn(*args, buf, need.value, ctypes.byref(need)))
+    return buf.value.decode()
+
+
+# ---------------------------------------------------------------- IR
+
+class Einsum:
+    """be_parse handle."""
+
+    def __init__(self, text: str):
+        h = ctypes.c_void_p()
+        check(lib().be_parse(text.encode(), ctypes.byref(h)))
+        self._h = h
+        self.text = text
+        v = [ctypes.c_int32() for _ in range(7)]
+        check(lib().be_einsum_info(h, *[ctypes.byref(x) for x in v]))
+        self.b, self.n, self.n_buffers, self.n_args, self.n_scalars, self.out_ndim, self.out_dtype = \
+            [x.value for x in v]
+        shp = (ctypes.c_int64 * max(1, self.out_ndim))()
+        check(lib().be_einsum_out_shape(h, shp))
+        self.out_shape = tuple(shp[k] for k in range(self.out_ndim))
+        self.buffers = []
+        for k in range(self.n_buffers):
+            dt, nd = ctypes.c_int32(), ctypes.c_int32()
+            s = (ctypes.c_int64 * 26)()
+            need = ctypes.c_size_t(0)
+            lib().be_einsum_buffer(h, k, None, 0, ctypes.byref(need), None, None, None)
+            nm = ctypes.create_string_buffer(need.value)
+            check(lib().be_einsum_buffer(h, k, nm, need.value, ctypes.byref(need), ctypes.byref(dt),
+                                         ctypes.byref(nd), s))
+            self.buffers.append((nm.value.decode(), dt.value, tuple(s[d] for d in range(nd.value))))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.be_free_einsum(self._h)
+            self._h = None
+
+    def canonicalize(self) -> "Canon":
+        return Canon(self)
+
+    def induced_graph(self):
+        n, ne = ctypes.c_int32(), ctypes.c_int64()
+        check(lib().be_induced_graph(self._h, ctypes.byref(n), None, 0, None, 0, ctypes.byref(ne)))
+        cols = (ctypes.c_int32 * max(1, n.value))()
+        eds = (ctypes.c_int32 * max(2, 2 * ne.value))()
+        check(lib().be_induced_graph(self._h, ctypes.byref(n), cols, n.value, eds, ne.value, ctypes.byref(ne)))
+        colors = np.array(cols[:n.value], dtype=np.int32)
+        edges = np.array(eds[:2 * ne.value], dtype=np.int32).reshape(-1, 2)
+        return colors, edges
+
+
+def graph_check(colors, edges) -> int:
+    colors = np.ascontiguousarray(colors, dtype=np.int32)
+    edges = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1)
+    failed = ctypes.c_int32()
+    check(lib().be_graph_check(len(colors), colors.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                               edges.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(edges) // 2,
+                               ctypes.byref(failed)))
+    return failed.value
+
+
+class Canon:
+    """be_canonicalize handle: C(e), its printed key and the sigma maps."""
+
+    def __init__(self, e: Einsum):
+        h = ctypes.c_void_p()
+        check(lib().be_canonicalize(e.handle, ctypes.byref(h)))
+        self._h = h
+        self.key = _string(lib().be_canon_key, h)
+        n = ctypes.c_size_t()
+        lib().be_canon_tokens(h, None, 0, ctypes.byref(n))
+        t = (ctypes.c_int64 * max(1, n.value))()
+        check(lib().be_canon_tokens(h, t, n.value, ctypes.byref(n)))
+        self.tokens = list(t[:n.value])
+
+    @property
+    def handle(self):
+        return self._h
+
+    def sigma(self, kind: int, k: int) -> str:
+        return _string(lib().be_canon_sigma, self._h, kind, k)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.be_free_canon(self._h)
+            self._h = None
+
+
+def identify(ref: Einsum, target: Einsum) -> dict:
+    """Alg. 2: ref's names -> target's names (BEError if the forms differ)."""
+    s = _string(lib().be_identify, ref.handle, target.handle)
+    return dict(kv.split("=") for kv in s.split(";") if kv)
+
+
+# ---------------------------------------------------------------- context / DB
+
+class Context:
+    def __init__(self, db_path=None, device_name=None, device=0, hbm_budget=0):
+        h = ctypes.c_void_p()
+        check(lib().be_ctx_create(db_path.encode() if db_path else None,
+                                  device_name.encode() if device_name else None, device, hbm_budget,
+                                  ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def lookup(self, canon: Canon, precision=PREC_FP64):
+        c = Config()
+        sec = ctypes.c_double()
+        code = lib().be_lookup(self._h, canon.handle, precision, ctypes.byref(c), ctypes.byref(sec))
+        if code == ENOTFOUND:
+            return None
+        check(code)
+        return c, sec.value
+
+    def record(self, canon: Canon, cfg: Config, seconds: float, precision=PREC_FP64):
+        check(lib().be_record(self._h, canon.handle, precision, ctypes.byref(cfg), seconds))
+
+    def db_size(self) -> int:
+        n = ctypes.c_int64()
+        check(lib().be_db_size(self._h, ctypes.byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.be_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+# ---------------------------------------------------------------- execution
+
+_TORCH_DT = None
+
+
+def _torch_dtype_code(t):
+    global _TORCH_DT
+    if _TORCH_DT is None:
+        import torch
+        _TORCH_DT = {torch.float64: F64, torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16,
+                     torch.int32: I32, torch.int64: I64, torch.int8: I8}
+    return _TORCH_DT[t.dtype]
+
+
+_NP_DT = {np.dtype(np.float64): F64, np.dtype(np.float32): F32, np.dtype(np.float16): F16,
+          np.dtype(np.int32): I32, np.dtype(np.int64): I64, np.dtype(np.int8): I8}
+
+
+def _bufs_torch(tensors, keep, dense_only=False):
+    arr = (Buf * max(1, len(tensors)))()
+    for k, t in enumerate(tensors):
+        arr[k].ptr = t.data_ptr()
+        arr[k].ndim = t.dim()
+        arr[k].dtype = _torch_dtype_code(t)
+        if not dense_only and not t.is_contiguous():
+            st = (ctypes.c_int64 * max(1, t.dim()))(*t.stride())
+            keep.append(st)
+            arr[k].strides = st
+        else:
+            arr[k].strides = None
+    return arr
+
+
+def _scalars(vals):
+    vals = list(vals or [])
+    return (ctypes.c_double * max(1, len(vals)))(*vals), len(vals)
+
+
+def _order(e: Einsum, bufs):
+    if isinstance(bufs, dict):
+        return [bufs[name] for name, _, _ in e.buffers]
+    return list(bufs)
+
+
+def execute(ctx, e: Einsum, bufs, outs, cfg: Config | None = None, precision=PREC_FP64, scalars=(),
+            stream=None):
+    """Evaluate every row of e on the GPU.  bufs: dict name -> tensor or a
+    list in declaration order; outs: one tensor per row; stream: a
+    torch.cuda.Stream (default: the current stream)."""
+    import torch
+    keep = []
+    bl = _order(e, bufs)
+    bi = _bufs_torch(bl, keep)
+    bo = _bufs_torch(outs, keep, dense_only=True)
+    sc, ns = _scalars(scalars)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    check(lib().be_execute(ctx.handle if ctx else None, e.handle, ctypes.byref(cfg) if cfg else None, precision,
+                           bi, len(bl), bo, len(outs), sc, ns, ctypes.c_void_p(stream.cuda_stream)))
+
+
+def execute_host(ctx, e: Einsum, bufs, outs, cfg: Config | None = None, precision=PREC_FP64, scalars=(),
+                 stream=None):
+    """As execute, with dense host numpy arrays; blocks until done."""
+    bl = [np.ascontiguousarray(x) for x in _order(e, bufs)]
+    arr = (Buf * max(1, len(bl)))()
+    for k, x in enumerate(bl):
+        arr[k].ptr, arr[k].ndim, arr[k].dtype, arr[k].strides = x.ctypes.data, x.ndim, _NP_DT[x.dtype], None
+    oarr = (Buf * max(1, len(outs)))()
+    for k, x in enumerate(outs):
+        assert x.flags.c_contiguous
+        oarr[k].ptr, oarr[k].ndim, oarr[k].dtype, oarr[k].strides = x.ctypes.data, x.ndim, _NP_DT[x.dtype], None
+    sc, ns = _scalars(scalars)
+    s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    check(lib().be_execute_host(ctx.handle, e.handle, ctypes.byref(cfg) if cfg else None, precision, arr, len(bl),
+                                oarr, len(outs), sc, ns, s))
+
+
+def plan_strategy(ctx, e: Einsum, cfg: Config | None = None, precision=PREC_FP64) -> int:
+    s = ctypes.c_int32()
+    check(lib().be_plan_strategy(ctx.handle if ctx else None, e.handle, ctypes.byref(cfg) if cfg else None,
+                                 precision, ctypes.byref(s)))
+    return s.value

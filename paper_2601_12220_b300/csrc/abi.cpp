@@ -1,0 +1,521 @@
+// C ABI of the engine (include/be.h): handles, error reporting, the
+// tuning database keyed by the normal form, Alg. 2 (identify a reference
+// einsum in a target's names) and strategy dispatch for be_execute.
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <unordered_map>
+
+#include <cuda_runtime.h>
+
+#include "../../include/be.h"
+#include "canon.hpp"
+#include "plan.hpp"
+
+using namespace be;
+
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+struct be_einsum {
+  Einsum e;
+  std::mutex mu;
+  std::unique_ptr<Canon> canon;   // cached C(e) for lookups
+};
+
+struct be_canon {
+  Canon c;
+};
+
+struct DbEntry {
+  be_config cfg;
+  double seconds;
+};
+
+struct be_ctx {
+  std::string db_path, device_name;
+  int device = -1;
+  size_t hbm_budget = 0;
+  std::mutex mu;
+  std::unordered_map<std::string, DbEntry> db;
+  // staging memory of be_execute_host
+  std::vector<void *> stage;
+  std::vector<size_t> stage_size;
+};
+
+static std::string db_key(const std::string &nf, const std::string &dev, int prec) {
+  return nf + "\t" + dev + "\t" + std::to_string(prec);
+}
+
+static int put_string(const std::string &s, char *buf, size_t len, size_t *needed) {
+  if (needed) *needed = s.size() + 1;
+  if (!buf || len < s.size() + 1) return fail(BE_EARG, "buffer too small");
+  std::memcpy(buf, s.c_str(), s.size() + 1);
+  return BE_OK;
+}
+
+static const Canon *canon_of(be_einsum *e, std::string &err, int &st) {
+  std::lock_guard<std::mutex> g(e->mu);
+  if (!e->canon) {
+    auto c = std::make_unique<Canon>();
+    st = canonicalize(e->e, *c, err);
+    if (st) return nullptr;
+    e->canon = std::move(c);
+  }
+  st = BE_OK;
+  return e->canon.get();
+}
+
+extern "C" {
+
+int be_version(void) { return 10000; }
+
+const char *be_last_error(void) { return g_err.c_str(); }
+
+int be_parse(const char *text, be_einsum **out) {
+  if (!text || !out) return fail(BE_EARG, "NULL argument");
+  auto h = std::make_unique<be_einsum>();
+  std::string err;
+  int st = parse(text, h->e, err);
+  if (st) return fail(st, err);
+  *out = h.release();
+  return BE_OK;
+}
+
+void be_free_einsum(be_einsum *e) { delete e; }
+
+int be_einsum_info(const be_einsum *h, int32_t *b, int32_t *n, int32_t *n_buffers, int32_t *n_args,
+                   int32_t *n_scalars, int32_t *out_ndim, int32_t *out_dtype) {
+  if (!h) return fail(BE_EARG, "NULL einsum");
+  const Einsum &e = h->e;
+  if (b) *b = e.b;
+  if (n) *n = e.n;
+  if (n_buffers) *n_buffers = (int32_t)e.buffers.size();
+  if (n_args) *n_args = (int32_t)e.args.size();
+  if (n_scalars) *n_scalars = (int32_t)e.scalars.size();
+  if (out_ndim) *out_ndim = (int32_t)e.out.size();
+  if (out_dtype) *out_dtype = e.out_dtype;
+  return BE_OK;
+}
+
+int be_einsum_out_shape(const be_einsum *h, int64_t *shape) {
+  if (!h || !shape) return fail(BE_EARG, "NULL argument");
+  auto s = h->e.out_shape();
+  for (size_t k = 0; k < s.size(); ++k) shape[k] = s[k];
+  return BE_OK;
+}
+
+int be_einsum_buffer(const be_einsum *h, int32_t k, char *name, size_t len, size_t *needed, int32_t *dtype,
+                     int32_t *ndim, int64_t *shape) {
+  if (!h) return fail(BE_EARG, "NULL einsum");
+  if (k < 0 || k >= (int)h->e.buffers.size()) return fail(BE_EARG, "buffer index out of range");
+  const Buffer &bf = h->e.buffers[k];
+  if (dtype) *dtype = bf.dtype;
+  if (ndim) *ndim = (int32_t)bf.shape.size();
+  if (shape)
+    for (size_t d = 0; d < bf.shape.size(); ++d) shape[d] = bf.shape[d];
+  if (name || needed) return put_string(bf.name, name, len, needed);
+  return BE_OK;
+}
+
+int be_canonicalize(const be_einsum *h, be_canon **out) {
+  if (!h || !out) return fail(BE_EARG, "NULL argument");
+  auto c = std::make_unique<be_canon>();
+  std::string err;
+  int st = canonicalize(h->e, c->c, err);
+  if (st) return fail(st, err);
+  *out = c.release();
+  return BE_OK;
+}
+
+void be_free_canon(be_canon *c) { delete c; }
+
+int be_canon_key(const be_canon *c, char *buf, size_t len, size_t *needed) {
+  if (!c) return fail(BE_EARG, "NULL canon");
+  return put_string(c->c.key, buf, len, needed);
+}
+
+int be_canon_sigma(const be_canon *c, int32_t kind, int32_t id, char *user, size_t len, size_t *needed) {
+  if (!c) return fail(BE_EARG, "NULL canon");
+  const Canon &k = c->c;
+  std::string s;
+  switch (kind) {
+    case BE_SIGMA_INDEX:
+      if (id < 0 || id >= (int)k.sigma_index.size()) return fail(BE_EARG, "index id out of range");
+      s = std::string(1, char('a' + k.sigma_index[id]));
+      break;
+    case BE_SIGMA_ARG:
+      if (id < 0 || id >= (int)k.sigma_arg_name.size()) return fail(BE_EARG, "argument id out of range");
+      s = k.sigma_arg_name[id];
+      break;
+    case BE_SIGMA_ROW:
+      if (id < 0 || id >= (int)k.sigma_row.size()) return fail(BE_EARG, "row out of range");
+      s = std::to_string(k.sigma_row[id]);
+      break;
+    case BE_SIGMA_POS:
+      if (id < 0 || id >= (int)k.sigma_pos.size()) return fail(BE_EARG, "position out of range");
+      s = std::to_string(k.sigma_pos[id]);
+      break;
+    default:
+      return fail(BE_EARG, "unknown sigma kind");
+  }
+  return put_string(s, user, len, needed);
+}
+
+int be_canon_tokens(const be_canon *c, int64_t *tokens, size_t cap, size_t *n_tokens) {
+  if (!c) return fail(BE_EARG, "NULL canon");
+  const auto &t = c->c.tokens;
+  if (n_tokens) *n_tokens = t.size();
+  if (!tokens || cap < t.size()) return fail(BE_EARG, "buffer too small");
+  for (size_t k = 0; k < t.size(); ++k) tokens[k] = t[k];
+  return BE_OK;
+}
+
+int be_induced_graph(const be_einsum *h, int32_t *n_nodes, int32_t *colors, int32_t cap_nodes, int32_t *edges,
+                     int64_t cap_edges, int64_t *n_edges) {
+  if (!h) return fail(BE_EARG, "NULL einsum");
+  Graph g = to_induced_graph(h->e);
+  if (n_nodes) *n_nodes = g.n;
+  if (n_edges) *n_edges = (int64_t)g.edges.size();
+  if (colors) {
+    if (cap_nodes < g.n) return fail(BE_EARG, "colors buffer too small");
+    for (int v = 0; v < g.n; ++v) colors[v] = g.color[v];
+  }
+  if (edges) {
+    if (cap_edges < (int64_t)g.edges.size()) return fail(BE_EARG, "edges buffer too small");
+    for (size_t k = 0; k < g.edges.size(); ++k) {
+      edges[2 * k] = g.edges[k].first;
+      edges[2 * k + 1] = g.edges[k].second;
+    }
+  }
+  return BE_OK;
+}
+
+int be_graph_check(int32_t n_nodes, const int32_t *colors, const int32_t *edges, int64_t n_edges, int32_t *failed) {
+  if (n_nodes < 0 || (!colors && n_nodes) || (!edges && n_edges) || !failed) return fail(BE_EARG, "bad graph");
+  Graph g;
+  g.n = n_nodes;
+  g.color.assign(colors, colors + n_nodes);
+  for (int64_t k = 0; k < n_edges; ++k) {
+    int a = edges[2 * k], b = edges[2 * k + 1];
+    if (a < 0 || b < 0 || a >= n_nodes || b >= n_nodes) return fail(BE_EARG, "edge endpoint out of range");
+    g.edges.push_back({a, b});
+  }
+  *failed = graph_check(g);
+  return BE_OK;
+}
+
+int be_identify(const be_einsum *ref, const be_einsum *target, char *buf, size_t len, size_t *needed) {
+  if (!ref || !target) return fail(BE_EARG, "NULL einsum");
+  Canon cr, ct;
+  std::string err;
+  int st = canonicalize(ref->e, cr, err);
+  if (!st) st = canonicalize(target->e, ct, err);
+  if (st) return fail(st, err);
+  if (cr.key != ct.key) return fail(BE_EINVALID, "normal forms differ: " + cr.key + " vs " + ct.key);
+  // sigma[canon_to_ref[(canon_to_target)^-1[x_target]]] = x_target, written ref -> target
+  std::string s;
+  for (size_t k = 0; k < cr.sigma_index.size(); ++k) {
+    s += char('a' + cr.sigma_index[k]);
+    s += "=";
+    s += char('a' + ct.sigma_index[k]);
+    s += ";";
+  }
+  for (size_t k = 0; k < cr.sigma_arg.size(); ++k)
+    s += ref->e.args[cr.sigma_arg[k]].name + "=" + target->e.args[ct.sigma_arg[k]].name + ";";
+  return put_string(s, buf, len, needed);
+}
+
+// ------------------------------------------------------------ database
+
+static bool parse_record(const std::string &line, std::string &key, DbEntry &d) {
+  std::vector<std::string> f;
+  std::string cur;
+  for (char ch : line) {
+    if (ch == '\t') { f.push_back(cur); cur.clear(); }
+    else cur += ch;
+  }
+  f.push_back(cur);
+  if (f.size() != 5 || f[0].rfind("be1:", 0) != 0) return false;
+  char *end = nullptr;
+  long prec = std::strtol(f[2].c_str(), &end, 10);
+  if (*end || f[2].empty()) return false;
+  std::istringstream cs(f[3]);
+  be_config c;
+  std::memset(&c, 0, sizeof(c));
+  if (!(cs >> c.strategy >> c.tile[0] >> c.tile[1] >> c.tile[2] >> c.tile[3] >> c.stages >> c.stage_mask >> c.vec >> c.split))
+    return false;
+  std::string rest;
+  if (cs >> rest) return false;
+  d.seconds = std::strtod(f[4].c_str(), &end);
+  if (*end || f[4].empty() || !(d.seconds >= 0)) return false;
+  d.cfg = c;
+  key = db_key(f[0], f[1], (int)prec);
+  return true;
+}
+
+int be_ctx_create(const char *db_path, const char *device_name, int32_t device, size_t hbm_budget, be_ctx **out) {
+  if (!out) return fail(BE_EARG, "NULL out");
+  auto x = std::make_unique<be_ctx>();
+  x->device = device;
+  x->hbm_budget = hbm_budget;
+  if (device_name) {
+    x->device_name = device_name;
+  } else {
+    cudaDeviceProp prop;
+    cudaError_t ce = cudaGetDeviceProperties(&prop, device);
+    if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("cudaGetDeviceProperties: ") + cudaGetErrorString(ce));
+    x->device_name = prop.name;
+  }
+  for (auto &ch : x->device_name)
+    if (ch == '\t' || ch == '\n') ch = ' ';
+  if (db_path) {
+    x->db_path = db_path;
+    std::ifstream f(db_path);
+    if (f) {
+      std::string line;
+      int lineno = 0;
+      while (std::getline(f, line)) {
+        ++lineno;
+        if (line.empty()) continue;
+        std::string key;
+        DbEntry d;
+        if (!parse_record(line, key, d))
+          return fail(BE_EDB, std::string(db_path) + ":" + std::to_string(lineno) + ": malformed record");
+        auto it = x->db.find(key);
+        if (it == x->db.end() || d.seconds < it->second.seconds) x->db[key] = d;
+      }
+    }
+  }
+  *out = x.release();
+  return BE_OK;
+}
+
+void be_ctx_destroy(be_ctx *x) {
+  if (!x) return;
+  for (void *p : x->stage)
+    if (p) cudaFree(p);
+  delete x;
+}
+
+int be_lookup(be_ctx *x, const be_canon *c, int32_t precision, be_config *out, double *seconds) {
+  if (!x || !c || !out) return fail(BE_EARG, "NULL argument");
+  std::lock_guard<std::mutex> g(x->mu);
+  auto it = x->db.find(db_key(c->c.key, x->device_name, precision));
+  if (it == x->db.end()) return fail(BE_ENOTFOUND, "no record for " + c->c.key);
+  *out = it->second.cfg;
+  if (seconds) *seconds = it->second.seconds;
+  return BE_OK;
+}
+
+int be_record(be_ctx *x, const be_canon *c, int32_t precision, const be_config *cfg, double seconds) {
+  if (!x || !c || !cfg) return fail(BE_EARG, "NULL argument");
+  if (!(seconds >= 0)) return fail(BE_EARG, "seconds must be >= 0");
+  std::lock_guard<std::mutex> g(x->mu);
+  std::string key = db_key(c->c.key, x->device_name, precision);
+  if (!x->db_path.empty()) {
+    std::ofstream f(x->db_path, std::ios::app);
+    if (!f) return fail(BE_EDB, "cannot append to " + x->db_path);
+    char line[256];
+    std::snprintf(line, sizeof line, "%d %d %d %d %d %d %u %d %d", cfg->strategy, cfg->tile[0], cfg->tile[1],
+                  cfg->tile[2], cfg->tile[3], cfg->stages, cfg->stage_mask, cfg->vec, cfg->split);
+    f << c->c.key << '\t' << x->device_name << '\t' << precision << '\t' << line << '\t';
+    char sec[64];
+    std::snprintf(sec, sizeof sec, "%.9e", seconds);
+    f << sec << '\n';
+    if (!f) return fail(BE_EDB, "write failed on " + x->db_path);
+  }
+  auto it = x->db.find(key);
+  if (it == x->db.end() || seconds < it->second.seconds) x->db[key] = DbEntry{*cfg, seconds};
+  return BE_OK;
+}
+
+int be_db_size(be_ctx *x, int64_t *n) {
+  if (!x || !n) return fail(BE_EARG, "NULL argument");
+  std::lock_guard<std::mutex> g(x->mu);
+  *n = (int64_t)x->db.size();
+  return BE_OK;
+}
+
+// ------------------------------------------------------------ execution
+
+static int resolve_config(be_ctx *x, be_einsum *h, const be_config *cfg, int32_t precision, be_config_t &out) {
+  std::memset(&out, 0, sizeof(out));
+  if (cfg) {
+    std::memcpy(&out, cfg, sizeof(out));
+    return BE_OK;
+  }
+  if (x) {
+    std::string err;
+    int st;
+    const Canon *c = canon_of(h, err, st);
+    if (st) return fail(st, err);
+    std::lock_guard<std::mutex> g(x->mu);
+    auto it = x->db.find(db_key(c->key, x->device_name, precision));
+    if (it != x->db.end()) std::memcpy(&out, &it->second.cfg, sizeof(out));
+  }
+  return BE_OK;
+}
+
+static int choose(const Einsum &e, const std::vector<BufIn> &bufs, const std::vector<BufIn> &outs,
+                  const be_config_t &cfg, int32_t precision, int &strategy, EParams *ep, std::string &why) {
+  strategy = cfg.strategy;
+  EParams tmp;
+  EParams &p = ep ? *ep : tmp;
+  if (strategy == BE_STRAT_AUTO) {
+    if (precision == BE_PREC_FP64 && plan_element(e, bufs, outs, cfg, p, why) == OK) strategy = BE_STRAT_ELEMENT;
+    else strategy = BE_STRAT_GENERIC;
+    return BE_OK;
+  }
+  if (strategy == BE_STRAT_ELEMENT) {
+    int st = plan_element(e, bufs, outs, cfg, p, why);
+    if (st) return st;
+  } else if (strategy == BE_STRAT_DENSE_SPLIT) {
+    why = "dense split strategy not available";
+    return EUNSUPPORTED;
+  } else if (strategy != BE_STRAT_GENERIC) {
+    why = "unknown strategy";
+    return EARG;
+  }
+  return BE_OK;
+}
+
+static int do_execute(be_ctx *x, const be_einsum *hc, const be_config *cfg, int32_t precision, const be_buf *bufs,
+                      int32_t n_bufs, const be_buf *outs, int32_t n_outs, const double *scalars, int32_t n_scalars,
+                      void *stream) {
+  be_einsum *h = const_cast<be_einsum *>(hc);
+  if (!h) return fail(BE_EARG, "NULL einsum");
+  if (n_bufs < 0 || n_outs < 0 || n_scalars < 0) return fail(BE_EARG, "negative count");
+  const Einsum &e = h->e;
+  std::vector<BufIn> bi(n_bufs), bo(n_outs);
+  for (int k = 0; k < n_bufs; ++k) bi[k] = BufIn{bufs[k].ptr, bufs[k].strides, bufs[k].ndim, bufs[k].dtype};
+  for (int k = 0; k < n_outs; ++k) bo[k] = BufIn{outs[k].ptr, outs[k].strides, outs[k].ndim, outs[k].dtype};
+  std::string err;
+  int st = check_buffers(e, bi, bo, err);
+  if (st) return fail(st, err);
+  if (n_scalars != (int)e.scalars.size()) return fail(BE_EARG, "scalar count differs from the spec");
+  std::vector<double> sc(scalars, scalars + n_scalars);
+  be_config_t c;
+  st = resolve_config(x, h, cfg, precision, c);
+  if (st) return st;
+  int strategy;
+  EParams ep;
+  st = choose(e, bi, bo, c, precision, strategy, &ep, err);
+  if (st) return fail(st, err);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t ce = cudaSuccess;
+  if (strategy == BE_STRAT_ELEMENT) {
+    int block = c.tile[1] > 0 ? c.tile[1] : 256;
+    int dev = 0, sms = 148, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    size_t smem = sizeof(double) * ((size_t)ep.R * ep.NI * ep.NJ + (size_t)ep.n_groups * ep.tile_e * ep.NJ +
+                                    (size_t)ep.n_rows * ep.tile_e * ep.R);
+    per_sm = (int)std::max<size_t>(1, std::min<size_t>(2048 / block, (220 * 1024) / (smem + 1024)));
+    int64_t tiles = (ep.E + ep.tile_e - 1) / ep.tile_e;
+    int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * per_sm));
+    if (ep.E > 0) ce = launch_element(ep, grid, block, s);
+  } else {
+    for (int i = 0; i < e.b && ce == cudaSuccess; ++i) {
+      GParams p;
+      st = plan_generic_row(e, i, bi, bo[i], sc, p, err);
+      if (st) return fail(st, err);
+      ce = launch_generic(p, s);
+    }
+  }
+  if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("launch: ") + cudaGetErrorString(ce));
+  return BE_OK;
+}
+
+int be_execute(be_ctx *x, const be_einsum *h, const be_config *cfg, int32_t precision, const be_buf *bufs,
+               int32_t n_bufs, const be_buf *outs, int32_t n_outs, const double *scalars, int32_t n_scalars,
+               void *stream) {
+  return do_execute(x, h, cfg, precision, bufs, n_bufs, outs, n_outs, scalars, n_scalars, stream);
+}
+
+int be_plan_strategy(be_ctx *x, const be_einsum *hc, const be_config *cfg, int32_t precision, int32_t *strategy) {
+  be_einsum *h = const_cast<be_einsum *>(hc);
+  if (!h || !strategy) return fail(BE_EARG, "NULL argument");
+  be_config_t c;
+  int st = resolve_config(x, h, cfg, precision, c);
+  if (st) return st;
+  // plan on placeholder buffers (pointers are not dereferenced while planning)
+  const Einsum &e = h->e;
+  std::vector<BufIn> bi, bo;
+  static double dummy;
+  for (auto &b : e.buffers) bi.push_back(BufIn{&dummy, nullptr, (int32_t)b.shape.size(), b.dtype});
+  for (int i = 0; i < e.b; ++i) bo.push_back(BufIn{&dummy, nullptr, (int32_t)e.out.size(), e.out_dtype});
+  std::string why;
+  int s;
+  st = choose(e, bi, bo, c, precision, s, nullptr, why);
+  if (st) return fail(st, why);
+  *strategy = s;
+  return BE_OK;
+}
+
+static size_t dense_bytes(const Buffer &b) {
+  size_t n = (size_t)dtype_size(b.dtype);
+  for (auto d : b.shape) n *= (size_t)d;
+  return n;
+}
+
+int be_execute_host(be_ctx *x, const be_einsum *h, const be_config *cfg, int32_t precision, const be_buf *bufs,
+                    int32_t n_bufs, const be_buf *outs, int32_t n_outs, const double *scalars, int32_t n_scalars,
+                    void *stream) {
+  if (!x || !h) return fail(BE_EARG, "NULL argument");
+  const Einsum &e = h->e;
+  if (n_bufs != (int)e.buffers.size() || n_outs != e.b) return fail(BE_EARG, "buffer counts differ from the spec");
+  std::vector<size_t> need;
+  for (int k = 0; k < n_bufs; ++k) {
+    if (bufs[k].strides) return fail(BE_EARG, "host buffers must be dense row-major");
+    need.push_back(dense_bytes(e.buffers[k]));
+  }
+  size_t out_bytes = (size_t)dtype_size(e.out_dtype);
+  for (auto d : e.out_shape()) out_bytes *= (size_t)d;
+  for (int k = 0; k < n_outs; ++k) need.push_back(out_bytes);
+  be_config_t c;
+  int rst = resolve_config(x, const_cast<be_einsum *>(h), cfg, precision, c);
+  if (rst) return rst;
+  std::lock_guard<std::mutex> g(x->mu);
+  cudaError_t ce = cudaSuccess;
+  if (x->stage.size() < need.size()) {
+    x->stage.resize(need.size(), nullptr);
+    x->stage_size.resize(need.size(), 0);
+  }
+  for (size_t k = 0; k < need.size(); ++k) {
+    if (x->stage_size[k] < need[k]) {
+      if (x->stage[k]) cudaFree(x->stage[k]);
+      x->stage[k] = nullptr;
+      ce = cudaMalloc(&x->stage[k], need[k] ? need[k] : 16);
+      if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("cudaMalloc: ") + cudaGetErrorString(ce));
+      x->stage_size[k] = need[k];
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<be_buf> db(n_bufs), dout(n_outs);
+  for (int k = 0; k < n_bufs; ++k) {
+    if (need[k]) ce = cudaMemcpyAsync(x->stage[k], bufs[k].ptr, need[k], cudaMemcpyHostToDevice, s);
+    if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("H2D: ") + cudaGetErrorString(ce));
+    db[k] = be_buf{x->stage[k], nullptr, bufs[k].ndim, bufs[k].dtype};
+  }
+  for (int k = 0; k < n_outs; ++k) dout[k] = be_buf{x->stage[n_bufs + k], nullptr, outs[k].ndim, outs[k].dtype};
+  int st = do_execute(nullptr, h, reinterpret_cast<const be_config *>(&c), precision, db.data(), n_bufs, dout.data(),
+                      n_outs, scalars, n_scalars, stream);
+  if (st) return st;
+  for (int k = 0; k < n_outs; ++k) {
+    if (out_bytes) ce = cudaMemcpyAsync(outs[k].ptr, x->stage[n_bufs + k], out_bytes, cudaMemcpyDeviceToHost, s);
+    if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("D2H: ") + cudaGetErrorString(ce));
+  }
+  ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("sync: ") + cudaGetErrorString(ce));
+  return BE_OK;
+}
+
+}  // extern "C"

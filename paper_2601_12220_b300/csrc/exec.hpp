@@ -1,0 +1,91 @@
+// Execution layer: operand views, producer programs, kernel parameter
+// blocks and the launchers of every strategy.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "ir.hpp"
+
+namespace be {
+
+// ---------------------------------------------------------------- generic
+
+#define GMAXL 16      // distinct index letters an executed einsum may use
+#define GMAXOPS 8     // operands per einsum on the generic path
+#define GMAXINS 48    // producer instructions per einsum (all operands)
+#define GSTACK 8      // producer evaluation stack depth
+
+// One producer instruction.  X_REF reads ptr + sum_L coef[L] * value(L)
+// (as dtype); X_PARAM pushes value(letter); X_SCALAR pushes scalars[letter].
+struct GIns {
+  int32_t op, dtype, letter, pad;
+  double num;
+  const char *ptr;
+  int64_t coef[GMAXL];
+};
+
+struct GOp {
+  int32_t kind;      // 0: strided view (ptr, coef, dtype); 1: producer program
+  int32_t dtype;
+  int32_t prog_begin, prog_len;
+  const char *ptr;
+  int64_t coef[GMAXL];
+};
+
+struct GParams {
+  int32_t n_ops, n_letters, n_out, n_con;
+  int64_t len[GMAXL];
+  int32_t out_letter[GMAXL];
+  int32_t con_letter[GMAXL];
+  int64_t total_out, total_con;
+  void *out;
+  int32_t out_dtype, pad;
+  double scalars[8];
+  GOp ops[GMAXOPS];
+  GIns ins[GMAXINS];
+};
+
+cudaError_t launch_generic(const GParams &p, cudaStream_t s);
+
+// ---------------------------------------------------------------- element
+
+#define EM_MAXROWS 16
+#define EM_MAXN 64
+#define EM_MAXR 4
+
+// strided 2-index view x[e, k] = ptr[e * se + k * sk]
+struct EView {
+  const double *ptr;
+  int64_t se, sk;
+};
+
+// producer of a per-element operand: 0 view a; 1 sin(a) * b
+struct EProd {
+  int32_t kind, pad;
+  EView a, b;
+};
+
+struct ERow {
+  EView g;          // g[e, r] (unused without r)
+  int32_t group;    // index of this row's u-producer group
+  int32_t pad;
+  double *out;      // dense out[e, i]
+};
+
+struct EParams {
+  const double *D;
+  int64_t sr, si, sj;          // D[r, i, j] strides
+  int32_t R, NI, NJ, has_g;
+  int64_t E;
+  int32_t n_rows, n_groups, tile_e, pad;
+  ERow rows[EM_MAXROWS];
+  EProd groups[EM_MAXROWS];
+};
+
+cudaError_t launch_element(const EParams &p, int grid, int block, cudaStream_t s);
+
+}  // namespace be

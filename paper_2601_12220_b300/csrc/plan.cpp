@@ -1,0 +1,327 @@
+// Planner: turns a parsed batched einsum plus the caller's buffers into the
+// parameter block of one strategy and launches it.
+//
+// Every argument at every operand position is resolved either to a strided
+// view (the identity lambda of an idealized argument, or a lambda whose
+// body is a single buffer reference, e.g. G[e,r,0]) or to a producer
+// program in postfix form that the kernel evaluates at each access, so
+// elementwise producers run inside the operand loads (Def. "Functional
+// Batched Einstein Summation"; the fused listing of the Feinsum section).
+#include <algorithm>
+#include <cstring>
+
+#include "plan.hpp"
+
+namespace be {
+
+namespace {
+
+int esz(int dt) { return dtype_size(dt); }
+
+// strides of declared buffer k as the caller passed them (row-major if none)
+void strides_of(const BufIn &b, const Buffer &decl, std::vector<int64_t> &st) {
+  st.assign(decl.shape.size(), 0);
+  if (b.strides) {
+    for (size_t d = 0; d < decl.shape.size(); ++d) st[d] = b.strides[d];
+  } else {
+    int64_t s = 1;
+    for (int d = (int)decl.shape.size() - 1; d >= 0; --d) {
+      st[d] = s;
+      s *= decl.shape[d];
+    }
+  }
+}
+
+}  // namespace
+
+bool arg_view(const Einsum &e, int arg, int pos, const std::vector<BufIn> &bufs, View &v) {
+  const Arg &a = e.args[arg];
+  std::fill(v.coef, v.coef + 26, 0);
+  std::vector<int64_t> st;
+  if (!a.functional()) {
+    const Buffer &bf = e.buffers[a.buffer];
+    strides_of(bufs[a.buffer], bf, st);
+    for (size_t d = 0; d < bf.shape.size(); ++d) v.coef[e.in[pos][d]] += st[d];
+    v.ptr = (const char *)bufs[a.buffer].ptr;
+    v.dtype = bf.dtype;
+    return true;
+  }
+  const XNode &root = a.nodes[a.root];
+  if (root.op != X_REF) return false;
+  const Buffer &bf = e.buffers[root.id];
+  strides_of(bufs[root.id], bf, st);
+  int64_t off = 0;
+  for (size_t d = 0; d < root.sub.size(); ++d) {
+    int s = root.sub[d];
+    if (s >= 0) v.coef[e.in[pos][s]] += st[d];
+    else off += (int64_t)(-(s + 1)) * st[d];
+  }
+  v.ptr = (const char *)bufs[root.id].ptr + off * esz(bf.dtype);
+  v.dtype = bf.dtype;
+  return true;
+}
+
+// view of a REF node of arg's body at position pos
+static void ref_view(const Einsum &e, const XNode &nd, int pos, const std::vector<BufIn> &bufs, View &v) {
+  const Buffer &bf = e.buffers[nd.id];
+  std::vector<int64_t> st;
+  strides_of(bufs[nd.id], bf, st);
+  std::fill(v.coef, v.coef + 26, 0);
+  int64_t off = 0;
+  for (size_t d = 0; d < nd.sub.size(); ++d) {
+    int s = nd.sub[d];
+    if (s >= 0) v.coef[e.in[pos][s]] += st[d];
+    else off += (int64_t)(-(s + 1)) * st[d];
+  }
+  v.ptr = (const char *)bufs[nd.id].ptr + off * esz(bf.dtype);
+  v.dtype = bf.dtype;
+}
+
+int check_buffers(const Einsum &e, const std::vector<BufIn> &bufs, const std::vector<BufIn> &outs,
+                  std::string &err) {
+  if (bufs.size() != e.buffers.size()) {
+    err = "expected " + std::to_string(e.buffers.size()) + " buffers, got " + std::to_string(bufs.size());
+    return EARG;
+  }
+  for (size_t k = 0; k < bufs.size(); ++k) {
+    const Buffer &d = e.buffers[k];
+    if (!bufs[k].ptr && !d.shape.empty()) {
+      bool empty = false;
+      for (auto x : d.shape) empty |= x == 0;
+      if (!empty) { err = "buffer " + d.name + " is NULL"; return EARG; }
+    }
+    if (bufs[k].dtype != d.dtype) { err = "dtype of buffer " + d.name + " differs from its declaration"; return EDTYPE; }
+    if (bufs[k].ndim != (int)d.shape.size()) { err = "rank of buffer " + d.name + " differs from its declaration"; return ESHAPE; }
+    if (d.dtype != F64 && d.dtype != F32 && d.dtype != F16 && d.dtype != BF16 && d.dtype != I32 &&
+        d.dtype != I64 && d.dtype != I8) {
+      err = std::string("buffers of dtype ") + dtype_name(d.dtype) + " are not evaluated";
+      return EUNSUPPORTED;
+    }
+  }
+  if ((int)outs.size() != e.b) { err = "expected one output per row"; return EARG; }
+  for (auto &o : outs) {
+    if (o.dtype != e.out_dtype) { err = std::string("output dtype must be ") + dtype_name(e.out_dtype); return EDTYPE; }
+    if (o.ndim != (int)e.out.size()) { err = "output rank differs from the notation"; return ESHAPE; }
+    if (o.strides) { err = "outputs must be dense row-major (strides = NULL)"; return EARG; }
+  }
+  if (e.out_dtype != F64 && e.out_dtype != F32) {
+    err = "outputs of dtype other than float64 / float32 are not evaluated";
+    return EUNSUPPORTED;
+  }
+  return OK;
+}
+
+// ------------------------------------------------------------ generic
+
+int plan_generic_row(const Einsum &e, int row, const std::vector<BufIn> &bufs, const BufIn &out,
+                     const std::vector<double> &scalars, GParams &p, std::string &err) {
+  std::memset(&p, 0, sizeof(p));
+  int compact[26];
+  int nl = 0;
+  for (int c = 0; c < 26; ++c) compact[c] = e.used[c] ? nl++ : -1;
+  if (nl > GMAXL) { err = "more than 16 distinct indices on the generic path"; return EUNSUPPORTED; }
+  if (e.n > GMAXOPS) { err = "more than 8 operands on the generic path"; return EUNSUPPORTED; }
+  if (scalars.size() > 8) { err = "more than 8 runtime scalars"; return EUNSUPPORTED; }
+  p.n_letters = nl;
+  p.n_ops = e.n;
+  for (int c = 0; c < 26; ++c)
+    if (e.used[c]) p.len[compact[c]] = e.len[c];
+  p.n_out = (int)e.out.size();
+  bool is_out[26] = {false};
+  p.total_out = 1;
+  for (int d = 0; d < p.n_out; ++d) {
+    p.out_letter[d] = compact[e.out[d]];
+    is_out[e.out[d]] = true;
+    p.total_out *= e.len[e.out[d]];
+  }
+  p.total_con = 1;
+  for (int c = 0; c < 26; ++c)
+    if (e.used[c] && !is_out[c]) {
+      p.con_letter[p.n_con++] = compact[c];
+      p.total_con *= e.len[c];
+    }
+  p.out = out.ptr;
+  p.out_dtype = e.out_dtype;
+  for (size_t k = 0; k < scalars.size(); ++k) p.scalars[k] = scalars[k];
+  int n_ins = 0;
+  for (int j = 0; j < e.n; ++j) {
+    int a = e.rows[row][j];
+    GOp &op = p.ops[j];
+    View v;
+    if (arg_view(e, a, j, bufs, v)) {
+      op.kind = 0;
+      op.ptr = v.ptr;
+      op.dtype = v.dtype;
+      for (int c = 0; c < 26; ++c)
+        if (compact[c] >= 0) op.coef[compact[c]] = v.coef[c];
+      continue;
+    }
+    // producer program: postfix walk of the lambda body
+    const Arg &arg = e.args[a];
+    op.kind = 1;
+    op.prog_begin = n_ins;
+    int depth = 0, max_depth = 0;
+    std::vector<std::pair<int, bool>> stack{{arg.root, false}};
+    while (!stack.empty()) {
+      auto [id, done] = stack.back();
+      stack.pop_back();
+      const XNode &nd = arg.nodes[id];
+      if (!done && nd.op != X_REF) {
+        stack.push_back({id, true});
+        for (int k = (int)nd.kids.size() - 1; k >= 0; --k) stack.push_back({nd.kids[k], false});
+        continue;
+      }
+      if (n_ins >= GMAXINS) { err = "producer programs longer than 48 instructions"; return EUNSUPPORTED; }
+      GIns &in = p.ins[n_ins++];
+      in.op = nd.op;
+      switch (nd.op) {
+        case X_NUM: in.num = nd.num; ++depth; break;
+        case X_SCALAR:
+          if (nd.id >= (int)scalars.size()) { err = "missing value of scalar $" + e.scalars[nd.id]; return EARG; }
+          in.letter = nd.id;
+          ++depth;
+          break;
+        case X_PARAM: in.letter = compact[e.in[j][nd.id]]; ++depth; break;
+        case X_REF: {
+          View rv;
+          ref_view(e, nd, j, bufs, rv);
+          in.ptr = rv.ptr;
+          in.dtype = rv.dtype;
+          for (int c = 0; c < 26; ++c)
+            if (compact[c] >= 0) in.coef[compact[c]] = rv.coef[c];
+          ++depth;
+          break;
+        }
+        case X_ADD: case X_SUB: case X_MUL: case X_DIV: case X_EQ: case X_NE: --depth; break;
+        case X_SELECT: depth -= 2; break;
+        default: break;
+      }
+      max_depth = std::max(max_depth, depth);
+    }
+    if (max_depth > GSTACK) { err = "producer expression deeper than 8"; return EUNSUPPORTED; }
+    op.prog_len = n_ins - op.prog_begin;
+    op.dtype = arg.dtype;
+  }
+  return OK;
+}
+
+// ------------------------------------------------------------ element
+
+int plan_element(const Einsum &e, const std::vector<BufIn> &bufs, const std::vector<BufIn> &outs,
+                 const be_config_t &cfg, EParams &p, std::string &why) {
+  std::memset(&p, 0, sizeof(p));
+  if (e.out_dtype != F64) { why = "element strategy runs FP64 only"; return EUNSUPPORTED; }
+  for (auto &a : e.args)
+    if (a.dtype != F64) { why = "element strategy runs FP64 only"; return EUNSUPPORTED; }
+  for (auto &b : e.buffers)
+    if (b.dtype != F64) { why = "element strategy runs FP64 only"; return EUNSUPPORTED; }
+  if (e.out.size() != 2 || (e.n != 2 && e.n != 3)) { why = "notation is not R[e,i] = sum D u (g)"; return EUNSUPPORTED; }
+  if (e.b > EM_MAXROWS) { why = "more than 16 rows"; return EUNSUPPORTED; }
+  const int le = e.out[0], li = e.out[1];
+  // D: the operand without e that holds i
+  int pD = -1, pU = -1, pG = -1;
+  for (int j = 0; j < e.n; ++j) {
+    bool has_e = std::find(e.in[j].begin(), e.in[j].end(), le) != e.in[j].end();
+    bool has_i = std::find(e.in[j].begin(), e.in[j].end(), li) != e.in[j].end();
+    if (!has_e && has_i) pD = j;
+  }
+  if (pD < 0) { why = "no shared operator operand"; return EUNSUPPORTED; }
+  const auto &dl = e.in[pD];
+  if ((e.n == 2 && dl.size() != 2) || (e.n == 3 && dl.size() != 3)) { why = "operator rank"; return EUNSUPPORTED; }
+  int lj = -1, lr = -1;
+  // identify u (e, j) and g (e, r); when n = 3 both are (e, x) operands
+  std::vector<int> ex;
+  for (int j = 0; j < e.n; ++j)
+    if (j != pD) {
+      if (e.in[j].size() != 2 || e.in[j][0] != le || e.in[j][1] == le) { why = "per-element operands must be (e, x)"; return EUNSUPPORTED; }
+      ex.push_back(j);
+    }
+  std::vector<int8_t> others;
+  for (int8_t c : dl)
+    if (c != li) others.push_back(c);
+  if (e.n == 2) {
+    pU = ex[0];
+    lj = e.in[pU][1];
+    if (others.size() != 1 || others[0] != lj) { why = "u does not share j with D"; return EUNSUPPORTED; }
+  } else {
+    // two letters besides i in D: j (shared with u) and r (shared with g)
+    if (others.size() != 2 || others[0] == others[1]) { why = "operator letters"; return EUNSUPPORTED; }
+    int8_t x0 = e.in[ex[0]][1], x1 = e.in[ex[1]][1];
+    if (x0 == x1) { why = "g and u index the same letter"; return EUNSUPPORTED; }
+    // u is the operand with the larger extent (dofs), g the smaller one (dimension r)
+    if (e.len[x0] >= e.len[x1]) { pU = ex[0]; pG = ex[1]; } else { pU = ex[1]; pG = ex[0]; }
+    lj = e.in[pU][1];
+    lr = e.in[pG][1];
+    if (!((others[0] == lj && others[1] == lr) || (others[0] == lr && others[1] == lj))) { why = "operator letters"; return EUNSUPPORTED; }
+  }
+  p.NI = (int)e.len[li];
+  p.NJ = (int)e.len[lj];
+  p.R = lr >= 0 ? (int)e.len[lr] : 1;
+  p.has_g = pG >= 0;
+  p.E = e.len[le];
+  if (p.NI > EM_MAXN || p.NJ > EM_MAXN || p.R > EM_MAXR || p.NI < 1 || p.NJ < 1) { why = "operator extents beyond 64 x 64 x 4"; return EUNSUPPORTED; }
+  // D shared by every row
+  int dArg = e.rows[0][pD];
+  for (int i = 0; i < e.b; ++i)
+    if (e.rows[i][pD] != dArg) { why = "operator differs between rows"; return EUNSUPPORTED; }
+  View dv;
+  if (!arg_view(e, dArg, pD, bufs, dv)) { why = "operator is not a plain view"; return EUNSUPPORTED; }
+  p.D = (const double *)dv.ptr;
+  p.si = dv.coef[li];
+  p.sj = dv.coef[lj];
+  p.sr = lr >= 0 ? dv.coef[lr] : 0;
+  // per-row producers and geometric factors
+  std::vector<int> uargs;
+  p.n_rows = e.b;
+  for (int i = 0; i < e.b; ++i) {
+    int ua = e.rows[i][pU];
+    int g = -1;
+    for (size_t k = 0; k < uargs.size(); ++k)
+      if (uargs[k] == ua) g = (int)k;
+    if (g < 0) {
+      EProd q;
+      std::memset(&q, 0, sizeof(q));
+      View v;
+      if (arg_view(e, ua, pU, bufs, v)) {
+        q.kind = 0;
+        q.a = EView{(const double *)v.ptr, v.coef[le], v.coef[lj]};
+      } else {
+        const Arg &A = e.args[ua];
+        const XNode &rt = A.nodes[A.root];
+        int sin_kid = -1, ref_kid = -1;
+        if (rt.op == X_MUL && rt.kids.size() == 2) {
+          for (int k = 0; k < 2; ++k) {
+            const XNode &kd = A.nodes[rt.kids[k]];
+            if (kd.op == X_SIN && A.nodes[kd.kids[0]].op == X_REF) sin_kid = k;
+            else if (kd.op == X_REF) ref_kid = k;
+          }
+        }
+        if (sin_kid < 0 || ref_kid < 0 || sin_kid == ref_kid) { why = "producer is not a view or sin(a)*b"; return EUNSUPPORTED; }
+        View va, vb;
+        ref_view(e, A.nodes[A.nodes[rt.kids[sin_kid]].kids[0]], pU, bufs, va);
+        ref_view(e, A.nodes[rt.kids[ref_kid]], pU, bufs, vb);
+        q.kind = 1;
+        q.a = EView{(const double *)va.ptr, va.coef[le], va.coef[lj]};
+        q.b = EView{(const double *)vb.ptr, vb.coef[le], vb.coef[lj]};
+      }
+      uargs.push_back(ua);
+      g = (int)uargs.size() - 1;
+      p.groups[g] = q;
+    }
+    p.rows[i].group = g;
+    p.rows[i].out = (double *)outs[i].ptr;
+    if (pG >= 0) {
+      View gv;
+      if (!arg_view(e, e.rows[i][pG], pG, bufs, gv)) { why = "geometric factor is not a plain view"; return EUNSUPPORTED; }
+      p.rows[i].g = EView{(const double *)gv.ptr, gv.coef[le], gv.coef[lr]};
+    }
+  }
+  p.n_groups = (int)uargs.size();
+  int te = cfg.tile[0] > 0 ? cfg.tile[0] : (p.NI >= 16 ? 32 : 256);
+  p.tile_e = te;
+  size_t smem = sizeof(double) * ((size_t)p.R * p.NI * p.NJ + (size_t)p.n_groups * te * p.NJ + (size_t)p.n_rows * te * p.R);
+  if (smem > 200 * 1024) { why = "tile does not fit shared memory"; return EUNSUPPORTED; }
+  return OK;
+}
+
+}  // namespace be

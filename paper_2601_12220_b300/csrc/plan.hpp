@@ -1,0 +1,45 @@
+// Planner interface: caller buffers, operand views and strategy planners.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "exec.hpp"
+#include "ir.hpp"
+
+namespace be {
+
+// mirror of be_config (include/be.h)
+struct be_config_t {
+  int32_t strategy;
+  int32_t tile[4];
+  int32_t stages;
+  uint32_t stage_mask;
+  int32_t vec;
+  int32_t split;
+};
+
+// a caller buffer (device pointer for execution)
+struct BufIn {
+  void *ptr;
+  const int64_t *strides;
+  int32_t ndim;
+  int32_t dtype;
+};
+
+// strided view of an operand at one position: ptr + sum_c coef[c] * value(c)
+struct View {
+  const char *ptr;
+  int dtype;
+  int64_t coef[26];
+};
+
+bool arg_view(const Einsum &e, int arg, int pos, const std::vector<BufIn> &bufs, View &v);
+int check_buffers(const Einsum &e, const std::vector<BufIn> &bufs, const std::vector<BufIn> &outs,
+                  std::string &err);
+int plan_generic_row(const Einsum &e, int row, const std::vector<BufIn> &bufs, const BufIn &out,
+                     const std::vector<double> &scalars, GParams &p, std::string &err);
+int plan_element(const Einsum &e, const std::vector<BufIn> &bufs, const std::vector<BufIn> &outs,
+                 const be_config_t &cfg, EParams &p, std::string &why);
+
+}  // namespace be
