@@ -1,0 +1,325 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched-einsum engine.
+
+Workload (one "step"): the DG local-gradient functional batched einsum on a
+P4 tetrahedral mesh -- b = 3 einsums 'rij,er,ej->ei' (one per derivative
+direction x) sharing the derivative matrices D (3 x 35 x 35), with per-row
+geometric factors G[e, r, x] and the field u = sin(a) * b fused into the
+operand load; E = 262144 elements, FP64, synthetic N(0,1) data.  A step runs
+the whole hot path through the C ABI: parse -> canonicalize -> lookup in the
+tuning database -> evaluate on the GPU.
+
+  value  : algorithmic GB/s over all ranks (operands read once, outputs
+           written once, per step), inputs already resident in HBM
+  e2e    : same metric through be_execute_host with pinned host buffers
+           (host -> device copies of the inputs and device -> host copies of
+           the results inside the timed region)
+  roofline: the dominant kernel, achieved vs peak, from CUDA events on the
+           launching stream
+
+``--impl reference`` times the CPU oracle (plain FP64 loops, all host
+cores) on a bounded sample of the same workload instead.
+Multi-GPU: the path shards by replicas (each rank evaluates its own batch).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "batched-einsum GB/s & TFLOP/s vs roofline; served einsums/s, p50/p99 latency"
+E_FULL, NDOF, DIM = 262144, 35, 3
+
+
+def algorithmic(E, ndof=NDOF, dim=DIM):
+    """Bytes (each operand read once, each output written once) and flops
+    (hoisted: t = D u once per element, then G t per row, plus the producer
+    multiply; sin counted as 0) of one DG-gradient step."""
+    byts = 8 * (2 * E * ndof + E * dim * dim + dim * ndof * ndof + dim * E * ndof)
+    flops = E * (2 * dim * ndof * ndof + 2 * dim * dim * ndof + ndof)
+    return byts, flops
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "source": "fallback"}
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        peaks.update({k: d[k] for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained") if k in d})
+        peaks["source"] = "measured"
+    return peaks
+
+
+# FP64 vector-pipe peak of B300 (nominal figure of the profiling notes:
+# 1.25 TFLOP/s dense FP64); the element kernel's bound while it runs on the
+# FP64 pipe.
+FP64_PEAK_TFLOPS = 1.25
+
+
+def kernel_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary of ``kernel``,
+    valid only while the kernel source hashes to the value recorded there."""
+    src = os.path.join(ROOT, "paper_2601_12220_b300", "csrc", kernel["source"])
+    summ = os.path.join(ROOT, "profiles", kernel["profile"])
+    if not (os.path.exists(src) and os.path.exists(summ)):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    got = {}
+    for line in open(summ):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            got[k.strip().lstrip("-* ").strip()] = v.strip()
+    if got.get("source_sha256_16") != h:
+        return None
+    try:
+        return float(got["dram_bytes_per_full_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.proc is None:
+            return
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_baseline(E_sample, reps=1, data=None):
+    """The oracle as it stands, on E_sample elements of the same workload."""
+    from oracle import evaluate as ev
+    D, G, a, b = data if data is not None else W.dg_gradient(E=E_sample)
+    text = W.dg_gradient_spec(E=E_sample)
+    threads = ev.set_threads(cpu_cores())
+    t = time.perf_counter()
+    for _ in range(reps):
+        ev.evaluate(text, dict(D=D, G=G, a=a, b=b))
+    dt = (time.perf_counter() - t) / reps
+    byts, _ = algorithmic(E_sample)
+    return {"value": byts / dt / 1e9, "unit": "GB/s", "cores": threads, "kind": "oracle",
+            "sample": f"DG gradient with E={E_sample} of {E_FULL} elements (all outputs, FP64 nested loops), "
+                      f"{reps} pass(es), {dt:.2f} s per pass"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    E_s = args.ref_sample
+    data = W.dg_gradient(E=E_s)
+    for _ in range(args.warmup):
+        oracle_baseline(E_s, data=data)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        cb = oracle_baseline(E_s, data=data)
+    dt = (time.perf_counter() - t) / args.steps
+    byts, flops = algorithmic(E_s)
+    value = byts / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"dg_gradient_p4 (CPU oracle on E={E_s} per step)", "E": E_s,
+                       "ndof": NDOF, "b": DIM, "producer": "sin(a)*b", "parallelism": "none (host cores)"},
+            "cpu_baseline": {**cb, "value": value},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "tflops": flops / dt / 1e12}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_2601_12220_b300 as be
+
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    E = args.elements
+    D, G, a, b = W.dg_gradient(E=E)
+    host = dict(D=D, G=G, a=a, b=b)
+    bufs = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
+    outs = [torch.empty((E, NDOF), dtype=torch.float64, device=dev) for _ in range(DIM)]
+    text = W.dg_gradient_spec(E=E)
+    ctx = be.Context(None, device=local)
+    stream = torch.cuda.current_stream(dev)
+    byts, flops = algorithmic(E)
+
+    strat = be.plan_strategy(ctx, be.Einsum(text))
+    launches_per_step = 1 if strat == be.STRAT_ELEMENT else DIM
+
+    def step(k_ev=None):
+        e = be.Einsum(text)                       # parse
+        c = e.canonicalize()                      # normal form
+        hit = ctx.lookup(c, be.PREC_FP64)         # tuning database
+        cfg = hit[0] if hit else None
+        if k_ev is not None:
+            k_ev[0].record(stream)
+        be.execute(ctx, e, bufs, outs, cfg=cfg, precision=be.PREC_FP64, stream=stream)
+        if k_ev is not None:
+            k_ev[1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t0.record(stream)
+        for k in range(args.steps):
+            step(evs[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ms = t0.elapsed_time(t1) / args.steps
+    kms = statistics.mean(s.elapsed_time(e) for s, e in evs)
+    if pg:
+        tt = torch.tensor([ms, kms], device=dev, dtype=torch.float64)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        ms, kms = tt.tolist()
+    value = world * byts / (ms * 1e-3) / 1e9
+
+    # end to end through the public API with pinned host buffers
+    pinned = {k: torch.from_numpy(v).pin_memory().numpy() for k, v in host.items()}
+    host_outs = [torch.empty((E, NDOF), dtype=torch.float64).pin_memory().numpy() for _ in range(DIM)]
+    e_host = be.Einsum(text)
+    for _ in range(max(1, args.warmup)):
+        be.execute_host(ctx, e_host, pinned, host_outs, stream=stream)
+    if pg:
+        pg.barrier()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        e2 = be.Einsum(text)
+        c2 = e2.canonicalize()
+        hit = ctx.lookup(c2, be.PREC_FP64)
+        be.execute_host(ctx, e2, pinned, host_outs, cfg=hit[0] if hit else None, stream=stream)
+    e2e_s = (time.perf_counter() - t) / args.steps
+    if pg:
+        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        e2e_s = tt.item()
+    h2d = sum(v.nbytes for v in host.values())
+    d2h = sum(o.nbytes for o in host_outs)
+
+    peaks = load_peaks()
+    kernel = {"name": "element_kernel", "source": "kernels_element.cu", "profile": "element_kernel_dg_p4.md"}
+    ach_tf = flops / (kms * 1e-3) / 1e12
+    ach_gb = byts / (kms * 1e-3) / 1e9
+    traffic = kernel_traffic(kernel)
+    roofline = {"kernel": kernel["name"], "bound": "alu", "achieved": ach_tf, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach_tf / FP64_PEAK_TFLOPS,
+                "peak_source": "nominal B300 FP64 (1.25 TFLOP/s)",
+                "traffic": traffic, "algorithmic_bytes": byts,
+                "hbm": {"achieved": ach_gb, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": ach_gb / peaks["hbm_gbs"], "peak_source": peaks["source"]}}
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"dg_gradient_p4: b=3 'rij,er,ej->ei', D 3x35x35 shared, G[E,3,3] sliced per row, "
+                                   f"u=sin(a)*b fused, E={E}", "E": E, "ndof": NDOF, "b": DIM,
+                       "global_batch": world * E, "parallelism": f"replicas x{world}",
+                       "l2": f"inputs larger than L2 ({byts / 1e6:.0f} MB per step), no flush",
+                       "strategy": {1: "generic", 2: "element"}.get(strat, str(strat))},
+            "tflops": world * flops / (ms * 1e-3) / 1e12, "kernel_ms": kms,
+            "roofline": roofline,
+            "e2e": {"value": world * byts / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
+            "clocks": clk.summary(), "gpu_launches": args.steps * launches_per_step}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_baseline(args.cpu_sample)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--elements", type=int, default=E_FULL)
+    ap.add_argument("--cpu-sample", type=int, default=E_FULL)
+    ap.add_argument("--ref-sample", type=int, default=32768)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -308,6 +308,14 @@ def execute(ctx, e: Einsum, bufs, outs, cfg: Config | None = None, precision=PRE
     import torch
     keep = []
     bl = _order(e, bufs)
+    if len(bl) != len(e.buffers):
+        raise BEError(EARG, f"expected {len(e.buffers)} buffers, got {len(bl)}")
+    for t, (name, _, shape) in zip(bl, e.buffers):
+        if tuple(t.shape) != shape or not t.is_cuda:
+            raise BEError(ESHAPE, f"buffer {name}: expected a CUDA tensor of shape {shape}, got {tuple(t.shape)}")
+    for t in outs:
+        if tuple(t.shape) != e.out_shape or not t.is_cuda or not t.is_contiguous():
+            raise BEError(ESHAPE, f"outputs must be dense CUDA tensors of shape {e.out_shape}")
     bi = _bufs_torch(bl, keep)
     bo = _bufs_torch(outs, keep, dense_only=True)
     sc, ns = _scalars(scalars)
@@ -321,6 +329,12 @@ def execute_host(ctx, e: Einsum, bufs, outs, cfg: Config | None = None, precisio
                  stream=None):
     """As execute, with dense host numpy arrays; blocks until done."""
     bl = [np.ascontiguousarray(x) for x in _order(e, bufs)]
+    for x, (name, _, shape) in zip(bl, e.buffers):
+        if tuple(x.shape) != shape:
+            raise BEError(ESHAPE, f"buffer {name}: expected shape {shape}, got {tuple(x.shape)}")
+    for x in outs:
+        if tuple(x.shape) != e.out_shape:
+            raise BEError(ESHAPE, f"outputs must have shape {e.out_shape}")
     arr = (Buf * max(1, len(bl)))()
     for k, x in enumerate(bl):
         arr[k].ptr, arr[k].ndim, arr[k].dtype, arr[k].strides = x.ctypes.data, x.ndim, _NP_DT[x.dtype], None

@@ -63,7 +63,7 @@ struct EView {
   int64_t se, sk;
 };
 
-// producer of a per-element operand: 0 view a; 1 sin(a) * b
+// producer of a per-element operand: 0 view a; 1 sin(a) * b; 2 a * b
 struct EProd {
   int32_t kind, pad;
   EView a, b;

@@ -26,6 +26,7 @@ __device__ __forceinline__ double prod_value(const EProd &q, int64_t e, int k) {
   double a = q.a.ptr[e * q.a.se + k * q.a.sk];
   if (q.kind == 0) return a;
   double b = q.b.ptr[e * q.b.se + k * q.b.sk];
+  if (q.kind == 2) return a * b;
   return sin(a) * b;
 }
 

@@ -289,18 +289,27 @@ int plan_element(const Einsum &e, const std::vector<BufIn> &bufs, const std::vec
         const Arg &A = e.args[ua];
         const XNode &rt = A.nodes[A.root];
         int sin_kid = -1, ref_kid = -1;
+        bool both_ref = false;
         if (rt.op == X_MUL && rt.kids.size() == 2) {
+          both_ref = A.nodes[rt.kids[0]].op == X_REF && A.nodes[rt.kids[1]].op == X_REF;
           for (int k = 0; k < 2; ++k) {
             const XNode &kd = A.nodes[rt.kids[k]];
             if (kd.op == X_SIN && A.nodes[kd.kids[0]].op == X_REF) sin_kid = k;
             else if (kd.op == X_REF) ref_kid = k;
           }
         }
-        if (sin_kid < 0 || ref_kid < 0 || sin_kid == ref_kid) { why = "producer is not a view or sin(a)*b"; return EUNSUPPORTED; }
         View va, vb;
-        ref_view(e, A.nodes[A.nodes[rt.kids[sin_kid]].kids[0]], pU, bufs, va);
-        ref_view(e, A.nodes[rt.kids[ref_kid]], pU, bufs, vb);
-        q.kind = 1;
+        if (both_ref) {
+          ref_view(e, A.nodes[rt.kids[0]], pU, bufs, va);
+          ref_view(e, A.nodes[rt.kids[1]], pU, bufs, vb);
+          q.kind = 2;
+        } else {
+          if (sin_kid < 0 || ref_kid < 0 || sin_kid == ref_kid) { why = "producer is not a view, a*b or sin(a)*b"; return EUNSUPPORTED; }
+          ref_view(e, A.nodes[A.nodes[rt.kids[sin_kid]].kids[0]], pU, bufs, va);
+          ref_view(e, A.nodes[rt.kids[ref_kid]], pU, bufs, vb);
+          q.kind = 1;
+        }
+        if (va.dtype != F64 || vb.dtype != F64) { why = "producer operands must be float64"; return EUNSUPPORTED; }
         q.a = EView{(const double *)va.ptr, va.coef[le], va.coef[lj]};
         q.b = EView{(const double *)vb.ptr, vb.coef[le], vb.coef[lj]};
       }

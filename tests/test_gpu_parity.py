@@ -1,0 +1,252 @@
+"""GPU parity: the CUDA path through the C ABI vs the FP64 oracle.
+
+Tolerances (componentwise, against the oracle's absolute contraction S):
+  FP64 paths       |got - ref| <= 1e-12 * S
+  FP32-output path |got - ref| <= max(gamma_K(2^-24), 1e-6) * S,
+                   gamma_K = K u / (1 - K u), K = contracted terms + operands
+Integer-valued inputs make every correct evaluation order exact, so those
+cases are compared bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
+
+import paper_2601_12220_b300 as be  # noqa: E402
+from oracle import evaluate as ev  # noqa: E402
+import workloads as W  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def to_dev(arrs):
+    return {k: torch.from_numpy(np.ascontiguousarray(v)).to(DEV) for k, v in arrs.items()}
+
+
+def run(text, arrs, cfg=None, scalars=(), precision=be.PREC_FP64, ctx=None):
+    e = be.Einsum(text)
+    dt = torch.float64 if e.out_dtype == be.F64 else torch.float32
+    outs = [torch.full(e.out_shape, float("nan"), dtype=dt, device=DEV) for _ in range(e.b)]
+    be.execute(ctx, e, to_dev(arrs), outs, cfg=cfg, scalars=scalars, precision=precision)
+    torch.cuda.synchronize()
+    return [o.cpu().numpy().astype(np.float64) for o in outs], e
+
+
+def assert_close(got, ref, S, tol):
+    assert got.shape == ref.shape
+    assert np.all(np.isfinite(got))
+    err = np.abs(got - ref)
+    bound = tol * S
+    bad = err > bound
+    if bad.any():
+        k = np.argmax(err - bound)
+        raise AssertionError(f"{bad.sum()} entries off; worst err {err.flat[k]:.3e} vs bound {bound.flat[k]:.3e}")
+
+
+def gamma(K, u=2.0 ** -24):
+    return K * u / (1 - K * u)
+
+
+# ------------------------------------------------------------- element strategy
+
+@pytest.mark.parametrize("strategy", [be.STRAT_AUTO, be.STRAT_ELEMENT, be.STRAT_GENERIC])
+def test_fem_action_full(strategy):
+    D, us = W.fem_action()
+    arrs = {"D": D, **{f"u{k}": u for k, u in enumerate(us)}}
+    text = W.fem_action_spec()
+    got, e = run(text, arrs, cfg=be.make_config(strategy))
+    ref = ev.evaluate(text, arrs)
+    for k in range(4):
+        assert_close(got[k], ref[k][0], ref[k][1], 1e-12)
+
+
+def test_fem_action_integers_bit_exact():
+    D, us = W.fem_action(ints=True)
+    arrs = {"D": D, **{f"u{k}": u for k, u in enumerate(us)}}
+    text = W.fem_action_spec()
+    for strategy in (be.STRAT_ELEMENT, be.STRAT_GENERIC):
+        got, _ = run(text, arrs, cfg=be.make_config(strategy))
+        ref = ev.evaluate(text, arrs)
+        for k in range(4):
+            assert np.array_equal(got[k], ref[k][0])
+
+
+@pytest.mark.parametrize("E", [1, 31, 33, 1000, 4099])
+def test_dg_gradient_ragged(E):
+    D, G, a, b = W.dg_gradient(E=E)
+    arrs = dict(D=D, G=G, a=a, b=b)
+    text = W.dg_gradient_spec(E=E)
+    assert be.plan_strategy(None, be.Einsum(text)) == be.STRAT_ELEMENT
+    got, _ = run(text, arrs)
+    ref = ev.evaluate(text, arrs)
+    for x in range(3):
+        assert_close(got[x], ref[x][0], ref[x][1], 1e-12)
+
+
+def test_dg_gradient_integers_bit_exact():
+    E = 777
+    D, G, a, b = W.dg_gradient(E=E, ints=True)
+    arrs = dict(D=D, G=G, a=a, b=b)
+    text = W.dg_gradient_spec(E=E, producer="a[e,j]*b[e,j]")
+    for strategy in (be.STRAT_ELEMENT, be.STRAT_GENERIC):
+        got, _ = run(text, arrs, cfg=be.make_config(strategy))
+        ref = ev.evaluate(text, arrs)
+        for x in range(3):
+            assert np.array_equal(got[x], ref[x][0])
+
+
+@pytest.mark.parametrize("tile", [8, 32, 64])
+def test_dg_gradient_tiles(tile):
+    E = 2048 + 17
+    D, G, a, b = W.dg_gradient(E=E)
+    arrs = dict(D=D, G=G, a=a, b=b)
+    text = W.dg_gradient_spec(E=E)
+    got, _ = run(text, arrs, cfg=be.make_config(be.STRAT_ELEMENT, (tile, 256)))
+    ref = ev.evaluate(text, arrs)
+    for x in range(3):
+        assert_close(got[x], ref[x][0], ref[x][1], 1e-12)
+
+
+def test_dg_gradient_full_size_sampled():
+    """E = 262144, the benchmark's launch configuration; sampled outputs per
+    row against the oracle evaluated one by one."""
+    E = 262144
+    D, G, a, b = W.dg_gradient(E=E)
+    arrs = dict(D=D, G=G, a=a, b=b)
+    text = W.dg_gradient_spec(E=E)
+    got, _ = run(text, arrs)
+    g = np.random.default_rng(0)
+    sel = np.unique(np.concatenate([g.integers(0, E * 35, 4096), [0, E * 35 - 1]]))
+    ref = ev.evaluate(text, arrs, sel=sel)
+    for x in range(3):
+        assert_close(got[x].reshape(-1)[sel], ref[x][0], ref[x][1], 1e-12)
+
+
+# ------------------------------------------------------------- generic strategy
+
+@pytest.mark.parametrize("k", range(24))
+def test_uneven_mix_notations(k):
+    g = np.random.default_rng(100 + k)
+    inst = W.mix_instance(g, lo_exp=1.0, hi_exp=3.5, max_operand=1 << 14, max_flops=1 << 22)
+    text = W.instance_spec(inst)
+    arrs = W.instance_arrays(inst, g)
+    got, e = run(text, arrs)
+    ref = ev.evaluate(text, arrs)
+    K = 1 + math.prod(v for c, v in inst.lens.items() if c not in inst.out) + len(inst.ins)
+    tol = 1e-12 if inst.dtype == "f64" else max(gamma(K), 1e-6)
+    for r in range(e.b):
+        assert_close(got[r], ref[r][0], ref[r][1], tol)
+
+
+def test_producers_generic():
+    rng = np.random.default_rng(8)
+    E, N = 300, 10
+    u, v, w = (rng.standard_normal((E, N)) for _ in range(3))
+    J = rng.standard_normal((3, 3, E))
+    D = rng.standard_normal((3, N, N))
+    text = (f"xre,rij,xej->ei | J,D,F ; J:f64[3,3,{E}] ; D:f64[3,{N},{N}] ; u:f64[{E},{N}] ; "
+            f"v:f64[{E},{N}] ; w:f64[{E},{N}] ; F(x,e,j):f64[3,{E},{N}] := x==0 ? u[e,j] : (x==1 ? v[e,j] : w[e,j])")
+    arrs = dict(J=J, D=D, u=u, v=v, w=w)
+    got, _ = run(text, arrs)
+    ref = ev.evaluate(text, arrs)
+    assert_close(got[0], ref[0][0], ref[0][1], 1e-12)
+    # affine producers with runtime scalars, (alpha1 A + beta1)(alpha2 B + beta2)
+    A = rng.standard_normal((40, 30))
+    B = rng.standard_normal((30, 50))
+    text = ("ik,kj->ij | P,Q ; A:f64[40,30] ; B:f64[30,50] ; P(i,k) := $a1*A[i,k]+$b1 ; "
+            "Q(k,j) := $a2*B[k,j]+$b2")
+    sc = (0.5, -1.25, 2.0, 0.75)
+    got, _ = run(text, dict(A=A, B=B), scalars=sc)
+    ref = ev.evaluate(text, dict(A=A, B=B), scalars=dict(a1=sc[0], b1=sc[1], a2=sc[2], b2=sc[3]))
+    assert_close(got[0], ref[0][0], ref[0][1], 1e-12)
+
+
+def test_feinsum_listing(golden):
+    text = golden("einsum_examples.json")["feinsum_listing"]["spec"]
+    rng = np.random.default_rng(3)
+    arrs = dict(P=rng.standard_normal((96, 4)), Q=rng.standard_normal(4), R=rng.standard_normal(4))
+    got, _ = run(text, arrs)
+    ref = ev.evaluate(text, arrs)
+    for r in range(2):
+        assert_close(got[r], ref[r][0], ref[r][1], 1e-12)
+
+
+def test_strided_views():
+    rng = np.random.default_rng(4)
+    D = torch.from_numpy(rng.standard_normal((35, 35))).to(DEV)
+    U = torch.from_numpy(rng.standard_normal((35, 500))).to(DEV)
+    e = be.Einsum("ij,ej->ei | D,U ; D:f64[35,35] ; U:f64[500,35]")
+    out = torch.empty((500, 35), dtype=torch.float64, device=DEV)
+    for strategy in (be.STRAT_ELEMENT, be.STRAT_GENERIC):
+        be.execute(None, e, {"D": D.t(), "U": U.t()}, [out], cfg=be.make_config(strategy))
+        torch.cuda.synchronize()
+        ref, S = ev.einsum_f64("ei", ["ij", "ej"], [D.t().cpu().numpy(), U.t().cpu().numpy()])
+        assert_close(out.cpu().numpy(), ref, S, 1e-12)
+
+
+def test_edge_cases():
+    # empty contracted axis -> zeros
+    got, _ = run("ij->i | A ; A:f64[5,0]", {"A": np.zeros((5, 0))})
+    assert np.array_equal(got[0], np.zeros(5))
+    # scalar output (full contraction) of a diagonal
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((7, 7))
+    got, _ = run("ii-> | A ; A:f64[7,7]", {"A": A})
+    ref, S = ev.einsum_f64("", ["ii"], [A])
+    assert_close(got[0], ref, S, 1e-12)
+    # empty element axis
+    D, G, a, b = W.dg_gradient(E=0)
+    got, _ = run(W.dg_gradient_spec(E=0), dict(D=D, G=G, a=a, b=b))
+    assert got[0].shape == (0, 35)
+
+
+def test_execute_host_matches_device():
+    E = 5000
+    D, G, a, b = W.dg_gradient(E=E)
+    arrs = dict(D=D, G=G, a=a, b=b)
+    text = W.dg_gradient_spec(E=E)
+    e = be.Einsum(text)
+    ctx = be.Context(None, device=0)
+    outs = [np.empty((E, 35)) for _ in range(3)]
+    be.execute_host(ctx, e, arrs, outs)
+    dev, _ = run(text, arrs)
+    for x in range(3):
+        assert np.array_equal(outs[x], dev[x])
+
+
+def test_deterministic():
+    E = 3001
+    D, G, a, b = W.dg_gradient(E=E)
+    arrs = dict(D=D, G=G, a=a, b=b)
+    text = W.dg_gradient_spec(E=E)
+    first, _ = run(text, arrs)
+    for _ in range(3):
+        again, _ = run(text, arrs)
+        for x in range(3):
+            assert np.array_equal(first[x], again[x])
+
+
+def test_lookup_transfer_same_bits():
+    """A config stored under the normal form and applied to a renamed,
+    permuted copy gives the same bits as on the original (transfer, Alg. 2)."""
+    E = 2000
+    D, G, a, b = W.dg_gradient(E=E)
+    arrs = dict(D=D, G=G, a=a, b=b)
+    text = W.dg_gradient_spec(E=E)
+    ctx = be.Context(None, device=0)
+    e = be.Einsum(text)
+    ctx.record(e.canonicalize(), be.make_config(be.STRAT_ELEMENT, (16, 128)), 1e-3)
+    got, _ = run(text, arrs, ctx=ctx)
+    rows = " | ".join(f"D,G{x},U" for x in (2, 1, 0))
+    decls = text.split(";", 1)[1]
+    text2 = f"pqs,ep,es->eq | {rows} ;" + decls.replace("G[e,r,", "G[e,p,").replace("(e,r)", "(e,p)") \
+        .replace("(e,j)", "(e,s)").replace("a[e,j]", "a[e,s]").replace("b[e,j]", "b[e,s]")
+    e2 = be.Einsum(text2)
+    assert e2.canonicalize().key == e.canonicalize().key
+    got2, _ = run(text2, arrs, ctx=ctx)
+    for x in range(3):
+        assert np.array_equal(got[x], got2[2 - x])
