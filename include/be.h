@@ -63,7 +63,8 @@ extern "C" {
 #define BE_STRAT_AUTO 0        /* pick by pattern: ELEMENT, DENSE_SPLIT, else GENERIC   */
 #define BE_STRAT_GENERIC 1     /* one thread per output element, any notation           */
 #define BE_STRAT_ELEMENT 2     /* shared small operators x streamed per-element operands */
-#define BE_STRAT_DENSE_SPLIT 3 /* FP64 contraction as split FP16 products on tcgen05   */
+#define BE_STRAT_DENSE_SPLIT 3 /* FP64 contraction as split FP16 products on tcgen05;
+                                  needs a context (its workspace holds the split operands) */
 
 /* ---- precision modes (part of the tuning key, not of the normal form) ---- */
 #define BE_PREC_FP64 0         /* results within 1e-12 of the absolute contraction */
@@ -214,6 +215,26 @@ int be_execute(be_ctx *x, const be_einsum *e, const be_config *cfg, int32_t prec
 int be_execute_host(be_ctx *x, const be_einsum *e, const be_config *cfg, int32_t precision,
                     const be_buf *bufs, int32_t n_bufs, const be_buf *outs, int32_t n_outs,
                     const double *scalars, int32_t n_scalars, void *stream);
+
+/*
+ * be_status -- wait for the device, then read and clear x's device status
+ * word: BE_OK, or BE_ETIMEOUT when a bounded device-side wait of a kernel
+ * launched through x ran out (the kernel then stopped early and its output
+ * is not valid).
+ */
+int be_status(be_ctx *x, int32_t *device_status);
+
+/* ---- per-kernel timing (CUDA events on the launching stream) ---- */
+#define BE_KERNEL_ELEMENT 0     /* element-streaming kernel              */
+#define BE_KERNEL_GENERIC 1     /* generic loop-nest kernel              */
+#define BE_KERNEL_DENSE_GEMM 2  /* tcgen05 split-precision GEMM          */
+#define BE_KERNEL_SPLIT 3       /* operand split kernels of that strategy */
+#define BE_KERNEL_PERSISTENT 4  /* persistent multi-instance executor    */
+
+/* Enable (1) or disable (0) event timing of every kernel launched through x. */
+int be_ctx_set_timing(be_ctx *x, int32_t enable);
+/* Wait for, sum and forget the recorded launches of one kernel id. */
+int be_ctx_timing(be_ctx *x, int32_t kernel, int64_t *launches, double *total_ms);
 
 /* Strategy the engine would run for e under cfg (after AUTO resolution). */
 int be_plan_strategy(be_ctx *x, const be_einsum *e, const be_config *cfg, int32_t precision,

@@ -10,6 +10,7 @@ from .binding import (  # noqa: F401
     OK, EPARSE, EINVALID, ESHAPE, EDTYPE, ETOOMANY, ENOTFOUND, EDB, EBUDGET, ETIMEOUT, ECUDA,
     EUNSUPPORTED, EARG, I8, I32, I64, F16, F32, F64, C64, C128, BF16, STRAT_AUTO, STRAT_GENERIC,
     STRAT_ELEMENT, STRAT_DENSE_SPLIT, PREC_FP64, PREC_SPLIT, SIGMA_INDEX, SIGMA_ARG, SIGMA_ROW, SIGMA_POS,
+    KERNEL_ELEMENT, KERNEL_GENERIC, KERNEL_DENSE_GEMM, KERNEL_SPLIT, KERNEL_PERSISTENT,
 )
 
 lib()

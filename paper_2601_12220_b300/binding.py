@@ -31,8 +31,9 @@ EXPORTS = [
     "be_einsum_buffer", "be_canonicalize", "be_free_canon", "be_canon_key", "be_canon_sigma",
     "be_canon_tokens", "be_induced_graph", "be_graph_check", "be_identify", "be_ctx_create",
     "be_ctx_destroy", "be_lookup", "be_record", "be_db_size", "be_execute", "be_execute_host",
-    "be_plan_strategy",
+    "be_plan_strategy", "be_status", "be_ctx_set_timing", "be_ctx_timing",
 ]
+KERNEL_ELEMENT, KERNEL_GENERIC, KERNEL_DENSE_GEMM, KERNEL_SPLIT, KERNEL_PERSISTENT = 0, 1, 2, 3, 4
 
 
 class BEError(RuntimeError):
@@ -100,6 +101,9 @@ def lib():
             "be_execute_host": (ctypes.c_int, [vp, vp, P(Config), i32, P(Buf), i32, P(Buf), i32,
                                                P(ctypes.c_double), i32, vp]),
             "be_plan_strategy": (ctypes.c_int, [vp, vp, P(Config), i32, P(i32)]),
+            "be_status": (ctypes.c_int, [vp, P(i32)]),
+            "be_ctx_set_timing": (ctypes.c_int, [vp, i32]),
+            "be_ctx_timing": (ctypes.c_int, [vp, i32, P(i64), P(ctypes.c_double)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -246,6 +250,21 @@ class Context:
         n = ctypes.c_int64()
         check(lib().be_db_size(self._h, ctypes.byref(n)))
         return n.value
+
+    def status(self) -> int:
+        """Wait for the device and read (and clear) the device status word."""
+        v = ctypes.c_int32()
+        check(lib().be_status(self._h, ctypes.byref(v)))
+        return v.value
+
+    def set_timing(self, enable=True):
+        check(lib().be_ctx_set_timing(self._h, 1 if enable else 0))
+
+    def timing(self, kernel: int):
+        """(launches, total ms) of kernel id since the last read."""
+        n, ms = ctypes.c_int64(), ctypes.c_double()
+        check(lib().be_ctx_timing(self._h, kernel, ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value
 
     def close(self):
         if getattr(self, "_h", None) and _lib is not None:

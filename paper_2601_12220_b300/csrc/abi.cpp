@@ -7,12 +7,14 @@
 #include <memory>
 #include <mutex>
 #include <sstream>
+#include <tuple>
 #include <unordered_map>
 
 #include <cuda_runtime.h>
 
 #include "../../include/be.h"
 #include "canon.hpp"
+#include "dense.hpp"
 #include "plan.hpp"
 
 using namespace be;
@@ -48,7 +50,54 @@ struct be_ctx {
   // staging memory of be_execute_host
   std::vector<void *> stage;
   std::vector<size_t> stage_size;
+  // workspace of the dense split strategy and the device status word
+  void *ws = nullptr;
+  size_t ws_size = 0;
+  int *status = nullptr;
+  // optional per-kernel timing: (kernel id, start, stop) event pairs
+  bool timing = false;
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> marks;
 };
+
+// brackets one kernel launch with events when x has timing enabled
+struct KernelMark {
+  be_ctx *x;
+  int id;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  KernelMark(be_ctx *x_, int id_, cudaStream_t s_) : x(x_), id(id_), s(s_) {
+    if (x && x->timing && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+      cudaEventRecord(a, s);
+  }
+  ~KernelMark() {
+    if (a && b) {
+      cudaEventRecord(b, s);
+      x->marks.emplace_back(id, a, b);
+    }
+  }
+};
+
+static int ensure_status(be_ctx *x) {
+  if (x->status) return BE_OK;
+  cudaError_t ce = cudaMalloc(&x->status, sizeof(int));
+  if (ce == cudaSuccess) ce = cudaMemset(x->status, 0, sizeof(int));
+  if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("status word: ") + cudaGetErrorString(ce));
+  return BE_OK;
+}
+
+static int ensure_ws(be_ctx *x, size_t need) {
+  if (x->ws_size >= need) return BE_OK;
+  if (x->ws) {
+    cudaDeviceSynchronize();
+    cudaFree(x->ws);
+    x->ws = nullptr;
+    x->ws_size = 0;
+  }
+  cudaError_t ce = cudaMalloc(&x->ws, need);
+  if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("workspace (") + std::to_string(need) + " B): " + cudaGetErrorString(ce));
+  x->ws_size = need;
+  return BE_OK;
+}
 
 static std::string db_key(const std::string &nf, const std::string &dev, int prec) {
   return nf + "\t" + dev + "\t" + std::to_string(prec);
@@ -302,6 +351,12 @@ void be_ctx_destroy(be_ctx *x) {
   if (!x) return;
   for (void *p : x->stage)
     if (p) cudaFree(p);
+  if (x->ws) cudaFree(x->ws);
+  if (x->status) cudaFree(x->status);
+  for (auto &m : x->marks) {
+    cudaEventDestroy(std::get<1>(m));
+    cudaEventDestroy(std::get<2>(m));
+  }
   delete x;
 }
 
@@ -370,7 +425,9 @@ static int choose(const Einsum &e, const std::vector<BufIn> &bufs, const std::ve
   EParams tmp;
   EParams &p = ep ? *ep : tmp;
   if (strategy == BE_STRAT_AUTO) {
+    DensePlan dp;
     if (precision == BE_PREC_FP64 && plan_element(e, bufs, outs, cfg, p, why) == OK) strategy = BE_STRAT_ELEMENT;
+    else if (precision == BE_PREC_SPLIT && plan_dense(e, bufs, outs, dp, why) == OK) strategy = BE_STRAT_DENSE_SPLIT;
     else strategy = BE_STRAT_GENERIC;
     return BE_OK;
   }
@@ -378,8 +435,9 @@ static int choose(const Einsum &e, const std::vector<BufIn> &bufs, const std::ve
     int st = plan_element(e, bufs, outs, cfg, p, why);
     if (st) return st;
   } else if (strategy == BE_STRAT_DENSE_SPLIT) {
-    why = "dense split strategy not available";
-    return EUNSUPPORTED;
+    DensePlan dp;
+    int st = plan_dense(e, bufs, outs, dp, why);
+    if (st) return st;
   } else if (strategy != BE_STRAT_GENERIC) {
     why = "unknown strategy";
     return EARG;
@@ -411,6 +469,38 @@ static int do_execute(be_ctx *x, const be_einsum *hc, const be_config *cfg, int3
   if (st) return fail(st, err);
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t ce = cudaSuccess;
+  if (strategy == BE_STRAT_DENSE_SPLIT) {
+    if (!x) return fail(BE_EARG, "the dense split strategy needs a context (workspace)");
+    DensePlan dp;
+    st = plan_dense(e, bi, bo, dp, err);
+    if (st) return fail(st, err);
+    if (dp.M == 0 || dp.N == 0) return BE_OK;
+    std::lock_guard<std::mutex> g(x->mu);
+    if ((st = ensure_status(x)) || (st = ensure_ws(x, dense_workspace_bytes(dp.M, dp.N, dp.K)))) return st;
+    int prevB = -1;
+    for (auto &r : dp.rows) {
+      if (dp.K == 0) {
+        ce = cudaMemsetAsync(r.C, 0, sizeof(double) * (size_t)(dp.M * dp.N), s);
+      } else {
+        if (r.argB != prevB) {
+          KernelMark km(x, BE_KERNEL_SPLIT, s);
+          ce = dense_split_b(DenseB{r.B, dp.K, dp.N, r.ldb, r.snb, dp.M}, x->ws, s);
+          prevB = r.argB;
+        }
+        if (ce == cudaSuccess) {
+          KernelMark km(x, BE_KERNEL_SPLIT, s);
+          ce = dense_split_a(DenseA{r.A, dp.M, r.lda, r.ska}, dp.K, dp.M, dp.N, x->ws, s);
+        }
+        if (ce == cudaSuccess) {
+          KernelMark km(x, BE_KERNEL_DENSE_GEMM, s);
+          ce = dense_split_gemm(DenseA{r.A, dp.M, r.lda, r.ska}, dp.N, dp.K, dp.M, r.C, dp.N, x->ws, c.split >= 4,
+                                c.tile[2] > 0 ? c.tile[2] : 2, x->status, s);
+        }
+      }
+      if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("dense split: ") + cudaGetErrorString(ce));
+    }
+    return BE_OK;
+  }
   if (strategy == BE_STRAT_ELEMENT) {
     int block = c.tile[1] > 0 ? c.tile[1] : 256;
     int dev = 0, sms = 148, per_sm = 1;
@@ -421,12 +511,16 @@ static int do_execute(be_ctx *x, const be_einsum *hc, const be_config *cfg, int3
     per_sm = (int)std::max<size_t>(1, std::min<size_t>(2048 / block, (220 * 1024) / (smem + 1024)));
     int64_t tiles = (ep.E + ep.tile_e - 1) / ep.tile_e;
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * per_sm));
-    if (ep.E > 0) ce = launch_element(ep, grid, block, s);
+    if (ep.E > 0) {
+      KernelMark km(x, BE_KERNEL_ELEMENT, s);
+      ce = launch_element(ep, grid, block, s);
+    }
   } else {
     for (int i = 0; i < e.b && ce == cudaSuccess; ++i) {
       GParams p;
       st = plan_generic_row(e, i, bi, bo[i], sc, p, err);
       if (st) return fail(st, err);
+      KernelMark km(x, BE_KERNEL_GENERIC, s);
       ce = launch_generic(p, s);
     }
   }
@@ -515,6 +609,50 @@ int be_execute_host(be_ctx *x, const be_einsum *h, const be_config *cfg, int32_t
   }
   ce = cudaStreamSynchronize(s);
   if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("sync: ") + cudaGetErrorString(ce));
+  return BE_OK;
+}
+
+int be_ctx_set_timing(be_ctx *x, int32_t enable) {
+  if (!x) return fail(BE_EARG, "NULL context");
+  std::lock_guard<std::mutex> g(x->mu);
+  x->timing = enable != 0;
+  return BE_OK;
+}
+
+int be_ctx_timing(be_ctx *x, int32_t kernel, int64_t *launches, double *total_ms) {
+  if (!x || !launches || !total_ms) return fail(BE_EARG, "NULL argument");
+  std::lock_guard<std::mutex> g(x->mu);
+  *launches = 0;
+  *total_ms = 0.0;
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> keep;
+  for (auto &m : x->marks) {
+    if (std::get<0>(m) != kernel) {
+      keep.push_back(m);
+      continue;
+    }
+    float ms = 0.f;
+    cudaError_t ce = cudaEventSynchronize(std::get<2>(m));
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, std::get<1>(m), std::get<2>(m));
+    cudaEventDestroy(std::get<1>(m));
+    cudaEventDestroy(std::get<2>(m));
+    if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("timing: ") + cudaGetErrorString(ce));
+    *launches += 1;
+    *total_ms += ms;
+  }
+  x->marks.swap(keep);
+  return BE_OK;
+}
+
+int be_status(be_ctx *x, int32_t *device_status) {
+  if (!x || !device_status) return fail(BE_EARG, "NULL argument");
+  *device_status = BE_OK;
+  if (!x->status) return BE_OK;
+  cudaError_t ce = cudaDeviceSynchronize();
+  int v = 0;
+  if (ce == cudaSuccess) ce = cudaMemcpy(&v, x->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (ce == cudaSuccess) ce = cudaMemset(x->status, 0, sizeof(int));
+  if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("status: ") + cudaGetErrorString(ce));
+  *device_status = v;
   return BE_OK;
 }
 

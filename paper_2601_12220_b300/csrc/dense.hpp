@@ -1,0 +1,42 @@
+// Dense split-precision strategy: workspace layout and launchers.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+namespace be {
+
+// A (M x K) of one row, element (m, k) at A[m * lda + k * ska]
+struct DenseA {
+  const double *A;
+  int64_t M, lda, ska;
+};
+
+// B (K x N), element (k, n) at B[k * ldb + n * snb]; M_max sizes the workspace
+struct DenseB {
+  const double *B;
+  int64_t K, N, ldb, snb, M_max;
+};
+
+// workspace carve-up: split operands (TF32, K-major, zero-padded to the
+// tile grid), power-of-two scales, and the per-column maxima of B
+struct DenseWs {
+  float *ah, *al, *bh, *bl;     // TF32 parts stored as FP32 words
+  int *sa, *sb;
+  unsigned long long *bmax;
+};
+
+size_t dense_workspace_bytes(int64_t M_max, int64_t N, int64_t K);
+DenseWs dense_ws_layout(void *ws, int64_t M_max, int64_t N, int64_t K);
+// split the shared operand B into the workspace
+cudaError_t dense_split_b(const DenseB &b, void *ws, cudaStream_t s);
+// split A (one row of the batch) into the workspace
+cudaError_t dense_split_a(const DenseA &a, int64_t K, int64_t M_max, int64_t N, void *ws, cudaStream_t s);
+// tensor-core GEMM of the split operands into C (M x N, row stride ldc)
+// lolo adds the lo*lo product (tighter bound, one more MMA per k-step)
+cudaError_t dense_split_gemm(const DenseA &a, int64_t N, int64_t K, int64_t M_max, double *C, int64_t ldc,
+                             void *ws, bool lolo, int hdrain, int *status, cudaStream_t s);
+
+}  // namespace be

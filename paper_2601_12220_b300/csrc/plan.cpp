@@ -334,3 +334,88 @@ int plan_element(const Einsum &e, const std::vector<BufIn> &bufs, const std::vec
 }
 
 }  // namespace be
+
+// ------------------------------------------------------------ dense split
+
+namespace be {
+
+// stride of the flattened letters ls (row-major over ls) in a view, or -1
+static int64_t flat_stride(const Einsum &e, const View &v, const std::vector<int8_t> &ls) {
+  if (ls.empty()) return 0;
+  int64_t st = v.coef[ls.back()];
+  int64_t expect = st;
+  for (int k = (int)ls.size() - 1; k >= 0; --k) {
+    if (v.coef[ls[k]] != expect) return -1;
+    expect *= e.len[ls[k]];
+  }
+  return st;
+}
+
+int plan_dense(const Einsum &e, const std::vector<BufIn> &bufs, const std::vector<BufIn> &outs, DensePlan &p,
+               std::string &why) {
+  p = DensePlan();
+  if (e.n != 2) { why = "dense strategy needs two operands"; return EUNSUPPORTED; }
+  if (e.out_dtype != F64) { why = "dense strategy evaluates float64"; return EUNSUPPORTED; }
+  for (auto &a : e.args)
+    if (a.dtype != F64) { why = "dense strategy evaluates float64"; return EUNSUPPORTED; }
+  bool in0[26] = {false}, in1[26] = {false}, is_out[26] = {false};
+  for (int j = 0; j < 2; ++j) {
+    bool seen[26] = {false};
+    for (int8_t c : e.in[j]) {
+      if (seen[c]) { why = "repeated index inside an operand"; return EUNSUPPORTED; }
+      seen[c] = true;
+      (j ? in1 : in0)[c] = true;
+    }
+  }
+  for (int8_t c : e.out) is_out[c] = true;
+  // output = M letters (from operand 0) then N letters (from operand 1)
+  std::vector<int8_t> Ml, Nl, Kl;
+  for (int8_t c : e.out) {
+    if (in0[c] && in1[c]) { why = "batch index shared by both operands and the output"; return EUNSUPPORTED; }
+    (in0[c] ? Ml : Nl).push_back(c);
+  }
+  for (size_t k = 0; k < e.out.size(); ++k)
+    if (k < Ml.size() ? e.out[k] != Ml[k] : e.out[k] != Nl[k - Ml.size()]) {
+      why = "output letters are not (free letters of operand 1, free letters of operand 2)";
+      return EUNSUPPORTED;
+    }
+  for (int8_t c : e.in[0])
+    if (!is_out[c]) {
+      if (!in1[c]) { why = "index summed inside one operand"; return EUNSUPPORTED; }
+      Kl.push_back(c);
+    }
+  for (int8_t c : e.in[1])
+    if (!is_out[c] && !in0[c]) { why = "index summed inside one operand"; return EUNSUPPORTED; }
+  p.M = 1;
+  for (auto c : Ml) p.M *= e.len[c];
+  p.N = 1;
+  for (auto c : Nl) p.N *= e.len[c];
+  p.K = 1;
+  for (auto c : Kl) p.K *= e.len[c];
+  p.rows.clear();
+  for (int i = 0; i < e.b; ++i) {
+    View va, vb;
+    if (!arg_view(e, e.rows[i][0], 0, bufs, va) || !arg_view(e, e.rows[i][1], 1, bufs, vb)) {
+      why = "dense operands must be plain views";
+      return EUNSUPPORTED;
+    }
+    DenseRow r;
+    r.argA = e.rows[i][0];
+    r.argB = e.rows[i][1];
+    r.A = (const double *)va.ptr;
+    r.B = (const double *)vb.ptr;
+    r.lda = flat_stride(e, va, Ml);
+    r.ska = flat_stride(e, va, Kl);
+    r.ldb = flat_stride(e, vb, Kl);
+    r.snb = flat_stride(e, vb, Nl);
+    if (r.lda < 0 || r.ska < 0 || r.ldb < 0 || r.snb < 0) {
+      why = "operand letters cannot be flattened to a matrix";
+      return EUNSUPPORTED;
+    }
+    r.C = (double *)outs[i].ptr;
+    p.rows.push_back(r);
+  }
+  return OK;
+}
+
+}  // namespace be

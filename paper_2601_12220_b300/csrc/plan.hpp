@@ -34,6 +34,18 @@ struct View {
   int64_t coef[26];
 };
 
+// dense split strategy: per row C = A B after flattening (M, K) x (K, N)
+struct DenseRow {
+  int argA, argB;
+  const double *A, *B;
+  int64_t lda, ska, ldb, snb;
+  double *C;
+};
+struct DensePlan {
+  int64_t M = 0, N = 0, K = 0;
+  std::vector<DenseRow> rows;
+};
+
 bool arg_view(const Einsum &e, int arg, int pos, const std::vector<BufIn> &bufs, View &v);
 int check_buffers(const Einsum &e, const std::vector<BufIn> &bufs, const std::vector<BufIn> &outs,
                   std::string &err);
@@ -41,5 +53,7 @@ int plan_generic_row(const Einsum &e, int row, const std::vector<BufIn> &bufs, c
                      const std::vector<double> &scalars, GParams &p, std::string &err);
 int plan_element(const Einsum &e, const std::vector<BufIn> &bufs, const std::vector<BufIn> &outs,
                  const be_config_t &cfg, EParams &p, std::string &why);
+int plan_dense(const Einsum &e, const std::vector<BufIn> &bufs, const std::vector<BufIn> &outs, DensePlan &p,
+               std::string &why);
 
 }  // namespace be

@@ -1,0 +1,127 @@
+"""GPU parity of the dense split-precision strategy (tcgen05) vs the FP64 oracle.
+
+Split-precision tolerance: |got - ref| <= 1e-6 * S componentwise (S the
+absolute contraction).  A priori the split drops lo*lo and the residuals of
+two 11-bit TF32 parts (about 3 * 2^-22 relative per product) and adds FP32
+rounding inside each 1024-long chunk; the measured error is reported
+alongside.  Small-integer inputs (|x| <= 3) are exact in every TF32 part and every
+partial sum, so those cases must match bit for bit.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
+
+import paper_2601_12220_b300 as be  # noqa: E402
+from oracle import evaluate as ev  # noqa: E402
+import workloads as W  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return be.Context(None, device=0)
+
+
+def run_split(ctx, text, arrs):
+    e = be.Einsum(text)
+    assert be.plan_strategy(ctx, e, precision=be.PREC_SPLIT) == be.STRAT_DENSE_SPLIT
+    outs = [torch.full(e.out_shape, float("nan"), dtype=torch.float64, device=DEV) for _ in range(e.b)]
+    be.execute(ctx, e, {k: torch.from_numpy(np.ascontiguousarray(v)).to(DEV) for k, v in arrs.items()}, outs,
+               precision=be.PREC_SPLIT)
+    assert ctx.status() == be.OK
+    return [o.cpu().numpy() for o in outs]
+
+
+def rel_err(got, ref, S):
+    d = np.abs(got - ref)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r = np.where(S > 0, d / S, np.where(d == 0, 0.0, np.inf))
+    return r
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (1, 1, 1), (129, 5, 65), (200, 300, 1000), (256, 128, 4096),
+                                   (64, 257, 2049)])
+def test_gemm_shapes(ctx, M, N, K):
+    g = np.random.default_rng(M * 7 + N * 3 + K)
+    A, B = g.standard_normal((M, K)), g.standard_normal((K, N))
+    text = f"ik,kj->ij | A,B ; A:f64[{M},{K}] ; B:f64[{K},{N}]"
+    got, = run_split(ctx, text, dict(A=A, B=B))
+    (ref, S), = ev.evaluate(text, dict(A=A, B=B))
+    r = rel_err(got, ref, S)
+    assert r.max() <= 1e-6, r.max()
+
+
+def test_integers_bit_exact(ctx):
+    g = np.random.default_rng(1)
+    M, N, K = 300, 200, 3000
+    A = g.integers(-3, 4, size=(M, K)).astype(np.float64)
+    B = g.integers(-3, 4, size=(K, N)).astype(np.float64)
+    text = f"ik,kj->ij | A,B ; A:f64[{M},{K}] ; B:f64[{K},{N}]"
+    got, = run_split(ctx, text, dict(A=A, B=B))
+    assert np.array_equal(got, A @ B)
+
+
+def test_wide_dynamic_range(ctx):
+    """Rows and columns spanning many binades: the per-row / per-column
+    power-of-two scales keep every part in FP16 range."""
+    g = np.random.default_rng(2)
+    M, N, K = 130, 140, 700
+    A = g.standard_normal((M, K)) * np.exp2(g.integers(-40, 40, size=(M, 1)))
+    B = g.standard_normal((K, N)) * np.exp2(g.integers(-40, 40, size=(1, N)))
+    text = f"ik,kj->ij | A,B ; A:f64[{M},{K}] ; B:f64[{K},{N}]"
+    got, = run_split(ctx, text, dict(A=A, B=B))
+    (ref, S), = ev.evaluate(text, dict(A=A, B=B))
+    assert rel_err(got, ref, S).max() <= 1e-6
+
+
+def test_chem_reduced(ctx):
+    """Workload 3 shape at v=16, o=8: 'abef,efij->abij', b=4, shared efij."""
+    As, T = W.chem_dense(v=16, o=8)
+    arrs = {f"A{k}": A for k, A in enumerate(As)} | {"T": T}
+    text = W.chem_dense_spec(v=16, o=8)
+    got = run_split(ctx, text, arrs)
+    ref = ev.evaluate(text, arrs)
+    for k in range(4):
+        assert rel_err(got[k], ref[k][0], ref[k][1]).max() <= 1e-6
+
+
+def test_transposed_output_rejected_then_generic(ctx):
+    """'kj,ik->ij' puts the free letters of the second operand first: not a
+    plain GEMM layout; AUTO falls back to the generic kernel."""
+    e = be.Einsum("kj,ik->ij | B,A ; A:f64[30,20] ; B:f64[20,40]")
+    assert be.plan_strategy(ctx, e, precision=be.PREC_SPLIT) == be.STRAT_GENERIC
+    with pytest.raises(be.BEError) as ex:
+        be.plan_strategy(ctx, e, be.make_config(be.STRAT_DENSE_SPLIT), precision=be.PREC_SPLIT)
+    assert ex.value.code == be.EUNSUPPORTED
+
+
+def test_needs_context():
+    e = be.Einsum("ik,kj->ij | A,B ; A:f64[8,8] ; B:f64[8,8]")
+    t = torch.zeros((8, 8), dtype=torch.float64, device=DEV)
+    with pytest.raises(be.BEError) as ex:
+        be.execute(None, e, {"A": t, "B": t}, [torch.empty_like(t)], precision=be.PREC_SPLIT,
+                   cfg=be.make_config(be.STRAT_DENSE_SPLIT))
+    assert ex.value.code == be.EARG
+
+
+def test_chem_full_size_sampled(ctx):
+    """Workload 3 at full size (v=128, o=32, b=4): 4096 sampled entries per
+    row against the oracle, plus the error statistics."""
+    As, T = W.chem_dense()
+    arrs = {f"A{k}": A for k, A in enumerate(As)} | {"T": T}
+    text = W.chem_dense_spec()
+    got = run_split(ctx, text, arrs)
+    g = np.random.default_rng(0)
+    n_out = 128 * 128 * 32 * 32
+    sel = np.unique(np.concatenate([g.integers(0, n_out, 4096), [0, n_out - 1]]))
+    ref = ev.evaluate(text, arrs, sel=sel)
+    worst = 0.0
+    for k in range(4):
+        r = rel_err(got[k].reshape(-1)[sel], ref[k][0], ref[k][1])
+        worst = max(worst, r.max())
+    print(f"split-precision max error / S over samples: {worst:.3e}")
+    assert worst <= 1e-6
