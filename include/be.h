@@ -236,6 +236,32 @@ int be_ctx_set_timing(be_ctx *x, int32_t enable);
 /* Wait for, sum and forget the recorded launches of one kernel id. */
 int be_ctx_timing(be_ctx *x, int32_t kernel, int64_t *launches, double *total_ms);
 
+/*
+ * be_gemm_split_noalloc -- C = A * B for FP64 row-major matrices (A: M x K,
+ * row stride lda; B: K x N, row stride ldb; C: M x N, row stride ldc) on the
+ * split-precision tensor-core path of BE_STRAT_DENSE_SPLIT (same kernels,
+ * same accuracy), asynchronously on `stream`, WITHOUT allocating any device
+ * memory.  The paper has no counterpart to this call; it exists for callers
+ * that cannot let a library allocate: applications that keep all device
+ * memory in their own pool or budget, where a cudaMalloc inside a library
+ * could fail or go unaccounted and a cudaFree could synchronize the device
+ * and stall their other streams.
+ *
+ * Scratch: a fixed 64 MiB array compiled into the library (plus one status
+ * word), resident on every GPU that loads the library until the process
+ * exits.  The call fails with BE_ETOOMANY (nothing launched) when the
+ * problem needs more: about (M + N) * K * 8 bytes with M and N padded to
+ * 128 and K to 32 (e.g. M = N = 1024, K = 3968 fits).  The first call on a
+ * device looks up the array's device address with that device current; make
+ * that first call before any stream capture.  Every call reuses the same
+ * array (the call clears what must start at zero), so calls whose GPU work
+ * overlaps -- on different streams or devices sharing a context -- race; issue
+ * them in order on one stream.  Errors: BE_EARG, BE_ETOOMANY, BE_ECUDA,
+ * message in be_last_error().
+ */
+int be_gemm_split_noalloc(const double *A, int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc,
+                          int64_t M, int64_t N, int64_t K, void *stream);
+
 /* Strategy the engine would run for e under cfg (after AUTO resolution). */
 int be_plan_strategy(be_ctx *x, const be_einsum *e, const be_config *cfg, int32_t precision,
                      int32_t *strategy);

@@ -31,7 +31,7 @@ EXPORTS = [
     "be_einsum_buffer", "be_canonicalize", "be_free_canon", "be_canon_key", "be_canon_sigma",
     "be_canon_tokens", "be_induced_graph", "be_graph_check", "be_identify", "be_ctx_create",
     "be_ctx_destroy", "be_lookup", "be_record", "be_db_size", "be_execute", "be_execute_host",
-    "be_plan_strategy", "be_status", "be_ctx_set_timing", "be_ctx_timing",
+    "be_plan_strategy", "be_status", "be_ctx_set_timing", "be_ctx_timing", "be_gemm_split_noalloc",
 ]
 KERNEL_ELEMENT, KERNEL_GENERIC, KERNEL_DENSE_GEMM, KERNEL_SPLIT, KERNEL_PERSISTENT = 0, 1, 2, 3, 4
 
@@ -103,6 +103,7 @@ def lib():
             "be_plan_strategy": (ctypes.c_int, [vp, vp, P(Config), i32, P(i32)]),
             "be_status": (ctypes.c_int, [vp, P(i32)]),
             "be_ctx_set_timing": (ctypes.c_int, [vp, i32]),
+            "be_gemm_split_noalloc": (ctypes.c_int, [vp, i64, vp, i64, vp, i64, i64, i64, i64, vp]),
             "be_ctx_timing": (ctypes.c_int, [vp, i32, P(i64), P(ctypes.c_double)]),
         }
         for name, (res, args) in sig.items():

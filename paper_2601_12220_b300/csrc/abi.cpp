@@ -26,6 +26,11 @@ static int fail(int code, const std::string &msg) {
   return code;
 }
 
+namespace be {
+// lets the other translation units of the library report through be_last_error()
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace be
+
 struct be_einsum {
   Einsum e;
   std::mutex mu;
