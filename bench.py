@@ -380,6 +380,81 @@ def run_chem(args):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- workload 4
+
+def run_mix(args):
+    """Uneven batch: N instances drawn from twelve notations of the paper, each
+    under a random rename / row / operand permutation, lengths round(2^U(3,12))
+    capped, f64 or f32, b in 1..4 -- evaluated by one persistent launch (CUDA
+    graph replay) and, for comparison, by one be_execute launch per instance."""
+    import torch
+    import paper_2601_12220_b300 as be
+
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    g = W.rng(4, 0)
+    items, byts, n_rows = [], 0, 0
+    for _ in range(args.mix_n):
+        inst = W.mix_instance(g, max_operand=1 << args.mix_operand_log2, max_flops=1 << args.mix_flops_log2)
+        arrs = W.instance_arrays(inst, g)
+        e = be.Einsum(W.instance_spec(inst))
+        dt = torch.float64 if e.out_dtype == be.F64 else torch.float32
+        bufs = {k: torch.from_numpy(v).to(dev) for k, v in arrs.items()}
+        outs = [torch.empty(e.out_shape, dtype=dt, device=dev) for _ in range(e.b)]
+        items.append((e, bufs, outs))
+        byts += sum(v.nbytes for v in arrs.values()) + sum(o.numel() * o.element_size() for o in outs)
+        n_rows += e.b
+    ctx = be.Context(None, device=local)
+    stream = torch.cuda.current_stream(dev)
+    t_plan = time.perf_counter()
+    batch = be.Batch(ctx, items)
+    t_plan = time.perf_counter() - t_plan
+    info = batch.info()
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b2.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b2) / steps
+
+    def per_instance():
+        for e, bufs, outs in items:
+            be.execute(ctx, e, bufs, outs, stream=stream)
+
+    ctx.set_timing(True)
+    with Clocks(local) as clk:
+        ms_batch = timed(lambda: batch.run(stream), args.steps, args.warmup)
+    ctx.set_timing(False)
+    n_k, t_k = ctx.timing(be.KERNEL_PERSISTENT)
+    ms_single = timed(per_instance, max(1, args.steps // 2), 1)
+    peaks = load_peaks()
+    kms = t_k / max(1, n_k)
+    line = {"metric": METRIC, "value": world * args.mix_n / (ms_batch * 1e-3), "unit": "einsums/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32 mix",
+            "data": "synthetic",
+            "config": {"workload": f"uneven_mix: {args.mix_n} instances of 12 notations, lengths round(2^U(3,12)), "
+                                   f"operands <= 2^{args.mix_operand_log2}, flops <= 2^{args.mix_flops_log2}",
+                       "rows": n_rows, "tiles": info["tiles"], "plan_s": t_plan, "parallelism": "replicas"},
+            "rows_per_s": world * n_rows / (ms_batch * 1e-3),
+            "one_launch_per_einsum": {"ms_per_step": ms_single, "einsums_per_s": args.mix_n / (ms_single * 1e-3)},
+            "speedup_vs_one_launch_per_einsum": ms_single / ms_batch,
+            "gb_s": world * byts / (ms_batch * 1e-3) / 1e9,
+            "roofline": {"kernel": "persistent_kernel", "bound": "hbm", "achieved": byts / (kms * 1e-3) / 1e9,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": byts / (kms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                         "traffic": None, "algorithmic_bytes": byts},
+            "clocks": clk.summary(), "gpu_launches": n_k}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -390,7 +465,10 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=E_FULL)
     ap.add_argument("--ref-sample", type=int, default=32768)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="dg_gradient", choices=["dg_gradient", "chem_dense"])
+    ap.add_argument("--workload", default="dg_gradient", choices=["dg_gradient", "chem_dense", "uneven_mix"])
+    ap.add_argument("--mix-n", type=int, default=512)
+    ap.add_argument("--mix-operand-log2", type=int, default=22)
+    ap.add_argument("--mix-flops-log2", type=int, default=26)
     ap.add_argument("--chem-v", type=int, default=V_FULL)
     ap.add_argument("--chem-o", type=int, default=O_FULL)
     args = ap.parse_args()
@@ -400,6 +478,8 @@ def main():
         run_reference(args)
     elif args.workload == "chem_dense":
         run_chem(args)
+    elif args.workload == "uneven_mix":
+        run_mix(args)
     else:
         run_ours(args)
 

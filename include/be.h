@@ -79,6 +79,7 @@ extern "C" {
 typedef struct be_ctx be_ctx;
 typedef struct be_einsum be_einsum;
 typedef struct be_canon be_canon;
+typedef struct be_batch be_batch;
 
 /* A tuned configuration, stated on the canonical form's names. */
 typedef struct {
@@ -215,6 +216,35 @@ int be_execute(be_ctx *x, const be_einsum *e, const be_config *cfg, int32_t prec
 int be_execute_host(be_ctx *x, const be_einsum *e, const be_config *cfg, int32_t precision,
                     const be_buf *bufs, int32_t n_bufs, const be_buf *outs, int32_t n_outs,
                     const double *scalars, int32_t n_scalars, void *stream);
+
+/*
+ * Persistent multi-instance executor: many batched einsums (any notations,
+ * sizes and dtypes) evaluated by ONE persistent launch, replayed as a CUDA
+ * graph.  The batched einsum is the paper's primitive (Sec. "Batched
+ * Einstein Summation"); grouping several of them into one launch removes
+ * the per-launch overhead that dominates small einsums.
+ *
+ * be_batch_create -- plan n instances: es[k] with its declared buffers
+ *   bufs[k][0..n_bufs[k]) and outputs outs[k][0..n_outs[k]) (device
+ *   pointers, as for be_execute) and runtime scalars scalars[k] (may be
+ *   NULL when n_scalars is NULL or 0).  Every row becomes a descriptor; its
+ *   outputs are cut into tiles of about 2^tile[1] operand terms (default
+ *   18); cfg->tile[0] is the block size (default 256), cfg->tile[2] CTAs per
+ *   SM (default 4); cfg may be NULL.  The buffers are borrowed and must stay
+ *   valid while the batch is used; their CONTENTS may change between runs.
+ *   Device memory for descriptors and tiles is allocated here.
+ * be_batch_run -- replay the captured graph on `stream` (asynchronous).
+ *   Every output has a single owner and a fixed evaluation order, so the
+ *   results are bitwise those of BE_STRAT_GENERIC on each instance alone.
+ * be_batch_info -- rows, tiles and total operand terms of the batch.
+ */
+int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_buf *const *bufs,
+                    const int32_t *n_bufs, const be_buf *const *outs, const int32_t *n_outs,
+                    const double *const *scalars, const int32_t *n_scalars, const be_config *cfg,
+                    be_batch **out);
+int be_batch_run(be_batch *b, void *stream);
+int be_batch_info(const be_batch *b, int64_t *rows, int64_t *tiles, double *terms);
+void be_batch_destroy(be_batch *b);
 
 /*
  * be_status -- wait for the device, then read and clear x's device status

@@ -5,7 +5,7 @@ is its thin Python binding.  Importing it loads the library and fails loudly
 if it has not been built (``python -m paper_2601_12220_b300.build``).
 """
 from .binding import (  # noqa: F401
-    BEError, Canon, Config, Context, Einsum, execute, execute_host, graph_check, identify, lib,
+    BEError, Batch, Canon, Config, Context, Einsum, execute, execute_host, graph_check, identify, lib,
     make_config, plan_strategy,
     OK, EPARSE, EINVALID, ESHAPE, EDTYPE, ETOOMANY, ENOTFOUND, EDB, EBUDGET, ETIMEOUT, ECUDA,
     EUNSUPPORTED, EARG, I8, I32, I64, F16, F32, F64, C64, C128, BF16, STRAT_AUTO, STRAT_GENERIC,

@@ -32,6 +32,7 @@ EXPORTS = [
     "be_canon_tokens", "be_induced_graph", "be_graph_check", "be_identify", "be_ctx_create",
     "be_ctx_destroy", "be_lookup", "be_record", "be_db_size", "be_execute", "be_execute_host",
     "be_plan_strategy", "be_status", "be_ctx_set_timing", "be_ctx_timing", "be_gemm_split_noalloc",
+    "be_batch_create", "be_batch_run", "be_batch_info", "be_batch_destroy",
 ]
 KERNEL_ELEMENT, KERNEL_GENERIC, KERNEL_DENSE_GEMM, KERNEL_SPLIT, KERNEL_PERSISTENT = 0, 1, 2, 3, 4
 
@@ -104,6 +105,11 @@ def lib():
             "be_status": (ctypes.c_int, [vp, P(i32)]),
             "be_ctx_set_timing": (ctypes.c_int, [vp, i32]),
             "be_gemm_split_noalloc": (ctypes.c_int, [vp, i64, vp, i64, vp, i64, i64, i64, i64, vp]),
+            "be_batch_create": (ctypes.c_int, [vp, i32, P(vp), P(P(Buf)), P(i32), P(P(Buf)), P(i32),
+                                               P(P(ctypes.c_double)), P(i32), P(Config), P(vp)]),
+            "be_batch_run": (ctypes.c_int, [vp, vp]),
+            "be_batch_info": (ctypes.c_int, [vp, P(i64), P(i64), P(ctypes.c_double)]),
+            "be_batch_destroy": (None, [vp]),
             "be_ctx_timing": (ctypes.c_int, [vp, i32, P(i64), P(ctypes.c_double)]),
         }
         for name, (res, args) in sig.items():
@@ -366,6 +372,65 @@ def execute_host(ctx, e: Einsum, bufs, outs, cfg: Config | None = None, precisio
     s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
     check(lib().be_execute_host(ctx.handle, e.handle, ctypes.byref(cfg) if cfg else None, precision, arr, len(bl),
                                 oarr, len(outs), sc, ns, s))
+
+
+class Batch:
+    """Persistent multi-instance executor over many (einsum, buffers, outputs)
+    instances, replayed as one CUDA graph per run."""
+
+    def __init__(self, ctx, items, cfg: Config | None = None):
+        keep = []
+        n = len(items)
+        es = (ctypes.c_void_p * max(1, n))()
+        bptr = (ctypes.POINTER(Buf) * max(1, n))()
+        optr = (ctypes.POINTER(Buf) * max(1, n))()
+        nb = (ctypes.c_int32 * max(1, n))()
+        no = (ctypes.c_int32 * max(1, n))()
+        sptr = (ctypes.POINTER(ctypes.c_double) * max(1, n))()
+        ns = (ctypes.c_int32 * max(1, n))()
+        for k, item in enumerate(items):
+            e, bufs, outs = item[0], item[1], item[2]
+            scal = item[3] if len(item) > 3 else ()
+            bl = _order(e, bufs)
+            for t, (name, _, shape) in zip(bl, e.buffers):
+                if tuple(t.shape) != shape or not t.is_cuda:
+                    raise BEError(ESHAPE, f"instance {k} buffer {name}: expected shape {shape}")
+            for t in outs:
+                if tuple(t.shape) != e.out_shape or not t.is_contiguous():
+                    raise BEError(ESHAPE, f"instance {k}: outputs must be dense of shape {e.out_shape}")
+            bi = _bufs_torch(bl, keep)
+            bo = _bufs_torch(outs, keep, dense_only=True)
+            sc, nsc = _scalars(scal)
+            keep += [bi, bo, sc, e, bl, outs]
+            es[k] = e.handle.value
+            bptr[k] = ctypes.cast(bi, ctypes.POINTER(Buf))
+            optr[k] = ctypes.cast(bo, ctypes.POINTER(Buf))
+            nb[k], no[k], ns[k] = len(bl), len(outs), nsc
+            sptr[k] = ctypes.cast(sc, ctypes.POINTER(ctypes.c_double))
+        h = ctypes.c_void_p()
+        check(lib().be_batch_create(ctx.handle if ctx else None, n, es, bptr, nb, optr, no, sptr, ns,
+                                    ctypes.byref(cfg) if cfg else None, ctypes.byref(h)))
+        self._h = h
+        self._keep = keep
+
+    def run(self, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        check(lib().be_batch_run(self._h, ctypes.c_void_p(stream.cuda_stream)))
+
+    def info(self):
+        r, t, w = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        check(lib().be_batch_info(self._h, ctypes.byref(r), ctypes.byref(t), ctypes.byref(w)))
+        return {"rows": r.value, "tiles": t.value, "terms": w.value}
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.be_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 def plan_strategy(ctx, e: Einsum, cfg: Config | None = None, precision=PREC_FP64) -> int:

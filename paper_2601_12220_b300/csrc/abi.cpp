@@ -6,6 +6,8 @@
 #include <fstream>
 #include <memory>
 #include <mutex>
+#include <algorithm>
+#include <cmath>
 #include <sstream>
 #include <tuple>
 #include <unordered_map>
@@ -647,6 +649,142 @@ int be_ctx_timing(be_ctx *x, int32_t kernel, int64_t *launches, double *total_ms
   x->marks.swap(keep);
   return BE_OK;
 }
+
+// ------------------------------------------------------------ persistent batch
+
+}  // extern "C"
+
+struct be_batch {
+  be_ctx *x = nullptr;
+  std::vector<GParams> rows;
+  std::vector<PTile> tiles;
+  GParams *d_rows = nullptr;
+  PTile *d_tiles = nullptr;
+  unsigned long long *d_counter = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int grid = 0, block = 256;
+  double terms = 0;
+  ~be_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+    if (d_rows) cudaFree(d_rows);
+    if (d_tiles) cudaFree(d_tiles);
+    if (d_counter) cudaFree(d_counter);
+  }
+};
+
+extern "C" {
+
+int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_buf *const *bufs,
+                    const int32_t *n_bufs, const be_buf *const *outs, const int32_t *n_outs,
+                    const double *const *scalars, const int32_t *n_scalars, const be_config *cfg, be_batch **out) {
+  if (!out || n < 0 || (n > 0 && (!es || !bufs || !n_bufs || !outs || !n_outs))) return fail(BE_EARG, "bad batch arguments");
+  auto b = std::make_unique<be_batch>();
+  b->x = x;
+  be_config_t c;
+  std::memset(&c, 0, sizeof(c));
+  if (cfg) std::memcpy(&c, cfg, sizeof(c));
+  b->block = c.tile[0] > 0 ? c.tile[0] : 256;
+  if (b->block % 32 || b->block > 256) return fail(BE_EARG, "block size must be a multiple of 32 up to 256");
+  const int cost_log2 = c.tile[1] > 0 ? c.tile[1] : 18;
+  const int per_sm = c.tile[2] > 0 ? c.tile[2] : 4;
+  const double cost_target = std::ldexp(1.0, cost_log2);
+  std::string err;
+  for (int k = 0; k < n; ++k) {
+    if (!es[k]) return fail(BE_EARG, "NULL einsum in batch");
+    const Einsum &e = es[k]->e;
+    std::vector<BufIn> bi(n_bufs[k]), bo(n_outs[k]);
+    for (int q = 0; q < n_bufs[k]; ++q) bi[q] = BufIn{bufs[k][q].ptr, bufs[k][q].strides, bufs[k][q].ndim, bufs[k][q].dtype};
+    for (int q = 0; q < n_outs[k]; ++q) bo[q] = BufIn{outs[k][q].ptr, outs[k][q].strides, outs[k][q].ndim, outs[k][q].dtype};
+    int st = check_buffers(e, bi, bo, err);
+    if (st) return fail(st, "instance " + std::to_string(k) + ": " + err);
+    const int ns = n_scalars ? n_scalars[k] : 0;
+    if (ns != (int)e.scalars.size()) return fail(BE_EARG, "instance " + std::to_string(k) + ": scalar count");
+    std::vector<double> sc(ns);
+    for (int q = 0; q < ns; ++q) sc[q] = scalars[k][q];
+    for (int i = 0; i < e.b; ++i) {
+      GParams p;
+      st = plan_generic_row(e, i, bi, bo[i], sc, p, err);
+      if (st) return fail(st, "instance " + std::to_string(k) + ": " + err);
+      if (p.total_out == 0) continue;
+      const int row = (int)b->rows.size();
+      b->rows.push_back(p);
+      // outputs per tile so that each tile costs about cost_target operand terms
+      const double per_out = (double)std::max<int64_t>(1, p.total_con) * std::max(1, p.n_ops);
+      int64_t tile = (int64_t)(cost_target / per_out);
+      if (p.mode == 0) {
+        tile = std::max<int64_t>(32, std::min<int64_t>(tile, 65536));
+        tile = (tile + 31) / 32 * 32;
+      } else {
+        tile = std::max<int64_t>(1, std::min<int64_t>(tile, 65536));
+      }
+      for (int64_t s0 = 0; s0 < p.total_out; s0 += tile)
+        b->tiles.push_back(PTile{row, 0, s0, std::min(tile, p.total_out - s0)});
+      b->terms += per_out * (double)p.total_out;
+    }
+  }
+  // longest tiles first (cost = outputs x terms per output); ties by position
+  std::vector<double> cost(b->tiles.size());
+  for (size_t t = 0; t < b->tiles.size(); ++t) {
+    const GParams &p = b->rows[b->tiles[t].row];
+    cost[t] = (double)b->tiles[t].count * (double)std::max<int64_t>(1, p.total_con) * std::max(1, p.n_ops);
+  }
+  std::vector<size_t> order(b->tiles.size());
+  for (size_t t = 0; t < order.size(); ++t) order[t] = t;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t c2) { return cost[a] > cost[c2]; });
+  std::vector<PTile> sorted;
+  for (size_t t : order) sorted.push_back(b->tiles[t]);
+  b->tiles.swap(sorted);
+
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  b->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->tiles.size(), (int64_t)sms * per_sm));
+  cudaError_t ce = cudaMalloc(&b->d_rows, sizeof(GParams) * std::max<size_t>(1, b->rows.size()));
+  if (ce == cudaSuccess) ce = cudaMalloc(&b->d_tiles, sizeof(PTile) * std::max<size_t>(1, b->tiles.size()));
+  if (ce == cudaSuccess) ce = cudaMalloc(&b->d_counter, sizeof(unsigned long long));
+  if (ce == cudaSuccess && !b->rows.empty())
+    ce = cudaMemcpy(b->d_rows, b->rows.data(), sizeof(GParams) * b->rows.size(), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess && !b->tiles.empty())
+    ce = cudaMemcpy(b->d_tiles, b->tiles.data(), sizeof(PTile) * b->tiles.size(), cudaMemcpyHostToDevice);
+  // capture counter reset + launch once; every run replays the graph
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+  if (ce == cudaSuccess) {
+    cudaError_t c1 = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), b->cap);
+    cudaError_t c2 = c1 == cudaSuccess ? launch_persistent(b->d_rows, b->d_tiles, (int64_t)b->tiles.size(),
+                                                         b->d_counter, b->grid, b->block, b->cap)
+                                       : c1;
+    ce = cudaStreamEndCapture(b->cap, &b->graph);
+    if (c2 != cudaSuccess) ce = c2;
+  }
+  if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("batch setup: ") + cudaGetErrorString(ce));
+  *out = b.release();
+  return BE_OK;
+}
+
+int be_batch_run(be_batch *b, void *stream) {
+  if (!b) return fail(BE_EARG, "NULL batch");
+  cudaStream_t s = (cudaStream_t)stream;
+  KernelMark km(b->x, BE_KERNEL_PERSISTENT, s);
+  cudaError_t ce = cudaGraphLaunch(b->exec, s);
+  if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
+  return BE_OK;
+}
+
+int be_batch_info(const be_batch *b, int64_t *rows, int64_t *tiles, double *terms) {
+  if (!b) return fail(BE_EARG, "NULL batch");
+  if (rows) *rows = (int64_t)b->rows.size();
+  if (tiles) *tiles = (int64_t)b->tiles.size();
+  if (terms) *terms = b->terms;
+  return BE_OK;
+}
+
+void be_batch_destroy(be_batch *b) { delete b; }
 
 int be_status(be_ctx *x, int32_t *device_status) {
   if (!x || !device_status) return fail(BE_EARG, "NULL argument");

@@ -36,20 +36,32 @@ struct GOp {
   int64_t coef[GMAXL];
 };
 
-struct GParams {
+struct alignas(16) GParams {
   int32_t n_ops, n_letters, n_out, n_con;
   int64_t len[GMAXL];
   int32_t out_letter[GMAXL];
   int32_t con_letter[GMAXL];
   int64_t total_out, total_con;
   void *out;
-  int32_t out_dtype, pad;
+  int32_t out_dtype;
+  int32_t mode;         // 0 thread, 1 warp, 2 CTA per output (by contraction length)
   double scalars[8];
   GOp ops[GMAXOPS];
   GIns ins[GMAXINS];
 };
 
 cudaError_t launch_generic(const GParams &p, cudaStream_t s);
+
+// ---------------------------------------------------------------- persistent
+
+// one unit of work of the persistent executor: outputs [start, start+count) of row
+struct PTile {
+  int32_t row, pad;
+  int64_t start, count;
+};
+
+cudaError_t launch_persistent(const GParams *rows, const PTile *tiles, int64_t n_tiles, unsigned long long *counter,
+                              int grid, int block, cudaStream_t s);
 
 // ---------------------------------------------------------------- element
 

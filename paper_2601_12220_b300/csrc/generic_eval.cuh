@@ -1,0 +1,212 @@
+// Per-output-element evaluation of one einsum row (Eq. (1)): decode the
+// output indices, run the contracted indices as an odometer, multiply the
+// operand values (strided loads or producer programs evaluated at the
+// access) and accumulate in the output's type.  Long contractions are split
+// over a warp or a CTA with a fixed assignment and a fixed reduction order,
+// so the result is deterministic.  Shared by the generic
+// kernel and the persistent multi-instance executor, so both produce the
+// same bits for the same row.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "exec.hpp"
+
+namespace be {
+namespace gen {
+
+template <typename T>
+__device__ __forceinline__ T load_as(const char *p, int dtype) {
+  switch (dtype) {
+    case F64: return (T)*(const double *)p;
+    case F32: return (T)*(const float *)p;
+    case F16: return (T)__half2float(*(const __half *)p);
+    case BF16: return (T)__bfloat162float(*(const __nv_bfloat16 *)p);
+    case I32: return (T)*(const int32_t *)p;
+    case I64: return (T)*(const int64_t *)p;
+    case I8: return (T)*(const int8_t *)p;
+  }
+  return (T)0;
+}
+
+__device__ __forceinline__ int esize(int dtype) {
+  switch (dtype) {
+    case I8: return 1;
+    case F16: case BF16: return 2;
+    case F32: case I32: return 4;
+  }
+  return 8;
+}
+
+template <typename T>
+__device__ T eval_prog(const GParams &p, int begin, int count, const int64_t *val) {
+  T st[GSTACK];
+  int sp = 0;
+  for (int k = begin; k < begin + count; ++k) {
+    const GIns &in = p.ins[k];
+    switch (in.op) {
+      case X_NUM: st[sp++] = (T)in.num; break;
+      case X_SCALAR: st[sp++] = (T)p.scalars[in.letter]; break;
+      case X_PARAM: st[sp++] = (T)val[in.letter]; break;
+      case X_REF: {
+        int64_t off = 0;
+        for (int L = 0; L < p.n_letters; ++L) off += in.coef[L] * val[L];
+        st[sp++] = load_as<T>(in.ptr + off * esize(in.dtype), in.dtype);
+        break;
+      }
+      case X_NEG: st[sp - 1] = -st[sp - 1]; break;
+      case X_ADD: st[sp - 2] = st[sp - 2] + st[sp - 1]; --sp; break;
+      case X_SUB: st[sp - 2] = st[sp - 2] - st[sp - 1]; --sp; break;
+      case X_MUL: st[sp - 2] = st[sp - 2] * st[sp - 1]; --sp; break;
+      case X_DIV: st[sp - 2] = st[sp - 2] / st[sp - 1]; --sp; break;
+      case X_SIN: st[sp - 1] = sin(st[sp - 1]); break;
+      case X_COS: st[sp - 1] = cos(st[sp - 1]); break;
+      case X_EXP: st[sp - 1] = exp(st[sp - 1]); break;
+      case X_ABS: st[sp - 1] = fabs(st[sp - 1]); break;
+      case X_EQ: st[sp - 2] = (T)(st[sp - 2] == st[sp - 1]); --sp; break;
+      case X_NE: st[sp - 2] = (T)(st[sp - 2] != st[sp - 1]); --sp; break;
+      case X_SELECT: st[sp - 3] = st[sp - 3] != (T)0 ? st[sp - 2] : st[sp - 1]; sp -= 2; break;
+    }
+  }
+  return st[0];
+}
+
+// contracted letters of val[] set to the digits of iteration index it
+__device__ __forceinline__ void set_con(const GParams &p, int64_t *val, int64_t it) {
+  for (int t = p.n_con - 1; t >= 0; --t) {
+    const int L = p.con_letter[t];
+    val[L] = it % p.len[L];
+    it /= p.len[L];
+  }
+}
+
+// advance the contracted odometer by s iterations (mixed-radix add)
+__device__ __forceinline__ void add_con(const GParams &p, int64_t *val, int64_t s) {
+  for (int t = p.n_con - 1; t >= 0 && s > 0; --t) {
+    const int L = p.con_letter[t];
+    int64_t v = val[L] + s;
+    if (v < p.len[L]) {
+      val[L] = v;
+      return;
+    }
+    s = v / p.len[L];
+    val[L] = v - s * p.len[L];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T term(const GParams &p, const int64_t *val) {
+  T prod = (T)1;
+  for (int k = 0; k < p.n_ops; ++k) {
+    const GOp &op = p.ops[k];
+    T v;
+    if (op.kind == 0) {
+      int64_t off = 0;
+      for (int L = 0; L < p.n_letters; ++L) off += op.coef[L] * val[L];
+      v = load_as<T>(op.ptr + off * esize(op.dtype), op.dtype);
+    } else {
+      v = eval_prog<T>(p, op.prog_begin, op.prog_len, val);
+    }
+    prod *= v;
+  }
+  return prod;
+}
+
+// sum of the terms of output o over iterations first, first + stride, ...
+template <typename T>
+__device__ T contract(const GParams &p, int64_t o, int64_t first, int64_t stride) {
+  int64_t val[GMAXL];
+  for (int L = 0; L < GMAXL; ++L) val[L] = 0;
+  int64_t rem = o;
+  for (int d = p.n_out - 1; d >= 0; --d) {
+    const int L = p.out_letter[d];
+    val[L] = rem % p.len[L];
+    rem /= p.len[L];
+  }
+  T acc = (T)0;
+  if (first >= p.total_con) return acc;
+  set_con(p, val, first);
+  for (int64_t it = first; it < p.total_con; it += stride) {
+    acc += term<T>(p, val);
+    if (stride == 1) {
+      for (int t = p.n_con - 1; t >= 0; --t) {
+        const int L = p.con_letter[t];
+        if (++val[L] < p.len[L]) break;
+        val[L] = 0;
+      }
+    } else {
+      add_con(p, val, stride);
+    }
+  }
+  return acc;
+}
+
+// One output, evaluated the same way by every kernel that uses the row:
+//   mode 0: one thread, iterations in order;
+//   mode 1: one warp, lane l takes iterations l, l+32, ..., then a fixed
+//           butterfly sum (lane 0's value is used);
+//   mode 2: one CTA, virtual lane v in [0, 256) takes v, v+256, ..., then a
+//           fixed tree over the 256 partials in shared memory.
+// Modes 1 and 2 must be called by the whole warp / CTA; the result is valid
+// in lane 0 / thread 0.
+template <typename T>
+__device__ __forceinline__ T out_thread(const GParams &p, int64_t o) {
+  return contract<T>(p, o, 0, 1);
+}
+
+template <typename T>
+__device__ __forceinline__ T out_warp(const GParams &p, int64_t o) {
+  const int lane = threadIdx.x & 31;
+  T v = contract<T>(p, o, lane, 32);
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T out_block(const GParams &p, int64_t o, double *red) {
+  for (int v = threadIdx.x; v < 256; v += blockDim.x) red[v] = (double)contract<T>(p, o, v, 256);
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    for (int v = threadIdx.x; v < w; v += blockDim.x) red[v] = (double)((T)red[v] + (T)red[v + w]);
+    __syncthreads();
+  }
+  T r = (T)red[0];
+  __syncthreads();
+  return r;
+}
+
+// every output of [start, start + count) of row p, by the row's mode
+__device__ __forceinline__ void eval_range(const GParams &p, int64_t start, int64_t count, double *red) {
+  const int64_t end = start + count;
+  if (p.mode == 0) {
+    for (int64_t o = start + threadIdx.x; o < end; o += blockDim.x) {
+      if (p.out_dtype == F64) ((double *)p.out)[o] = out_thread<double>(p, o);
+      else ((float *)p.out)[o] = out_thread<float>(p, o);
+    }
+  } else if (p.mode == 1) {
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t o = start + warp; o < end; o += nw) {
+      if (p.out_dtype == F64) {
+        double v = out_warp<double>(p, o);
+        if (lane == 0) ((double *)p.out)[o] = v;
+      } else {
+        float v = out_warp<float>(p, o);
+        if (lane == 0) ((float *)p.out)[o] = v;
+      }
+    }
+  } else {
+    for (int64_t o = start; o < end; ++o) {
+      if (p.out_dtype == F64) {
+        double v = out_block<double>(p, o, red);
+        if (threadIdx.x == 0) ((double *)p.out)[o] = v;
+      } else {
+        float v = out_block<float>(p, o, red);
+        if (threadIdx.x == 0) ((float *)p.out)[o] = v;
+      }
+    }
+  }
+}
+
+}  // namespace gen
+}  // namespace be

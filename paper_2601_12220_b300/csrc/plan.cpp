@@ -142,6 +142,7 @@ int plan_generic_row(const Einsum &e, int row, const std::vector<BufIn> &bufs, c
     }
   p.out = out.ptr;
   p.out_dtype = e.out_dtype;
+  p.mode = p.total_con < 64 ? 0 : (p.total_con < 16384 ? 1 : 2);
   for (size_t k = 0; k < scalars.size(); ++k) p.scalars[k] = scalars[k];
   int n_ins = 0;
   for (int j = 0; j < e.n; ++j) {

@@ -229,19 +229,23 @@ class Instance:
 def mix_instance(gen: np.random.Generator, lo_exp=3.0, hi_exp=12.0,
                  max_operand=1 << 22, max_flops=1 << 30, max_tries=1000) -> Instance:
     """One instance of the uneven mix: a notation picked uniformly, index
-    lengths round(2^U(lo,hi)), resampled while an operand is too large or the
-    instance's flop count exceeds the cap; dtype f64 or f32 with p = 1/2;
+    lengths round(2^U(lo,hi)); while an operand is too large or the
+    instance's flop count exceeds the cap, every exponent is shrunk by 10 %
+    toward lo; dtype f64 or f32 with p = 1/2;
     b in {1..4} with the first operand shared by all rows; then a random
     rename and row / operand permutation."""
     name, notation = MIX_NOTATIONS[int(gen.integers(len(MIX_NOTATIONS)))]
     lhs, out = notation.split("->")
     ins = lhs.split(",")
     letters = sorted(set(out).union(*[set(s) for s in ins]))
+    u = {c: gen.uniform(lo_exp, hi_exp) for c in letters}
     for _ in range(max_tries):
-        lens = {c: int(round(2.0 ** gen.uniform(lo_exp, hi_exp))) for c in letters}
+        lens = {c: int(round(2.0 ** u[c])) for c in letters}
         sizes = [math.prod(lens[c] for c in s) for s in ins] + [math.prod(lens[c] for c in out)]
         if max(sizes) <= max_operand and _flops(out, ins, lens) <= max_flops:
             break
+        # over a cap: shrink every exponent toward the lower end and retry
+        u = {c: lo_exp + 0.9 * (v - lo_exp) for c, v in u.items()}
     else:
         raise RuntimeError("could not draw an instance under the caps")
     dtype = "f64" if gen.random() < 0.5 else "f32"
