@@ -455,6 +455,95 @@ def run_mix(args):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- workload 5
+
+def run_serving(args):
+    """Poisson request stream through the serving loop: 80 % requests drawn
+    from the uneven mix (lengths 8..512), 10 % FEM-action and 10 % DG-gradient
+    shaped requests (E = 4096 so the stream is servable), operands resident
+    on the device.  Reports einsums/s and p50/p99 latency, and the same
+    arrival sequence served one launch per einsum (a single FIFO server
+    whose per-request times are measured, with queueing replayed)."""
+    import torch
+    import paper_2601_12220_b300 as be
+
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    g = W.rng(5, 1)
+    templates = []
+    for k in range(args.serve_templates):
+        kind = g.random()
+        if kind < 0.1:
+            D, us = W.fem_action(E=4096)
+            e = be.Einsum(W.fem_action_spec(E=4096))
+            host = {"D": D, **{f"u{q}": u for q, u in enumerate(us)}}
+        elif kind < 0.2:
+            D, G, a, b = W.dg_gradient(E=4096)
+            e = be.Einsum(W.dg_gradient_spec(E=4096))
+            host = dict(D=D, G=G, a=a, b=b)
+        else:
+            inst = W.mix_instance(g, lo_exp=3.0, hi_exp=9.0, max_operand=1 << 20, max_flops=1 << 24)
+            e = be.Einsum(W.instance_spec(inst))
+            host = W.instance_arrays(inst, g)
+        dt = torch.float64 if e.out_dtype == be.F64 else torch.float32
+        bufs = {a: torch.from_numpy(v).to(dev) for a, v in host.items()}
+        outs = [torch.empty(e.out_shape, dtype=dt, device=dev) for _ in range(e.b)]
+        templates.append((e, bufs, outs))
+    ctx = be.Context(None, device=local, hbm_budget=64 << 30)
+    srv = be.Server(ctx, n_streams=args.serve_streams, hbm_budget=64 << 30)
+    prepared = [srv.prepare(*t) for t in templates]
+    arrivals = W.poisson_arrivals(args.serve_rate, args.serve_seconds)
+    pick = W.rng(5, 2).integers(0, len(templates), size=len(arrivals))
+    # warm-up: every template once
+    for p in prepared:
+        srv.submit(p)
+    srv.drain(60.0)
+    srv.reset_stats()
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        for t, k in zip(arrivals, pick):
+            while time.perf_counter() - t0 < t:
+                pass
+            srv.submit(prepared[k])
+        srv.drain(300.0)
+    st = srv.stats()
+    # one launch per einsum, same sequence: measured service times, FIFO replay
+    service = np.zeros(len(templates))
+    for k, (e, bufs, outs) in enumerate(templates):
+        be.execute(ctx, e, bufs, outs)
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        for _ in range(3):
+            be.execute(ctx, e, bufs, outs)
+            torch.cuda.synchronize()
+        service[k] = (time.perf_counter() - a) / 3
+    fin, lat = 0.0, []
+    for t, k in zip(arrivals, pick):
+        fin = max(fin, t) + service[k]
+        lat.append(fin - t)
+    lat = np.sort(np.asarray(lat))
+    single_rate = len(arrivals) / (fin - arrivals[0])
+    line = {"metric": METRIC, "value": world * st["throughput"], "unit": "einsums/s", "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": 1e3 / max(st["throughput"], 1e-9), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32 mix", "data": "synthetic",
+            "config": {"workload": f"serving: Poisson {args.serve_rate:.0f}/s for {args.serve_seconds} s, "
+                                   f"{len(templates)} resident request templates (80 % uneven mix 8..512, "
+                                   "10 % FEM action E=4096, 10 % DG gradient E=4096)",
+                       "streams": args.serve_streams, "hbm_budget_gb": 64, "requests": len(arrivals),
+                       "parallelism": "replicas"},
+            "latency_p50_ms": st["p50_s"] * 1e3, "latency_p99_ms": st["p99_s"] * 1e3,
+            "completed": st["completed"], "failed": st["failed"], "max_inflight": st["max_inflight"],
+            "peak_inflight_bytes": st["peak_bytes"],
+            "one_launch_per_einsum": {"einsums_per_s": single_rate,
+                                      "latency_p50_ms": float(lat[len(lat) // 2]) * 1e3,
+                                      "latency_p99_ms": float(lat[int(0.99 * (len(lat) - 1))]) * 1e3},
+            "clocks": clk.summary()}
+    srv.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -465,7 +554,12 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=E_FULL)
     ap.add_argument("--ref-sample", type=int, default=32768)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="dg_gradient", choices=["dg_gradient", "chem_dense", "uneven_mix"])
+    ap.add_argument("--workload", default="dg_gradient",
+                    choices=["dg_gradient", "chem_dense", "uneven_mix", "serving"])
+    ap.add_argument("--serve-rate", type=float, default=20000.0)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-templates", type=int, default=256)
+    ap.add_argument("--serve-streams", type=int, default=8)
     ap.add_argument("--mix-n", type=int, default=512)
     ap.add_argument("--mix-operand-log2", type=int, default=22)
     ap.add_argument("--mix-flops-log2", type=int, default=26)
@@ -480,6 +574,8 @@ def main():
         run_chem(args)
     elif args.workload == "uneven_mix":
         run_mix(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -80,6 +80,7 @@ typedef struct be_ctx be_ctx;
 typedef struct be_einsum be_einsum;
 typedef struct be_canon be_canon;
 typedef struct be_batch be_batch;
+typedef struct be_server be_server;
 
 /* A tuned configuration, stated on the canonical form's names. */
 typedef struct {
@@ -218,6 +219,23 @@ int be_execute_host(be_ctx *x, const be_einsum *e, const be_config *cfg, int32_t
                     const double *scalars, int32_t n_scalars, void *stream);
 
 /*
+ * be_tune -- the autotuner that fills the database (the paper's transform
+ * writer recording performance facts under the normal form, Sec.
+ * "Integration of Optimized Batched Einsums into Practical Programs").
+ * Every configuration of every strategy that fits e and `precision` is run
+ * `warmup` times, then timed with CUDA events on `stream` until at least
+ * `min_reps` runs and `min_seconds` of kernel time (the paper's protocol is
+ * warmup = 5, min_reps = 20, min_seconds = 2); each mean is recorded with
+ * be_record under C(e), and the fastest is returned in *best.  With force = 0
+ * a key already in the database is returned without timing (resume).
+ * The outputs are overwritten while timing.  *n_tried counts timed configs.
+ */
+int be_tune(be_ctx *x, const be_einsum *e, int32_t precision, const be_buf *bufs, int32_t n_bufs,
+            const be_buf *outs, int32_t n_outs, const double *scalars, int32_t n_scalars, int32_t warmup,
+            int32_t min_reps, double min_seconds, int32_t force, void *stream, be_config *best,
+            double *best_seconds, int32_t *n_tried);
+
+/*
  * Persistent multi-instance executor: many batched einsums (any notations,
  * sizes and dtypes) evaluated by ONE persistent launch, replayed as a CUDA
  * graph.  The batched einsum is the paper's primitive (Sec. "Batched
@@ -245,6 +263,39 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
 int be_batch_run(be_batch *b, void *stream);
 int be_batch_info(const be_batch *b, int64_t *rows, int64_t *tiles, double *terms);
 void be_batch_destroy(be_batch *b);
+
+/*
+ * Serving loop with continuous batching.  Requests are parsed batched
+ * einsums whose buffers and outputs are already on the device.
+ * be_server_create -- a worker thread plus n_streams CUDA streams on the
+ *   current device; requests run in `precision` with the configuration
+ *   stored under their normal form in x's database (memoized by text).
+ *   hbm_budget_bytes (0: x's budget; 0 there too: unbounded) caps the bytes
+ *   that requests in flight may pin (their declared buffers and outputs).
+ * be_server_submit -- queue a request (asynchronous; returns an id).  The
+ *   einsum handle and the buffers must stay valid until the request is done.
+ *   Requests are admitted in arrival order while the budget allows and are
+ *   launched at once on the next stream, so they overlap on the device with
+ *   requests already running; a request larger than the whole budget
+ *   finishes with status BE_EBUDGET.  Split-precision requests share the
+ *   context's workspace and therefore run on one stream.
+ * be_server_wait -- block until request id is done (timeout_s < 0: no
+ *   limit; BE_ETIMEOUT otherwise), return its status and latency (submit to
+ *   completion of its last kernel), and forget it.
+ * be_server_drain -- block until nothing is queued or running.
+ * be_server_stats -- completed / failed counts, p50 / p99 latency,
+ *   throughput (completed / span from first submit to last completion), peak
+ *   bytes and peak number of requests in flight.
+ */
+int be_server_create(be_ctx *x, int32_t precision, int32_t n_streams, size_t hbm_budget_bytes, be_server **out);
+int be_server_submit(be_server *s, const be_einsum *e, const be_buf *bufs, int32_t n_bufs, const be_buf *outs,
+                     int32_t n_outs, const double *scalars, int32_t n_scalars, int64_t *id);
+int be_server_wait(be_server *s, int64_t id, double timeout_s, int32_t *status, double *latency_s);
+int be_server_drain(be_server *s, double timeout_s);
+int be_server_stats(be_server *s, int64_t *completed, int64_t *failed, double *p50_s, double *p99_s,
+                    double *throughput, size_t *peak_bytes, int64_t *max_inflight);
+int be_server_reset_stats(be_server *s);
+void be_server_destroy(be_server *s);
 
 /*
  * be_status -- wait for the device, then read and clear x's device status

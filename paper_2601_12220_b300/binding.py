@@ -32,7 +32,9 @@ EXPORTS = [
     "be_canon_tokens", "be_induced_graph", "be_graph_check", "be_identify", "be_ctx_create",
     "be_ctx_destroy", "be_lookup", "be_record", "be_db_size", "be_execute", "be_execute_host",
     "be_plan_strategy", "be_status", "be_ctx_set_timing", "be_ctx_timing", "be_gemm_split_noalloc",
-    "be_batch_create", "be_batch_run", "be_batch_info", "be_batch_destroy",
+    "be_batch_create", "be_batch_run", "be_batch_info", "be_batch_destroy", "be_tune",
+    "be_server_create", "be_server_submit", "be_server_wait", "be_server_drain", "be_server_stats",
+    "be_server_reset_stats", "be_server_destroy",
 ]
 KERNEL_ELEMENT, KERNEL_GENERIC, KERNEL_DENSE_GEMM, KERNEL_SPLIT, KERNEL_PERSISTENT = 0, 1, 2, 3, 4
 
@@ -110,6 +112,16 @@ def lib():
             "be_batch_run": (ctypes.c_int, [vp, vp]),
             "be_batch_info": (ctypes.c_int, [vp, P(i64), P(i64), P(ctypes.c_double)]),
             "be_batch_destroy": (None, [vp]),
+            "be_server_create": (ctypes.c_int, [vp, i32, i32, sz, P(vp)]),
+            "be_server_submit": (ctypes.c_int, [vp, vp, P(Buf), i32, P(Buf), i32, P(ctypes.c_double), i32, P(i64)]),
+            "be_server_wait": (ctypes.c_int, [vp, i64, ctypes.c_double, P(i32), P(ctypes.c_double)]),
+            "be_server_drain": (ctypes.c_int, [vp, ctypes.c_double]),
+            "be_server_stats": (ctypes.c_int, [vp, P(i64), P(i64), P(ctypes.c_double), P(ctypes.c_double),
+                                               P(ctypes.c_double), P(sz), P(i64)]),
+            "be_server_reset_stats": (ctypes.c_int, [vp]),
+            "be_server_destroy": (None, [vp]),
+            "be_tune": (ctypes.c_int, [vp, vp, i32, P(Buf), i32, P(Buf), i32, P(ctypes.c_double), i32, i32, i32,
+                                       ctypes.c_double, i32, vp, P(Config), P(ctypes.c_double), P(i32)]),
             "be_ctx_timing": (ctypes.c_int, [vp, i32, P(i64), P(ctypes.c_double)]),
         }
         for name, (res, args) in sig.items():
@@ -372,6 +384,81 @@ def execute_host(ctx, e: Einsum, bufs, outs, cfg: Config | None = None, precisio
     s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
     check(lib().be_execute_host(ctx.handle, e.handle, ctypes.byref(cfg) if cfg else None, precision, arr, len(bl),
                                 oarr, len(outs), sc, ns, s))
+
+
+def tune(ctx, e: Einsum, bufs, outs, precision=PREC_FP64, scalars=(), warmup=2, min_reps=5, min_seconds=0.0,
+         force=False, stream=None):
+    """Autotune e on these buffers; returns (best Config, seconds, configs timed)."""
+    import torch
+    keep = []
+    bl = _order(e, bufs)
+    bi = _bufs_torch(bl, keep)
+    bo = _bufs_torch(outs, keep, dense_only=True)
+    sc, ns = _scalars(scalars)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    best, sec, n = Config(), ctypes.c_double(), ctypes.c_int32()
+    check(lib().be_tune(ctx.handle, e.handle, precision, bi, len(bl), bo, len(outs), sc, ns, warmup, min_reps,
+                        min_seconds, 1 if force else 0, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(best),
+                        ctypes.byref(sec), ctypes.byref(n)))
+    return best, sec.value, n.value
+
+
+class Server:
+    """Serving loop with continuous batching (native worker thread + streams)."""
+
+    def __init__(self, ctx, precision=PREC_FP64, n_streams=8, hbm_budget=0):
+        h = ctypes.c_void_p()
+        check(lib().be_server_create(ctx.handle if ctx else None, precision, n_streams, hbm_budget,
+                                     ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def prepare(self, e: Einsum, bufs, outs, scalars=()):
+        """Marshal a request once; the returned object can be submitted many times."""
+        keep = []
+        bl = _order(e, bufs)
+        bi = _bufs_torch(bl, keep)
+        bo = _bufs_torch(outs, keep, dense_only=True)
+        sc, ns = _scalars(scalars)
+        return (e, bi, len(bl), bo, len(outs), sc, ns, keep, bl, outs)
+
+    def submit(self, req) -> int:
+        e, bi, nb, bo, no, sc, ns = req[:7]
+        i = ctypes.c_int64()
+        check(lib().be_server_submit(self._h, e.handle, bi, nb, bo, no, sc, ns, ctypes.byref(i)))
+        self._keep[i.value] = req
+        return i.value
+
+    def wait(self, rid: int, timeout=-1.0):
+        st, lat = ctypes.c_int32(), ctypes.c_double()
+        check(lib().be_server_wait(self._h, rid, timeout, ctypes.byref(st), ctypes.byref(lat)))
+        self._keep.pop(rid, None)
+        return st.value, lat.value
+
+    def drain(self, timeout=-1.0):
+        check(lib().be_server_drain(self._h, timeout))
+        self._keep.clear()
+
+    def stats(self):
+        c, f = ctypes.c_int64(), ctypes.c_int64()
+        p50, p99, thr = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        pk, mi = ctypes.c_size_t(), ctypes.c_int64()
+        check(lib().be_server_stats(self._h, ctypes.byref(c), ctypes.byref(f), ctypes.byref(p50), ctypes.byref(p99),
+                                    ctypes.byref(thr), ctypes.byref(pk), ctypes.byref(mi)))
+        return {"completed": c.value, "failed": f.value, "p50_s": p50.value, "p99_s": p99.value,
+                "throughput": thr.value, "peak_bytes": pk.value, "max_inflight": mi.value}
+
+    def reset_stats(self):
+        check(lib().be_server_reset_stats(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.be_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 class Batch:

@@ -14,10 +14,8 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/be.h"
-#include "canon.hpp"
 #include "dense.hpp"
-#include "plan.hpp"
+#include "handles.hpp"
 
 using namespace be;
 
@@ -32,57 +30,6 @@ namespace be {
 // lets the other translation units of the library report through be_last_error()
 void set_last_error(const std::string &msg) { g_err = msg; }
 }  // namespace be
-
-struct be_einsum {
-  Einsum e;
-  std::mutex mu;
-  std::unique_ptr<Canon> canon;   // cached C(e) for lookups
-};
-
-struct be_canon {
-  Canon c;
-};
-
-struct DbEntry {
-  be_config cfg;
-  double seconds;
-};
-
-struct be_ctx {
-  std::string db_path, device_name;
-  int device = -1;
-  size_t hbm_budget = 0;
-  std::mutex mu;
-  std::unordered_map<std::string, DbEntry> db;
-  // staging memory of be_execute_host
-  std::vector<void *> stage;
-  std::vector<size_t> stage_size;
-  // workspace of the dense split strategy and the device status word
-  void *ws = nullptr;
-  size_t ws_size = 0;
-  int *status = nullptr;
-  // optional per-kernel timing: (kernel id, start, stop) event pairs
-  bool timing = false;
-  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> marks;
-};
-
-// brackets one kernel launch with events when x has timing enabled
-struct KernelMark {
-  be_ctx *x;
-  int id;
-  cudaStream_t s;
-  cudaEvent_t a = nullptr, b = nullptr;
-  KernelMark(be_ctx *x_, int id_, cudaStream_t s_) : x(x_), id(id_), s(s_) {
-    if (x && x->timing && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
-      cudaEventRecord(a, s);
-  }
-  ~KernelMark() {
-    if (a && b) {
-      cudaEventRecord(b, s);
-      x->marks.emplace_back(id, a, b);
-    }
-  }
-};
 
 static int ensure_status(be_ctx *x) {
   if (x->status) return BE_OK;
@@ -117,7 +64,7 @@ static int put_string(const std::string &s, char *buf, size_t len, size_t *neede
   return BE_OK;
 }
 
-static const Canon *canon_of(be_einsum *e, std::string &err, int &st) {
+const Canon *be::canon_cached(be_einsum *e, std::string &err, int &st) {
   std::lock_guard<std::mutex> g(e->mu);
   if (!e->canon) {
     auto c = std::make_unique<Canon>();
@@ -417,7 +364,7 @@ static int resolve_config(be_ctx *x, be_einsum *h, const be_config *cfg, int32_t
   if (x) {
     std::string err;
     int st;
-    const Canon *c = canon_of(h, err, st);
+    const Canon *c = be::canon_cached(h, err, st);
     if (st) return fail(st, err);
     std::lock_guard<std::mutex> g(x->mu);
     auto it = x->db.find(db_key(c->key, x->device_name, precision));
@@ -541,6 +488,16 @@ int be_execute(be_ctx *x, const be_einsum *h, const be_config *cfg, int32_t prec
   return do_execute(x, h, cfg, precision, bufs, n_bufs, outs, n_outs, scalars, n_scalars, stream);
 }
 
+}  // extern "C"
+
+int be::execute_internal(be_ctx *x, const be_einsum *h, const be_config *cfg, int32_t precision, const be_buf *bufs,
+                         int32_t n_bufs, const be_buf *outs, int32_t n_outs, const double *scalars,
+                         int32_t n_scalars, void *stream) {
+  return do_execute(x, h, cfg, precision, bufs, n_bufs, outs, n_outs, scalars, n_scalars, stream);
+}
+
+extern "C" {
+
 int be_plan_strategy(be_ctx *x, const be_einsum *hc, const be_config *cfg, int32_t precision, int32_t *strategy) {
   be_einsum *h = const_cast<be_einsum *>(hc);
   if (!h || !strategy) return fail(BE_EARG, "NULL argument");
@@ -648,6 +605,37 @@ int be_ctx_timing(be_ctx *x, int32_t kernel, int64_t *launches, double *total_ms
   }
   x->marks.swap(keep);
   return BE_OK;
+}
+
+// ------------------------------------------------------------ autotuner
+
+static void tune_candidates(const Einsum &e, const std::vector<BufIn> &bi, const std::vector<BufIn> &bo,
+                            int32_t precision, std::vector<be_config_t> &out) {
+  be_config_t c;
+  std::string why;
+  EParams ep;
+  DensePlan dp;
+  std::memset(&c, 0, sizeof(c));
+  c.strategy = BE_STRAT_ELEMENT;
+  if (precision == BE_PREC_FP64 && plan_element(e, bi, bo, c, ep, why) == OK) {
+    for (int te : {8, 16, 32, 64, 128})
+      for (int blk : {128, 256}) {
+        c.tile[0] = te;
+        c.tile[1] = blk;
+        if (plan_element(e, bi, bo, c, ep, why) == OK) out.push_back(c);
+      }
+  }
+  std::memset(&c, 0, sizeof(c));
+  if (precision == BE_PREC_SPLIT && plan_dense(e, bi, bo, dp, why) == OK) {
+    c.strategy = BE_STRAT_DENSE_SPLIT;
+    for (int hd : {1, 2}) {
+      c.tile[2] = hd;
+      out.push_back(c);
+    }
+  }
+  std::memset(&c, 0, sizeof(c));
+  c.strategy = BE_STRAT_GENERIC;
+  out.push_back(c);
 }
 
 // ------------------------------------------------------------ persistent batch
@@ -785,6 +773,79 @@ int be_batch_info(const be_batch *b, int64_t *rows, int64_t *tiles, double *term
 }
 
 void be_batch_destroy(be_batch *b) { delete b; }
+
+int be_tune(be_ctx *x, const be_einsum *hc, int32_t precision, const be_buf *bufs, int32_t n_bufs, const be_buf *outs,
+            int32_t n_outs, const double *scalars, int32_t n_scalars, int32_t warmup, int32_t min_reps,
+            double min_seconds, int32_t force, void *stream, be_config *best, double *best_seconds,
+            int32_t *n_tried) {
+  be_einsum *h = const_cast<be_einsum *>(hc);
+  if (!x || !h || !best) return fail(BE_EARG, "NULL argument");
+  if (n_tried) *n_tried = 0;
+  std::string err;
+  int st;
+  const Canon *cn = be::canon_cached(h, err, st);
+  if (st) return fail(st, err);
+  const std::string key = db_key(cn->key, x->device_name, precision);
+  if (!force) {
+    std::lock_guard<std::mutex> g(x->mu);
+    auto it = x->db.find(key);
+    if (it != x->db.end()) {          // resume: a tuned key is not timed again
+      *best = it->second.cfg;
+      if (best_seconds) *best_seconds = it->second.seconds;
+      return BE_OK;
+    }
+  }
+  const Einsum &e = h->e;
+  std::vector<BufIn> bi(n_bufs), bo(n_outs);
+  for (int k = 0; k < n_bufs; ++k) bi[k] = BufIn{bufs[k].ptr, bufs[k].strides, bufs[k].ndim, bufs[k].dtype};
+  for (int k = 0; k < n_outs; ++k) bo[k] = BufIn{outs[k].ptr, outs[k].strides, outs[k].ndim, outs[k].dtype};
+  st = check_buffers(e, bi, bo, err);
+  if (st) return fail(st, err);
+  std::vector<be_config_t> cands;
+  tune_candidates(e, bi, bo, precision, cands);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return fail(BE_ECUDA, "event");
+  double best_t = -1;
+  be_canon bc;
+  bc.c = *cn;
+  for (auto &c : cands) {
+    const be_config *cfg = reinterpret_cast<const be_config *>(&c);
+    for (int w = 0; w < warmup; ++w) {
+      st = do_execute(x, h, cfg, precision, bufs, n_bufs, outs, n_outs, scalars, n_scalars, stream);
+      if (st) break;
+    }
+    if (st) { st = BE_OK; continue; }     // a candidate that cannot run is skipped
+    int reps = 0;
+    double total = 0;
+    while (reps < std::max(1, min_reps) || total < min_seconds) {
+      cudaEventRecord(a, s);
+      st = do_execute(x, h, cfg, precision, bufs, n_bufs, outs, n_outs, scalars, n_scalars, stream);
+      cudaEventRecord(b, s);
+      if (st) break;
+      if (cudaEventSynchronize(b) != cudaSuccess) { st = BE_ECUDA; break; }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, a, b);
+      total += ms * 1e-3;
+      ++reps;
+      if (reps > 100000) break;
+    }
+    if (st) { st = BE_OK; continue; }
+    const double sec = total / reps;
+    if (n_tried) ++*n_tried;
+    int rs = be_record(x, &bc, precision, cfg, sec);
+    if (rs) { cudaEventDestroy(a); cudaEventDestroy(b); return rs; }
+    if (best_t < 0 || sec < best_t) {
+      best_t = sec;
+      *best = *cfg;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (best_t < 0) return fail(BE_EUNSUPPORTED, "no candidate configuration ran");
+  if (best_seconds) *best_seconds = best_t;
+  return BE_OK;
+}
 
 int be_status(be_ctx *x, int32_t *device_status) {
   if (!x || !device_status) return fail(BE_EARG, "NULL argument");

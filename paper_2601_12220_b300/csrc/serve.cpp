@@ -1,0 +1,298 @@
+// Serving loop: continuous batching of batched-einsum requests.
+//
+// A request is a parsed batched einsum with device-resident operands and
+// outputs (the operands stay on the device; only descriptors travel).  The
+// caller submits requests at any time; a worker thread admits them in
+// arrival order as long as the bytes pinned by requests in flight (their
+// declared buffers and outputs) stay within the HBM budget, and launches each
+// admitted request at once on one of several streams, so requests that
+// arrive while others run overlap with them on the device.  A host callback
+// queued behind each request's kernels stamps its completion time, releases
+// its budget and wakes the worker, which then admits what was waiting.
+// The configuration of each request comes from the tuning database under its
+// normal form (Alg. 1 + lookup), memoized by the request's text.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <thread>
+
+#include "handles.hpp"
+
+namespace {
+
+double now_s() {
+  using clk = std::chrono::steady_clock;
+  return std::chrono::duration<double>(clk::now().time_since_epoch()).count();
+}
+
+int sfail(int code, const std::string &m) {
+  be::set_last_error(m);
+  return code;
+}
+
+}  // namespace
+
+struct ServeReq;
+
+struct be_server {
+  be_ctx *x = nullptr;
+  int device = 0;
+  int32_t precision = BE_PREC_FP64;
+  size_t budget = 0;
+  size_t inflight_bytes = 0, peak_bytes = 0;
+  int64_t inflight = 0, max_inflight = 0;
+  std::vector<cudaStream_t> streams;
+  size_t next_stream = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<ServeReq *> pending;
+  std::unordered_map<int64_t, std::unique_ptr<ServeReq>> reqs;
+  int64_t next_id = 1;
+  std::vector<double> latencies;
+  int64_t completed = 0, failed = 0;
+  double first_submit = -1, last_done = -1;
+  std::unordered_map<std::string, be_config> cfg_memo;
+  std::unordered_map<std::string, bool> cfg_have;
+  bool stop = false;
+  std::thread worker;
+};
+
+struct ServeReq {
+  be_server *srv;
+  int64_t id;
+  be_einsum *e;
+  std::vector<be_buf> bufs, outs;
+  std::vector<std::vector<int64_t>> strides;
+  std::vector<double> scalars;
+  size_t bytes = 0;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  int state = 0;      // 0 queued, 1 running, 2 done
+  int status = BE_OK;
+};
+
+static void CUDART_CB on_done(void *arg) {
+  ServeReq *r = (ServeReq *)arg;
+  be_server *s = r->srv;
+  const double t = now_s();
+  std::lock_guard<std::mutex> g(s->mu);
+  r->t_done = t;
+  r->state = 2;
+  s->inflight_bytes -= r->bytes;
+  s->inflight -= 1;
+  s->latencies.push_back(t - r->t_submit);
+  s->completed += 1;
+  s->last_done = std::max(s->last_done, t);
+  s->cv_work.notify_one();
+  s->cv_done.notify_all();
+}
+
+static void worker_loop(be_server *s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (true) {
+    while (!s->pending.empty()) {
+      ServeReq *r = s->pending.front();
+      if (r->bytes > s->budget && s->budget > 0) {            // can never fit
+        r->status = BE_EBUDGET;
+        r->state = 2;
+        r->t_done = now_s();
+        s->failed += 1;
+        s->pending.pop_front();
+        s->cv_done.notify_all();
+        continue;
+      }
+      if (s->budget > 0 && s->inflight > 0 && s->inflight_bytes + r->bytes > s->budget) break;   // wait for room
+      s->pending.pop_front();
+      // configuration under the normal form, memoized by text
+      be_config cfg;
+      bool have = false;
+      auto it = s->cfg_have.find(r->e->e.text);
+      if (it != s->cfg_have.end()) {
+        have = it->second;
+        if (have) cfg = s->cfg_memo[r->e->e.text];
+      } else {
+        std::string err;
+        int st;
+        const Canon *c = be::canon_cached(r->e, err, st);
+        if (!st && s->x) {
+          lk.unlock();
+          double sec;
+          be_canon bc;
+          bc.c = *c;
+          have = be_lookup(s->x, &bc, s->precision, &cfg, &sec) == BE_OK;
+          lk.lock();
+        }
+        s->cfg_have[r->e->e.text] = have;
+        if (have) s->cfg_memo[r->e->e.text] = cfg;
+      }
+      // the dense split strategy shares its context's workspace: keep it on one stream
+      cudaStream_t st = s->streams[s->precision == BE_PREC_SPLIT ? 0 : s->next_stream];
+      s->next_stream = (s->next_stream + 1) % s->streams.size();
+      r->t_admit = now_s();
+      r->state = 1;
+      s->inflight_bytes += r->bytes;
+      s->inflight += 1;
+      s->peak_bytes = std::max(s->peak_bytes, s->inflight_bytes);
+      s->max_inflight = std::max(s->max_inflight, s->inflight);
+      lk.unlock();
+      int rc = be::execute_internal(s->x, r->e, have ? &cfg : nullptr, s->precision, r->bufs.data(),
+                                    (int32_t)r->bufs.size(), r->outs.data(), (int32_t)r->outs.size(),
+                                    r->scalars.data(), (int32_t)r->scalars.size(), st);
+      if (rc == BE_OK && cudaLaunchHostFunc(st, on_done, r) == cudaSuccess) {
+        lk.lock();
+        continue;
+      }
+      lk.lock();
+      r->status = rc ? rc : BE_ECUDA;
+      r->state = 2;
+      r->t_done = now_s();
+      s->inflight_bytes -= r->bytes;
+      s->inflight -= 1;
+      s->failed += 1;
+      s->cv_done.notify_all();
+    }
+    if (s->stop && s->pending.empty() && s->inflight == 0) break;
+    s->cv_work.wait(lk);
+  }
+}
+
+static size_t decl_bytes(const Einsum &e) {
+  size_t n = 0;
+  for (auto &b : e.buffers) {
+    size_t k = (size_t)dtype_size(b.dtype);
+    for (auto d : b.shape) k *= (size_t)d;
+    n += k;
+  }
+  size_t o = (size_t)dtype_size(e.out_dtype);
+  for (auto d : e.out_shape()) o *= (size_t)d;
+  return n + o * (size_t)e.b;
+}
+
+extern "C" {
+
+int be_server_create(be_ctx *x, int32_t precision, int32_t n_streams, size_t hbm_budget_bytes, be_server **out) {
+  if (!out || n_streams < 1 || n_streams > 64) return sfail(BE_EARG, "n_streams must be in 1..64");
+  auto s = std::make_unique<be_server>();
+  s->x = x;
+  s->precision = precision;
+  s->budget = hbm_budget_bytes ? hbm_budget_bytes : (x ? x->hbm_budget : 0);
+  cudaGetDevice(&s->device);
+  for (int k = 0; k < n_streams; ++k) {
+    cudaStream_t st;
+    cudaError_t ce = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) {
+      for (auto q : s->streams) cudaStreamDestroy(q);
+      return sfail(BE_ECUDA, std::string("stream: ") + cudaGetErrorString(ce));
+    }
+    s->streams.push_back(st);
+  }
+  be_server *raw = s.get();
+  raw->worker = std::thread(worker_loop, raw);
+  *out = s.release();
+  return BE_OK;
+}
+
+int be_server_submit(be_server *s, const be_einsum *e, const be_buf *bufs, int32_t n_bufs, const be_buf *outs,
+                     int32_t n_outs, const double *scalars, int32_t n_scalars, int64_t *id) {
+  if (!s || !e || !id || n_bufs < 0 || n_outs < 0 || n_scalars < 0) return sfail(BE_EARG, "bad request");
+  auto r = std::make_unique<ServeReq>();
+  r->srv = s;
+  r->e = const_cast<be_einsum *>(e);
+  r->bufs.assign(bufs, bufs + n_bufs);
+  r->outs.assign(outs, outs + n_outs);
+  // keep copies of the caller's stride arrays (reserved: no reallocation)
+  r->strides.reserve(r->bufs.size());
+  for (auto &b : r->bufs)
+    if (b.strides) {
+      r->strides.emplace_back(b.strides, b.strides + b.ndim);
+      b.strides = r->strides.back().data();
+    }
+  if (scalars) r->scalars.assign(scalars, scalars + n_scalars);
+  r->bytes = decl_bytes(e->e);
+  r->t_submit = now_s();
+  std::lock_guard<std::mutex> g(s->mu);
+  if (s->stop) return sfail(BE_EARG, "server is shutting down");
+  if (s->first_submit < 0) s->first_submit = r->t_submit;
+  r->id = s->next_id++;
+  *id = r->id;
+  s->pending.push_back(r.get());
+  s->reqs.emplace(r->id, std::move(r));
+  s->cv_work.notify_one();
+  return BE_OK;
+}
+
+int be_server_wait(be_server *s, int64_t id, double timeout_s, int32_t *status, double *latency_s) {
+  if (!s) return sfail(BE_EARG, "NULL server");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return sfail(BE_EARG, "unknown request id");
+  ServeReq *r = it->second.get();
+  auto pred = [&] { return r->state == 2; };
+  if (timeout_s < 0) s->cv_done.wait(lk, pred);
+  else if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred))
+    return sfail(BE_ETIMEOUT, "request not finished within the timeout");
+  if (status) *status = r->status;
+  if (latency_s) *latency_s = r->t_done - r->t_submit;
+  s->reqs.erase(it);
+  return BE_OK;
+}
+
+int be_server_drain(be_server *s, double timeout_s) {
+  if (!s) return sfail(BE_EARG, "NULL server");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto pred = [&] { return s->pending.empty() && s->inflight == 0; };
+  if (timeout_s < 0) s->cv_done.wait(lk, pred);
+  else if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred))
+    return sfail(BE_ETIMEOUT, "requests still in flight after the timeout");
+  for (auto it = s->reqs.begin(); it != s->reqs.end();)
+    it = it->second->state == 2 ? s->reqs.erase(it) : std::next(it);
+  return BE_OK;
+}
+
+int be_server_stats(be_server *s, int64_t *completed, int64_t *failed, double *p50_s, double *p99_s,
+                    double *throughput, size_t *peak_bytes, int64_t *max_inflight) {
+  if (!s) return sfail(BE_EARG, "NULL server");
+  std::lock_guard<std::mutex> g(s->mu);
+  std::vector<double> l = s->latencies;
+  std::sort(l.begin(), l.end());
+  auto q = [&](double f) { return l.empty() ? 0.0 : l[std::min(l.size() - 1, (size_t)(f * (double)(l.size() - 1) + 0.5))]; };
+  if (completed) *completed = s->completed;
+  if (failed) *failed = s->failed;
+  if (p50_s) *p50_s = q(0.50);
+  if (p99_s) *p99_s = q(0.99);
+  if (throughput)
+    *throughput = (s->completed > 0 && s->last_done > s->first_submit) ? s->completed / (s->last_done - s->first_submit) : 0.0;
+  if (peak_bytes) *peak_bytes = s->peak_bytes;
+  if (max_inflight) *max_inflight = s->max_inflight;
+  return BE_OK;
+}
+
+int be_server_reset_stats(be_server *s) {
+  if (!s) return sfail(BE_EARG, "NULL server");
+  std::lock_guard<std::mutex> g(s->mu);
+  s->latencies.clear();
+  s->completed = s->failed = 0;
+  s->first_submit = s->last_done = -1;
+  s->peak_bytes = s->inflight_bytes;
+  s->max_inflight = s->inflight;
+  return BE_OK;
+}
+
+void be_server_destroy(be_server *s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->stop = true;
+    s->cv_work.notify_one();
+  }
+  s->worker.join();
+  for (auto st : s->streams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+"""Autotuner and serving loop on the GPU.
+
+The tuner must record its timings under the normal form, so an isomorphic
+copy retrieves the same config, and must skip keys already present (resume).
+The server must give each request the same bits alone and in a mix of
+concurrent requests, respect its HBM admission budget and report latencies.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
+
+import paper_2601_12220_b300 as be  # noqa: E402
+import workloads as W  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def dg_request(E, seed_scale=1.0):
+    D, G, a, b = W.dg_gradient(E=E)
+    e = be.Einsum(W.dg_gradient_spec(E=E))
+    bufs = {k: torch.from_numpy(v * seed_scale).to(DEV) for k, v in dict(D=D, G=G, a=a, b=b).items()}
+    outs = [torch.empty((E, 35), dtype=torch.float64, device=DEV) for _ in range(3)]
+    return e, bufs, outs
+
+
+def test_tune_records_transfers_and_resumes(tmp_path):
+    db = str(tmp_path / "tune.db")
+    ctx = be.Context(db, device=0)
+    e, bufs, outs = dg_request(20000)
+    best, sec, n = be.tune(ctx, e, bufs, outs, warmup=1, min_reps=3)
+    assert n >= 5 and sec > 0
+    assert best.strategy in (be.STRAT_ELEMENT, be.STRAT_GENERIC)
+    # an isomorphic copy (rows reversed, letters renamed) finds the same record
+    text = W.dg_gradient_spec(E=20000)
+    rows = " | ".join(f"D,G{x},U" for x in (2, 1, 0))
+    copy = be.Einsum(f"pqs,ep,es->eq | {rows} ;" + text.split(";", 1)[1])
+    got, sec2 = ctx.lookup(copy.canonicalize())
+    assert got.as_tuple() == best.as_tuple() and sec2 == sec
+    # resume: nothing is timed again
+    best2, _, n2 = be.tune(ctx, e, bufs, outs, warmup=1, min_reps=3)
+    assert n2 == 0 and best2.as_tuple() == best.as_tuple()
+    ctx.close()
+    ctx2 = be.Context(db, device=0)
+    assert ctx2.lookup(e.canonicalize())[0].as_tuple() == best.as_tuple()
+    # the dense split strategy is among the candidates in split precision
+    A = torch.randn(256, 512, dtype=torch.float64, device=DEV)
+    B = torch.randn(512, 128, dtype=torch.float64, device=DEV)
+    mm = be.Einsum("ik,kj->ij | A,B ; A:f64[256,512] ; B:f64[512,128]")
+    C = torch.empty(256, 128, dtype=torch.float64, device=DEV)
+    best3, _, n3 = be.tune(ctx2, mm, {"A": A, "B": B}, [C], precision=be.PREC_SPLIT, warmup=1, min_reps=3)
+    assert n3 >= 2
+
+
+def make_requests(n, seed):
+    g = np.random.default_rng(seed)
+    reqs = []
+    for k in range(n):
+        if k % 10 == 0:
+            reqs.append(dg_request(2000, 1.0 + k))
+            continue
+        inst = W.mix_instance(g, lo_exp=2.0, hi_exp=7.0, max_operand=1 << 16, max_flops=1 << 22)
+        e = be.Einsum(W.instance_spec(inst))
+        dt = torch.float64 if e.out_dtype == be.F64 else torch.float32
+        bufs = {a: torch.from_numpy(v).to(DEV) for a, v in W.instance_arrays(inst, g).items()}
+        outs = [torch.empty(e.out_shape, dtype=dt, device=DEV) for _ in range(e.b)]
+        reqs.append((e, bufs, outs))
+    return reqs
+
+
+def test_server_alone_vs_mix():
+    ctx = be.Context(None, device=0)
+    reqs = make_requests(60, 3)
+    srv = be.Server(ctx, n_streams=8)
+    ids = [srv.submit(srv.prepare(e, bufs, outs)) for e, bufs, outs in reqs]
+    for i in ids:
+        st, lat = srv.wait(i, timeout=120.0)
+        assert st == be.OK and lat > 0
+    stats = srv.stats()
+    assert stats["completed"] == 60 and stats["failed"] == 0
+    assert stats["p50_s"] <= stats["p99_s"]
+    assert stats["max_inflight"] >= 2          # requests overlapped on the device
+    for e, bufs, outs in reqs:
+        alone = [torch.empty_like(o) for o in outs]
+        be.execute(ctx, e, bufs, alone)
+        torch.cuda.synchronize()
+        for o, a in zip(outs, alone):
+            assert torch.equal(o, a)
+    srv.close()
+
+
+def test_server_budget():
+    ctx = be.Context(None, device=0)
+    big = dg_request(4000)
+    small = make_requests(12, 5)[1:]
+    need = 8 * (2 * 4000 * 35 + 4000 * 9 + 3 * 35 * 35 + 3 * 4000 * 35)
+    srv = be.Server(ctx, n_streams=4, hbm_budget=need - 1)
+    st, _ = srv.wait(srv.submit(srv.prepare(*big)), timeout=60.0)
+    assert st == be.EBUDGET
+    srv.close()
+    budget = 2 * need
+    srv = be.Server(ctx, n_streams=4, hbm_budget=budget)
+    ids = [srv.submit(srv.prepare(*r)) for r in [big] + small + [big]]
+    srv.drain(timeout=120.0)
+    stats = srv.stats()
+    assert stats["completed"] == len(ids) and stats["peak_bytes"] <= budget
+    srv.close()
