@@ -139,6 +139,19 @@ def dist_setup(n_gpus):
     return world, rank, local
 
 
+def aggregate(pg, per_rank_ms, units_per_rank, device=None):
+    """Whole-job numbers of a replica run: the step time is the MAX over ranks
+    (every rank waited at a barrier before and after its timed region) and
+    the value counts the units of all ranks.  pg is torch.distributed or None."""
+    import torch
+    world = pg.get_world_size() if pg else 1
+    t = torch.tensor([float(x) for x in per_rank_ms], dtype=torch.float64, device=device)
+    if pg:
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    ms = t.tolist()
+    return ms, world * units_per_rank / (ms[0] * 1e-3)
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -241,11 +254,7 @@ def run_ours(args):
     n_launch, k_total = ctx.timing(kid)
     kms = k_total / max(1, n_launch)
     launches_per_step = n_launch / args.steps
-    if pg:
-        tt = torch.tensor([ms, kms], device=dev, dtype=torch.float64)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        ms, kms = tt.tolist()
-    value = world * byts / (ms * 1e-3) / 1e9
+    (ms, kms), value = aggregate(pg, [ms, kms], byts / 1e9, device=dev)
 
     # end to end through the public API with pinned host buffers
     pinned = {k: torch.from_numpy(v).pin_memory().numpy() for k, v in host.items()}
