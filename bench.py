@@ -63,10 +63,17 @@ def load_peaks():
     return peaks
 
 
-# FP64 vector-pipe peak of B300 (nominal figure of the profiling notes:
-# 1.25 TFLOP/s dense FP64); the element kernel's bound while it runs on the
-# FP64 pipe.
+# FP64 vector-pipe peak of B300 (nominal 1.25 TFLOP/s dense FP64): the bound
+# of the FP64-pipe variant of the element kernel.
 FP64_PEAK_TFLOPS = 1.25
+# FP32 pipe of B300 from unit counts and clock: 148 SMs x 128 FP32 lanes x
+# 2 flops (FMA) x 2.032 GHz: the bound of the double-float element kernel.
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# FP32 flops the double-float kernel spends per element on its compensated
+# dot products: 15 per term (1 mul + 3 fma + 8 add, FMA counted twice) over
+# 3*35*35 + 3*3*35 terms, plus 3 per normalisation of 2*105 results (the
+# sine and the conversions are not counted, so this is a lower bound)
+DF_FLOPS_PER_ELEMENT = 15 * (3 * 35 * 35 + 3 * 3 * 35) + 3 * 2 * 105
 
 
 def kernel_traffic(kernel):
@@ -226,11 +233,13 @@ def run_ours(args):
     strat = be.plan_strategy(ctx, be.Einsum(text))
     kid = be.KERNEL_ELEMENT if strat == be.STRAT_ELEMENT else be.KERNEL_GENERIC
 
+    forced = be.make_config(be.STRAT_ELEMENT, (0, 0, args.element_variant)) if args.element_variant else None
+
     def step():
         e = be.Einsum(text)                       # parse
         c = e.canonicalize()                      # normal form
         hit = ctx.lookup(c, be.PREC_FP64)         # tuning database
-        cfg = hit[0] if hit else None
+        cfg = forced or (hit[0] if hit else None)
         be.execute(ctx, e, bufs, outs, cfg=cfg, precision=be.PREC_FP64, stream=stream)
 
     for _ in range(args.warmup):
@@ -279,13 +288,21 @@ def run_ours(args):
     d2h = sum(o.nbytes for o in host_outs)
 
     peaks = load_peaks()
-    kernel = {"name": "element_kernel", "source": "kernels_element.cu", "profile": "element_kernel_dg_p4.md"}
-    ach_tf = flops / (kms * 1e-3) / 1e12
+    kernel = ({"name": "element_kernel", "source": "kernels_element.cu", "profile": "element_kernel_dg_p4.md"}
+              if args.element_variant == 1 else
+              {"name": "element_df_kernel", "source": "kernels_element_df.cu", "profile": "element_df_kernel_dg_p4.md"})
     ach_gb = byts / (kms * 1e-3) / 1e9
     traffic = kernel_traffic(kernel)
-    roofline = {"kernel": kernel["name"], "bound": "alu", "achieved": ach_tf, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach_tf / FP64_PEAK_TFLOPS,
-                "peak_source": "nominal B300 FP64 (1.25 TFLOP/s)",
+    if args.element_variant == 1:     # FP64 pipe
+        ach_tf, peak, src = flops / (kms * 1e-3) / 1e12, FP64_PEAK_TFLOPS, "nominal B300 FP64 (1.25 TFLOP/s)"
+        what = "algorithmic FP64 flops"
+    else:                             # double-float on the FP32 pipe
+        ach_tf = DF_FLOPS_PER_ELEMENT * E / (kms * 1e-3) / 1e12
+        peak, src = FP32_PEAK_TFLOPS, "FP32 pipe from unit counts and clock: 148 SMs x 128 lanes x 2 x 2.032 GHz"
+        what = f"FP32 flops of the compensated dot products ({DF_FLOPS_PER_ELEMENT} per element)"
+    roofline = {"kernel": kernel["name"], "bound": "alu", "achieved": ach_tf, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach_tf / peak, "counts": what,
+                "peak_source": src,
                 "traffic": traffic, "algorithmic_bytes": byts,
                 "hbm": {"achieved": ach_gb, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": ach_gb / peaks["hbm_gbs"], "peak_source": peaks["source"]}}
@@ -563,6 +580,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=E_FULL)
     ap.add_argument("--ref-sample", type=int, default=32768)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--element-variant", type=int, default=0,
+                    help="0 default (double-float on the FP32 pipe), 1 FP64 pipe")
     ap.add_argument("--workload", default="dg_gradient",
                     choices=["dg_gradient", "chem_dense", "uneven_mix", "serving"])
     ap.add_argument("--serve-rate", type=float, default=20000.0)

@@ -467,7 +467,8 @@ static int do_execute(be_ctx *x, const be_einsum *hc, const be_config *cfg, int3
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * per_sm));
     if (ep.E > 0) {
       KernelMark km(x, BE_KERNEL_ELEMENT, s);
-      ce = launch_element(ep, grid, block, s);
+      // tile[2]: 1 = FP64 pipe, otherwise double-float on the FP32 pipe
+      ce = c.tile[2] == 1 ? launch_element(ep, grid, block, s) : launch_element_df(ep, grid, block, s);
     }
   } else {
     for (int i = 0; i < e.b && ce == cudaSuccess; ++i) {
@@ -618,12 +619,15 @@ static void tune_candidates(const Einsum &e, const std::vector<BufIn> &bi, const
   std::memset(&c, 0, sizeof(c));
   c.strategy = BE_STRAT_ELEMENT;
   if (precision == BE_PREC_FP64 && plan_element(e, bi, bo, c, ep, why) == OK) {
-    for (int te : {8, 16, 32, 64, 128})
-      for (int blk : {128, 256}) {
-        c.tile[0] = te;
-        c.tile[1] = blk;
-        if (plan_element(e, bi, bo, c, ep, why) == OK) out.push_back(c);
-      }
+    for (int variant : {2, 1})
+      for (int te : {8, 16, 32, 64, 128})
+        for (int blk : {128, 256}) {
+          if (variant == 1 && te != 32) continue;      // the FP64-pipe variant: one candidate per block size
+          c.tile[0] = te;
+          c.tile[1] = blk;
+          c.tile[2] = variant;
+          if (plan_element(e, bi, bo, c, ep, why) == OK) out.push_back(c);
+        }
   }
   std::memset(&c, 0, sizeof(c));
   if (precision == BE_PREC_SPLIT && plan_dense(e, bi, bo, dp, why) == OK) {

@@ -1,0 +1,130 @@
+// Double-float ("df") arithmetic on the FP32 pipe: a value is an unevaluated
+// sum hi + lo of two floats with |lo| <= ulp(hi) / 2, about 48 significant
+// bits.  On B300 the FP64 pipe runs near 1.1 TFLOP/s while FP32 runs near
+// 66 TFLOP/s, so FP64-accuracy work is done here in df.
+//
+// Building blocks (published error-free transformations): TwoSum (Knuth),
+// Fast2Sum (Dekker, 1971) for |a| >= |b|, and TwoProd through a fused
+// multiply-add (the product's rounding error is exactly fma(a, b, -p)).
+// sine: Cody-Waite reduction by pi/2 (pi/2 held in three floats; x - k*p1
+// with one FP64 fma, k*p2 formed exactly with TwoProd) followed by the Taylor series of sin or
+// cos on |r| <= pi/4, the small high-order terms in plain float and the
+// leading ones in df.  The constants are 1/k! and pi/2 rounded into float
+// pairs (hex literals, derived with exact rational arithmetic).
+#pragma once
+
+#include <cstdint>
+
+namespace be {
+namespace dfm {
+
+struct df {
+  float hi, lo;
+};
+
+constexpr float PIO2_1 = 0x1.921fb60000000p+0f, PIO2_2 = -0x1.777a5c0000000p-25f, PIO2_3 = -0x1.ee59da0000000p-50f;
+constexpr float TWO_OVER_PI = 0x1.45f3060000000p-1f;
+// (-1)^n / (2n+1)!, n = 0..11, as (hi, lo)
+static __device__ __constant__ float SIN_C[12][2] = {{0x1.0000000000000p+0f, 0.0f}, {-0x1.5555560000000p-3f, 0x1.5555560000000p-28f}, {0x1.1111120000000p-7f, -0x1.ddddde0000000p-32f}, {-0x1.a01a020000000p-13f, 0x1.7f97fa0000000p-39f}, {0x1.71de3a0000000p-19f, 0x1.55b1cc0000000p-45f}, {-0x1.ae64560000000p-26f, -0x1.fd51380000000p-52f}, {0x1.6124620000000p-33f, -0x1.8af25e0000000p-58f}, {-0x1.ae7f3e0000000p-41f, -0x1.ccee080000000p-67f}, {0x1.952c780000000p-49f, -0x1.f9ea560000000p-74f}, {-0x1.2f49b40000000p-57f, -0x1.a050560000000p-83f}, {0x1.71b8f00000000p-66f, -0x1.2461520000000p-91f}, {-0x1.761b420000000p-75f, 0x1.9d38fc0000000p-100f}};
+// (-1)^n / (2n)!, n = 0..11, as (hi, lo)
+static __device__ __constant__ float COS_C[12][2] = {{0x1.0000000000000p+0f, 0.0f}, {-0x1.0000000000000p-1f, 0.0f}, {0x1.5555560000000p-5f, -0x1.5555560000000p-30f}, {-0x1.6c16c20000000p-10f, 0x1.27d27e0000000p-35f}, {0x1.a01a020000000p-16f, -0x1.7f97fa0000000p-42f}, {-0x1.27e4fc0000000p-22f, 0x1.10ec140000000p-47f}, {0x1.1eed8e0000000p-29f, 0x1.ff1b120000000p-54f}, {-0x1.93974a0000000p-37f, -0x1.180f940000000p-62f}, {0x1.ae7f3e0000000p-45f, 0x1.ccee080000000p-71f}, {-0x1.6827860000000p-53f, -0x1.dcbecc0000000p-80f}, {0x1.e542ba0000000p-62f, 0x1.00808a0000000p-88f}, {-0x1.0ce3960000000p-70f, -0x1.b6ff0a0000000p-95f}};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = a + b, bp = s - a;
+  return df{s, (a - (s - bp)) + (b - bp)};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = a + b;
+  return df{s, b - (s - a)};
+}
+__device__ __forceinline__ df two_prod(float a, float b) {
+  const float p = a * b;
+  return df{p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ df df_add(df x, df y) {
+  df s = two_sum(x.hi, y.hi);
+  s.lo += x.lo + y.lo;
+  return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_mul(df x, df y) {
+  df p = two_prod(x.hi, y.hi);
+  p.lo = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, p.lo));
+  return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ df df_neg(df x) { return df{-x.hi, -x.lo}; }
+
+// x * y accumulated into the unnormalized pair (s, c): s carries the running
+// sum of the leading products exactly through TwoSum, c the rounding errors
+// and the cross terms; normalize with fast_two_sum(s, c) at the end
+__device__ __forceinline__ void dot_acc(float &s, float &c, df x, df y) {
+  const float p = x.hi * y.hi;
+  const float pe = fmaf(x.hi, y.hi, -p);
+  const float cr = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, pe));
+  const float ns = s + p, bp = ns - s;
+  c += ((s - (ns - bp)) + (p - bp)) + cr;
+  s = ns;
+}
+
+// exact float -> double for normal floats and zero (integer bit moves, no
+// FP64 instruction); other encodings go through the hardware conversion
+__device__ __forceinline__ double f2d(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t ef = (u >> 23) & 0xFFu;
+  if (ef == 0u || ef == 0xFFu) return (double)f;
+  const uint64_t s = (uint64_t)(u >> 31) << 63;
+  const uint64_t e = (uint64_t)(ef - 127u + 1023u);
+  return __longlong_as_double((long long)(s | (e << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29)));
+}
+
+__device__ __forceinline__ double df_to_double(df x) { return f2d(x.hi) + f2d(x.lo); }
+
+// double -> df with |x - hi - lo| <= 2^-48 |x|, by integer operations on the
+// bits when both parts land in FP32's normal range (2^-70 <= |x| < 2^100)
+__device__ __forceinline__ df df_from_double(double x) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e < 1023 - 70 || e > 1023 + 100) {
+    const float h = __double2float_rn(x);
+    return df{h, __double2float_rn(x - (double)h)};
+  }
+  const uint64_t m = ((uint64_t)b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const uint64_t mh = (m + (1ull << 28)) >> 29;                    // top 24 bits, rounded
+  const int rem = (int)((long long)m - (long long)(mh << 29));      // |rem| <= 2^28
+  const int eh = e - 1023;
+  const uint32_t sign = (uint32_t)((uint64_t)b >> 63) << 31;
+  const float hi = mh == (1ull << 24) ? __uint_as_float(sign | ((uint32_t)(eh + 1 + 127) << 23))
+                                      : __uint_as_float(sign | ((uint32_t)(eh + 127) << 23) | (uint32_t)(mh & 0x7FFFFFu));
+  float lo = (float)rem * __uint_as_float((uint32_t)(eh - 52 + 127) << 23);
+  if (sign) lo = -lo;
+  return df{hi, lo};
+}
+
+// sin(x) as df; |x| < 2^20 (the reduction's exact range), else FP64 sin
+__device__ __forceinline__ df df_sin(double x) {
+  if (!(fabs(x) < 1048576.0)) return df_from_double(sin(x));
+  const float k = rintf(df_from_double(x).hi * TWO_OVER_PI);
+  // r = x - k * (p1 + p2 + p3): k * p1 is exact in FP64 (45 bits), so one FP64
+  // fma gives x - k p1 rounded once; the smaller pieces follow in df
+  df r = df_from_double(fma(-f2d(k), f2d(PIO2_1), x));
+  r = df_add(r, df_neg(two_prod(k, PIO2_2)));
+  r = df_add(r, df{-k * PIO2_3, 0.f});
+  const int q = ((int)k) & 3;
+  const df x2 = df_mul(r, r);
+  df p;
+  if (q & 1) {               // cos(r) = sum (-1)^n r^(2n) / (2n)!
+    float t = COS_C[11][0];
+    for (int n = 10; n >= 6; --n) t = fmaf(t, x2.hi, COS_C[n][0]);
+    p = df{t, 0.f};
+    for (int n = 5; n >= 0; --n) p = df_add(df_mul(p, x2), df{COS_C[n][0], COS_C[n][1]});
+  } else {                   // sin(r) = r * sum (-1)^n r^(2n) / (2n+1)!
+    float t = SIN_C[11][0];
+    for (int n = 10; n >= 5; --n) t = fmaf(t, x2.hi, SIN_C[n][0]);
+    p = df{t, 0.f};
+    for (int n = 4; n >= 0; --n) p = df_add(df_mul(p, x2), df{SIN_C[n][0], SIN_C[n][1]});
+    p = df_mul(p, r);
+  }
+  return (q & 2) ? df_neg(p) : p;
+}
+
+}  // namespace dfm
+}  // namespace be

@@ -99,5 +99,7 @@ struct EParams {
 };
 
 cudaError_t launch_element(const EParams &p, int grid, int block, cudaStream_t s);
+// same strategy in double-float arithmetic on the FP32 pipe (FP64 accuracy)
+cudaError_t launch_element_df(const EParams &p, int grid, int block, cudaStream_t s);
 
 }  // namespace be

@@ -99,6 +99,32 @@ def test_dg_gradient_integers_bit_exact():
             assert np.array_equal(got[x], ref[x][0])
 
 
+def test_dg_gradient_fp64_pipe_variant():
+    E = 1001
+    D, G, a, b = W.dg_gradient(E=E)
+    arrs = dict(D=D, G=G, a=a, b=b)
+    text = W.dg_gradient_spec(E=E)
+    got, _ = run(text, arrs, cfg=be.make_config(be.STRAT_ELEMENT, (32, 256, 1)))
+    ref = ev.evaluate(text, arrs)
+    for x in range(3):
+        assert_close(got[x], ref[x][0], ref[x][1], 1e-12)
+
+
+def test_df_sine_matches_fp64_sin():
+    """The fused producer sin(a) * b with b = 1 through an identity operator
+    returns the double-float sine itself; compare with CUDA's FP64 sin."""
+    E, N = 4096, 35
+    g = np.random.default_rng(12)
+    a = np.concatenate([g.standard_normal((E // 2, N)) * 3, g.uniform(-1e4, 1e4, (E // 2, N))])
+    a[0, :5] = [0.0, np.pi, -np.pi / 2, 1e-30, 2.0 ** 21]
+    text = (f"ij,ej->ei | D,U ; D:f64[{N},{N}] ; a:f64[{E},{N}] ; b:f64[{E},{N}] ; "
+            f"U(e,j) := sin(a[e,j])*b[e,j]")
+    got, _ = run(text, dict(D=np.eye(N), a=a, b=np.ones((E, N))))
+    ref = torch.sin(torch.from_numpy(a).to(DEV)).cpu().numpy()
+    # double-float carries about 46-48 significant bits
+    assert np.max(np.abs(got[0] - ref)) <= 1e-14
+
+
 @pytest.mark.parametrize("tile", [8, 32, 64])
 def test_dg_gradient_tiles(tile):
     E = 2048 + 17
