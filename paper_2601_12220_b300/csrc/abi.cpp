@@ -456,7 +456,7 @@ static int do_execute(be_ctx *x, const be_einsum *hc, const be_config *cfg, int3
     return BE_OK;
   }
   if (strategy == BE_STRAT_ELEMENT) {
-    int block = c.tile[1] > 0 ? c.tile[1] : 256;
+    int block = c.tile[1] > 0 ? c.tile[1] : (c.tile[2] == 1 ? 256 : element_df_block(ep));
     int dev = 0, sms = 148, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -76,7 +76,32 @@ __device__ __forceinline__ double f2d(float f) {
   return __longlong_as_double((long long)(s | (e << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29)));
 }
 
-__device__ __forceinline__ double df_to_double(df x) { return f2d(x.hi) + f2d(x.lo); }
+// hi + lo as a double, by integer operations on the bits (no FP64
+// instruction): hi's 24-bit significand fills the top of the 53-bit one and
+// lo's is aligned below it and added or subtracted; bits of lo below the
+// double's last place are dropped, so the result is within one unit in the
+// last place of hi + lo.  Zeros and non-normal parts use the FP64 path.
+__device__ __forceinline__ double df_to_double(df x) {
+  const uint32_t uh = __float_as_uint(x.hi), ul = __float_as_uint(x.lo);
+  const int eh = (int)((uh >> 23) & 0xFFu), el = (int)((ul >> 23) & 0xFFu);
+  if (eh == 0 || eh == 0xFF || (ul & 0x7FFFFFFFu) == 0u) return f2d(x.hi) + f2d(x.lo);
+  if (el == 0 || el == 0xFF) return f2d(x.hi) + f2d(x.lo);
+  const int64_t mh = (int64_t)((uh & 0x7FFFFFu) | 0x800000u) << 29;   // value mh * 2^(eh-127-52)
+  const int sh = 29 - (eh - el);                                       // lo's alignment
+  int64_t ml = (int64_t)((ul & 0x7FFFFFu) | 0x800000u);
+  ml = sh >= 0 ? (ml << sh) : (sh > -40 ? (ml >> (-sh)) : 0);
+  int64_t m = ((uh ^ ul) >> 31) ? mh - ml : mh + ml;
+  int e = eh - 127 + 1023;
+  if (m >= (1ll << 53)) {
+    m >>= 1;
+    ++e;
+  } else if (m < (1ll << 52)) {
+    m <<= 1;
+    --e;
+  }
+  const uint64_t sign = (uint64_t)(uh >> 31) << 63;
+  return __longlong_as_double((long long)(sign | ((uint64_t)e << 52) | ((uint64_t)m & 0xFFFFFFFFFFFFFull)));
+}
 
 // double -> df with |x - hi - lo| <= 2^-48 |x|, by integer operations on the
 // bits when both parts land in FP32's normal range (2^-70 <= |x| < 2^100)
@@ -101,7 +126,8 @@ __device__ __forceinline__ df df_from_double(double x) {
 
 // sin(x) as df; |x| < 2^20 (the reduction's exact range), else FP64 sin
 __device__ __forceinline__ df df_sin(double x) {
-  if (!(fabs(x) < 1048576.0)) return df_from_double(sin(x));
+  // |x| < 2^20 (and finite), tested on the exponent bits
+  if ((int)((__double_as_longlong(x) >> 52) & 0x7FF) >= 1023 + 20) return df_from_double(sin(x));
   const float k = rintf(df_from_double(x).hi * TWO_OVER_PI);
   // r = x - k * (p1 + p2 + p3): k * p1 is exact in FP64 (45 bits), so one FP64
   // fma gives x - k p1 rounded once; the smaller pieces follow in df

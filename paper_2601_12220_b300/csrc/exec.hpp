@@ -101,5 +101,6 @@ struct EParams {
 cudaError_t launch_element(const EParams &p, int grid, int block, cudaStream_t s);
 // same strategy in double-float arithmetic on the FP32 pipe (FP64 accuracy)
 cudaError_t launch_element_df(const EParams &p, int grid, int block, cudaStream_t s);
+int element_df_block(const EParams &p);   // block size matching one tile's work items
 
 }  // namespace be

@@ -7,6 +7,8 @@
 // second float, and the fused producer u = sin(a) * b is evaluated with the
 // df sine.  Results reach FP64 accuracy (about 2^-46 of the absolute
 // contraction) while the FP64 pipe only adds the two halves of each output.
+#include <algorithm>
+
 #include "df_math.cuh"
 #include "exec.hpp"
 
@@ -24,7 +26,9 @@ __device__ __forceinline__ df prod_df(const EProd &q, int64_t e, int k) {
   return dfm::df_mul(dfm::df_sin(a), dfm::df_from_double(b));
 }
 
-__global__ void __launch_bounds__(256) element_df_kernel(const __grid_constant__ EParams p) {
+constexpr int DF_EPT = 4;   // elements per thread in the contraction phase
+
+__global__ void __launch_bounds__(512, 2) element_df_kernel(const __grid_constant__ EParams p) {
   extern __shared__ float2 smf[];
   const int R = p.R, NI = p.NI, NJ = p.NJ, TE = p.tile_e;
   float2 *Ds = smf;                                   // [R][NI][NJ]
@@ -60,32 +64,53 @@ __global__ void __launch_bounds__(256) element_df_kernel(const __grid_constant__
       }
     }
     __syncthreads();
-    for (int item = tid; item < te * NI; item += nt) {
-      const int el = item / NI, i = item % NI;
+    // each item: one dof i for DF_EPT consecutive elements, so D[r, i, :] is
+    // read once from shared memory for all of them
+    const int groups_e = (te + DF_EPT - 1) / DF_EPT;
+    for (int item = tid; item < groups_e * NI; item += nt) {
+      const int eg = item / NI, i = item % NI;
+      const int el0 = eg * DF_EPT;
+      const int nq = min(DF_EPT, te - el0);
       for (int g = 0; g < p.n_groups; ++g) {
-        df t[EM_MAXR];
-        const float2 *u = Us + (g * TE + el) * NJ;
-        for (int r = 0; r < R; ++r) {
+        df t[DF_EPT][EM_MAXR];
+        const float2 *u0 = Us + (g * TE + el0) * NJ;
+#pragma unroll
+        for (int r = 0; r < EM_MAXR; ++r) {
+          if (r >= R) break;
           const float2 *d = Ds + (r * NI + i) * NJ;
-          float s = 0.f, c = 0.f;
+          float s[DF_EPT], c[DF_EPT];
+#pragma unroll
+          for (int q = 0; q < DF_EPT; ++q) s[q] = c[q] = 0.f;
           for (int j = 0; j < NJ; ++j) {
-            const float2 dj = d[j], uj = u[j];
-            dfm::dot_acc(s, c, df{dj.x, dj.y}, df{uj.x, uj.y});
+            const float2 dj = d[j];
+#pragma unroll
+            for (int q = 0; q < DF_EPT; ++q) {
+              const float2 uq = u0[q * NJ + j];       // beyond te: unused values, never stored
+              dfm::dot_acc(s[q], c[q], df{dj.x, dj.y}, df{uq.x, uq.y});
+            }
           }
-          t[r] = dfm::fast_two_sum(s, c);
+#pragma unroll
+          for (int q = 0; q < DF_EPT; ++q) t[q][r] = dfm::fast_two_sum(s[q], c[q]);
         }
         for (int k = 0; k < p.n_rows; ++k) {
           if (p.rows[k].group != g) continue;
-          df acc;
-          if (p.has_g) {
-            const float2 *gg = Gs + (k * TE + el) * R;
-            float s = 0.f, c = 0.f;
-            for (int r = 0; r < R; ++r) dfm::dot_acc(s, c, df{gg[r].x, gg[r].y}, t[r]);
-            acc = dfm::fast_two_sum(s, c);
-          } else {
-            acc = t[0];
+#pragma unroll
+          for (int q = 0; q < DF_EPT; ++q) {
+            if (q >= nq) break;
+            const int el = el0 + q;
+            df acc;
+            if (p.has_g) {
+              const float2 *gg = Gs + (k * TE + el) * R;
+              float s = 0.f, c = 0.f;
+#pragma unroll
+              for (int r = 0; r < EM_MAXR; ++r)
+                if (r < R) dfm::dot_acc(s, c, df{gg[r].x, gg[r].y}, t[q][r]);
+              acc = dfm::fast_two_sum(s, c);
+            } else {
+              acc = t[q][0];
+            }
+            p.rows[k].out[(e0 + el) * NI + i] = dfm::df_to_double(acc);
           }
-          p.rows[k].out[(e0 + el) * NI + i] = dfm::df_to_double(acc);
         }
       }
     }
@@ -94,7 +119,13 @@ __global__ void __launch_bounds__(256) element_df_kernel(const __grid_constant__
 
 }  // namespace
 
+int element_df_block(const EParams &p) {
+  const int items = (p.tile_e + DF_EPT - 1) / DF_EPT * p.NI;
+  return std::min(512, std::max(32, (items + 31) / 32 * 32));
+}
+
 cudaError_t launch_element_df(const EParams &p, int grid, int block, cudaStream_t s) {
+  if (p.tile_e % DF_EPT) return cudaErrorInvalidValue;          // element groups never straddle a tile
   const size_t smem = sizeof(float2) * ((size_t)p.R * p.NI * p.NJ + (size_t)p.n_groups * p.tile_e * p.NJ +
                                         (size_t)p.n_rows * p.tile_e * p.R);
   if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;

@@ -328,6 +328,7 @@ int plan_element(const Einsum &e, const std::vector<BufIn> &bufs, const std::vec
   }
   p.n_groups = (int)uargs.size();
   int te = cfg.tile[0] > 0 ? cfg.tile[0] : (p.NI >= 16 ? 32 : 256);
+  if (cfg.tile[2] != 1) te = (te + 3) / 4 * 4;   // the double-float kernel works on groups of 4 elements
   p.tile_e = te;
   size_t smem = sizeof(double) * ((size_t)p.R * p.NI * p.NJ + (size_t)p.n_groups * te * p.NJ + (size_t)p.n_rows * te * p.R);
   if (smem > 200 * 1024) { why = "tile does not fit shared memory"; return EUNSUPPORTED; }
