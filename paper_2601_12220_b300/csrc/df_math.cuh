@@ -152,5 +152,51 @@ __device__ __forceinline__ df df_sin(double x) {
   return (q & 2) ? df_neg(p) : p;
 }
 
+// ---- table-driven sine: sin(x0 + d) = sin x0 cos d + cos x0 sin d ----
+// x0 = k / 256, k in [-SIN_TAB_K, SIN_TAB_K] covers the reduced range |r| <= pi/4;
+// the table holds sin x0, cos x0 as df (s.hi, s.lo, c.hi, c.lo), filled once
+// per CTA with df_sin (exact argument k / 256).  |d| <= 2^-9, so
+// sin d = d - d^3/6 and cos d = 1 - d^2/2 + d^4/24 leave terms below 2^-51.
+constexpr int SIN_TAB_K = 202;
+constexpr int SIN_TAB_N = 2 * SIN_TAB_K + 1;
+
+__device__ __forceinline__ void sin_table_fill(float4 *tab) {
+  for (int k = threadIdx.x; k < SIN_TAB_N; k += blockDim.x) {
+    const double x0 = (double)(k - SIN_TAB_K) / 256.0;
+    const df s = df_sin(x0);
+    // cos x0 by its series directly (|x0| <= 0.79)
+    const df xr = df_from_double(x0);
+    const df x2 = df_mul(xr, xr);
+    float t = COS_C[11][0];
+    for (int n = 10; n >= 6; --n) t = fmaf(t, x2.hi, COS_C[n][0]);
+    df cc{t, 0.f};
+    for (int n = 5; n >= 0; --n) cc = df_add(df_mul(cc, x2), df{COS_C[n][0], COS_C[n][1]});
+    tab[k] = make_float4(s.hi, s.lo, cc.hi, cc.lo);
+  }
+}
+
+// sin(x) as df using the table (|x| < 2^20, else FP64 sin)
+__device__ __forceinline__ df df_sin_tab(double x, const float4 *tab) {
+  if ((int)((__double_as_longlong(x) >> 52) & 0x7FF) >= 1023 + 20) return df_from_double(sin(x));
+  const float k = rintf(df_from_double(x).hi * TWO_OVER_PI);
+  df r = df_from_double(fma(-f2d(k), f2d(PIO2_1), x));
+  r = df_add(r, df_neg(two_prod(k, PIO2_2)));
+  r = df_add(r, df{-k * PIO2_3, 0.f});
+  const float fk = rintf(r.hi * 256.f);
+  const df d = df_add(r, df{-fk * 0.00390625f, 0.f});             // r - k/256, exact grid point
+  const float4 t = tab[(int)fk + SIN_TAB_K];
+  const float d3 = d.hi * d.hi * d.hi;
+  const df sd = df_add(d, df{-d3 * (1.f / 6.f), 0.f});
+  df d2 = two_prod(d.hi, d.hi);
+  d2.lo = fmaf(2.f * d.hi, d.lo, d2.lo);
+  const df cd = df_add(df_add(df{1.f, 0.f}, df{-0.5f * d2.hi, -0.5f * d2.lo}), df{d2.hi * d2.hi * (1.f / 24.f), 0.f});
+  const df s0{t.x, t.y}, c0{t.z, t.w};
+  const int q = ((int)k) & 3;
+  df res;
+  if (q & 1) res = df_add(df_mul(c0, cd), df_neg(df_mul(s0, sd)));   // cos r
+  else res = df_add(df_mul(s0, cd), df_mul(c0, sd));                   // sin r
+  return (q & 2) ? df_neg(res) : res;
+}
+
 }  // namespace dfm
 }  // namespace be

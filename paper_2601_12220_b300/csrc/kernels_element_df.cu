@@ -18,12 +18,12 @@ namespace {
 
 using dfm::df;
 
-__device__ __forceinline__ df prod_df(const EProd &q, int64_t e, int k) {
+__device__ __forceinline__ df prod_df(const EProd &q, int64_t e, int k, const float4 *sin_tab) {
   const double a = q.a.ptr[e * q.a.se + k * q.a.sk];
   if (q.kind == 0) return dfm::df_from_double(a);
   const double b = q.b.ptr[e * q.b.se + k * q.b.sk];
   if (q.kind == 2) return dfm::df_mul(dfm::df_from_double(a), dfm::df_from_double(b));
-  return dfm::df_mul(dfm::df_sin(a), dfm::df_from_double(b));
+  return dfm::df_mul(dfm::df_sin_tab(a, sin_tab), dfm::df_from_double(b));
 }
 
 constexpr int DF_EPT = 4;   // elements per thread in the contraction phase
@@ -34,7 +34,10 @@ __global__ void __launch_bounds__(512, 2) element_df_kernel(const __grid_constan
   float2 *Ds = smf;                                   // [R][NI][NJ]
   float2 *Us = Ds + R * NI * NJ;                      // [groups][TE][NJ]
   float2 *Gs = Us + p.n_groups * TE * NJ;             // [rows][TE][R]
+  const int n_f2 = R * NI * NJ + p.n_groups * TE * NJ + p.n_rows * TE * R;
+  float4 *sin_tab = (float4 *)(smf + n_f2 + (n_f2 & 1));              // 16-byte aligned
   const int tid = threadIdx.x, nt = blockDim.x;
+  dfm::sin_table_fill(sin_tab);
 
   for (int idx = tid; idx < R * NI * NJ; idx += nt) {
     const int r = idx / (NI * NJ), rem = idx % (NI * NJ);
@@ -51,7 +54,7 @@ __global__ void __launch_bounds__(512, 2) element_df_kernel(const __grid_constan
     for (int idx = tid; idx < p.n_groups * te * NJ; idx += nt) {
       const int g = idx / (te * NJ), rem = idx % (te * NJ);
       const int el = rem / NJ, j = rem % NJ;
-      const df u = prod_df(p.groups[g], e0 + el, j);
+      const df u = prod_df(p.groups[g], e0 + el, j, sin_tab);
       Us[(g * TE + el) * NJ + j] = make_float2(u.hi, u.lo);
     }
     if (p.has_g) {
@@ -127,7 +130,8 @@ int element_df_block(const EParams &p) {
 cudaError_t launch_element_df(const EParams &p, int grid, int block, cudaStream_t s) {
   if (p.tile_e % DF_EPT) return cudaErrorInvalidValue;          // element groups never straddle a tile
   const size_t smem = sizeof(float2) * ((size_t)p.R * p.NI * p.NJ + (size_t)p.n_groups * p.tile_e * p.NJ +
-                                        (size_t)p.n_rows * p.tile_e * p.R);
+                                        (size_t)p.n_rows * p.tile_e * p.R + 1) +
+                      sizeof(float4) * dfm::SIN_TAB_N;
   if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
   static bool attr = false;
   if (!attr) {
