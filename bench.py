@@ -74,6 +74,10 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # 3*35*35 + 3*3*35 terms, plus 3 per normalisation of 2*105 results (the
 # sine and the conversions are not counted, so this is a lower bound)
 DF_FLOPS_PER_ELEMENT = 15 * (3 * 35 * 35 + 3 * 3 * 35) + 3 * 2 * 105
+# bf16 MMA flops the tensor-core variant issues per element: 21 digit
+# products x 3 K-steps of 16 x 144 accumulator columns (three blocks of 48:
+# 35 dofs x 3 terms padded to 4 columns per dof) x 2
+TC_MMA_FLOPS_PER_ELEMENT = 21 * 3 * 16 * 144 * 2
 
 
 def kernel_traffic(kernel):
@@ -288,24 +292,36 @@ def run_ours(args):
     d2h = sum(o.nbytes for o in host_outs)
 
     peaks = load_peaks()
-    kernel = ({"name": "element_kernel", "source": "kernels_element.cu", "profile": "element_kernel_dg_p4.md"}
-              if args.element_variant == 1 else
-              {"name": "element_df_kernel", "source": "kernels_element_df.cu", "profile": "element_df_kernel_dg_p4.md"})
+    # the default for this shape is the tensor-core variant (3)
+    variant = args.element_variant or 3
+    kernel = {1: {"name": "element_kernel", "source": "kernels_element.cu", "profile": "element_kernel_dg_p4.md"},
+              2: {"name": "element_df_kernel", "source": "kernels_element_df.cu",
+                  "profile": "element_df_kernel_dg_p4.md"},
+              3: {"name": "element_tc_kernel", "source": "kernels_element_tc.cu",
+                  "profile": "element_tc_kernel_dg_p4.md"}}[variant]
     ach_gb = byts / (kms * 1e-3) / 1e9
     traffic = kernel_traffic(kernel)
-    if args.element_variant == 1:     # FP64 pipe
-        ach_tf, peak, src = flops / (kms * 1e-3) / 1e12, FP64_PEAK_TFLOPS, "nominal B300 FP64 (1.25 TFLOP/s)"
-        what = "algorithmic FP64 flops"
-    else:                             # double-float on the FP32 pipe
-        ach_tf = DF_FLOPS_PER_ELEMENT * E / (kms * 1e-3) / 1e12
-        peak, src = FP32_PEAK_TFLOPS, "FP32 pipe from unit counts and clock: 148 SMs x 128 lanes x 2 x 2.032 GHz"
-        what = f"FP32 flops of the compensated dot products ({DF_FLOPS_PER_ELEMENT} per element)"
-    roofline = {"kernel": kernel["name"], "bound": "alu", "achieved": ach_tf, "peak": peak,
-                "unit": "TFLOP/s", "frac": ach_tf / peak, "counts": what,
-                "peak_source": src,
-                "traffic": traffic, "algorithmic_bytes": byts,
-                "hbm": {"achieved": ach_gb, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                        "frac": ach_gb / peaks["hbm_gbs"], "peak_source": peaks["source"]}}
+    hbm = {"achieved": ach_gb, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach_gb / peaks["hbm_gbs"],
+           "peak_source": peaks["source"]}
+    if variant == 3:                  # tensor cores: the path's roofline is HBM
+        mma_tf = TC_MMA_FLOPS_PER_ELEMENT * E / (kms * 1e-3) / 1e12
+        roofline = {"kernel": kernel["name"], "bound": "hbm", "achieved": ach_gb, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": ach_gb / peaks["hbm_gbs"], "peak_source": peaks["source"],
+                    "traffic": traffic, "algorithmic_bytes": byts,
+                    "tensor": {"achieved": mma_tf, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                               "frac": mma_tf / peaks["bf16_tflops"],
+                               "counts": f"bf16 digit-product MMA flops issued ({TC_MMA_FLOPS_PER_ELEMENT} per element)"}}
+    else:
+        if variant == 1:              # FP64 pipe
+            ach_tf, peak, src = flops / (kms * 1e-3) / 1e12, FP64_PEAK_TFLOPS, "nominal B300 FP64 (1.25 TFLOP/s)"
+            what = "algorithmic FP64 flops"
+        else:                         # double-float on the FP32 pipe
+            ach_tf = DF_FLOPS_PER_ELEMENT * E / (kms * 1e-3) / 1e12
+            peak, src = FP32_PEAK_TFLOPS, "FP32 pipe from unit counts and clock: 148 SMs x 128 lanes x 2 x 2.032 GHz"
+            what = f"FP32 flops of the compensated dot products ({DF_FLOPS_PER_ELEMENT} per element)"
+        roofline = {"kernel": kernel["name"], "bound": "alu", "achieved": ach_tf, "peak": peak,
+                    "unit": "TFLOP/s", "frac": ach_tf / peak, "counts": what,
+                    "peak_source": src, "traffic": traffic, "algorithmic_bytes": byts, "hbm": hbm}
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -313,7 +329,8 @@ def run_ours(args):
                                    f"u=sin(a)*b fused, E={E}", "E": E, "ndof": NDOF, "b": DIM,
                        "global_batch": world * E, "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2 ({byts / 1e6:.0f} MB per step), no flush",
-                       "strategy": {1: "generic", 2: "element"}.get(strat, str(strat))},
+                       "strategy": {1: "generic", 2: "element"}.get(strat, str(strat)),
+                       "element_variant": {1: "fp64 pipe", 2: "double-float", 3: "tensor cores"}[variant]},
             "tflops": world * flops / (ms * 1e-3) / 1e12, "kernel_ms": kms,
             "roofline": roofline,
             "e2e": {"value": world * byts / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,

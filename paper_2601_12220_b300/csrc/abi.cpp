@@ -456,7 +456,25 @@ static int do_execute(be_ctx *x, const be_einsum *hc, const be_config *cfg, int3
     return BE_OK;
   }
   if (strategy == BE_STRAT_ELEMENT) {
-    int block = c.tile[1] > 0 ? c.tile[1] : (c.tile[2] == 1 ? 256 : element_df_block(ep));
+    // tile[2]: 1 = FP64 pipe, 2 = double-float on the FP32 pipe, 3 = tensor
+    // cores; unset = tensor cores where the shape allows, else double-float
+    std::string why_tc;
+    const bool tc_ok = element_tc_supported(ep, why_tc);
+    const int variant = c.tile[2] > 0 ? c.tile[2] : (tc_ok ? 3 : 2);
+    if (variant == 3) {
+      if (!tc_ok) return fail(BE_EUNSUPPORTED, "tensor-core element variant: " + why_tc);
+      int *status = nullptr;
+      if (x) {
+        std::lock_guard<std::mutex> g(x->mu);
+        if ((st = ensure_status(x))) return st;
+        status = x->status;
+      }
+      KernelMark km(x, BE_KERNEL_ELEMENT, s);
+      ce = launch_element_tc(ep, status, s);
+      if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("launch: ") + cudaGetErrorString(ce));
+      return BE_OK;
+    }
+    int block = c.tile[1] > 0 ? c.tile[1] : (variant == 1 ? 256 : element_df_block(ep));
     int dev = 0, sms = 148, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -467,8 +485,7 @@ static int do_execute(be_ctx *x, const be_einsum *hc, const be_config *cfg, int3
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * per_sm));
     if (ep.E > 0) {
       KernelMark km(x, BE_KERNEL_ELEMENT, s);
-      // tile[2]: 1 = FP64 pipe, otherwise double-float on the FP32 pipe
-      ce = c.tile[2] == 1 ? launch_element(ep, grid, block, s) : launch_element_df(ep, grid, block, s);
+      ce = variant == 1 ? launch_element(ep, grid, block, s) : launch_element_df(ep, grid, block, s);
     }
   } else {
     for (int i = 0; i < e.b && ce == cudaSuccess; ++i) {
@@ -619,6 +636,10 @@ static void tune_candidates(const Einsum &e, const std::vector<BufIn> &bi, const
   std::memset(&c, 0, sizeof(c));
   c.strategy = BE_STRAT_ELEMENT;
   if (precision == BE_PREC_FP64 && plan_element(e, bi, bo, c, ep, why) == OK) {
+    if (element_tc_supported(ep, why)) {
+      c.tile[2] = 3;                                   // the tensor-core variant has one launch shape
+      out.push_back(c);
+    }
     for (int variant : {2, 1})
       for (int te : {8, 16, 32, 64, 128})
         for (int blk : {128, 256}) {

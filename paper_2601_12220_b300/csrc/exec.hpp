@@ -102,5 +102,9 @@ cudaError_t launch_element(const EParams &p, int grid, int block, cudaStream_t s
 // same strategy in double-float arithmetic on the FP32 pipe (FP64 accuracy)
 cudaError_t launch_element_df(const EParams &p, int grid, int block, cudaStream_t s);
 int element_df_block(const EParams &p);   // block size matching one tile's work items
+// same strategy with t = u D^T as a digit-split GEMM on the tcgen05 tensor
+// cores (FP64 accuracy); status receives BE_ETIMEOUT if a bounded wait expires
+bool element_tc_supported(const EParams &p, std::string &why);
+cudaError_t launch_element_tc(const EParams &p, int *status, cudaStream_t s);
 
 }  // namespace be

@@ -1,0 +1,552 @@
+// Element strategy on the tensor cores: the same batched einsums as
+// element_kernel (R_k[e,i] = sum_{r,j} D[r,i,j] g_k[e,r] u[e,j], D shared by
+// all elements, Sec. "Batched einsums in DG-FEM Operators"), with the hoisted
+// contraction t[e,r,i] = sum_j D[r,i,j] u[e,j] evaluated as a GEMM on
+// tcgen05 (M = 128 elements, N = (i, r) pairs, K = j) to FP64 accuracy by
+// an error-free split of both operands into small integer digits:
+//
+//  * u[e, :] (one element, produced by the fused producer in double-float)
+//    is scaled by 2^-k_e so that every |v_j| < 1 and written as six
+//    balanced base-512 digits, v = 2^-8 sum_q d_q 2^-9q with |d_q| <= 256;
+//    d_q 2^-9q is exact in bf16.  Each row n = (r, i) of D gets its own
+//    2^-k_n and digits c_p the same way (from FP64, once per CTA).
+//  * sum_j D[n,j] u[e,j] = 2^(k_e + k_n - 16) sum_{p,q} sum_j (c_p 2^-9p)(d_q 2^-9q).
+//    The digit products are grouped by level L = p + q.  Levels 0..3 each
+//    accumulate in their own FP32 tensor-memory accumulator: every partial
+//    sum is an integer multiple of 2^-9L below 2^24 * 2^-9L (at most 4 pairs
+//    x 64 terms x 2^16), so the tensor core adds them exactly.  Levels 4 and
+//    5 share a fifth accumulator (its truncation stays below 2^-49 of
+//    NJ max|u| max|D|); levels 6 and up are dropped (below 2^-50 of the same).
+//  * The epilogue adds the five accumulators of each column in double-float,
+//    applies the scales, contracts with g_k[e, :] in double-float and stores
+//    FP64.
+// Bound per output: |err| <= 2^-48 NJ max_j|u_j| sum_r |g_r| max_j|D_rij|
+// plus double-float rounding (about 2^-46 of the absolute contraction S).
+// The bound is normwise (the digits share one exponent per row): on dense
+// data of moderate dynamic range it is far below 1e-12 S (about 2e-15 S on
+// the DG workload), but for rows whose entries span many orders of
+// magnitude it can exceed 1e-12 S; element_df_kernel is the componentwise
+// path for such data.
+//
+// Warp roles (416 threads, one CTA per SM, persistent over tiles of 128
+// elements): warps 0-3 produce the digit planes of u (thread m = element m of
+// the tile) into shared memory in the 128-byte-swizzle K-major layout;
+// warp 4 issues the MMAs (one thread) into three tensor-memory slots of
+// 5 accumulators x 32 columns, one column block (up to 32 (i, r) columns) per
+// slot; warps 5-12 drain a slot (two warps per TMEM lane quarter, one per
+// half of the block's columns) while the next blocks accumulate.  Every
+// accumulator starts on a 32-column boundary: with accumulators at 48-column
+// offsets, MMAs issued back to back into neighbouring accumulators gave
+// wrong sums on B300 (correct when the issue was slowed down).  Every
+// wait is bounded: on expiry the CTA records BE_ETIMEOUT, stops issuing and
+// frees its tensor memory after its MMAs complete.
+#include <algorithm>
+
+#include <cuda_bf16.h>
+
+#include "df_math.cuh"
+#include "exec.hpp"
+#include "tc_common.cuh"
+
+namespace be {
+
+namespace {
+
+using dfm::df;
+
+constexpr int TC_M = 128;                       // elements per tile
+constexpr int TC_P = 6;                         // digits per operand
+constexpr int TC_LEV = 5;                       // accumulators per column block
+constexpr int TC_NCOL = 32;                     // accumulator columns per level (32-column aligned)
+constexpr int TC_SLOT = TC_LEV * TC_NCOL;       // 160 columns per slot
+constexpr int TC_NSLOT = 3;                     // 480 of the 512 tensor-memory columns
+constexpr int TC_APLANE = TC_M * 128;           // one digit plane of u: 128 rows x 128 bytes
+constexpr int NPROD = 128, NEPI = 256;
+constexpr int TC_THREADS = NPROD + 32 + NEPI;   // producer warps 0-3, MMA warp 4, epilogue warps 5-12
+constexpr int TC_MAXROWS = 4;                   // einsums (rows) per launch
+constexpr int TC_MAXNB = 160;                   // B rows (all column blocks)
+
+// the 21 digit products (level, digit of D, digit of u) with level <= 5, in
+// accumulator order: levels 0..3 alone, levels 4 and 5 into accumulator 4
+struct TcParams {
+  EParams p;
+  int *status;
+  int ncb, IB, NBtot, KS, NG;                   // column blocks, i per block, B rows, K steps, j groups of 8
+  int ncol[8], n0[8];                           // per block: MMA N and first B row
+};
+
+// scale exponent k with |x| < 2^k for the largest |x| of a row, clamped so
+// that the scaled values stay in FP32's normal range
+__device__ __forceinline__ int row_exp(double mx) {
+  const int ex = (int)((__double_as_longlong(mx) >> 52) & 0x7FF);
+  if (ex == 0) return -100;
+  return min(100, max(-100, ex - 1023 + 1));
+}
+__device__ __forceinline__ float pow2f(int k) { return __uint_as_float((uint32_t)(k + 127) << 23); }   // |k| <= 126
+__device__ __forceinline__ double pow2d(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
+
+// six balanced base-512 digits of v (|v| < 1 + 2^-20), each times 2^-9q
+__device__ __forceinline__ void digits_f64(double v, float *d) {
+#pragma unroll
+  for (int q = 0; q < TC_P - 1; ++q) {
+    const double t = rint(v * 256.0);
+    v = fma(t, -0.00390625, v) * 512.0;         // exact
+    d[q] = (float)t * pow2f(-9 * q);
+  }
+  d[TC_P - 1] = (float)rint(v * 256.0) * pow2f(-9 * (TC_P - 1));
+}
+// the same for v = h + l in double-float: every step is exact
+__device__ __forceinline__ void digits_df(float h, float l, float *d) {
+  const float MAGIC = 12582912.0f;              // 1.5 * 2^23: adding it rounds to an integer
+#pragma unroll
+  for (int q = 0; q < TC_P - 1; ++q) {
+    const float t = __fadd_rn(__fmaf_rn(h, 256.0f, MAGIC), -MAGIC);
+    h = __fmaf_rn(t, -0.00390625f, h);          // h - t/256, exact
+    const df s = dfm::two_sum(h, l);
+    h = s.hi * 512.0f;
+    l = s.lo * 512.0f;
+    d[q] = t * pow2f(-9 * q);
+  }
+  d[TC_P - 1] = __fadd_rn(__fmaf_rn(h, 256.0f, MAGIC), -MAGIC) * pow2f(-9 * (TC_P - 1));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // lo at the lower address
+  return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// byte offset of the 16-byte chunk g (8 values of K) of row m in a 128-byte
+// swizzled K-major plane (1024-byte aligned)
+__device__ __forceinline__ uint32_t swz(int m, int g) { return (uint32_t)(m * 128 + ((g ^ (m & 7)) << 4)); }
+
+// bound on |u_j| for the row's scale (|sin a| <= 1)
+__device__ __forceinline__ double prod_bound(const EProd &q, int64_t e, int j) {
+  if (q.kind == 1) return fabs(q.b.ptr[e * q.b.se + j * q.b.sk]);
+  const double a = fabs(q.a.ptr[e * q.a.se + j * q.a.sk]);
+  return q.kind == 2 ? a * fabs(q.b.ptr[e * q.b.se + j * q.b.sk]) : a;
+}
+
+// operands of the flat values f, f + 128, f + 256, f + 384 of a tile
+__device__ __forceinline__ void load_batch(const EProd &q, int64_t e0, int f, int n, int NJ, double *av, double *bv) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int g = f + u * 128;
+    const int m = g < n ? g / NJ : 0, j = g - m * NJ;
+    const int64_t e = e0 + m;
+    av[u] = g < n ? q.a.ptr[e * q.a.se + j * q.a.sk] : 0.0;
+    bv[u] = (g < n && q.kind != 0) ? q.b.ptr[e * q.b.se + j * q.b.sk] : 0.0;
+  }
+}
+
+// named barrier of the four producer warps, and the same barrier returning
+// the AND of a predicate over them (so that all of them leave together)
+__device__ __forceinline__ void prod_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ bool prod_all(bool v) {
+  uint32_t r;
+  asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred p, 1, 128, q;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(r)
+               : "r"((uint32_t)v)
+               : "memory");
+  return r != 0;
+}
+
+// L2 prefetch of rows e1 .. e1+te1-1 (j = 0..NJ-1) of a view whose rows are
+// contiguous; the range is shrunk to 16-byte boundaries inside it
+__device__ __forceinline__ void prefetch_rows(const EView &v, int64_t e1, int te1, int NJ) {
+  if (v.sk != 1 || te1 <= 0) return;
+  const uintptr_t lo = (uintptr_t)(v.ptr + e1 * v.se);
+  const uintptr_t hi = (uintptr_t)(v.ptr + (e1 + te1 - 1) * v.se + NJ);
+  const uintptr_t a = (lo + 15) & ~(uintptr_t)15, b = hi & ~(uintptr_t)15;
+  if (b <= a) return;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(b - a)) : "memory");
+}
+
+template <int R>
+__global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_constant__ TcParams tp) {
+  constexpr int RP = R == 3 ? 4 : R;            // columns per i (R padded to divide 8)
+  constexpr int IPC = 8 / RP;                   // i per 8-column chunk
+  constexpr int IB = TC_NCOL / RP;              // i per column block (4 chunks)
+  constexpr int H0 = IB / 2;                    // i per epilogue half (2 chunks, 16 columns)
+  const EParams &p = tp.p;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *Bp = smem;                                       // TC_P planes x NBtot rows x 128 B
+  const int bplane = tp.NBtot * 128;
+  uint8_t *Ap = Bp + TC_P * bplane;                         // TC_P planes x 128 rows x 128 B
+  float4 *sin_tab = (float4 *)(Ap + TC_P * TC_APLANE);
+  int *kD = (int *)(sin_tab + dfm::SIN_TAB_N);              // [TC_MAXNB]
+  int *kU = kD + TC_MAXNB;                                  // [2][TC_M]
+  int *mxw = kU + 2 * TC_M;                                 // [TC_M] high words of the row bounds
+  uint64_t *bars = (uint64_t *)(mxw + TC_M);
+  uint64_t *a_full = bars, *a_empty = bars + 1, *s_full = bars + 2, *s_empty = bars + 2 + TC_NSLOT;
+  uint64_t *fin = bars + 2 + 2 * TC_NSLOT;
+  uint32_t *tmem_slot = (uint32_t *)(fin + 1);
+  volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int NJ = p.NJ, NI = p.NI;
+
+  if (tid == 0) {
+    tc::mbar_init(a_full, NPROD);
+    tc::mbar_init(a_empty, 1);
+    for (int b = 0; b < TC_NSLOT; ++b) {
+      tc::mbar_init(&s_full[b], 1);
+      tc::mbar_init(&s_empty[b], NEPI);
+    }
+    tc::mbar_init(fin, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 4) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(tc::smem_u32(tmem_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // zero both operand regions (K padding and padding rows stay zero)
+  {
+    uint4 *z = (uint4 *)smem;
+    const int n16 = (TC_P * bplane + TC_P * TC_APLANE) / 16;
+    for (int k = tid; k < n16; k += TC_THREADS) z[k] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  dfm::sin_table_fill(sin_tab);
+  // B row n -> (block, column c = il * RP + r); scale exponent per real row
+  for (int n = tid; n < tp.NBtot; n += TC_THREADS) {
+    int cb = 0;
+    while (cb + 1 < tp.ncb && n >= tp.n0[cb + 1]) ++cb;
+    const int c = n - tp.n0[cb], il = c / RP, r = c % RP, i = cb * IB + il;
+    double mx = 0.0;
+    if (r < R && il < IB && i < NI)
+      for (int j = 0; j < NJ; ++j) mx = fmax(mx, fabs(p.D[r * p.sr + i * p.si + j * p.sj]));
+    kD[n] = row_exp(mx);
+  }
+  __syncthreads();
+  // digit planes of D: item (row n, group g of 8 values of j)
+  for (int item = tid; item < tp.NBtot * tp.NG; item += TC_THREADS) {
+    const int n = item / tp.NG, g = item % tp.NG;
+    int cb = 0;
+    while (cb + 1 < tp.ncb && n >= tp.n0[cb + 1]) ++cb;
+    const int c = n - tp.n0[cb], il = c / RP, r = c % RP, i = cb * IB + il;
+    if (r >= R || il >= IB || i >= NI) continue;
+    const double sc = pow2d(-kD[n]);
+    uint32_t w[TC_P][4];
+#pragma unroll
+    for (int jp = 0; jp < 4; ++jp) {
+      float d0[TC_P], d1[TC_P];
+      const int j = g * 8 + 2 * jp;
+      digits_f64(j < NJ ? p.D[r * p.sr + i * p.si + j * p.sj] * sc : 0.0, d0);
+      digits_f64(j + 1 < NJ ? p.D[r * p.sr + i * p.si + (j + 1) * p.sj] * sc : 0.0, d1);
+#pragma unroll
+      for (int q = 0; q < TC_P; ++q) w[q][jp] = pack_bf16(d0[q], d1[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < TC_P; ++q)
+      *(uint4 *)(Bp + q * bplane + swz(n, g)) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+  }
+  tc::fence_proxy_async();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const int64_t n_tiles = (p.E + TC_M - 1) / TC_M;
+  int *status = tp.status;
+
+  if (warp < 4) {
+    // ------------------------------------------------------------ producer
+    // flat over the tile's te x NJ values (consecutive threads read
+    // consecutive addresses of row-major operands): pass 1 takes the largest
+    // |u| bound per element (exponent of the row scale), pass 2 evaluates
+    // u in double-float and writes its digits into the planes
+    const EProd &q = p.groups[0];
+    int t = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++t) {
+      const int64_t e0 = tile * TC_M;
+      const int te = (int)(p.E - e0 < TC_M ? p.E - e0 : TC_M);
+      const int n = te * NJ;
+      if (tid == 0 && tile + gridDim.x < n_tiles) {      // next tile's rows into L2
+        const int64_t e1 = e0 + (int64_t)gridDim.x * TC_M;
+        const int te1 = (int)(p.E - e1 < TC_M ? p.E - e1 : TC_M);
+        prefetch_rows(q.a, e1, te1, NJ);
+        if (q.kind != 0) prefetch_rows(q.b, e1, te1, NJ);
+      }
+      mxw[tid] = 0;
+      prod_sync();
+      // pass 1, one warp per row (lanes over j, coalesced), 8 rows in flight
+      for (int r0 = warp; r0 < te; r0 += 4 * 8) {
+        int hw[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int row = r0 + 4 * u;
+          const bool okr = row < te;
+          const double v0 = (okr && lane < NJ) ? prod_bound(q, e0 + row, lane) : 0.0;
+          const double v1 = (okr && lane + 32 < NJ) ? prod_bound(q, e0 + row, lane + 32) : 0.0;
+          hw[u] = max(__double2hiint(v0), __double2hiint(v1));
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int h = __reduce_max_sync(0xffffffffu, hw[u]);
+          if (lane == 0 && r0 + 4 * u < te) mxw[r0 + 4 * u] = h;
+        }
+      }
+      if (!prod_all(tc::mbar_wait(a_empty, ((uint32_t)t & 1u) ^ 1u, abort_flag, status))) break;
+      int *ku = kU + (t & 1) * TC_M;
+      ku[tid] = row_exp(__hiloint2double(mxw[tid], 0));
+      prod_sync();
+      // pass 2: batches of 4 values per thread, the next batch's loads
+      // issued before the current batch is evaluated
+      double an[4], bn[4];
+      load_batch(q, e0, tid, n, NJ, an, bn);
+      for (int f0 = tid; f0 < n; f0 += 4 * NPROD) {
+        double av[4], bv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          av[u] = an[u];
+          bv[u] = bn[u];
+        }
+        if (f0 + 4 * NPROD < n) load_batch(q, e0, f0 + 4 * NPROD, n, NJ, an, bn);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int f = f0 + u * NPROD;
+          if (f < n) {
+            const int m = f / NJ, j = f - m * NJ;
+            df uu;
+            if (q.kind == 0) uu = dfm::df_from_double(av[u]);
+            else if (q.kind == 2) uu = dfm::df_mul(dfm::df_from_double(av[u]), dfm::df_from_double(bv[u]));
+            else uu = dfm::df_mul(dfm::df_sin_tab(av[u], sin_tab), dfm::df_from_double(bv[u]));
+            const float sc = pow2f(-ku[m]);
+            float d[TC_P];
+            digits_df(uu.hi * sc, uu.lo * sc, d);
+            uint8_t *dst = Ap + swz(m, j >> 3) + (j & 7) * 2;
+#pragma unroll
+            for (int k = 0; k < TC_P; ++k) *(__nv_bfloat16 *)(dst + k * TC_APLANE) = __float2bfloat16_rn(d[k]);
+          }
+        }
+      }
+      tc::fence_proxy_async();
+      tc::mbar_arrive(a_full);
+    }
+  } else if (warp == 4) {
+    // ------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+      const uint32_t bbase = tc::smem_u32(Bp);
+      const uint64_t adesc0 = tc::sdesc(tc::smem_u32(Ap));
+      int t = 0;
+      int64_t cnt = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++t) {
+        if (!tc::mbar_wait(a_full, (uint32_t)t & 1u, abort_flag, status)) break;
+        tc::fence_after();
+        for (int cb = 0; cb < tp.ncb; ++cb, ++cnt) {
+          const int slot = (int)(cnt % TC_NSLOT);
+          const uint32_t use = (uint32_t)(cnt / TC_NSLOT);
+          if (!tc::mbar_wait(&s_empty[slot], (use & 1u) ^ 1u, abort_flag, status)) { ok = false; break; }
+          tc::fence_after();
+          const uint32_t idesc = tc::idesc_bf16(TC_M, tp.ncol[cb]);
+          const uint32_t dslot = tmem + (uint32_t)(slot * TC_SLOT);
+          // descriptors differ only in the start-address field (bits 0-13,
+          // address >> 4), which stays below 2^14 for every operand here
+          const uint64_t bblk = tc::sdesc(bbase + (uint32_t)(tp.n0[cb] * 128));
+          // the 21 digit products with p + q <= 5 (p digit of D, q digit of
+          // u): level L < 4 into accumulator L, levels 4 and 5 into
+          // accumulator 4; the pair filter is resolved at compile time
+#pragma unroll
+          for (int L = 0; L < TC_LEV; ++L) {
+#pragma unroll
+            for (int pd = 0; pd < TC_P; ++pd) {
+#pragma unroll
+              for (int qd = 0; qd < TC_P; ++qd) {
+                const int lev = pd + qd;
+                if (L < TC_LEV - 1 ? lev != L : (lev < TC_LEV - 1 || lev > TC_LEV)) continue;
+                const bool first = pd == 0 && qd == L;     // first pair of accumulator L
+                const uint32_t d = dslot + (uint32_t)(L * TC_NCOL);
+                const uint64_t da = adesc0 + (uint64_t)((qd * TC_APLANE) >> 4);
+                const uint64_t db = bblk + (uint64_t)(pd * (bplane >> 4));
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks)
+                  if (ks < tp.KS)
+                    tc::mma_bf16(d, da + (uint64_t)(ks * 2), db + (uint64_t)(ks * 2), idesc, (first && ks == 0) ? 0u : 1u);
+              }
+            }
+          }
+          tc::mma_commit(&s_full[slot]);
+        }
+        if (!ok) break;
+        tc::mma_commit(a_empty);   // the digit planes of u may be overwritten once these MMAs are done
+      }
+      tc::mma_commit(fin);
+      const long long t0 = clock64();
+      while (!tc::mbar_try_wait(fin, 0) && clock64() - t0 < tc::TIMEOUT_CYCLES) {
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int quarter = warp & 3, half = (warp - 5) >> 2;
+    const int m = quarter * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * (TC_NCOL / 2));
+    const int n_rows = p.n_rows;
+    int t = 0;
+    int64_t cnt = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++t) {
+      const int64_t e = tile * TC_M + m;
+      const bool valid = e < p.E;
+      // g_k[e, r] of this thread's element as double-float (scaled by
+      // 2^(k_e - 16) once the tile's exponents are known)
+      df gk[TC_MAXROWS][R];
+#pragma unroll
+      for (int k = 0; k < TC_MAXROWS; ++k)
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          gk[k][r] = dfm::df_from_double(
+              (valid && k < n_rows) ? (p.has_g ? p.rows[k].g.ptr[e * p.rows[k].g.se + r * p.rows[k].g.sk] : 1.0) : 0.0);
+      for (int cb = 0; cb < tp.ncb; ++cb, ++cnt) {
+        const int slot = (int)(cnt % TC_NSLOT);
+        const uint32_t use = (uint32_t)(cnt / TC_NSLOT);
+        const bool got = tc::mbar_wait(&s_full[slot], use & 1u, abort_flag, status);
+        if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+        tc::fence_after();
+        if (cb == 0) {
+          const float sg = pow2f(kU[(t & 1) * TC_M + m] - 16);
+#pragma unroll
+          for (int k = 0; k < TC_MAXROWS; ++k)
+#pragma unroll
+            for (int r = 0; r < R; ++r) gk[k][r] = df{gk[k][r].hi * sg, gk[k][r].lo * sg};
+        }
+        const int nI = min(IB, NI - cb * IB);
+        const int nIh = max(0, min(H0, nI - half * H0));      // i of this half (warp-uniform)
+        const int nch = (nIh + IPC - 1) / IPC;
+        for (int ch = 0; ch < nch; ++ch) {
+          uint32_t v[TC_LEV][8];
+#pragma unroll
+          for (int L = 0; L < TC_LEV; ++L)
+            tc::tmem_ld8(lane_base + (uint32_t)(slot * TC_SLOT + L * TC_NCOL + ch * 8), v[L]);
+          tc::tmem_wait_ld();
+          if (ch == nch - 1) {                                 // this slot is drained
+            tc::fence_before();
+            tc::mbar_arrive(&s_empty[slot]);
+          }
+          // t for the chunk's IPC values of i: 5 accumulators per column in
+          // double-float, times 2^k_n of the column's row of D
+          df tt[IPC][R];
+#pragma unroll
+          for (int ii = 0; ii < IPC; ++ii)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              const int c = ii * RP + r;
+              const df s01 = dfm::two_sum(__uint_as_float(v[0][c]), __uint_as_float(v[1][c]));
+              df s23 = dfm::two_sum(__uint_as_float(v[2][c]), __uint_as_float(v[3][c]));
+              s23.lo += __uint_as_float(v[4][c]);
+              const df x = dfm::df_add(s01, s23);
+              const float sc = pow2f(kD[min(tp.n0[cb] + half * (TC_NCOL / 2) + ch * 8 + c, tp.NBtot - 1)]);
+              tt[ii][r] = df{x.hi * sc, x.lo * sc};
+            }
+          if (valid) {
+#pragma unroll
+            for (int ii = 0; ii < IPC; ++ii) {
+              const int il = ch * IPC + ii;
+              if (il < nIh) {
+                const int i = cb * IB + half * H0 + il;
+#pragma unroll
+                for (int k = 0; k < TC_MAXROWS; ++k) {
+                  if (k < n_rows) {
+                    float s = 0.f, c = 0.f;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) dfm::dot_acc(s, c, gk[k][r], tt[ii][r]);
+                    p.rows[k].out[e * NI + i] = dfm::df_to_double(dfm::fast_two_sum(s, c));
+                  }
+                }
+              }
+            }
+          }
+        }
+        if (nch == 0) {
+          tc::fence_before();
+          tc::mbar_arrive(&s_empty[slot]);
+        }
+      }
+    }
+  }
+
+  // teardown: every MMA of this CTA has completed (fin) before the tensor
+  // memory is released
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 4) {
+    tc::fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  }
+}
+
+bool build_params(const EParams &p, TcParams &tp, std::string &why) {
+  if (p.n_groups != 1) { why = "more than one fused operand"; return false; }
+  if (p.R < 1 || p.R > 4) { why = "R outside 1..4"; return false; }
+  if (p.NJ < 1 || p.NJ > 64) { why = "contracted extent outside 1..64"; return false; }
+  if (p.NI < 1) { why = "empty output extent"; return false; }
+  if (p.n_rows < 1 || p.n_rows > TC_MAXROWS) { why = "more than 4 einsums"; return false; }
+  if (!p.has_g && p.R != 1) { why = "no geometric factor with R > 1"; return false; }
+  tp.p = p;
+  const int rp = p.R == 3 ? 4 : p.R;
+  tp.IB = TC_NCOL / rp;
+  tp.ncb = (p.NI + tp.IB - 1) / tp.IB;
+  if (tp.ncb > 8) { why = "too many column blocks"; return false; }
+  int nb = 0;
+  for (int cb = 0; cb < tp.ncb; ++cb) {
+    const int nI = std::min(tp.IB, p.NI - cb * tp.IB);
+    tp.n0[cb] = nb;
+    tp.ncol[cb] = (nI * rp + 15) / 16 * 16;
+    nb += tp.ncol[cb];
+  }
+  if (nb > TC_MAXNB) { why = "R * NI too large for the shared D planes"; return false; }
+  tp.NBtot = nb;
+  tp.KS = (p.NJ + 15) / 16;
+  tp.NG = (p.NJ + 7) / 8;
+  return true;
+}
+
+size_t smem_bytes(const TcParams &tp) {
+  return 1024 + (size_t)TC_P * tp.NBtot * 128 + (size_t)TC_P * TC_APLANE + sizeof(float4) * dfm::SIN_TAB_N +
+         sizeof(int) * (TC_MAXNB + 3 * TC_M) + 8 * (3 + 2 * TC_NSLOT) + 16;
+}
+
+template <int R>
+cudaError_t launch_r(const TcParams &tp, int grid, size_t smem, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t st = cudaFuncSetAttribute(element_tc_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (st != cudaSuccess) return st;
+    attr = true;
+  }
+  element_tc_kernel<R><<<grid, TC_THREADS, smem, s>>>(tp);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool element_tc_supported(const EParams &p, std::string &why) {
+  TcParams tp;
+  if (!build_params(p, tp, why)) return false;
+  if (smem_bytes(tp) > 227 * 1024) { why = "shared memory"; return false; }
+  return true;
+}
+
+cudaError_t launch_element_tc(const EParams &p, int *status, cudaStream_t s) {
+  TcParams tp;
+  std::string why;
+  if (!build_params(p, tp, why)) return cudaErrorInvalidValue;
+  tp.status = status;
+  const size_t smem = smem_bytes(tp);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  if (p.E <= 0) return cudaSuccess;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = (p.E + TC_M - 1) / TC_M;
+  const int grid = (int)std::min<int64_t>(tiles, sms);
+  switch (p.R) {
+    case 1: return launch_r<1>(tp, grid, smem, s);
+    case 2: return launch_r<2>(tp, grid, smem, s);
+    case 3: return launch_r<3>(tp, grid, smem, s);
+    default: return launch_r<4>(tp, grid, smem, s);
+  }
+}
+
+}  // namespace be
