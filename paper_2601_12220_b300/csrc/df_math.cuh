@@ -184,7 +184,7 @@ __device__ __forceinline__ df df_sin_tab(double x, const float4 *tab) {
   r = df_add(r, df{-k * PIO2_3, 0.f});
   const float fk = rintf(r.hi * 256.f);
   const df d = df_add(r, df{-fk * 0.00390625f, 0.f});             // r - k/256, exact grid point
-  const float4 t = tab[(int)fk + SIN_TAB_K];
+  const float4 t = tab[min(max((int)fk + SIN_TAB_K, 0), SIN_TAB_N - 1)];   // |r| <= pi/4: always inside
   const float d3 = d.hi * d.hi * d.hi;
   const df sd = df_add(d, df{-d3 * (1.f / 6.f), 0.f});
   df d2 = two_prod(d.hi, d.hi);

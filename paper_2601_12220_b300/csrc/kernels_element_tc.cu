@@ -60,9 +60,9 @@ constexpr int TC_LEV = 5;                       // accumulators per column block
 constexpr int TC_NCOL = 32;                     // accumulator columns per level (32-column aligned)
 constexpr int TC_SLOT = TC_LEV * TC_NCOL;       // 160 columns per slot
 constexpr int TC_NSLOT = 3;                     // 480 of the 512 tensor-memory columns
-constexpr int TC_APLANE = TC_M * 128;           // one digit plane of u: 128 rows x 128 bytes
-constexpr int NPROD = 128, NEPI = 256;
-constexpr int TC_THREADS = NPROD + 32 + NEPI;   // producer warps 0-3, MMA warp 4, epilogue warps 5-12
+constexpr int NPROD = 224, NEPI = 256;
+constexpr int MMA_WARP = NPROD / 32;            // 7
+constexpr int TC_THREADS = NPROD + 32 + NEPI;   // producer warps 0-6, MMA warp 7, epilogue warps 8-15
 constexpr int TC_MAXROWS = 4;                   // einsums (rows) per launch
 constexpr int TC_MAXNB = 160;                   // B rows (all column blocks)
 
@@ -95,8 +95,10 @@ __device__ __forceinline__ void digits_f64(double v, float *d) {
   }
   d[TC_P - 1] = (float)rint(v * 256.0) * pow2f(-9 * (TC_P - 1));
 }
-// the same for v = h + l in double-float: every step is exact
-__device__ __forceinline__ void digits_df(float h, float l, float *d) {
+// the same for v = u * sc in double-float (sc a power of two): every step
+// is exact
+__device__ __forceinline__ void digits_df(df u, float sc, float *d) {
+  float h = u.hi * sc, l = u.lo * sc;
   const float MAGIC = 12582912.0f;              // 1.5 * 2^23: adding it rounds to an integer
 #pragma unroll
   for (int q = 0; q < TC_P - 1; ++q) {
@@ -115,9 +117,16 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<const uint32_t *>(&v);
 }
 
-// byte offset of the 16-byte chunk g (8 values of K) of row m in a 128-byte
-// swizzled K-major plane (1024-byte aligned)
-__device__ __forceinline__ uint32_t swz(int m, int g) { return (uint32_t)(m * 128 + ((g ^ (m & 7)) << 4)); }
+// Operand planes are K-major in the 32-byte-swizzle layout: for each slice
+// of 16 values of K (one MMA K-step) the rows are 32 bytes long and packed,
+// 8-row groups 256 bytes apart, slices rows * 32 bytes apart; within an
+// 8-row group the two 16-byte halves of a row swap places when the row's
+// bit 2 is set.  One MMA K-step thus reads one contiguous block.
+// Byte offset of the 16-byte chunk g (values 8g .. 8g+7 of K) of row m in a
+// plane of `rows` rows (256-byte aligned):
+__device__ __forceinline__ uint32_t sw32(int rows, int m, int g) {
+  return (uint32_t)((g >> 1) * rows * 32 + (m >> 3) * 256 + (m & 7) * 32 + (((g & 1) ^ ((m >> 2) & 1)) << 4));
+}
 
 // bound on |u_j| for the row's scale (|sin a| <= 1)
 __device__ __forceinline__ double prod_bound(const EProd &q, int64_t e, int j) {
@@ -126,24 +135,37 @@ __device__ __forceinline__ double prod_bound(const EProd &q, int64_t e, int j) {
   return q.kind == 2 ? a * fabs(q.b.ptr[e * q.b.se + j * q.b.sk]) : a;
 }
 
-// operands of the flat values f, f + 128, f + 256, f + 384 of a tile
-__device__ __forceinline__ void load_batch(const EProd &q, int64_t e0, int f, int n, int NJ, double *av, double *bv) {
+// operands of the pairs pi and pi + NPROD of a tile: (a, b) at j and j + 1
+// of the pair's row (zeros past the row's end or the tile's last pair)
+__device__ __forceinline__ void load_pairs(const EProd &q, int64_t e0, int pi, int np, int JP, int NJ, double *av,
+                                           double *bv) {
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int g = f + u * 128;
-    const int m = g < n ? g / NJ : 0, j = g - m * NJ;
+  for (int u = 0; u < 2; ++u) {
+    const int g = pi + u * NPROD;
+    const int m = g < np ? g / JP : 0, j = 2 * (g - m * JP);
     const int64_t e = e0 + m;
-    av[u] = g < n ? q.a.ptr[e * q.a.se + j * q.a.sk] : 0.0;
-    bv[u] = (g < n && q.kind != 0) ? q.b.ptr[e * q.b.se + j * q.b.sk] : 0.0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const bool ok = g < np && j + h < NJ;
+      av[2 * u + h] = ok ? q.a.ptr[e * q.a.se + (j + h) * q.a.sk] : 0.0;
+      bv[2 * u + h] = (ok && q.kind != 0) ? q.b.ptr[e * q.b.se + (j + h) * q.b.sk] : 0.0;
+    }
   }
 }
 
-// named barrier of the four producer warps, and the same barrier returning
+// the fused producer's value in double-float: a, a * b or sin(a) * b
+__device__ __forceinline__ df produce(const EProd &q, double a, double b, const float4 *sin_tab) {
+  if (q.kind == 0) return dfm::df_from_double(a);
+  if (q.kind == 2) return dfm::df_mul(dfm::df_from_double(a), dfm::df_from_double(b));
+  return dfm::df_mul(dfm::df_sin_tab(a, sin_tab), dfm::df_from_double(b));
+}
+
+// named barrier of the producer warps, and the same barrier returning
 // the AND of a predicate over them (so that all of them leave together)
-__device__ __forceinline__ void prod_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void prod_sync() { asm volatile("bar.sync 1, 224;" ::: "memory"); }
 __device__ __forceinline__ bool prod_all(bool v) {
   uint32_t r;
-  asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred p, 1, 128, q;\n selp.u32 %0, 1, 0, p;\n}"
+  asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred p, 1, 224, q;\n selp.u32 %0, 1, 0, p;\n}"
                : "=r"(r)
                : "r"((uint32_t)v)
                : "memory");
@@ -171,9 +193,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *Bp = smem;                                       // TC_P planes x NBtot rows x 128 B
-  const int bplane = tp.NBtot * 128;
-  uint8_t *Ap = Bp + TC_P * bplane;                         // TC_P planes x 128 rows x 128 B
-  float4 *sin_tab = (float4 *)(Ap + TC_P * TC_APLANE);
+  const int bplane = tp.KS * tp.NBtot * 32;                 // bytes per digit plane of D
+  const int aplane = tp.KS * TC_M * 32;                     // bytes per digit plane of u
+  uint8_t *Ap = Bp + TC_P * bplane;                         // TC_P planes x KS slices x 128 rows x 32 B
+  float4 *sin_tab = (float4 *)(Ap + TC_P * aplane);
   int *kD = (int *)(sin_tab + dfm::SIN_TAB_N);              // [TC_MAXNB]
   int *kU = kD + TC_MAXNB;                                  // [2][TC_M]
   int *mxw = kU + 2 * TC_M;                                 // [TC_M] high words of the row bounds
@@ -197,14 +220,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 4) {
+  if (warp == MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(tc::smem_u32(tmem_slot)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   // zero both operand regions (K padding and padding rows stay zero)
   {
     uint4 *z = (uint4 *)smem;
-    const int n16 = (TC_P * bplane + TC_P * TC_APLANE) / 16;
+    const int n16 = (TC_P * bplane + TC_P * aplane) / 16;
     for (int k = tid; k < n16; k += TC_THREADS) z[k] = make_uint4(0u, 0u, 0u, 0u);
   }
   dfm::sin_table_fill(sin_tab);
@@ -239,7 +262,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
     }
 #pragma unroll
     for (int q = 0; q < TC_P; ++q)
-      *(uint4 *)(Bp + q * bplane + swz(n, g)) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+      *(uint4 *)(Bp + q * bplane + sw32(tp.NBtot, n, g)) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
   }
   tc::fence_proxy_async();
   tc::fence_before();
@@ -250,7 +273,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
   const int64_t n_tiles = (p.E + TC_M - 1) / TC_M;
   int *status = tp.status;
 
-  if (warp < 4) {
+  if (warp < MMA_WARP) {
     // ------------------------------------------------------------ producer
     // flat over the tile's te x NJ values (consecutive threads read
     // consecutive addresses of row-major operands): pass 1 takes the largest
@@ -268,14 +291,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
         prefetch_rows(q.a, e1, te1, NJ);
         if (q.kind != 0) prefetch_rows(q.b, e1, te1, NJ);
       }
-      mxw[tid] = 0;
+      if (tid < TC_M) mxw[tid] = 0;
       prod_sync();
       // pass 1, one warp per row (lanes over j, coalesced), 8 rows in flight
-      for (int r0 = warp; r0 < te; r0 += 4 * 8) {
+      constexpr int NPW = NPROD / 32;
+      for (int r0 = warp; r0 < te; r0 += NPW * 8) {
         int hw[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          const int row = r0 + 4 * u;
+          const int row = r0 + NPW * u;
           const bool okr = row < te;
           const double v0 = (okr && lane < NJ) ? prod_bound(q, e0 + row, lane) : 0.0;
           const double v1 = (okr && lane + 32 < NJ) ? prod_bound(q, e0 + row, lane + 32) : 0.0;
@@ -284,51 +308,50 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int h = __reduce_max_sync(0xffffffffu, hw[u]);
-          if (lane == 0 && r0 + 4 * u < te) mxw[r0 + 4 * u] = h;
+          if (lane == 0 && r0 + NPW * u < te) mxw[r0 + NPW * u] = h;
         }
       }
       if (!prod_all(tc::mbar_wait(a_empty, ((uint32_t)t & 1u) ^ 1u, abort_flag, status))) break;
       int *ku = kU + (t & 1) * TC_M;
-      ku[tid] = row_exp(__hiloint2double(mxw[tid], 0));
+      if (tid < TC_M) ku[tid] = row_exp(__hiloint2double(mxw[tid], 0));
       prod_sync();
-      // pass 2: batches of 4 values per thread, the next batch's loads
-      // issued before the current batch is evaluated
+      // pass 2 over pairs (j, j + 1) of a row (one 32-bit word per digit
+      // plane), two pairs per thread per batch, the next batch's loads issued
+      // before the current batch is evaluated
+      const int JP = (NJ + 1) >> 1, np = te * JP;
       double an[4], bn[4];
-      load_batch(q, e0, tid, n, NJ, an, bn);
-      for (int f0 = tid; f0 < n; f0 += 4 * NPROD) {
+      load_pairs(q, e0, tid, np, JP, NJ, an, bn);
+      for (int p0 = tid; p0 < np; p0 += 2 * NPROD) {
         double av[4], bv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           av[u] = an[u];
           bv[u] = bn[u];
         }
-        if (f0 + 4 * NPROD < n) load_batch(q, e0, f0 + 4 * NPROD, n, NJ, an, bn);
+        if (p0 + 2 * NPROD < np) load_pairs(q, e0, p0 + 2 * NPROD, np, JP, NJ, an, bn);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int f = f0 + u * NPROD;
-          if (f < n) {
-            const int m = f / NJ, j = f - m * NJ;
-            df uu;
-            if (q.kind == 0) uu = dfm::df_from_double(av[u]);
-            else if (q.kind == 2) uu = dfm::df_mul(dfm::df_from_double(av[u]), dfm::df_from_double(bv[u]));
-            else uu = dfm::df_mul(dfm::df_sin_tab(av[u], sin_tab), dfm::df_from_double(bv[u]));
+        for (int u = 0; u < 2; ++u) {
+          const int pi = p0 + u * NPROD;
+          if (pi < np) {
+            const int m = pi / JP, j = 2 * (pi - m * JP);
             const float sc = pow2f(-ku[m]);
-            float d[TC_P];
-            digits_df(uu.hi * sc, uu.lo * sc, d);
-            uint8_t *dst = Ap + swz(m, j >> 3) + (j & 7) * 2;
+            float d0[TC_P], d1[TC_P];
+            digits_df(produce(q, av[2 * u], bv[2 * u], sin_tab), sc, d0);
+            digits_df(produce(q, av[2 * u + 1], bv[2 * u + 1], sin_tab), sc, d1);   // zero past NJ
+            uint8_t *dst = Ap + sw32(TC_M, m, j >> 3) + (j & 7) * 2;
 #pragma unroll
-            for (int k = 0; k < TC_P; ++k) *(__nv_bfloat16 *)(dst + k * TC_APLANE) = __float2bfloat16_rn(d[k]);
+            for (int k = 0; k < TC_P; ++k) *(uint32_t *)(dst + k * aplane) = pack_bf16(d0[k], d1[k]);
           }
         }
       }
       tc::fence_proxy_async();
       tc::mbar_arrive(a_full);
     }
-  } else if (warp == 4) {
+  } else if (warp == MMA_WARP) {
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
       const uint32_t bbase = tc::smem_u32(Bp);
-      const uint64_t adesc0 = tc::sdesc(tc::smem_u32(Ap));
+      const uint64_t adesc0 = tc::sdesc_sw32(tc::smem_u32(Ap));
       int t = 0;
       int64_t cnt = 0;
       bool ok = true;
@@ -344,7 +367,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
           const uint32_t dslot = tmem + (uint32_t)(slot * TC_SLOT);
           // descriptors differ only in the start-address field (bits 0-13,
           // address >> 4), which stays below 2^14 for every operand here
-          const uint64_t bblk = tc::sdesc(bbase + (uint32_t)(tp.n0[cb] * 128));
+          const uint64_t bblk = tc::sdesc_sw32(bbase + (uint32_t)(tp.n0[cb] * 32));
           // the 21 digit products with p + q <= 5 (p digit of D, q digit of
           // u): level L < 4 into accumulator L, levels 4 and 5 into
           // accumulator 4; the pair filter is resolved at compile time
@@ -358,12 +381,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
                 if (L < TC_LEV - 1 ? lev != L : (lev < TC_LEV - 1 || lev > TC_LEV)) continue;
                 const bool first = pd == 0 && qd == L;     // first pair of accumulator L
                 const uint32_t d = dslot + (uint32_t)(L * TC_NCOL);
-                const uint64_t da = adesc0 + (uint64_t)((qd * TC_APLANE) >> 4);
-                const uint64_t db = bblk + (uint64_t)(pd * (bplane >> 4));
+                const uint64_t da = adesc0 + (uint64_t)((qd * aplane) >> 4);
+                const uint64_t db = bblk + (uint64_t)((pd * bplane) >> 4);
 #pragma unroll
                 for (int ks = 0; ks < 4; ++ks)
                   if (ks < tp.KS)
-                    tc::mma_bf16(d, da + (uint64_t)(ks * 2), db + (uint64_t)(ks * 2), idesc, (first && ks == 0) ? 0u : 1u);
+                    tc::mma_bf16(d, da + (uint64_t)(ks * (TC_M * 32 >> 4)), db + (uint64_t)(ks * (tp.NBtot * 32 >> 4)), idesc,
+                                 (first && ks == 0) ? 0u : 1u);
               }
             }
           }
@@ -379,7 +403,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int quarter = warp & 3, half = (warp - 5) >> 2;
+    const int quarter = warp & 3, half = (warp - MMA_WARP - 1) >> 2;
     const int m = quarter * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * (TC_NCOL / 2));
     const int n_rows = p.n_rows;
@@ -416,6 +440,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
         const int nch = (nIh + IPC - 1) / IPC;
         for (int ch = 0; ch < nch; ++ch) {
           uint32_t v[TC_LEV][8];
+          __syncwarp();   // tcgen05.ld is .sync.aligned: reconverge after the lane-dependent stores
 #pragma unroll
           for (int L = 0; L < TC_LEV; ++L)
             tc::tmem_ld8(lane_base + (uint32_t)(slot * TC_SLOT + L * TC_NCOL + ch * 8), v[L]);
@@ -470,7 +495,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
   // memory is released
   tc::fence_before();
   __syncthreads();
-  if (warp == 4) {
+  if (warp == MMA_WARP) {
+    __syncwarp();   // lane 0 ran the issue loop alone
     tc::fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
   }
@@ -503,7 +529,7 @@ bool build_params(const EParams &p, TcParams &tp, std::string &why) {
 }
 
 size_t smem_bytes(const TcParams &tp) {
-  return 1024 + (size_t)TC_P * tp.NBtot * 128 + (size_t)TC_P * TC_APLANE + sizeof(float4) * dfm::SIN_TAB_N +
+  return 1024 + (size_t)TC_P * tp.KS * tp.NBtot * 32 + (size_t)TC_P * tp.KS * TC_M * 32 + sizeof(float4) * dfm::SIN_TAB_N +
          sizeof(int) * (TC_MAXNB + 3 * TC_M) + 8 * (3 + 2 * TC_NSLOT) + 16;
 }
 

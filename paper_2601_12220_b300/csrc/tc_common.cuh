@@ -58,6 +58,18 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 
+// the same for the 32-byte-swizzle layout: rows of 32 bytes (one K-step of
+// 16 bf16), 8-row groups 256 bytes apart
+__device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused: one swizzle atom along K)
+  d |= (uint64_t)(256 >> 4) << 32;        // stride byte offset
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  d |= (uint64_t)6 << 61;                 // 32-byte swizzle
+  return d;
+}
+
 // instruction descriptor of kind::f16 with D f32, A and B bf16, both K-major
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
