@@ -70,6 +70,7 @@ __device__ __forceinline__ void dot_acc(float &s, float &c, df x, df y) {
 __device__ __forceinline__ double f2d(float f) {
   const uint32_t u = __float_as_uint(f);
   const uint32_t ef = (u >> 23) & 0xFFu;
+  if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)(u >> 31) << 63);   // signed zero
   if (ef == 0u || ef == 0xFFu) return (double)f;
   const uint64_t s = (uint64_t)(u >> 31) << 63;
   const uint64_t e = (uint64_t)(ef - 127u + 1023u);
@@ -108,6 +109,7 @@ __device__ __forceinline__ double df_to_double(df x) {
 __device__ __forceinline__ df df_from_double(double x) {
   const long long b = __double_as_longlong(x);
   const int e = (int)((b >> 52) & 0x7FF);
+  if ((b & 0x7FFFFFFFFFFFFFFFll) == 0) return df{__uint_as_float((uint32_t)((unsigned long long)b >> 32)), 0.f};   // signed zero
   if (e < 1023 - 70 || e > 1023 + 100) {
     const float h = __double2float_rn(x);
     return df{h, __double2float_rn(x - (double)h)};

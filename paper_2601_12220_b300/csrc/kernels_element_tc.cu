@@ -28,18 +28,24 @@
 // magnitude it can exceed 1e-12 S; element_df_kernel is the componentwise
 // path for such data.
 //
-// Warp roles (416 threads, one CTA per SM, persistent over tiles of 128
-// elements): warps 0-3 produce the digit planes of u (thread m = element m of
-// the tile) into shared memory in the 128-byte-swizzle K-major layout;
-// warp 4 issues the MMAs (one thread) into three tensor-memory slots of
-// 5 accumulators x 32 columns, one column block (up to 32 (i, r) columns) per
-// slot; warps 5-12 drain a slot (two warps per TMEM lane quarter, one per
-// half of the block's columns) while the next blocks accumulate.  Every
-// accumulator starts on a 32-column boundary: with accumulators at 48-column
-// offsets, MMAs issued back to back into neighbouring accumulators gave
-// wrong sums on B300 (correct when the issue was slowed down).  Every
-// wait is bounded: on expiry the CTA records BE_ETIMEOUT, stops issuing and
-// frees its tensor memory after its MMAs complete.
+// Warp roles (512 threads, one CTA per SM, persistent over tiles of 128
+// elements):
+//  * warps 0-6 produce the digit planes of u (two buffers, so that tile t+1
+//    is produced while the MMAs of tile t run) in the 32-byte-swizzle
+//    K-major layout, reading a and b with coalesced loads and prefetching
+//    the next tile's rows into L2;
+//  * warp 7 issues the MMAs (one thread) into three tensor-memory slots of
+//    5 accumulators x 32 columns, one column block (two 16-column halves of
+//    16 / R values of i with their R terms) per slot.  Every accumulator
+//    starts on a 32-column boundary: with accumulators at 48-column offsets,
+//    MMAs issued back to back into neighbouring accumulators gave wrong sums
+//    on B300 (correct when the issue was slowed down);
+//  * warps 8-15 drain a slot (two warps per TMEM lane quarter, one per half
+//    of the block) while the next blocks accumulate, and write the outputs.
+// D's digit planes are built once per CTA with integer arithmetic on the
+// FP64 bits (no FP64 instruction).  Every wait is bounded: on expiry the
+// CTA records BE_ETIMEOUT, stops issuing and frees its tensor memory after
+// its MMAs complete.
 #include <algorithm>
 
 #include <cuda_bf16.h>
@@ -60,6 +66,7 @@ constexpr int TC_LEV = 5;                       // accumulators per column block
 constexpr int TC_NCOL = 32;                     // accumulator columns per level (32-column aligned)
 constexpr int TC_SLOT = TC_LEV * TC_NCOL;       // 160 columns per slot
 constexpr int TC_NSLOT = 3;                     // 480 of the 512 tensor-memory columns
+constexpr int TC_KU = 8;                        // buffers of per-element row scales
 constexpr int NPROD = 224, NEPI = 256;
 constexpr int MMA_WARP = NPROD / 32;            // 7
 constexpr int TC_THREADS = NPROD + 32 + NEPI;   // producer warps 0-6, MMA warp 7, epilogue warps 8-15
@@ -83,18 +90,7 @@ __device__ __forceinline__ int row_exp(double mx) {
   return min(100, max(-100, ex - 1023 + 1));
 }
 __device__ __forceinline__ float pow2f(int k) { return __uint_as_float((uint32_t)(k + 127) << 23); }   // |k| <= 126
-__device__ __forceinline__ double pow2d(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
 
-// six balanced base-512 digits of v (|v| < 1 + 2^-20), each times 2^-9q
-__device__ __forceinline__ void digits_f64(double v, float *d) {
-#pragma unroll
-  for (int q = 0; q < TC_P - 1; ++q) {
-    const double t = rint(v * 256.0);
-    v = fma(t, -0.00390625, v) * 512.0;         // exact
-    d[q] = (float)t * pow2f(-9 * q);
-  }
-  d[TC_P - 1] = (float)rint(v * 256.0) * pow2f(-9 * (TC_P - 1));
-}
 // the same for v = u * sc in double-float (sc a power of two): every step
 // is exact
 __device__ __forceinline__ void digits_df(df u, float sc, float *d) {
@@ -128,11 +124,14 @@ __device__ __forceinline__ uint32_t sw32(int rows, int m, int g) {
   return (uint32_t)((g >> 1) * rows * 32 + (m >> 3) * 256 + (m & 7) * 32 + (((g & 1) ^ ((m >> 2) & 1)) << 4));
 }
 
-// bound on |u_j| for the row's scale (|sin a| <= 1)
-__device__ __forceinline__ double prod_bound(const EProd &q, int64_t e, int j) {
-  if (q.kind == 1) return fabs(q.b.ptr[e * q.b.se + j * q.b.sk]);
-  const double a = fabs(q.a.ptr[e * q.a.se + j * q.a.sk]);
-  return q.kind == 2 ? a * fabs(q.b.ptr[e * q.b.se + j * q.b.sk]) : a;
+// high word of a bound on |u| for the row scale (|sin a| <= 1); for a
+// nonnegative double the high word orders like the value and carries its
+// exponent, so the row maximum is an integer maximum
+__device__ __forceinline__ int bound_hw(const EProd &q, int64_t e, int j) {
+  if (q.kind == 1) return __double2hiint(q.b.ptr[e * q.b.se + j * q.b.sk]) & 0x7FFFFFFF;
+  const double a = q.a.ptr[e * q.a.se + j * q.a.sk];
+  if (q.kind == 0) return __double2hiint(a) & 0x7FFFFFFF;
+  return __double2hiint(fabs(a) * fabs(q.b.ptr[e * q.b.se + j * q.b.sk]));
 }
 
 // operands of the pairs pi and pi + NPROD of a tile: (a, b) at j and j + 1
@@ -151,6 +150,38 @@ __device__ __forceinline__ void load_pairs(const EProd &q, int64_t e0, int pi, i
       bv[2 * u + h] = (ok && q.kind != 0) ? q.b.ptr[e * q.b.se + (j + h) * q.b.sk] : 0.0;
     }
   }
+}
+
+// L2 prefetch of rows e1 .. e1+te1-1 (j = 0..NJ-1) of a view whose rows are
+// contiguous; the range is shrunk to 16-byte boundaries inside it
+__device__ __forceinline__ void prefetch_rows(const EView &v, int64_t e1, int te1, int NJ) {
+  if (v.sk != 1 || te1 <= 0) return;
+  const uintptr_t lo = (uintptr_t)(v.ptr + e1 * v.se);
+  const uintptr_t hi = (uintptr_t)(v.ptr + (e1 + te1 - 1) * v.se + NJ);
+  const uintptr_t a = (lo + 15) & ~(uintptr_t)15, b = hi & ~(uintptr_t)15;
+  if (b <= a) return;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(b - a)) : "memory");
+}
+
+// six balanced base-512 digits of x * 2^-k (|x| < 2^k), each times 2^-9q,
+// by integer arithmetic on the bits of x: X = round(x * 2^(53 - k)) is split
+// from the bottom, d = ((X + 256) mod 512) - 256, X = (X - d) / 512
+__device__ __forceinline__ void digits_bits(double x, int k, float *d) {
+  const long long b = __double_as_longlong(x);
+  int ex = (int)((b >> 52) & 0x7FF);
+  long long m = b & 0xFFFFFFFFFFFFFll;
+  if (ex == 0) ex = 1;
+  else m |= 1ll << 52;
+  const int sh = 1022 + k - ex;                          // >= 0 since |x| < 2^k
+  long long X = sh >= 63 ? 0 : (sh == 0 ? m : ((m >> (sh - 1)) + 1) >> 1);
+  if (b < 0) X = -X;
+#pragma unroll
+  for (int q = TC_P - 1; q > 0; --q) {
+    const long long dq = ((X + 256) & 511) - 256;
+    X = (X - dq) >> 9;
+    d[q] = (float)(int)dq * pow2f(-9 * q);
+  }
+  d[0] = (float)(int)X;
 }
 
 // the fused producer's value in double-float: a, a * b or sin(a) * b
@@ -172,37 +203,42 @@ __device__ __forceinline__ bool prod_all(bool v) {
   return r != 0;
 }
 
-// L2 prefetch of rows e1 .. e1+te1-1 (j = 0..NJ-1) of a view whose rows are
-// contiguous; the range is shrunk to 16-byte boundaries inside it
-__device__ __forceinline__ void prefetch_rows(const EView &v, int64_t e1, int te1, int NJ) {
-  if (v.sk != 1 || te1 <= 0) return;
-  const uintptr_t lo = (uintptr_t)(v.ptr + e1 * v.se);
-  const uintptr_t hi = (uintptr_t)(v.ptr + (e1 + te1 - 1) * v.se + NJ);
-  const uintptr_t a = (lo + 15) & ~(uintptr_t)15, b = hi & ~(uintptr_t)15;
-  if (b <= a) return;
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(b - a)) : "memory");
+// Columns of a block: two halves of 16, each holding H0 = 16 / R values of
+// i with their R terms (column = il * R + r) and zero padding after them, so
+// that an epilogue thread's half never splits an i.  B row n -> (i, r).
+template <int R>
+__device__ __forceinline__ bool brow(const TcParams &tp, int n, int &i, int &r) {
+  constexpr int H0 = 16 / R;
+  int cb = 0;
+  while (cb + 1 < tp.ncb && n >= tp.n0[cb + 1]) ++cb;
+  const int c = n - tp.n0[cb], h = c >> 4, cc = c & 15;
+  r = cc % R;
+  const int il = cc / R;
+  i = cb * 2 * H0 + h * H0 + il;
+  return il < H0 && i < tp.p.NI;
 }
 
 template <int R>
 __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_constant__ TcParams tp) {
-  constexpr int RP = R == 3 ? 4 : R;            // columns per i (R padded to divide 8)
-  constexpr int IPC = 8 / RP;                   // i per 8-column chunk
-  constexpr int IB = TC_NCOL / RP;              // i per column block (4 chunks)
-  constexpr int H0 = IB / 2;                    // i per epilogue half (2 chunks, 16 columns)
+  constexpr int H0 = 16 / R;                    // i per 16-column half of a block
+  constexpr int IB = 2 * H0;                    // i per column block
   const EParams &p = tp.p;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *Bp = smem;                                       // TC_P planes x NBtot rows x 128 B
   const int bplane = tp.KS * tp.NBtot * 32;                 // bytes per digit plane of D
   const int aplane = tp.KS * TC_M * 32;                     // bytes per digit plane of u
-  uint8_t *Ap = Bp + TC_P * bplane;                         // TC_P planes x KS slices x 128 rows x 32 B
-  float4 *sin_tab = (float4 *)(Ap + TC_P * aplane);
+  uint8_t *Ap = Bp + TC_P * bplane;                         // 2 buffers x TC_P planes x KS slices x 128 rows x 32 B
+  float4 *sin_tab = (float4 *)(Ap + 2 * TC_P * aplane);
   int *kD = (int *)(sin_tab + dfm::SIN_TAB_N);              // [TC_MAXNB]
-  int *kU = kD + TC_MAXNB;                                  // [2][TC_M]
-  int *mxw = kU + 2 * TC_M;                                 // [TC_M] high words of the row bounds
+  // Row scales of u for the last TC_KU tiles: the epilogue can trail the
+  // producer by up to 2 + ceil(3 / ncb) tiles (two digit buffers ahead of
+  // the MMAs, which run at most three column blocks ahead of the epilogue)
+  int *kU = kD + TC_MAXNB;                                  // [TC_KU][TC_M]
+  int *mxw = kU + TC_KU * TC_M;                             // [TC_M] high words of the row bounds
   uint64_t *bars = (uint64_t *)(mxw + TC_M);
-  uint64_t *a_full = bars, *a_empty = bars + 1, *s_full = bars + 2, *s_empty = bars + 2 + TC_NSLOT;
-  uint64_t *fin = bars + 2 + 2 * TC_NSLOT;
+  uint64_t *a_full = bars, *a_empty = bars + 2, *s_full = bars + 4, *s_empty = bars + 4 + TC_NSLOT;
+  uint64_t *fin = bars + 4 + 2 * TC_NSLOT;
   uint32_t *tmem_slot = (uint32_t *)(fin + 1);
   volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
@@ -210,8 +246,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
   const int NJ = p.NJ, NI = p.NI;
 
   if (tid == 0) {
-    tc::mbar_init(a_full, NPROD);
-    tc::mbar_init(a_empty, 1);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&a_full[b], NPROD);
+      tc::mbar_init(&a_empty[b], 1);
+    }
     for (int b = 0; b < TC_NSLOT; ++b) {
       tc::mbar_init(&s_full[b], 1);
       tc::mbar_init(&s_empty[b], NEPI);
@@ -227,36 +265,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
   // zero both operand regions (K padding and padding rows stay zero)
   {
     uint4 *z = (uint4 *)smem;
-    const int n16 = (TC_P * bplane + TC_P * aplane) / 16;
+    const int n16 = (TC_P * bplane + 2 * TC_P * aplane) / 16;
     for (int k = tid; k < n16; k += TC_THREADS) z[k] = make_uint4(0u, 0u, 0u, 0u);
   }
   dfm::sin_table_fill(sin_tab);
-  // B row n -> (block, column c = il * RP + r); scale exponent per real row
+  // B row n -> (i, r); scale exponent per real row
   for (int n = tid; n < tp.NBtot; n += TC_THREADS) {
-    int cb = 0;
-    while (cb + 1 < tp.ncb && n >= tp.n0[cb + 1]) ++cb;
-    const int c = n - tp.n0[cb], il = c / RP, r = c % RP, i = cb * IB + il;
-    double mx = 0.0;
-    if (r < R && il < IB && i < NI)
-      for (int j = 0; j < NJ; ++j) mx = fmax(mx, fabs(p.D[r * p.sr + i * p.si + j * p.sj]));
-    kD[n] = row_exp(mx);
+    int i, r;
+    int hw = 0;
+    if (brow<R>(tp, n, i, r))
+      for (int j = 0; j < NJ; ++j) hw = max(hw, __double2hiint(p.D[r * p.sr + i * p.si + j * p.sj]) & 0x7FFFFFFF);
+    kD[n] = row_exp(__hiloint2double(hw, 0));
   }
   __syncthreads();
   // digit planes of D: item (row n, group g of 8 values of j)
   for (int item = tid; item < tp.NBtot * tp.NG; item += TC_THREADS) {
     const int n = item / tp.NG, g = item % tp.NG;
-    int cb = 0;
-    while (cb + 1 < tp.ncb && n >= tp.n0[cb + 1]) ++cb;
-    const int c = n - tp.n0[cb], il = c / RP, r = c % RP, i = cb * IB + il;
-    if (r >= R || il >= IB || i >= NI) continue;
-    const double sc = pow2d(-kD[n]);
+    int i, r;
+    if (!brow<R>(tp, n, i, r)) continue;
+    const int kn = kD[n];
     uint32_t w[TC_P][4];
 #pragma unroll
     for (int jp = 0; jp < 4; ++jp) {
       float d0[TC_P], d1[TC_P];
       const int j = g * 8 + 2 * jp;
-      digits_f64(j < NJ ? p.D[r * p.sr + i * p.si + j * p.sj] * sc : 0.0, d0);
-      digits_f64(j + 1 < NJ ? p.D[r * p.sr + i * p.si + (j + 1) * p.sj] * sc : 0.0, d1);
+      digits_bits(j < NJ ? p.D[r * p.sr + i * p.si + j * p.sj] : 0.0, kn, d0);
+      digits_bits(j + 1 < NJ ? p.D[r * p.sr + i * p.si + (j + 1) * p.sj] : 0.0, kn, d1);
 #pragma unroll
       for (int q = 0; q < TC_P; ++q) w[q][jp] = pack_bf16(d0[q], d1[q]);
     }
@@ -275,17 +309,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
 
   if (warp < MMA_WARP) {
     // ------------------------------------------------------------ producer
-    // flat over the tile's te x NJ values (consecutive threads read
-    // consecutive addresses of row-major operands): pass 1 takes the largest
-    // |u| bound per element (exponent of the row scale), pass 2 evaluates
-    // u in double-float and writes its digits into the planes
+    // Two buffers of digit planes: tile t+1 is produced while the MMAs of
+    // tile t run.  Pass 1 takes the largest |u| bound per element (the row
+    // scale, one warp per row, lanes over j); pass 2 evaluates u in
+    // double-float over pairs (j, j + 1) and writes its digits.  The next
+    // tile's rows are prefetched into L2.
     const EProd &q = p.groups[0];
     int t = 0;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++t) {
       const int64_t e0 = tile * TC_M;
       const int te = (int)(p.E - e0 < TC_M ? p.E - e0 : TC_M);
-      const int n = te * NJ;
-      if (tid == 0 && tile + gridDim.x < n_tiles) {      // next tile's rows into L2
+      if (tid == 0 && tile + gridDim.x < n_tiles) {
         const int64_t e1 = e0 + (int64_t)gridDim.x * TC_M;
         const int te1 = (int)(p.E - e1 < TC_M ? p.E - e1 : TC_M);
         prefetch_rows(q.a, e1, te1, NJ);
@@ -293,31 +327,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
       }
       if (tid < TC_M) mxw[tid] = 0;
       prod_sync();
-      // pass 1, one warp per row (lanes over j, coalesced), 8 rows in flight
       constexpr int NPW = NPROD / 32;
-      for (int r0 = warp; r0 < te; r0 += NPW * 8) {
-        int hw[8];
+      for (int r0 = warp; r0 < te; r0 += NPW * 4) {
+        int hw[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 4; ++u) {
           const int row = r0 + NPW * u;
           const bool okr = row < te;
-          const double v0 = (okr && lane < NJ) ? prod_bound(q, e0 + row, lane) : 0.0;
-          const double v1 = (okr && lane + 32 < NJ) ? prod_bound(q, e0 + row, lane + 32) : 0.0;
-          hw[u] = max(__double2hiint(v0), __double2hiint(v1));
+          const int h0 = (okr && lane < NJ) ? bound_hw(q, e0 + row, lane) : 0;
+          const int h1 = (okr && lane + 32 < NJ) ? bound_hw(q, e0 + row, lane + 32) : 0;
+          hw[u] = max(h0, h1);
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 4; ++u) {
           const int h = __reduce_max_sync(0xffffffffu, hw[u]);
           if (lane == 0 && r0 + NPW * u < te) mxw[r0 + NPW * u] = h;
         }
       }
-      if (!prod_all(tc::mbar_wait(a_empty, ((uint32_t)t & 1u) ^ 1u, abort_flag, status))) break;
-      int *ku = kU + (t & 1) * TC_M;
+      const int ab = t & 1;
+      const uint32_t use = (uint32_t)(t >> 1);
+      if (!prod_all(tc::mbar_wait(&a_empty[ab], (use & 1u) ^ 1u, abort_flag, status))) break;
+      int *ku = kU + (t & (TC_KU - 1)) * TC_M;
       if (tid < TC_M) ku[tid] = row_exp(__hiloint2double(mxw[tid], 0));
       prod_sync();
-      // pass 2 over pairs (j, j + 1) of a row (one 32-bit word per digit
-      // plane), two pairs per thread per batch, the next batch's loads issued
-      // before the current batch is evaluated
+      uint8_t *A = Ap + ab * TC_P * aplane;
       const int JP = (NJ + 1) >> 1, np = te * JP;
       double an[4], bn[4];
       load_pairs(q, e0, tid, np, JP, NJ, an, bn);
@@ -338,14 +371,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
             float d0[TC_P], d1[TC_P];
             digits_df(produce(q, av[2 * u], bv[2 * u], sin_tab), sc, d0);
             digits_df(produce(q, av[2 * u + 1], bv[2 * u + 1], sin_tab), sc, d1);   // zero past NJ
-            uint8_t *dst = Ap + sw32(TC_M, m, j >> 3) + (j & 7) * 2;
+            uint8_t *dst = A + sw32(TC_M, m, j >> 3) + (j & 7) * 2;
 #pragma unroll
             for (int k = 0; k < TC_P; ++k) *(uint32_t *)(dst + k * aplane) = pack_bf16(d0[k], d1[k]);
           }
         }
       }
       tc::fence_proxy_async();
-      tc::mbar_arrive(a_full);
+      tc::mbar_arrive(&a_full[ab]);
     }
   } else if (warp == MMA_WARP) {
     // ------------------------------------------------------------ MMA issue
@@ -356,7 +389,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
       int64_t cnt = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++t) {
-        if (!tc::mbar_wait(a_full, (uint32_t)t & 1u, abort_flag, status)) break;
+        const int ab = t & 1;
+        if (!tc::mbar_wait(&a_full[ab], (uint32_t)(t >> 1) & 1u, abort_flag, status)) break;
+        const uint64_t adesc = adesc0 + (uint64_t)((ab * TC_P * aplane) >> 4);
         tc::fence_after();
         for (int cb = 0; cb < tp.ncb; ++cb, ++cnt) {
           const int slot = (int)(cnt % TC_NSLOT);
@@ -381,7 +416,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
                 if (L < TC_LEV - 1 ? lev != L : (lev < TC_LEV - 1 || lev > TC_LEV)) continue;
                 const bool first = pd == 0 && qd == L;     // first pair of accumulator L
                 const uint32_t d = dslot + (uint32_t)(L * TC_NCOL);
-                const uint64_t da = adesc0 + (uint64_t)((qd * aplane) >> 4);
+                const uint64_t da = adesc + (uint64_t)((qd * aplane) >> 4);
                 const uint64_t db = bblk + (uint64_t)((pd * bplane) >> 4);
 #pragma unroll
                 for (int ks = 0; ks < 4; ++ks)
@@ -394,7 +429,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
           tc::mma_commit(&s_full[slot]);
         }
         if (!ok) break;
-        tc::mma_commit(a_empty);   // the digit planes of u may be overwritten once these MMAs are done
+        tc::mma_commit(&a_empty[ab]);   // this buffer of digit planes may be refilled once these MMAs are done
       }
       tc::mma_commit(fin);
       const long long t0 = clock64();
@@ -429,7 +464,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
         if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
         tc::fence_after();
         if (cb == 0) {
-          const float sg = pow2f(kU[(t & 1) * TC_M + m] - 16);
+          const float sg = pow2f(kU[(t & (TC_KU - 1)) * TC_M + m] - 16);
 #pragma unroll
           for (int k = 0; k < TC_MAXROWS; ++k)
 #pragma unroll
@@ -437,47 +472,47 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
         }
         const int nI = min(IB, NI - cb * IB);
         const int nIh = max(0, min(H0, nI - half * H0));      // i of this half (warp-uniform)
-        const int nch = (nIh + IPC - 1) / IPC;
-        for (int ch = 0; ch < nch; ++ch) {
-          uint32_t v[TC_LEV][8];
-          __syncwarp();   // tcgen05.ld is .sync.aligned: reconverge after the lane-dependent stores
+        const int nch = (nIh * R + 7) >> 3;                      // 8-column chunks holding them
+        // t for this half's columns: 5 accumulators per column added in
+        // double-float, times 2^k_n of the column's row of D
+        float th[16], tl[16];
 #pragma unroll
-          for (int L = 0; L < TC_LEV; ++L)
-            tc::tmem_ld8(lane_base + (uint32_t)(slot * TC_SLOT + L * TC_NCOL + ch * 8), v[L]);
-          tc::tmem_wait_ld();
-          if (ch == nch - 1) {                                 // this slot is drained
-            tc::fence_before();
-            tc::mbar_arrive(&s_empty[slot]);
-          }
-          // t for the chunk's IPC values of i: 5 accumulators per column in
-          // double-float, times 2^k_n of the column's row of D
-          df tt[IPC][R];
+        for (int ch = 0; ch < 2; ++ch) {
+          if (ch < nch) {
+            uint32_t v[TC_LEV][8];
+            __syncwarp();   // tcgen05.ld is .sync.aligned: reconverge after lane-dependent work
 #pragma unroll
-          for (int ii = 0; ii < IPC; ++ii)
+            for (int L = 0; L < TC_LEV; ++L)
+              tc::tmem_ld8(lane_base + (uint32_t)(slot * TC_SLOT + L * TC_NCOL + ch * 8), v[L]);
+            tc::tmem_wait_ld();
+            if (ch == nch - 1) {                               // this slot is drained
+              tc::fence_before();
+              tc::mbar_arrive(&s_empty[slot]);
+            }
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-              const int c = ii * RP + r;
+            for (int c = 0; c < 8; ++c) {
               const df s01 = dfm::two_sum(__uint_as_float(v[0][c]), __uint_as_float(v[1][c]));
               df s23 = dfm::two_sum(__uint_as_float(v[2][c]), __uint_as_float(v[3][c]));
               s23.lo += __uint_as_float(v[4][c]);
               const df x = dfm::df_add(s01, s23);
-              const float sc = pow2f(kD[min(tp.n0[cb] + half * (TC_NCOL / 2) + ch * 8 + c, tp.NBtot - 1)]);
-              tt[ii][r] = df{x.hi * sc, x.lo * sc};
+              const float sc = pow2f(kD[min(tp.n0[cb] + half * 16 + ch * 8 + c, tp.NBtot - 1)]);
+              th[ch * 8 + c] = x.hi * sc;
+              tl[ch * 8 + c] = x.lo * sc;
             }
-          if (valid) {
+          }
+        }
+        if (valid) {
 #pragma unroll
-            for (int ii = 0; ii < IPC; ++ii) {
-              const int il = ch * IPC + ii;
-              if (il < nIh) {
-                const int i = cb * IB + half * H0 + il;
+          for (int il = 0; il < H0; ++il) {
+            if (il < nIh) {
+              const int i = cb * IB + half * H0 + il;
 #pragma unroll
-                for (int k = 0; k < TC_MAXROWS; ++k) {
-                  if (k < n_rows) {
-                    float s = 0.f, c = 0.f;
+              for (int k = 0; k < TC_MAXROWS; ++k) {
+                if (k < n_rows) {
+                  float s = 0.f, c = 0.f;
 #pragma unroll
-                    for (int r = 0; r < R; ++r) dfm::dot_acc(s, c, gk[k][r], tt[ii][r]);
-                    p.rows[k].out[e * NI + i] = dfm::df_to_double(dfm::fast_two_sum(s, c));
-                  }
+                  for (int r = 0; r < R; ++r) dfm::dot_acc(s, c, gk[k][r], df{th[il * R + r], tl[il * R + r]});
+                  p.rows[k].out[e * NI + i] = dfm::df_to_double(dfm::fast_two_sum(s, c));
                 }
               }
             }
@@ -510,15 +545,15 @@ bool build_params(const EParams &p, TcParams &tp, std::string &why) {
   if (p.n_rows < 1 || p.n_rows > TC_MAXROWS) { why = "more than 4 einsums"; return false; }
   if (!p.has_g && p.R != 1) { why = "no geometric factor with R > 1"; return false; }
   tp.p = p;
-  const int rp = p.R == 3 ? 4 : p.R;
-  tp.IB = TC_NCOL / rp;
+  const int h0 = 16 / p.R;
+  tp.IB = 2 * h0;
   tp.ncb = (p.NI + tp.IB - 1) / tp.IB;
   if (tp.ncb > 8) { why = "too many column blocks"; return false; }
   int nb = 0;
   for (int cb = 0; cb < tp.ncb; ++cb) {
     const int nI = std::min(tp.IB, p.NI - cb * tp.IB);
     tp.n0[cb] = nb;
-    tp.ncol[cb] = (nI * rp + 15) / 16 * 16;
+    tp.ncol[cb] = nI <= h0 ? 16 : 32;                    // one or two 16-column halves
     nb += tp.ncol[cb];
   }
   if (nb > TC_MAXNB) { why = "R * NI too large for the shared D planes"; return false; }
@@ -529,8 +564,8 @@ bool build_params(const EParams &p, TcParams &tp, std::string &why) {
 }
 
 size_t smem_bytes(const TcParams &tp) {
-  return 1024 + (size_t)TC_P * tp.KS * tp.NBtot * 32 + (size_t)TC_P * tp.KS * TC_M * 32 + sizeof(float4) * dfm::SIN_TAB_N +
-         sizeof(int) * (TC_MAXNB + 3 * TC_M) + 8 * (3 + 2 * TC_NSLOT) + 16;
+  return 1024 + (size_t)TC_P * tp.KS * tp.NBtot * 32 + 2 * (size_t)TC_P * tp.KS * TC_M * 32 +
+         sizeof(float4) * dfm::SIN_TAB_N + sizeof(int) * (TC_MAXNB + (TC_KU + 1) * TC_M) + 8 * (5 + 2 * TC_NSLOT) + 16;
 }
 
 template <int R>

@@ -3,8 +3,8 @@ against the FP64 oracle, |got - ref| <= 1e-12 * S componentwise (S the
 oracle's absolute contraction), and bit for bit on integer-valued inputs.
 
 The cases walk the kernel's shape logic: ragged tiles of 128 elements, one
-to several column blocks (R * NI up to 48 per block, R = 3 padded to 4
-columns per i), K = NJ from 4 to 64 (one to four MMA K-steps), every fused
+to several column blocks (two 16-column halves of 16 / R values of i each),
+K = NJ from 1 to 40 (one to three MMA K-steps), every fused
 producer kind, R from 1 to 4, and elements whose magnitudes differ by many
 orders (per-element scaling of the digits).
 """
@@ -90,15 +90,24 @@ def test_dimensions(dim):
     check(W.dg_gradient_spec(E=E, ndof=20, dim=dim), dict(D=D, G=G, a=a, b=b))
 
 
-@pytest.mark.parametrize("NI,NJ", [(50, 64), (1, 1), (64, 17)])
+@pytest.mark.parametrize("NI,NJ", [(50, 40), (1, 1), (64, 17)])
 def test_plain_operator(NI, NJ):
-    """'ij,ej->ei' (R = 1, no geometric factor): up to two blocks of 48 i,
-    K up to the 64 limit."""
+    """'ij,ej->ei' (R = 1, no geometric factor): one or two blocks of 32 i,
+    K from 1 to 40 (one to three MMA K-steps)."""
     E = 333
     g = np.random.default_rng(NI * 100 + NJ)
     D = g.standard_normal((NI, NJ))
     u = g.standard_normal((E, NJ))
     check(f"ij,ej->ei | D,U ; D:f64[{NI},{NJ}] ; U:f64[{E},{NJ}]", dict(D=D, U=u))
+
+
+@pytest.mark.parametrize("ndof", [4, 10])
+def test_many_tiles_per_cta_one_block(ndof):
+    """E = 150000 gives every CTA several tiles; with one column block per
+    tile the producer runs furthest ahead of the epilogue."""
+    E = 150000
+    D, G, a, b = W.dg_gradient(E=E, ndof=ndof)
+    check(W.dg_gradient_spec(E=E, ndof=ndof), dict(D=D, G=G, a=a, b=b))
 
 
 def test_integers_bit_exact():
