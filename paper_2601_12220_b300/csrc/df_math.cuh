@@ -180,8 +180,12 @@ __device__ __forceinline__ void sin_table_fill(float4 *tab) {
 // sin(x) as df using the table (|x| < 2^20, else FP64 sin)
 __device__ __forceinline__ df df_sin_tab(double x, const float4 *tab) {
   if ((int)((__double_as_longlong(x) >> 52) & 0x7FF) >= 1023 + 20) return df_from_double(sin(x));
-  const float k = rintf(df_from_double(x).hi * TWO_OVER_PI);
-  df r = df_from_double(fma(-f2d(k), f2d(PIO2_1), x));
+  // the quadrant from x in FP64 (error far below 1/2 for |x| < 2^20, so
+  // |r| <= pi/4 + 2^-30 and the table index stays inside); x - k * PIO2_1 is
+  // exact in one fma (k * PIO2_1 has at most 44 bits)
+  const double kd = rint(x * 0.63661977236758134308);
+  const float k = __double2float_rn(kd);
+  df r = df_from_double(fma(-kd, (double)PIO2_1, x));
   r = df_add(r, df_neg(two_prod(k, PIO2_2)));
   r = df_add(r, df{-k * PIO2_3, 0.f});
   const float fk = rintf(r.hi * 256.f);

@@ -136,12 +136,12 @@ __device__ __forceinline__ int bound_hw(const EProd &q, int64_t e, int j) {
 
 // operands of the pairs pi and pi + NPROD of a tile: (a, b) at j and j + 1
 // of the pair's row (zeros past the row's end or the tile's last pair)
-__device__ __forceinline__ void load_pairs(const EProd &q, int64_t e0, int pi, int np, int JP, int NJ, double *av,
-                                           double *bv) {
+__device__ __forceinline__ void load_pairs(const EProd &q, int64_t e0, int pi, int np, int JP, uint32_t jinv, int NJ,
+                                           double *av, double *bv) {
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
     const int g = pi + u * NPROD;
-    const int m = g < np ? g / JP : 0, j = 2 * (g - m * JP);
+    const int m = g < np ? (int)(((uint32_t)g * jinv) >> 20) : 0, j = 2 * (g - m * JP);
     const int64_t e = e0 + m;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -184,7 +184,8 @@ __device__ __forceinline__ void digits_bits(double x, int k, float *d) {
   d[0] = (float)(int)X;
 }
 
-// the fused producer's value in double-float: a, a * b or sin(a) * b
+// the fused producer's value in double-float: a, a * b or sin(a) * b (the
+// conversions stay off the FP64 pipe, which the epilogue's output sums use)
 __device__ __forceinline__ df produce(const EProd &q, double a, double b, const float4 *sin_tab) {
   if (q.kind == 0) return dfm::df_from_double(a);
   if (q.kind == 2) return dfm::df_mul(dfm::df_from_double(a), dfm::df_from_double(b));
@@ -351,9 +352,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
       if (tid < TC_M) ku[tid] = row_exp(__hiloint2double(mxw[tid], 0));
       prod_sync();
       uint8_t *A = Ap + ab * TC_P * aplane;
+      // pairs per row; g / JP as (g * jinv) >> 20, exact for g < 2^12, JP <= 32
       const int JP = (NJ + 1) >> 1, np = te * JP;
+      const uint32_t jinv = ((1u << 20) + (uint32_t)JP - 1u) / (uint32_t)JP;
       double an[4], bn[4];
-      load_pairs(q, e0, tid, np, JP, NJ, an, bn);
+      load_pairs(q, e0, tid, np, JP, jinv, NJ, an, bn);
       for (int p0 = tid; p0 < np; p0 += 2 * NPROD) {
         double av[4], bv[4];
 #pragma unroll
@@ -361,12 +364,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
           av[u] = an[u];
           bv[u] = bn[u];
         }
-        if (p0 + 2 * NPROD < np) load_pairs(q, e0, p0 + 2 * NPROD, np, JP, NJ, an, bn);
+        if (p0 + 2 * NPROD < np) load_pairs(q, e0, p0 + 2 * NPROD, np, JP, jinv, NJ, an, bn);
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
           const int pi = p0 + u * NPROD;
           if (pi < np) {
-            const int m = pi / JP, j = 2 * (pi - m * JP);
+            const int m = (int)(((uint32_t)pi * jinv) >> 20), j = 2 * (pi - m * JP);
             const float sc = pow2f(-ku[m]);
             float d0[TC_P], d1[TC_P];
             digits_df(produce(q, av[2 * u], bv[2 * u], sin_tab), sc, d0);
@@ -512,7 +515,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
                   float s = 0.f, c = 0.f;
 #pragma unroll
                   for (int r = 0; r < R; ++r) dfm::dot_acc(s, c, gk[k][r], df{th[il * R + r], tl[il * R + r]});
-                  p.rows[k].out[e * NI + i] = dfm::df_to_double(dfm::fast_two_sum(s, c));
+                  // hi + lo on the FP64 pipe (otherwise idle here): 3 instructions
+                  // instead of the bit assembly's ~35 on the FP32/ALU pipes
+                  p.rows[k].out[e * NI + i] = (double)s + (double)c;
                 }
               }
             }

@@ -110,16 +110,21 @@ def test_dg_gradient_fp64_pipe_variant():
         assert_close(got[x], ref[x][0], ref[x][1], 1e-12)
 
 
-def test_df_sine_matches_fp64_sin():
+@pytest.mark.parametrize("variant", [2, 3])
+def test_df_sine_matches_fp64_sin(variant):
     """The fused producer sin(a) * b with b = 1 through an identity operator
-    returns the double-float sine itself; compare with CUDA's FP64 sin."""
-    E, N = 4096, 35
+    returns the double-float sine itself; compare with CUDA's FP64 sin.  The
+    arguments reach 2^19.9, where the quadrant must come from x in FP64 (a
+    float image of x can be a quadrant off there).  Variant 2 is the
+    double-float kernel, 3 the tensor-core kernel."""
+    E, N = 6144, 35
     g = np.random.default_rng(12)
-    a = np.concatenate([g.standard_normal((E // 2, N)) * 3, g.uniform(-1e4, 1e4, (E // 2, N))])
-    a[0, :5] = [0.0, np.pi, -np.pi / 2, 1e-30, 2.0 ** 21]
+    a = np.concatenate([g.standard_normal((E // 3, N)) * 3, g.uniform(-1e4, 1e4, (E // 3, N)),
+                        g.uniform(2.0 ** 18, 2.0 ** 19.9, (E // 3, N)) * g.choice([-1.0, 1.0], (E // 3, N))])
+    a[0, :5] = [0.0, np.pi, -np.pi / 2, 1e-30, 2.0 ** 19]
     text = (f"ij,ej->ei | D,U ; D:f64[{N},{N}] ; a:f64[{E},{N}] ; b:f64[{E},{N}] ; "
             f"U(e,j) := sin(a[e,j])*b[e,j]")
-    got, _ = run(text, dict(D=np.eye(N), a=a, b=np.ones((E, N))))
+    got, _ = run(text, dict(D=np.eye(N), a=a, b=np.ones((E, N))), cfg=be.make_config(be.STRAT_ELEMENT, (0, 0, variant)))
     ref = torch.sin(torch.from_numpy(a).to(DEV)).cpu().numpy()
     # double-float carries about 46-48 significant bits
     assert np.max(np.abs(got[0] - ref)) <= 1e-14
