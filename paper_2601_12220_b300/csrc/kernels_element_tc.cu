@@ -494,6 +494,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
             }
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
+              if (ch * 8 + c >= H0 * R) continue;              // padding column of the half
               const df s01 = dfm::two_sum(__uint_as_float(v[0][c]), __uint_as_float(v[1][c]));
               df s23 = dfm::two_sum(__uint_as_float(v[2][c]), __uint_as_float(v[3][c]));
               s23.lo += __uint_as_float(v[4][c]);
@@ -512,9 +513,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
 #pragma unroll
               for (int k = 0; k < TC_MAXROWS; ++k) {
                 if (k < n_rows) {
-                  float s = 0.f, c = 0.f;
+                  // first term: its exact product starts the pair (s, c)
+                  const df g0 = gk[k][0], t0{th[il * R], tl[il * R]};
+                  float s = g0.hi * t0.hi;
+                  float c = fmaf(g0.hi, t0.lo, fmaf(g0.lo, t0.hi, fmaf(g0.hi, t0.hi, -s)));
 #pragma unroll
-                  for (int r = 0; r < R; ++r) dfm::dot_acc(s, c, gk[k][r], df{th[il * R + r], tl[il * R + r]});
+                  for (int r = 1; r < R; ++r) dfm::dot_acc(s, c, gk[k][r], df{th[il * R + r], tl[il * R + r]});
                   // hi + lo on the FP64 pipe (otherwise idle here): 3 instructions
                   // instead of the bit assembly's ~35 on the FP32/ALU pipes
                   p.rows[k].out[e * NI + i] = (double)s + (double)c;
