@@ -177,6 +177,51 @@ __device__ __forceinline__ void sin_table_fill(float4 *tab) {
   }
 }
 
+// an integer-valued double with |v| < 2^31 as an int, by bit moves
+__device__ __forceinline__ int kd_to_int(double v) {
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;              // v = 0 or |v| in [2^e, 2^(e+1))
+  if (e < 0) return 0;
+  const long long m = (b & 0xFFFFFFFFFFFFFll) | (1ll << 52);
+  const int n = (int)(m >> (52 - e));
+  return b < 0 ? -n : n;
+}
+
+// Full-circle table: sin(n pi / 512) for n = 0..1023 as (hi, lo); cos of a
+// grid point is the entry a quarter turn (256) ahead.  Filled from the first
+// quadrant by symmetry, so every entry comes from an argument in [0, pi/2].
+constexpr int SIN2_N = 1024;
+constexpr double PI512_HI = 0x1.921fb54442d18p-8;                // pi / 512, leading double
+constexpr double PI512_LO = 0x1.1a62633145c07p-62;               // pi / 512 - PI512_HI
+__device__ __forceinline__ void sin2_table_fill(float2 *tab) {
+  for (int n = threadIdx.x; n < SIN2_N; n += blockDim.x) {
+    const int m = n & 511, mm = m <= 256 ? m : 512 - m;
+    const df s = df_sin((double)mm * PI512_HI);
+    tab[n] = n < 512 ? make_float2(s.hi, s.lo) : make_float2(-s.hi, -s.lo);
+  }
+}
+
+// sin(x) as df from the full-circle table (|x| < 2^20, else FP64 sin):
+// x = n pi / 512 + d with |d| <= pi / 1024 (two FP64 fmas), then
+// sin x = sin(n pi/512) cos d + cos(n pi/512) sin d with short series in d
+__device__ __forceinline__ df df_sin_tab2(double x, const float2 *tab) {
+  if ((int)((__double_as_longlong(x) >> 52) & 0x7FF) >= 1023 + 20) return df_from_double(sin(x));
+  const double nd = rint(x * 162.97466172610083);                // 512 / pi
+  const int n = kd_to_int(nd);
+  const double dr = fma(-nd, PI512_LO, fma(-nd, PI512_HI, x));
+  const df d = df_from_double(dr);
+  const float d2 = d.hi * d.hi;
+  // sin d = d - d^3/6 + d^5/120 (the cubic and quintic terms in float are
+  // below 2^-28 and 2^-48 of one)
+  const df sd = fast_two_sum(d.hi, fmaf(d.hi * d2, fmaf(d2, 1.f / 120.f, -1.f / 6.f), d.lo));
+  // cos d = 1 - d^2/2 + d^4/24 with d^2 exact as a pair
+  const df p = two_prod(d.hi, d.hi);
+  const df c1 = fast_two_sum(1.f, -0.5f * p.hi);
+  const df cd = fast_two_sum(c1.hi, c1.lo + fmaf(-d.hi, d.lo, fmaf(p.hi, p.hi * (1.f / 24.f), -0.5f * p.lo)));
+  const float2 s0 = tab[n & (SIN2_N - 1)], c0 = tab[(n + SIN2_N / 4) & (SIN2_N - 1)];
+  return df_add(df_mul(df{s0.x, s0.y}, cd), df_mul(df{c0.x, c0.y}, sd));
+}
+
 // sin(x) as df using the table (|x| < 2^20, else FP64 sin)
 __device__ __forceinline__ df df_sin_tab(double x, const float4 *tab) {
   if ((int)((__double_as_longlong(x) >> 52) & 0x7FF) >= 1023 + 20) return df_from_double(sin(x));

@@ -186,10 +186,10 @@ __device__ __forceinline__ void digits_bits(double x, int k, float *d) {
 
 // the fused producer's value in double-float: a, a * b or sin(a) * b (the
 // conversions stay off the FP64 pipe, which the epilogue's output sums use)
-__device__ __forceinline__ df produce(const EProd &q, double a, double b, const float4 *sin_tab) {
+__device__ __forceinline__ df produce(const EProd &q, double a, double b, const float2 *sin_tab) {
   if (q.kind == 0) return dfm::df_from_double(a);
   if (q.kind == 2) return dfm::df_mul(dfm::df_from_double(a), dfm::df_from_double(b));
-  return dfm::df_mul(dfm::df_sin_tab(a, sin_tab), dfm::df_from_double(b));
+  return dfm::df_mul(dfm::df_sin_tab2(a, sin_tab), dfm::df_from_double(b));
 }
 
 // named barrier of the producer warps, and the same barrier returning
@@ -230,8 +230,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
   const int bplane = tp.KS * tp.NBtot * 32;                 // bytes per digit plane of D
   const int aplane = tp.KS * TC_M * 32;                     // bytes per digit plane of u
   uint8_t *Ap = Bp + TC_P * bplane;                         // 2 buffers x TC_P planes x KS slices x 128 rows x 32 B
-  float4 *sin_tab = (float4 *)(Ap + 2 * TC_P * aplane);
-  int *kD = (int *)(sin_tab + dfm::SIN_TAB_N);              // [TC_MAXNB]
+  float2 *sin_tab = (float2 *)(Ap + 2 * TC_P * aplane);     // full-circle sine table
+  int *kD = (int *)(sin_tab + dfm::SIN2_N);                 // [TC_MAXNB]
   // Row scales of u for the last TC_KU tiles: the epilogue can trail the
   // producer by up to 2 + ceil(3 / ncb) tiles (two digit buffers ahead of
   // the MMAs, which run at most three column blocks ahead of the epilogue)
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
     const int n16 = (TC_P * bplane + 2 * TC_P * aplane) / 16;
     for (int k = tid; k < n16; k += TC_THREADS) z[k] = make_uint4(0u, 0u, 0u, 0u);
   }
-  dfm::sin_table_fill(sin_tab);
+  dfm::sin2_table_fill(sin_tab);
   // B row n -> (i, r); scale exponent per real row
   for (int n = tid; n < tp.NBtot; n += TC_THREADS) {
     int i, r;
@@ -574,7 +574,7 @@ bool build_params(const EParams &p, TcParams &tp, std::string &why) {
 
 size_t smem_bytes(const TcParams &tp) {
   return 1024 + (size_t)TC_P * tp.KS * tp.NBtot * 32 + 2 * (size_t)TC_P * tp.KS * TC_M * 32 +
-         sizeof(float4) * dfm::SIN_TAB_N + sizeof(int) * (TC_MAXNB + (TC_KU + 1) * TC_M) + 8 * (5 + 2 * TC_NSLOT) + 16;
+         sizeof(float2) * dfm::SIN2_N + sizeof(int) * (TC_MAXNB + (TC_KU + 1) * TC_M) + 8 * (5 + 2 * TC_NSLOT) + 16;
 }
 
 template <int R>
