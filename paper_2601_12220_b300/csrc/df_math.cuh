@@ -187,6 +187,10 @@ __device__ __forceinline__ int kd_to_int(double v) {
   return b < 0 ? -n : n;
 }
 
+// FP64 sine of an argument outside the double-float range, kept out of line
+// so that the callers' hot code stays small
+static __device__ __noinline__ df sin_far(double x) { return df_from_double(sin(x)); }
+
 // Full-circle table: sin(n pi / 512) for n = 0..1023 as (hi, lo); cos of a
 // grid point is the entry a quarter turn (256) ahead.  Filled from the first
 // quadrant by symmetry, so every entry comes from an argument in [0, pi/2].
@@ -205,7 +209,7 @@ __device__ __forceinline__ void sin2_table_fill(float2 *tab) {
 // x = n pi / 512 + d with |d| <= pi / 1024 (two FP64 fmas), then
 // sin x = sin(n pi/512) cos d + cos(n pi/512) sin d with short series in d
 __device__ __forceinline__ df df_sin_tab2(double x, const float2 *tab) {
-  if ((int)((__double_as_longlong(x) >> 52) & 0x7FF) >= 1023 + 20) return df_from_double(sin(x));
+  if ((int)((__double_as_longlong(x) >> 52) & 0x7FF) >= 1023 + 20) return sin_far(x);
   const double nd = rint(x * 162.97466172610083);                // 512 / pi
   const int n = kd_to_int(nd);
   const double dr = fma(-nd, PI512_LO, fma(-nd, PI512_HI, x));
