@@ -104,26 +104,28 @@ __device__ __forceinline__ double df_to_double(df x) {
   return __longlong_as_double((long long)(sign | ((uint64_t)e << 52) | ((uint64_t)m & 0xFFFFFFFFFFFFFull)));
 }
 
-// double -> df with |x - hi - lo| <= 2^-48 |x|, by integer operations on the
-// bits when both parts land in FP32's normal range (2^-70 <= |x| < 2^100)
+// double -> df for zeros, non-normal parts and out-of-range exponents: the
+// FP64 conversions, kept out of line so that callers' hot code stays small
+static __device__ __noinline__ df df_from_double_slow(double x) {
+  const float h = __double2float_rn(x);
+  return df{h, __double2float_rn(x - (double)h)};
+}
+
+// double -> df with |x - hi - lo| <= 2^-48 |x|, by 32-bit integer operations
+// on the two halves of the bits when both parts land in FP32's normal range
+// (2^-70 <= |x| < 2^101): hi keeps the top 24 significand bits rounded half
+// up (a carry into the exponent is the exact rounding), lo is the signed
+// remainder, rem * 2^(e - 1075), rounded to a float
 __device__ __forceinline__ df df_from_double(double x) {
-  const long long b = __double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7FF);
-  if ((b & 0x7FFFFFFFFFFFFFFFll) == 0) return df{__uint_as_float((uint32_t)((unsigned long long)b >> 32)), 0.f};   // signed zero
-  if (e < 1023 - 70 || e > 1023 + 100) {
-    const float h = __double2float_rn(x);
-    return df{h, __double2float_rn(x - (double)h)};
-  }
-  const uint64_t m = ((uint64_t)b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const uint64_t mh = (m + (1ull << 28)) >> 29;                    // top 24 bits, rounded
-  const int rem = (int)((long long)m - (long long)(mh << 29));      // |rem| <= 2^28
-  const int eh = e - 1023;
-  const uint32_t sign = (uint32_t)((uint64_t)b >> 63) << 31;
-  const float hi = mh == (1ull << 24) ? __uint_as_float(sign | ((uint32_t)(eh + 1 + 127) << 23))
-                                      : __uint_as_float(sign | ((uint32_t)(eh + 127) << 23) | (uint32_t)(mh & 0x7FFFFFu));
-  float lo = (float)rem * __uint_as_float((uint32_t)(eh - 52 + 127) << 23);
-  if (sign) lo = -lo;
-  return df{hi, lo};
+  const uint32_t hw = (uint32_t)__double2hiint(x), lw = (uint32_t)__double2loint(x);
+  const uint32_t ax = hw & 0x7FFFFFFFu;
+  if (ax - ((1023u - 70u) << 20) >= (171u << 20)) return df_from_double_slow(x);
+  const uint32_t rnd = (lw >> 28) & 1u;
+  const uint32_t hb = ((ax - (896u << 20)) << 3) + (lw >> 29) + rnd;
+  const float hi = __uint_as_float(hb | (hw & 0x80000000u));
+  const int rem = (int)(lw & 0x1FFFFFFFu) - (int)(rnd << 29);
+  const float lo = (float)rem * __uint_as_float((uint32_t)((int)(ax >> 20) - 948) << 23);
+  return df{hi, (int)hw < 0 ? -lo : lo};
 }
 
 // sin(x) as df; |x| < 2^20 (the reduction's exact range), else FP64 sin
@@ -210,8 +212,11 @@ __device__ __forceinline__ void sin2_table_fill(float2 *tab) {
 // sin x = sin(n pi/512) cos d + cos(n pi/512) sin d with short series in d
 __device__ __forceinline__ df df_sin_tab2(double x, const float2 *tab) {
   if ((int)((__double_as_longlong(x) >> 52) & 0x7FF) >= 1023 + 20) return sin_far(x);
-  const double nd = rint(x * 162.97466172610083);                // 512 / pi
-  const int n = kd_to_int(nd);
+  // n = round(x * 512 / pi): adding 1.5 * 2^52 rounds to an integer held in
+  // the low word of the sum (|x| < 2^20 keeps |n| far below 2^31)
+  const double nm = fma(x, 162.97466172610083, 6755399441055744.0);
+  const int n = __double2loint(nm);
+  const double nd = nm - 6755399441055744.0;
   const double dr = fma(-nd, PI512_LO, fma(-nd, PI512_HI, x));
   const df d = df_from_double(dr);
   const float d2 = d.hi * d.hi;
