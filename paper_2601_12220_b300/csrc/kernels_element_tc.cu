@@ -134,22 +134,22 @@ __device__ __forceinline__ int bound_hw(const EProd &q, int64_t e, int j) {
   return __double2hiint(fabs(a) * fabs(q.b.ptr[e * q.b.se + j * q.b.sk]));
 }
 
-// operands of the pairs pi and pi + NPROD of a tile: (a, b) at j and j + 1
-// of the pair's row (zeros past the row's end or the tile's last pair)
-__device__ __forceinline__ void load_pairs(const EProd &q, int64_t e0, int pi, int np, int JP, uint32_t jinv, int NJ,
-                                           double *av, double *bv) {
-#pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    const int g = pi + u * NPROD;
-    const int m = g < np ? (int)(((uint32_t)g * jinv) >> 20) : 0, j = 2 * (g - m * JP);
-    const int64_t e = e0 + m;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const bool ok = g < np && j + h < NJ;
-      av[2 * u + h] = ok ? q.a.ptr[e * q.a.se + (j + h) * q.a.sk] : 0.0;
-      bv[2 * u + h] = (ok && q.kind != 0) ? q.b.ptr[e * q.b.se + (j + h) * q.b.sk] : 0.0;
-    }
-  }
+// operands (a, b) at j and j + 1 of pair pi of a tile (row m = pi / JP,
+// j = 2 (pi mod JP)), from the tile's row pointers with 32-bit offsets;
+// zeros past the row's end or the tile's last pair
+struct TileRows {
+  const double *a, *b;
+  int sea, ska, seb, skb;
+};
+__device__ __forceinline__ void load_pair(const TileRows &t, bool need_b, int pi, int np, int JP, uint32_t jinv, int NJ,
+                                          double *v) {
+  const int m = pi < np ? (int)(((uint32_t)pi * jinv) >> 20) : 0, j = 2 * (pi - m * JP);
+  const bool ok0 = pi < np, ok1 = ok0 && j + 1 < NJ;
+  const int oa = m * t.sea + j * t.ska, ob = m * t.seb + j * t.skb;
+  v[0] = ok0 ? t.a[oa] : 0.0;
+  v[1] = ok1 ? t.a[oa + t.ska] : 0.0;
+  v[2] = (ok0 && need_b) ? t.b[ob] : 0.0;
+  v[3] = (ok1 && need_b) ? t.b[ob + t.skb] : 0.0;
 }
 
 // L2 prefetch of rows e1 .. e1+te1-1 (j = 0..NJ-1) of a view whose rows are
@@ -355,25 +355,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
       // pairs per row; g / JP as (g * jinv) >> 20, exact for g < 2^12, JP <= 32
       const int JP = (NJ + 1) >> 1, np = te * JP;
       const uint32_t jinv = ((1u << 20) + (uint32_t)JP - 1u) / (uint32_t)JP;
-      double an[4], bn[4];
-      load_pairs(q, e0, tid, np, JP, jinv, NJ, an, bn);
-      for (int p0 = tid; p0 < np; p0 += 2 * NPROD) {
-        double av[4], bv[4];
+      const bool need_b = q.kind != 0;
+      TileRows rows{q.a.ptr + e0 * q.a.se, need_b ? q.b.ptr + e0 * q.b.se : q.a.ptr, (int)q.a.se, (int)q.a.sk,
+                    (int)q.b.se, (int)q.b.sk};
+      // PB pairs per thread per batch (independent chains for the scheduler),
+      // the next batch's loads issued before this batch is evaluated
+      constexpr int PB = 3;
+      double an[4 * PB];                                   // per pair: a0 a1 b0 b1
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          av[u] = an[u];
-          bv[u] = bn[u];
+      for (int u = 0; u < PB; ++u) load_pair(rows, need_b, tid + u * NPROD, np, JP, jinv, NJ, an + 4 * u);
+      for (int p0 = tid; p0 < np; p0 += PB * NPROD) {
+        double av[4 * PB];
+#pragma unroll
+        for (int u = 0; u < 4 * PB; ++u) av[u] = an[u];
+        if (p0 + PB * NPROD < np) {
+#pragma unroll
+          for (int u = 0; u < PB; ++u) load_pair(rows, need_b, p0 + (PB + u) * NPROD, np, JP, jinv, NJ, an + 4 * u);
         }
-        if (p0 + 2 * NPROD < np) load_pairs(q, e0, p0 + 2 * NPROD, np, JP, jinv, NJ, an, bn);
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < PB; ++u) {
           const int pi = p0 + u * NPROD;
           if (pi < np) {
             const int m = (int)(((uint32_t)pi * jinv) >> 20), j = 2 * (pi - m * JP);
             const float sc = pow2f(-ku[m]);
             float d0[TC_P], d1[TC_P];
-            digits_df(produce(q, av[2 * u], bv[2 * u], sin_tab), sc, d0);
-            digits_df(produce(q, av[2 * u + 1], bv[2 * u + 1], sin_tab), sc, d1);   // zero past NJ
+            digits_df(produce(q, av[4 * u], av[4 * u + 2], sin_tab), sc, d0);
+            digits_df(produce(q, av[4 * u + 1], av[4 * u + 3], sin_tab), sc, d1);   // zero past NJ
             uint8_t *dst = A + sw32(TC_M, m, j >> 3) + (j & 7) * 2;
 #pragma unroll
             for (int k = 0; k < TC_P; ++k) *(uint32_t *)(dst + k * aplane) = pack_bf16(d0[k], d1[k]);
@@ -553,6 +560,14 @@ bool build_params(const EParams &p, TcParams &tp, std::string &why) {
   if (p.NI < 1) { why = "empty output extent"; return false; }
   if (p.n_rows < 1 || p.n_rows > TC_MAXROWS) { why = "more than 4 einsums"; return false; }
   if (!p.has_g && p.R != 1) { why = "no geometric factor with R > 1"; return false; }
+  {
+    const EProd &q = p.groups[0];
+    const int64_t lim = (int64_t)1 << 23;   // in-tile offsets m * se + j * sk stay 32-bit
+    if (std::abs(q.a.se) >= lim || std::abs(q.a.sk) >= lim || std::abs(q.b.se) >= lim || std::abs(q.b.sk) >= lim) {
+      why = "operand strides too large";
+      return false;
+    }
+  }
   tp.p = p;
   const int h0 = 16 / p.R;
   tp.IB = 2 * h0;
