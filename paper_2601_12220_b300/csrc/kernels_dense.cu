@@ -350,10 +350,23 @@ __device__ __forceinline__ void split_one(double x, float &h, float &l) {
   l = to_tf32(xf - h);
 }
 
-// x * 2^s in FP32 when the scaled row stays in FP32's normal range, else FP64 first
+// x * 2^s rounded to a float (half up) from the bits of x, integer operations
+// only; results below FP32's normal range (2^-100 and more below the row's
+// maximum, which scales to [2^13, 2^14)) become zero
+__device__ __forceinline__ float scaled_float(double x, int s) {
+  const uint32_t hw = (uint32_t)__double2hiint(x), lw = (uint32_t)__double2loint(x);
+  const uint32_t ax = hw & 0x7FFFFFFFu;
+  const int fe = (int)(ax >> 20) - 1023 + 127 + s;             // biased exponent of the float
+  if (fe <= 0) return 0.0f;
+  const uint32_t mag = (((uint32_t)fe << 23) | ((ax & 0xFFFFFu) << 3) | (lw >> 29)) + ((lw >> 28) & 1u);
+  return __uint_as_float(mag | (hw & 0x80000000u));
+}
+
+// x * 2^s split into TF32 hi + lo; in FP32 from the bits when the scaled row
+// stays in FP32's normal range, else through FP64
 __device__ __forceinline__ void split_scaled(double x, int s, bool fp32_ok, float &h, float &l) {
   if (fp32_ok) {
-    const float xf = __double2float_rn(x) * __int_as_float((127 + s) << 23);
+    const float xf = scaled_float(x, s);
     h = to_tf32(xf);
     l = to_tf32(xf - h);
   } else {
@@ -361,24 +374,79 @@ __device__ __forceinline__ void split_scaled(double x, int s, bool fp32_ok, floa
   }
 }
 
-// A (M x K): A[m*lda + k*ska] -> TF32 hi/lo [Mp x Kp], zero-padded; sa[m]
+// A (M x K): A[m*lda + k*ska] -> TF32 hi/lo [Mp x Kp], zero-padded; sa[m].
+// Rows with unit stride and 16-byte alignment are read as double2, four in
+// flight per thread, and written as float2.
 __global__ void __launch_bounds__(256) split_rows(const double *__restrict__ A, int64_t M, int64_t K, int64_t lda,
                                                   int64_t ska, float *__restrict__ hi, float *__restrict__ lo,
                                                   int64_t Kp, int *__restrict__ sa) {
   __shared__ double red[32];
   const int64_t m = blockIdx.x;
   const double *row = A + m * lda;
+  const bool vec = ska == 1 && ((uintptr_t)row & 15) == 0 && (K & 1) == 0 && (Kp & 1) == 0;
   // |x| compared as integers on the sign-cleared bit pattern (no FP64 pipe work)
   unsigned long long bits = 0;
-  if (m < M)
-    for (int64_t k = threadIdx.x; k < K; k += blockDim.x)
-      bits = max(bits, (unsigned long long)__double_as_longlong(row[k * ska]) & 0x7fffffffffffffffull);
+  if (m < M) {
+    if (vec) {
+      const double2 *r2 = (const double2 *)row;
+      const int64_t K2 = K >> 1;
+      int64_t k = threadIdx.x;
+      for (; k + 3 * blockDim.x < K2; k += 4 * blockDim.x) {
+        double2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = r2[k + u * blockDim.x];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          bits = max(bits, (unsigned long long)__double_as_longlong(v[u].x) & 0x7fffffffffffffffull);
+          bits = max(bits, (unsigned long long)__double_as_longlong(v[u].y) & 0x7fffffffffffffffull);
+        }
+      }
+      for (; k < K2; k += blockDim.x) {
+        const double2 v = r2[k];
+        bits = max(bits, (unsigned long long)__double_as_longlong(v.x) & 0x7fffffffffffffffull);
+        bits = max(bits, (unsigned long long)__double_as_longlong(v.y) & 0x7fffffffffffffffull);
+      }
+    } else {
+      for (int64_t k = threadIdx.x; k < K; k += blockDim.x)
+        bits = max(bits, (unsigned long long)__double_as_longlong(row[k * ska]) & 0x7fffffffffffffffull);
+    }
+  }
   double mx = block_max(__longlong_as_double((long long)bits), red);
   const int s = scale_for(mx);
   // the scaled row max is below 2^14; FP32 scaling is exact while |x| >= 2^-100 * max
   const bool fp32_ok = mx == 0.0 || (mx > 0x1p-26 && mx < 0x1p+100 && s > -120 && s < 120);
   if (threadIdx.x == 0 && m < M) sa[m] = s;
   float *hrow = hi + m * Kp, *lrow = lo + m * Kp;
+  if (vec && m < M) {
+    const double2 *r2 = (const double2 *)row;
+    float2 *h2 = (float2 *)hrow, *l2 = (float2 *)lrow;
+    const int64_t K2 = K >> 1, Kp2 = Kp >> 1;
+    int64_t k = threadIdx.x;
+    for (; k + 3 * blockDim.x < K2; k += 4 * blockDim.x) {
+      double2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = r2[k + u * blockDim.x];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float ha, la, hb, lb;
+        split_scaled(v[u].x, s, fp32_ok, ha, la);
+        split_scaled(v[u].y, s, fp32_ok, hb, lb);
+        h2[k + u * blockDim.x] = make_float2(ha, hb);
+        l2[k + u * blockDim.x] = make_float2(la, lb);
+      }
+    }
+    for (; k < Kp2; k += blockDim.x) {
+      float ha = 0.f, la = 0.f, hb = 0.f, lb = 0.f;
+      if (k < K2) {
+        const double2 v = r2[k];
+        split_scaled(v.x, s, fp32_ok, ha, la);
+        split_scaled(v.y, s, fp32_ok, hb, lb);
+      }
+      h2[k] = make_float2(ha, hb);
+      l2[k] = make_float2(la, lb);
+    }
+    return;
+  }
   for (int64_t k = threadIdx.x; k < Kp; k += blockDim.x) {
     float h = 0.f, l = 0.f;
     if (m < M && k < K) split_scaled(row[k * ska], s, fp32_ok, h, l);
