@@ -75,9 +75,10 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # sine and the conversions are not counted, so this is a lower bound)
 DF_FLOPS_PER_ELEMENT = 15 * (3 * 35 * 35 + 3 * 3 * 35) + 3 * 2 * 105
 # bf16 MMA flops the tensor-core variant issues per element: 21 digit
-# products x 3 K-steps of 16 x 144 accumulator columns (three blocks of 48:
-# 35 dofs x 3 terms padded to 4 columns per dof) x 2
-TC_MMA_FLOPS_PER_ELEMENT = 21 * 3 * 16 * 144 * 2
+# products x 3 K-steps of 16 x 112 accumulator columns (blocks of 32, 32, 32
+# and 16: halves of 16 columns holding 5 dofs x 3 terms and one padding
+# column) x 2
+TC_MMA_FLOPS_PER_ELEMENT = 21 * 3 * 16 * 112 * 2
 
 
 def kernel_traffic(kernel):
