@@ -6,14 +6,15 @@
 // an error-free split of both operands into small integer digits:
 //
 //  * u[e, :] (one element, produced by the fused producer in double-float)
-//    is scaled by 2^-k_e so that every |v_j| < 1 and written as six
-//    balanced base-512 digits, v = 2^-8 sum_q d_q 2^-9q with |d_q| <= 256;
-//    d_q 2^-9q is exact in bf16.  Each row n = (r, i) of D gets its own
-//    2^-k_n and digits c_p the same way (from FP64, once per CTA).
-//  * sum_j D[n,j] u[e,j] = 2^(k_e + k_n - 16) sum_{p,q} sum_j (c_p 2^-9p)(d_q 2^-9q).
+//    is scaled by 2^-k_e so that every |v_j| <= 1 and written as six
+//    balanced base-512 digits, v = sum_q d_q 2^(-8-9q) with |d_q| <= 256;
+//    each d_q 2^(-8-9q) is exact in bf16.  Each row n = (r, i) of D gets its
+//    own 2^-k_n and digits c_p (D 2^-k_n = 2^-8 sum_p c_p 2^-9p, c_p 2^-9p
+//    stored), from the FP64 bits once per CTA.
+//  * sum_j D[n,j] u[e,j] = 2^(k_e + k_n - 8) sum_{p,q} sum_j (c_p 2^-9p)(d_q 2^(-8-9q)).
 //    The digit products are grouped by level L = p + q.  Levels 0..3 each
 //    accumulate in their own FP32 tensor-memory accumulator: every partial
-//    sum is an integer multiple of 2^-9L below 2^24 * 2^-9L (at most 4 pairs
+//    sum is an integer multiple of 2^(-8-9L) below 2^24 times that (at most 4 pairs
 //    x 64 terms x 2^16), so the tensor core adds them exactly.  Levels 4 and
 //    5 share a fifth accumulator (its truncation stays below 2^-49 of
 //    NJ max|u| max|D|); levels 6 and up are dropped (below 2^-50 of the same).
@@ -91,21 +92,27 @@ __device__ __forceinline__ int row_exp(double mx) {
 }
 __device__ __forceinline__ float pow2f(int k) { return __uint_as_float((uint32_t)(k + 127) << 23); }   // |k| <= 126
 
-// the same for v = u * sc in double-float (sc a power of two): every step
-// is exact
-__device__ __forceinline__ void digits_df(df u, float sc, float *d) {
-  float h = u.hi * sc, l = u.lo * sc;
-  const float MAGIC = 12582912.0f;              // 1.5 * 2^23: adding it rounds to an integer
+// six digits of v = h + l (a double-float value, |v| <= 1): digit q is the
+// remainder rounded to a multiple of 2^(-8-9q), at most 256 such multiples
+// in magnitude and hence exact in bf16; v = sum_q r_q up to 2^-54.  The
+// rounding adds and subtracts 1.5 * 2^23 times the grid, taking the digit
+// off is exact (both are multiples of the remainder's last place), and the
+// low part is folded in by Fast2Sum after each of the first four digits
+// (valid since the remainder is zero or a multiple of that last place, at
+// least twice |l|), which keeps every later digit within its bound
+__device__ __forceinline__ void digits_df(float h, float l, float *r) {
+  const float M[TC_P] = {0x1.8p+15f, 0x1.8p+6f, 0x1.8p-3f, 0x1.8p-12f, 0x1.8p-21f, 0x1.8p-30f};
 #pragma unroll
-  for (int q = 0; q < TC_P - 1; ++q) {
-    const float t = __fadd_rn(__fmaf_rn(h, 256.0f, MAGIC), -MAGIC);
-    h = __fmaf_rn(t, -0.00390625f, h);          // h - t/256, exact
-    const df s = dfm::two_sum(h, l);
-    h = s.hi * 512.0f;
-    l = s.lo * 512.0f;
-    d[q] = t * pow2f(-9 * q);
+  for (int q = 0; q < TC_P; ++q) {
+    const float d = __fadd_rn(__fadd_rn(h, M[q]), -M[q]);
+    r[q] = d;
+    if (q + 1 < TC_P) h = __fadd_rn(h, -d);
+    if (q < 4) {
+      const float s = __fadd_rn(h, l);
+      l = __fadd_rn(l, -__fadd_rn(s, -h));
+      h = s;
+    }
   }
-  d[TC_P - 1] = __fadd_rn(__fmaf_rn(h, 256.0f, MAGIC), -MAGIC) * pow2f(-9 * (TC_P - 1));
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -219,9 +226,11 @@ __device__ __forceinline__ bool brow(const TcParams &tp, int n, int &i, int &r) 
   return il < H0 && i < tp.p.NI;
 }
 
-template <int R>
+// ROWS: the number of einsums when specialized, 0 for any count up to 4
+template <int R, int ROWS>
 __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_constant__ TcParams tp) {
   constexpr int H0 = 16 / R;                    // i per 16-column half of a block
+  constexpr int KR = ROWS ? ROWS : TC_MAXROWS;  // einsums held per thread
   constexpr int IB = 2 * H0;                    // i per column block
   const EParams &p = tp.p;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -232,10 +241,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
   uint8_t *Ap = Bp + TC_P * bplane;                         // 2 buffers x TC_P planes x KS slices x 128 rows x 32 B
   float2 *sin_tab = (float2 *)(Ap + 2 * TC_P * aplane);     // full-circle sine table
   int *kD = (int *)(sin_tab + dfm::SIN2_N);                 // [TC_MAXNB]
+  float *kDs = (float *)(kD + TC_MAXNB);                    // [TC_MAXNB] 2^kD
   // Row scales of u for the last TC_KU tiles: the epilogue can trail the
   // producer by up to 2 + ceil(3 / ncb) tiles (two digit buffers ahead of
   // the MMAs, which run at most three column blocks ahead of the epilogue)
-  int *kU = kD + TC_MAXNB;                                  // [TC_KU][TC_M]
+  int *kU = (int *)(kDs + TC_MAXNB);                        // [TC_KU][TC_M]
   int *mxw = kU + TC_KU * TC_M;                             // [TC_M] high words of the row bounds
   uint64_t *bars = (uint64_t *)(mxw + TC_M);
   uint64_t *a_full = bars, *a_empty = bars + 2, *s_full = bars + 4, *s_empty = bars + 4 + TC_NSLOT;
@@ -277,6 +287,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
     if (brow<R>(tp, n, i, r))
       for (int j = 0; j < NJ; ++j) hw = max(hw, __double2hiint(p.D[r * p.sr + i * p.si + j * p.sj]) & 0x7FFFFFFF);
     kD[n] = row_exp(__hiloint2double(hw, 0));
+    kDs[n] = pow2f(kD[n]);
   }
   __syncthreads();
   // digit planes of D: item (row n, group g of 8 values of j)
@@ -379,8 +390,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
             const int m = (int)(((uint32_t)pi * jinv) >> 20), j = 2 * (pi - m * JP);
             const float sc = pow2f(-ku[m]);
             float d0[TC_P], d1[TC_P];
-            digits_df(produce(q, av[4 * u], av[4 * u + 2], sin_tab), sc, d0);
-            digits_df(produce(q, av[4 * u + 1], av[4 * u + 3], sin_tab), sc, d1);   // zero past NJ
+            const df u0 = produce(q, av[4 * u], av[4 * u + 2], sin_tab);
+            const df u1 = produce(q, av[4 * u + 1], av[4 * u + 3], sin_tab);   // zero past NJ
+            digits_df(u0.hi * sc, u0.lo * sc, d0);
+            digits_df(u1.hi * sc, u1.lo * sc, d1);
             uint8_t *dst = A + sw32(TC_M, m, j >> 3) + (j & 7) * 2;
 #pragma unroll
             for (int k = 0; k < TC_P; ++k) *(uint32_t *)(dst + k * aplane) = pack_bf16(d0[k], d1[k]);
@@ -460,13 +473,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
       const bool valid = e < p.E;
       // g_k[e, r] of this thread's element as double-float (scaled by
       // 2^(k_e - 16) once the tile's exponents are known)
-      df gk[TC_MAXROWS][R];
+      df gk[KR][R];
 #pragma unroll
-      for (int k = 0; k < TC_MAXROWS; ++k)
+      for (int k = 0; k < KR; ++k)
 #pragma unroll
         for (int r = 0; r < R; ++r)
           gk[k][r] = dfm::df_from_double(
-              (valid && k < n_rows) ? (p.has_g ? p.rows[k].g.ptr[e * p.rows[k].g.se + r * p.rows[k].g.sk] : 1.0) : 0.0);
+              (valid && (ROWS || k < n_rows)) ? (p.has_g ? p.rows[k].g.ptr[e * p.rows[k].g.se + r * p.rows[k].g.sk] : 1.0) : 0.0);
       for (int cb = 0; cb < tp.ncb; ++cb, ++cnt) {
         const int slot = (int)(cnt % TC_NSLOT);
         const uint32_t use = (uint32_t)(cnt / TC_NSLOT);
@@ -474,9 +487,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
         if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
         tc::fence_after();
         if (cb == 0) {
-          const float sg = pow2f(kU[(t & (TC_KU - 1)) * TC_M + m] - 16);
+          const float sg = pow2f(kU[(t & (TC_KU - 1)) * TC_M + m] - 8);
 #pragma unroll
-          for (int k = 0; k < TC_MAXROWS; ++k)
+          for (int k = 0; k < KR; ++k)
 #pragma unroll
             for (int r = 0; r < R; ++r) gk[k][r] = df{gk[k][r].hi * sg, gk[k][r].lo * sg};
         }
@@ -506,7 +519,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
               df s23 = dfm::two_sum(__uint_as_float(v[2][c]), __uint_as_float(v[3][c]));
               s23.lo += __uint_as_float(v[4][c]);
               const df x = dfm::df_add(s01, s23);
-              const float sc = pow2f(kD[min(tp.n0[cb] + half * 16 + ch * 8 + c, tp.NBtot - 1)]);
+              const float sc = kDs[min(tp.n0[cb] + half * 16 + ch * 8 + c, tp.NBtot - 1)];
               th[ch * 8 + c] = x.hi * sc;
               tl[ch * 8 + c] = x.lo * sc;
             }
@@ -518,16 +531,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
             if (il < nIh) {
               const int i = cb * IB + half * H0 + il;
 #pragma unroll
-              for (int k = 0; k < TC_MAXROWS; ++k) {
-                if (k < n_rows) {
+              for (int k = 0; k < KR; ++k) {
+                if (ROWS || k < n_rows) {
                   // first term: its exact product starts the pair (s, c)
                   const df g0 = gk[k][0], t0{th[il * R], tl[il * R]};
                   float s = g0.hi * t0.hi;
                   float c = fmaf(g0.hi, t0.lo, fmaf(g0.lo, t0.hi, fmaf(g0.hi, t0.hi, -s)));
 #pragma unroll
                   for (int r = 1; r < R; ++r) dfm::dot_acc(s, c, gk[k][r], df{th[il * R + r], tl[il * R + r]});
-                  // hi + lo on the FP64 pipe (otherwise idle here): 3 instructions
-                  // instead of the bit assembly's ~35 on the FP32/ALU pipes
+                  // hi + lo on the FP64 pipe: 3 instructions
                   p.rows[k].out[e * NI + i] = (double)s + (double)c;
                 }
               }
@@ -589,19 +601,26 @@ bool build_params(const EParams &p, TcParams &tp, std::string &why) {
 
 size_t smem_bytes(const TcParams &tp) {
   return 1024 + (size_t)TC_P * tp.KS * tp.NBtot * 32 + 2 * (size_t)TC_P * tp.KS * TC_M * 32 +
-         sizeof(float2) * dfm::SIN2_N + sizeof(int) * (TC_MAXNB + (TC_KU + 1) * TC_M) + 8 * (5 + 2 * TC_NSLOT) + 16;
+         sizeof(float2) * dfm::SIN2_N + sizeof(int) * (2 * TC_MAXNB + (TC_KU + 1) * TC_M) + 8 * (5 + 2 * TC_NSLOT) + 16;
 }
 
-template <int R>
-cudaError_t launch_r(const TcParams &tp, int grid, size_t smem, cudaStream_t s) {
+template <int R, int ROWS>
+cudaError_t launch_rr(const TcParams &tp, int grid, size_t smem, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t st = cudaFuncSetAttribute(element_tc_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaError_t st =
+        cudaFuncSetAttribute(element_tc_kernel<R, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (st != cudaSuccess) return st;
     attr = true;
   }
-  element_tc_kernel<R><<<grid, TC_THREADS, smem, s>>>(tp);
+  element_tc_kernel<R, ROWS><<<grid, TC_THREADS, smem, s>>>(tp);
   return cudaGetLastError();
+}
+// one einsum per term direction (R einsums, as in a gradient) is
+// specialized; other counts take the generic row loop
+template <int R>
+cudaError_t launch_r(const TcParams &tp, int grid, size_t smem, cudaStream_t s) {
+  return tp.p.n_rows == R ? launch_rr<R, R>(tp, grid, smem, s) : launch_rr<R, 0>(tp, grid, smem, s);
 }
 
 }  // namespace
