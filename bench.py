@@ -345,6 +345,94 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
+# ------------------------------------------- DG divergence and face mass
+
+def run_stacked(args):
+    """DG local divergence 'xre,rij,xej->ei' (select producer over x) or
+    face mass 'fe,ifj,fej->ei', b rows sharing the operator, on the element
+    strategy's stacked form; the same einsum on the generic loop-nest
+    kernel is timed beside it."""
+    import torch
+    import paper_2601_12220_b300 as be
+
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    E, order, rows = args.stacked_elements, args.order, args.rows
+    N = W.tet_dofs(order)
+    if args.workload == "dg_divergence":
+        D, data = W.dg_divergence(E=E, order=order, rows=rows)
+        host = W.dg_divergence_arrays(D, data)
+        text = W.dg_divergence_spec(E=E, order=order, rows=rows)
+        X, S, NJ0 = 3, 3, N
+        desc = f"dg_divergence_p{order}: b={rows} 'xre,rij,xej->ei', D 3x{N}x{N} shared, F selects u/v/w by x, E={E}"
+    else:
+        M, data = W.face_mass(E=E, order=order, rows=rows)
+        host = W.face_mass_arrays(M, data)
+        text = W.face_mass_spec(E=E, order=order, rows=rows)
+        X, S, NJ0 = 1, 4, W.tri_dofs(order)
+        desc = f"face_mass_p{order}: b={rows} 'fe,ifj,fej->ei', M {N}x4x{NJ0} shared, E={E}"
+    K = S * NJ0
+    bufs = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
+    outs = [torch.empty((E, N), dtype=torch.float64, device=dev) for _ in range(rows)]
+    ctx = be.Context(None, device=local)
+    stream = torch.cuda.current_stream(dev)
+    byts = 8.0 * sum(v.size for k, v in host.items()) + 8.0 * rows * E * N
+    # FP32 flops of the double-float kernel: 15 per compensated term over the
+    # contraction (N x K) and the production of v (K x X), per row
+    df_flops = 15.0 * rows * E * (N * K + K * X)
+    strat = be.plan_strategy(ctx, be.Einsum(text))
+
+    def step(cfg=None):
+        e = be.Einsum(text)
+        c = e.canonicalize()
+        hit = ctx.lookup(c, be.PREC_FP64)
+        be.execute(ctx, e, bufs, outs, cfg=cfg or (hit[0] if hit else None), precision=be.PREC_FP64, stream=stream)
+
+    def timed(cfg, steps):
+        for _ in range(args.warmup):
+            step(cfg)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            step(cfg)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / steps
+
+    ctx.set_timing(True)
+    with Clocks(local) as clk:
+        ms = timed(None, args.steps)
+    ctx.set_timing(False)
+    n_launch, k_total = ctx.timing(be.KERNEL_ELEMENT)
+    kms = k_total / max(1, n_launch)
+    gen_ms = timed(be.make_config(be.STRAT_GENERIC), max(3, args.steps // 4))
+    peaks = load_peaks()
+    ach_tf = df_flops / (kms * 1e-3) / 1e12
+    ach_gb = byts / (kms * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": world * byts / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "E": E, "order": order, "b": rows, "K": K,
+                       "parallelism": f"replicas x{world}", "l2": f"{byts / 1e6:.0f} MB per step, no flush",
+                       "strategy": {1: "generic", 2: "element"}.get(strat, str(strat)),
+                       "element_variant": "double-float (stacked form)"},
+            "kernel_ms": kms,
+            "roofline": {"kernel": "element_df_kernel", "bound": "alu", "achieved": ach_tf,
+                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach_tf / FP32_PEAK_TFLOPS,
+                         "counts": "FP32 flops of the compensated terms (15 per term, contraction and production)",
+                         "peak_source": "FP32 pipe from unit counts and clock: 148 SMs x 128 lanes x 2 x 2.032 GHz",
+                         "traffic": None, "algorithmic_bytes": byts,
+                         "hbm": {"achieved": ach_gb, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                 "frac": ach_gb / peaks["hbm_gbs"], "peak_source": peaks["source"]}},
+            "generic": {"ms_per_step": gen_ms, "value": world * byts / (gen_ms * 1e-3) / 1e9,
+                        "speedup_of_element": gen_ms / ms},
+            "clocks": clk.summary(), "gpu_launches": n_launch}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------- workload 3
 
 V_FULL, O_FULL, B_CHEM = 128, 32, 4
@@ -601,7 +689,10 @@ def main():
     ap.add_argument("--element-variant", type=int, default=0,
                     help="0 default (double-float on the FP32 pipe), 1 FP64 pipe")
     ap.add_argument("--workload", default="dg_gradient",
-                    choices=["dg_gradient", "chem_dense", "uneven_mix", "serving"])
+                    choices=["dg_gradient", "chem_dense", "uneven_mix", "serving", "dg_divergence", "face_mass"])
+    ap.add_argument("--order", type=int, default=4, help="polynomial order of dg_divergence / face_mass")
+    ap.add_argument("--rows", type=int, default=1, help="einsums b of dg_divergence / face_mass")
+    ap.add_argument("--stacked-elements", type=int, default=100000)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-templates", type=int, default=256)
@@ -622,6 +713,8 @@ def main():
         run_mix(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload in ("dg_divergence", "face_mass"):
+        run_stacked(args)
     else:
         run_ours(args)
 

@@ -478,8 +478,7 @@ static int do_execute(be_ctx *x, const be_einsum *hc, const be_config *cfg, int3
     int dev = 0, sms = 148, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    size_t smem = sizeof(double) * ((size_t)ep.R * ep.NI * ep.NJ + (size_t)ep.n_groups * ep.tile_e * ep.NJ +
-                                    (size_t)ep.n_rows * ep.tile_e * ep.R);
+    size_t smem = sizeof(double) * element_smem_words(ep);
     per_sm = (int)std::max<size_t>(1, std::min<size_t>(2048 / block, (220 * 1024) / (smem + 1024)));
     int64_t tiles = (ep.E + ep.tile_e - 1) / ep.tile_e;
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * per_sm));

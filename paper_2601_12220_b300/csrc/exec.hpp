@@ -68,6 +68,8 @@ cudaError_t launch_persistent(const GParams *rows, const PTile *tiles, int64_t n
 #define EM_MAXROWS 16
 #define EM_MAXN 64
 #define EM_MAXR 4
+#define EM_MAXK 128     // flat contracted extent S * NJ0 of the stacked form
+#define EM_MAXX 4       // terms x of a stacked producer
 
 // strided 2-index view x[e, k] = ptr[e * se + k * sk]
 struct EView {
@@ -75,10 +77,19 @@ struct EView {
   int64_t se, sk;
 };
 
-// producer of a per-element operand: 0 view a; 1 sin(a) * b; 2 a * b
+// strided view over (e, s, j): ptr[e * se + s * ss + j * sj]
+struct ESView {
+  const double *ptr;
+  int64_t se, ss, sj;
+};
+
+// producer of a per-element operand: 0 view a; 1 sin(a) * b; 2 a * b;
+// 3 (stacked) v[e, s, j] = sum_{x < X} A_x[e, s, j] * B_x[e, s, j], read at
+// the flat index k = s * NJ0 + j (EParams::NJ0)
 struct EProd {
-  int32_t kind, pad;
+  int32_t kind, X;
   EView a, b;
+  ESView A[EM_MAXX], B[EM_MAXX];
 };
 
 struct ERow {
@@ -88,15 +99,37 @@ struct ERow {
   double *out;      // dense out[e, i]
 };
 
+// R_k[e, i] = sum_{r, j} D[r, i, j] g_k[e, r] u_k[e, j] with D[r, i, j] at
+// D[r * sr + i * si + j * sj].  In the stacked form (NJ0 > 0: R = 1, no g)
+// the contracted index is the flat k = s * NJ0 + j < NJ over two letters
+// of D, read at D[i * si + s * sr + j * sj].
 struct EParams {
   const double *D;
   int64_t sr, si, sj;          // D[r, i, j] strides
   int32_t R, NI, NJ, has_g;
   int64_t E;
-  int32_t n_rows, n_groups, tile_e, pad;
+  int32_t n_rows, n_groups, tile_e, NJ0;
   ERow rows[EM_MAXROWS];
   EProd groups[EM_MAXROWS];
 };
+
+// shared-memory doubles (or float pairs) of the FP64 and double-float
+// element kernels: the operator, one producer group's operand tile (groups
+// are staged one after another) and every row's geometric factors
+inline size_t element_smem_words(const EParams &p) {
+  return (size_t)p.R * p.NI * p.NJ + (size_t)p.tile_e * p.NJ + (size_t)p.n_rows * p.tile_e * p.R;
+}
+// budget for those words: 200 KB less the double-float kernel's sine table
+#define EM_SMEM_BUDGET (190 * 1024)
+
+// offset of D[r, i, k] (flat k in the stacked form)
+__host__ __device__ inline int64_t d_offset(const EParams &p, int r, int i, int k) {
+  if (p.NJ0 > 0) {
+    const int s = k / p.NJ0;
+    return (int64_t)i * p.si + (int64_t)s * p.sr + (int64_t)(k - s * p.NJ0) * p.sj;
+  }
+  return (int64_t)r * p.sr + (int64_t)i * p.si + (int64_t)k * p.sj;
+}
 
 cudaError_t launch_element(const EParams &p, int grid, int block, cudaStream_t s);
 // same strategy in double-float arithmetic on the FP32 pipe (FP64 accuracy)

@@ -12,17 +12,26 @@
 // reused by every row that shares it, then contracted with g_k.
 //
 // Layout: a persistent grid; each CTA stages D once in shared memory and
-// then walks element tiles.  Per tile the u producers are evaluated while
-// loading (e.g. u = sin(a) * b, fused into the operand load) into shared
-// memory together with g; threads then own (e, i) output points, so the
-// stores of R_k[e, i] are contiguous.
+// then walks element tiles.  Per tile g is staged for every row, then each
+// distinct u producer in turn is evaluated while loading (e.g. u = sin(a) *
+// b, fused into the operand load) into shared memory and contracted;
+// threads own (e, i) output points, so the stores of R_k[e, i] are
+// contiguous.
 #include "exec.hpp"
 
 namespace be {
 
 namespace {
 
-__device__ __forceinline__ double prod_value(const EProd &q, int64_t e, int k) {
+__device__ __forceinline__ double prod_value(const EProd &q, int64_t e, int k, int NJ0) {
+  if (q.kind == 3) {   // stacked: sum_x A_x[e, s, j] * B_x[e, s, j] at k = s * NJ0 + j
+    const int s = k / NJ0, j = k - s * NJ0;
+    double acc = 0.0;
+    for (int x = 0; x < q.X; ++x)
+      acc = fma(q.A[x].ptr[e * q.A[x].se + s * q.A[x].ss + j * q.A[x].sj],
+                q.B[x].ptr[e * q.B[x].se + s * q.B[x].ss + j * q.B[x].sj], acc);
+    return acc;
+  }
   double a = q.a.ptr[e * q.a.se + k * q.a.sk];
   if (q.kind == 0) return a;
   double b = q.b.ptr[e * q.b.se + k * q.b.sk];
@@ -34,14 +43,14 @@ __global__ void __launch_bounds__(256) element_kernel(const __grid_constant__ EP
   extern __shared__ double smem[];
   const int R = p.R, NI = p.NI, NJ = p.NJ, TE = p.tile_e;
   double *Ds = smem;                                   // [R][NI][NJ]
-  double *Us = Ds + R * NI * NJ;                       // [groups][TE][NJ]
-  double *Gs = Us + p.n_groups * TE * NJ;              // [rows][TE][R]
+  double *Us = Ds + R * NI * NJ;                       // [TE][NJ], one producer group at a time
+  double *Gs = Us + TE * NJ;                           // [rows][TE][R]
   const int tid = threadIdx.x, nt = blockDim.x;
 
   for (int idx = tid; idx < R * NI * NJ; idx += nt) {
     int r = idx / (NI * NJ), rem = idx % (NI * NJ);
     int i = rem / NJ, j = rem % NJ;
-    Ds[idx] = p.D[r * p.sr + i * p.si + j * p.sj];
+    Ds[idx] = p.D[d_offset(p, r, i, j)];
   }
 
   const int64_t n_tiles = (p.E + TE - 1) / TE;
@@ -49,11 +58,6 @@ __global__ void __launch_bounds__(256) element_kernel(const __grid_constant__ EP
     const int64_t e0 = tile * TE;
     const int te = (int)((p.E - e0) < TE ? (p.E - e0) : TE);
     __syncthreads();   // D ready / previous tile consumed
-    for (int idx = tid; idx < p.n_groups * te * NJ; idx += nt) {
-      int g = idx / (te * NJ), rem = idx % (te * NJ);
-      int el = rem / NJ, j = rem % NJ;
-      Us[(g * TE + el) * NJ + j] = prod_value(p.groups[g], e0 + el, j);
-    }
     if (p.has_g) {
       for (int idx = tid; idx < p.n_rows * te * R; idx += nt) {
         int k = idx / (te * R), rem = idx % (te * R);
@@ -62,12 +66,17 @@ __global__ void __launch_bounds__(256) element_kernel(const __grid_constant__ EP
         Gs[(k * TE + el) * R + r] = v.ptr[(e0 + el) * v.se + r * v.sk];
       }
     }
-    __syncthreads();
-    for (int item = tid; item < te * NI; item += nt) {
-      const int el = item / NI, i = item % NI;
-      for (int g = 0; g < p.n_groups; ++g) {
+    for (int g = 0; g < p.n_groups; ++g) {
+      if (g > 0) __syncthreads();   // the previous group's operand consumed
+      for (int idx = tid; idx < te * NJ; idx += nt) {
+        int el = idx / NJ, j = idx % NJ;
+        Us[el * NJ + j] = prod_value(p.groups[g], e0 + el, j, p.NJ0);
+      }
+      __syncthreads();
+      for (int item = tid; item < te * NI; item += nt) {
+        const int el = item / NI, i = item % NI;
         double t[EM_MAXR];
-        const double *u = Us + (g * TE + el) * NJ;
+        const double *u = Us + el * NJ;
         for (int r = 0; r < R; ++r) {
           const double *d = Ds + (r * NI + i) * NJ;
           double acc = 0.0;
@@ -94,8 +103,7 @@ __global__ void __launch_bounds__(256) element_kernel(const __grid_constant__ EP
 }  // namespace
 
 cudaError_t launch_element(const EParams &p, int grid, int block, cudaStream_t s) {
-  size_t smem = sizeof(double) * ((size_t)p.R * p.NI * p.NJ + (size_t)p.n_groups * p.tile_e * p.NJ +
-                                  (size_t)p.n_rows * p.tile_e * p.R);
+  size_t smem = sizeof(double) * element_smem_words(p);
   if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
   static bool attr = false;
   if (!attr) {

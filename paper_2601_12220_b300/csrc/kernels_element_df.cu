@@ -1,6 +1,7 @@
 // Element strategy on the FP32 pipe: the same batched einsums as
 // element_kernel (R_k[e,i] = sum_{r,j} D[r,i,j] g_k[e,r] u_k[e,j], D shared,
-// Sec. "Batched einsums in DG-FEM Operators"), with the same hoisting
+// Sec. "Batched einsums in DG-FEM Operators", and the stacked form of the
+// divergence and face mass), with the same hoisting
 // t[r,i] = sum_j D[r,i,j] u[e,j] once per distinct u, but every operation in
 // double-float (df) arithmetic: D, u and g are held as float pairs, the dot
 // products accumulate exactly through TwoSum with the cross terms in a
@@ -18,7 +19,15 @@ namespace {
 
 using dfm::df;
 
-__device__ __forceinline__ df prod_df(const EProd &q, int64_t e, int k, const float4 *sin_tab) {
+__device__ __forceinline__ df prod_df(const EProd &q, int64_t e, int k, int NJ0, const float4 *sin_tab) {
+  if (q.kind == 3) {   // stacked: sum_x A_x[e, s, j] * B_x[e, s, j] at k = s * NJ0 + j, in df
+    const int s = k / NJ0, j = k - s * NJ0;
+    float sh = 0.f, sl = 0.f;
+    for (int x = 0; x < q.X; ++x)
+      dfm::dot_acc(sh, sl, dfm::df_from_double(q.A[x].ptr[e * q.A[x].se + s * q.A[x].ss + j * q.A[x].sj]),
+                   dfm::df_from_double(q.B[x].ptr[e * q.B[x].se + s * q.B[x].ss + j * q.B[x].sj]));
+    return dfm::two_sum(sh, sl);
+  }
   const double a = q.a.ptr[e * q.a.se + k * q.a.sk];
   if (q.kind == 0) return dfm::df_from_double(a);
   const double b = q.b.ptr[e * q.b.se + k * q.b.sk];
@@ -32,9 +41,9 @@ __global__ void __launch_bounds__(512, 2) element_df_kernel(const __grid_constan
   extern __shared__ float2 smf[];
   const int R = p.R, NI = p.NI, NJ = p.NJ, TE = p.tile_e;
   float2 *Ds = smf;                                   // [R][NI][NJ]
-  float2 *Us = Ds + R * NI * NJ;                      // [groups][TE][NJ]
-  float2 *Gs = Us + p.n_groups * TE * NJ;             // [rows][TE][R]
-  const int n_f2 = R * NI * NJ + p.n_groups * TE * NJ + p.n_rows * TE * R;
+  float2 *Us = Ds + R * NI * NJ;                      // [TE][NJ], one producer group at a time
+  float2 *Gs = Us + TE * NJ;                          // [rows][TE][R]
+  const int n_f2 = R * NI * NJ + TE * NJ + p.n_rows * TE * R;
   float4 *sin_tab = (float4 *)(smf + n_f2 + (n_f2 & 1));              // 16-byte aligned
   const int tid = threadIdx.x, nt = blockDim.x;
   dfm::sin_table_fill(sin_tab);
@@ -42,7 +51,7 @@ __global__ void __launch_bounds__(512, 2) element_df_kernel(const __grid_constan
   for (int idx = tid; idx < R * NI * NJ; idx += nt) {
     const int r = idx / (NI * NJ), rem = idx % (NI * NJ);
     const int i = rem / NJ, j = rem % NJ;
-    const df d = dfm::df_from_double(p.D[r * p.sr + i * p.si + j * p.sj]);
+    const df d = dfm::df_from_double(p.D[d_offset(p, r, i, j)]);
     Ds[idx] = make_float2(d.hi, d.lo);
   }
 
@@ -51,12 +60,6 @@ __global__ void __launch_bounds__(512, 2) element_df_kernel(const __grid_constan
     const int64_t e0 = tile * TE;
     const int te = (int)((p.E - e0) < TE ? (p.E - e0) : TE);
     __syncthreads();
-    for (int idx = tid; idx < p.n_groups * te * NJ; idx += nt) {
-      const int g = idx / (te * NJ), rem = idx % (te * NJ);
-      const int el = rem / NJ, j = rem % NJ;
-      const df u = prod_df(p.groups[g], e0 + el, j, sin_tab);
-      Us[(g * TE + el) * NJ + j] = make_float2(u.hi, u.lo);
-    }
     if (p.has_g) {
       for (int idx = tid; idx < p.n_rows * te * R; idx += nt) {
         const int k = idx / (te * R), rem = idx % (te * R);
@@ -66,17 +69,23 @@ __global__ void __launch_bounds__(512, 2) element_df_kernel(const __grid_constan
         Gs[(k * TE + el) * R + r] = make_float2(gv.hi, gv.lo);
       }
     }
-    __syncthreads();
     // each item: one dof i for DF_EPT consecutive elements, so D[r, i, :] is
     // read once from shared memory for all of them
     const int groups_e = (te + DF_EPT - 1) / DF_EPT;
-    for (int item = tid; item < groups_e * NI; item += nt) {
-      const int eg = item / NI, i = item % NI;
-      const int el0 = eg * DF_EPT;
-      const int nq = min(DF_EPT, te - el0);
-      for (int g = 0; g < p.n_groups; ++g) {
+    for (int g = 0; g < p.n_groups; ++g) {
+      if (g > 0) __syncthreads();   // the previous group's operand consumed
+      for (int idx = tid; idx < te * NJ; idx += nt) {
+        const int el = idx / NJ, j = idx % NJ;
+        const df u = prod_df(p.groups[g], e0 + el, j, p.NJ0, sin_tab);
+        Us[el * NJ + j] = make_float2(u.hi, u.lo);
+      }
+      __syncthreads();
+      for (int item = tid; item < groups_e * NI; item += nt) {
+        const int eg = item / NI, i = item % NI;
+        const int el0 = eg * DF_EPT;
+        const int nq = min(DF_EPT, te - el0);
         df t[DF_EPT][EM_MAXR];
-        const float2 *u0 = Us + (g * TE + el0) * NJ;
+        const float2 *u0 = Us + el0 * NJ;
 #pragma unroll
         for (int r = 0; r < EM_MAXR; ++r) {
           if (r >= R) break;
@@ -129,9 +138,7 @@ int element_df_block(const EParams &p) {
 
 cudaError_t launch_element_df(const EParams &p, int grid, int block, cudaStream_t s) {
   if (p.tile_e % DF_EPT) return cudaErrorInvalidValue;          // element groups never straddle a tile
-  const size_t smem = sizeof(float2) * ((size_t)p.R * p.NI * p.NJ + (size_t)p.n_groups * p.tile_e * p.NJ +
-                                        (size_t)p.n_rows * p.tile_e * p.R + 1) +
-                      sizeof(float4) * dfm::SIN_TAB_N;
+  const size_t smem = sizeof(float2) * (element_smem_words(p) + 1) + sizeof(float4) * dfm::SIN_TAB_N;
   if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
   static bool attr = false;
   if (!attr) {

@@ -567,6 +567,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
 
 bool build_params(const EParams &p, TcParams &tp, std::string &why) {
   if (p.n_groups != 1) { why = "more than one fused operand"; return false; }
+  if (p.NJ0 > 0 || p.groups[0].kind == 3) { why = "stacked producer (divergence / face-mass form)"; return false; }
   if (p.R < 1 || p.R > 4) { why = "R outside 1..4"; return false; }
   if (p.NJ < 1 || p.NJ > 64) { why = "contracted extent outside 1..64"; return false; }
   if (p.NI < 1) { why = "empty output extent"; return false; }

@@ -208,8 +208,43 @@ int plan_generic_row(const Einsum &e, int row, const std::vector<BufIn> &bufs, c
 
 // ------------------------------------------------------------ element
 
+static int plan_element_stacked(const Einsum &e, const std::vector<BufIn> &bufs, const std::vector<BufIn> &outs,
+                                const be_config_t &cfg, EParams &p, std::string &why);
+
+// shared-memory tile: the configured element count, else the default shrunk
+// (in steps of 4 elements) until the operator, one group's produced operand
+// and the geometric factors fit the budget
+static int element_tile(const EParams &p, const be_config_t &cfg, std::string &why) {
+  auto bytes = [&](int te) {
+    EParams q = p;
+    q.tile_e = te;
+    return sizeof(double) * element_smem_words(q);
+  };
+  int te = cfg.tile[0] > 0 ? cfg.tile[0] : (p.NI >= 16 ? 32 : 256);
+  if (cfg.tile[2] != 1) te = (te + 3) / 4 * 4;   // the double-float kernel works on groups of 4 elements
+  if (cfg.tile[0] <= 0)
+    while (te > 4 && bytes(te) > EM_SMEM_BUDGET) te -= 4;
+  if (bytes(te) > EM_SMEM_BUDGET) { why = "tile does not fit shared memory"; return 0; }
+  return te;
+}
+
+static int plan_element_hoisted(const Einsum &e, const std::vector<BufIn> &bufs, const std::vector<BufIn> &outs,
+                                const be_config_t &cfg, EParams &p, std::string &why);
+
+// the hoisted form (t = D u shared by the rows) where it applies, else the
+// stacked form
 int plan_element(const Einsum &e, const std::vector<BufIn> &bufs, const std::vector<BufIn> &outs,
                  const be_config_t &cfg, EParams &p, std::string &why) {
+  const int st = plan_element_hoisted(e, bufs, outs, cfg, p, why);
+  if (st != EUNSUPPORTED || e.n != 3 || e.out_dtype != F64 || e.out.size() != 2) return st;
+  std::string why_s;
+  if (plan_element_stacked(e, bufs, outs, cfg, p, why_s) == OK) return OK;
+  why += "; stacked form: " + why_s;
+  return EUNSUPPORTED;
+}
+
+static int plan_element_hoisted(const Einsum &e, const std::vector<BufIn> &bufs, const std::vector<BufIn> &outs,
+                                const be_config_t &cfg, EParams &p, std::string &why) {
   std::memset(&p, 0, sizeof(p));
   if (e.out_dtype != F64) { why = "element strategy runs FP64 only"; return EUNSUPPORTED; }
   for (auto &a : e.args)
@@ -327,12 +362,155 @@ int plan_element(const Einsum &e, const std::vector<BufIn> &bufs, const std::vec
     }
   }
   p.n_groups = (int)uargs.size();
-  int te = cfg.tile[0] > 0 ? cfg.tile[0] : (p.NI >= 16 ? 32 : 256);
-  if (cfg.tile[2] != 1) te = (te + 3) / 4 * 4;   // the double-float kernel works on groups of 4 elements
-  p.tile_e = te;
-  size_t smem = sizeof(double) * ((size_t)p.R * p.NI * p.NJ + (size_t)p.n_groups * te * p.NJ + (size_t)p.n_rows * te * p.R);
-  if (smem > 200 * 1024) { why = "tile does not fit shared memory"; return EUNSUPPORTED; }
-  return OK;
+  p.tile_e = element_tile(p, cfg, why);
+  return p.tile_e > 0 ? OK : EUNSUPPORTED;
+}
+
+// Stacked form of the element strategy: three operands D (without e), A and
+// B (with e) such that R[e, i] = sum_k D[i, k] v[e, k], k running over the
+// one or two letters of D besides i (j, and s when present), with
+//     v[e, s, j] = sum_x A[e, x, s, j] * B[e, x, s, j],
+// where x is at most one letter shared by A and B only and each operand
+// holds any subset of s and j.  The DG local divergence 'xre,rij,xej->ei'
+// (v = sum_x J[x, r, e] F[x, e, j]) and the face mass 'fe,ifj,fej->ei'
+// (v = J[f, e] U[f, e, j]) have this form (Sec. "Batched einsums in DG-FEM
+// Operators", divergence and face-mass tuples).  A functional operand
+// whose body selects on x (F(x, e, j) := x == 0 ? u : ...) is resolved to
+// one view per value of x.
+
+// body node of functional argument A with parameter px fixed to xv: selects
+// whose condition compares that parameter with a number are resolved; -1
+// when a condition is anything else
+static int resolve_select(const Arg &A, int node, int px, int64_t xv) {
+  while (node >= 0 && A.nodes[node].op == X_SELECT) {
+    const XNode &sel = A.nodes[node];
+    const XNode &c = A.nodes[sel.kids[0]];
+    if (c.op != X_EQ && c.op != X_NE) return -1;
+    const XNode &l = A.nodes[c.kids[0]], &r = A.nodes[c.kids[1]];
+    double num;
+    if (l.op == X_PARAM && l.id == px && r.op == X_NUM) num = r.num;
+    else if (r.op == X_PARAM && r.id == px && l.op == X_NUM) num = l.num;
+    else return -1;
+    const bool eq = (double)xv == num;
+    node = (c.op == X_EQ ? eq : !eq) ? sel.kids[1] : sel.kids[2];
+  }
+  return node;
+}
+
+// the view of operand position pos (argument arg) over (e, s, j) with the
+// letter lx (if any) fixed to xv
+static bool stacked_view(const Einsum &e, int arg, int pos, int lx, int64_t xv, const std::vector<BufIn> &bufs, int le,
+                         int ls, int lj, ESView &out) {
+  const Arg &A = e.args[arg];
+  View v;
+  if (!A.functional()) {
+    arg_view(e, arg, pos, bufs, v);
+  } else {
+    int px = -1;
+    for (size_t d = 0; d < e.in[pos].size(); ++d)
+      if (lx >= 0 && e.in[pos][d] == lx) px = (int)d;
+    const int nd = px >= 0 ? resolve_select(A, A.root, px, xv) : A.root;
+    if (nd < 0 || A.nodes[nd].op != X_REF) return false;
+    ref_view(e, A.nodes[nd], pos, bufs, v);
+  }
+  if (v.dtype != F64) return false;
+  out.ptr = (const double *)v.ptr + (lx >= 0 ? v.coef[lx] * xv : 0);
+  out.se = v.coef[le];
+  out.ss = ls >= 0 ? v.coef[ls] : 0;
+  out.sj = v.coef[lj];
+  return true;
+}
+
+static int plan_element_stacked(const Einsum &e, const std::vector<BufIn> &bufs, const std::vector<BufIn> &outs,
+                                const be_config_t &cfg, EParams &p, std::string &why) {
+  std::memset(&p, 0, sizeof(p));
+  for (auto &a : e.args)
+    if (a.dtype != F64) { why = "element strategy runs FP64 only"; return EUNSUPPORTED; }
+  for (auto &b : e.buffers)
+    if (b.dtype != F64) { why = "element strategy runs FP64 only"; return EUNSUPPORTED; }
+  if (e.b > EM_MAXROWS) { why = "more than 16 rows"; return EUNSUPPORTED; }
+  const int le = e.out[0], li = e.out[1];
+  auto has = [&](int pos, int c) { return std::find(e.in[pos].begin(), e.in[pos].end(), c) != e.in[pos].end(); };
+  int pD = -1;
+  std::vector<int> pe;
+  for (int j = 0; j < 3; ++j) {
+    if (!has(j, le) && has(j, li)) pD = j;
+    else if (has(j, le) && !has(j, li)) pe.push_back(j);
+  }
+  if (pD < 0 || pe.size() != 2) { why = "not D[i, ..] with two per-element operands"; return EUNSUPPORTED; }
+  const int pA = pe[0], pB = pe[1];
+  for (int j = 0; j < 3; ++j)
+    for (size_t a = 0; a < e.in[j].size(); ++a)
+      for (size_t b = a + 1; b < e.in[j].size(); ++b)
+        if (e.in[j][a] == e.in[j][b]) { why = "repeated letter in an operand"; return EUNSUPPORTED; }
+  std::vector<int8_t> dl;
+  for (int8_t c : e.in[pD])
+    if (c != li) dl.push_back(c);
+  if (dl.empty() || dl.size() > 2) { why = "operator rank"; return EUNSUPPORTED; }
+  int lx = -1;
+  for (int8_t c : e.in[pA])
+    if (c != le && has(pB, c) && !has(pD, c)) {
+      if (lx >= 0) { why = "more than one stacking letter"; return EUNSUPPORTED; }
+      lx = c;
+    }
+  for (int pos : {pA, pB})
+    for (int8_t c : e.in[pos])
+      if (c != le && c != lx && !has(pD, c)) { why = "letter summed outside the operator"; return EUNSUPPORTED; }
+  for (int8_t c : dl)
+    if (!has(pA, c) && !has(pB, c)) { why = "operator letter not in the per-element operands"; return EUNSUPPORTED; }
+  int lj = dl[0], ls = -1;
+  if (dl.size() == 2) {
+    lj = e.len[dl[0]] >= e.len[dl[1]] ? dl[0] : dl[1];
+    ls = lj == dl[0] ? dl[1] : dl[0];
+  }
+  const int X = lx >= 0 ? (int)e.len[lx] : 1;
+  const int64_t S = ls >= 0 ? e.len[ls] : 1, NJ0 = e.len[lj];
+  if (X < 1 || X > EM_MAXX) { why = "stacking extent beyond 4"; return EUNSUPPORTED; }
+  if (e.len[li] < 1 || e.len[li] > EM_MAXN || NJ0 < 1 || S < 1 || S * NJ0 > EM_MAXK) {
+    why = "operator extents beyond 64 x 128";
+    return EUNSUPPORTED;
+  }
+  const int dArg = e.rows[0][pD];
+  for (int i = 0; i < e.b; ++i)
+    if (e.rows[i][pD] != dArg) { why = "operator differs between rows"; return EUNSUPPORTED; }
+  View dv;
+  if (!arg_view(e, dArg, pD, bufs, dv)) { why = "operator is not a plain view"; return EUNSUPPORTED; }
+  p.D = (const double *)dv.ptr;
+  p.si = dv.coef[li];
+  p.sj = dv.coef[lj];
+  p.sr = ls >= 0 ? dv.coef[ls] : 0;
+  p.NI = (int)e.len[li];
+  p.NJ0 = (int)NJ0;
+  p.NJ = (int)(S * NJ0);
+  p.R = 1;
+  p.has_g = 0;
+  p.E = e.len[le];
+  p.n_rows = e.b;
+  std::vector<std::pair<int, int>> keys;
+  for (int i = 0; i < e.b; ++i) {
+    const std::pair<int, int> key(e.rows[i][pA], e.rows[i][pB]);
+    int g = -1;
+    for (size_t k = 0; k < keys.size(); ++k)
+      if (keys[k] == key) g = (int)k;
+    if (g < 0) {
+      EProd &q = p.groups[keys.size()];
+      q.kind = 3;
+      q.X = X;
+      for (int x = 0; x < X; ++x)
+        if (!stacked_view(e, key.first, pA, lx, x, bufs, le, ls, lj, q.A[x]) ||
+            !stacked_view(e, key.second, pB, lx, x, bufs, le, ls, lj, q.B[x])) {
+          why = "per-element operand is not a view or a select of views over the stacking letter";
+          return EUNSUPPORTED;
+        }
+      keys.push_back(key);
+      g = (int)keys.size() - 1;
+    }
+    p.rows[i].group = g;
+    p.rows[i].out = (double *)outs[i].ptr;
+  }
+  p.n_groups = (int)keys.size();
+  p.tile_e = element_tile(p, cfg, why);
+  return p.tile_e > 0 ? OK : EUNSUPPORTED;
 }
 
 }  // namespace be

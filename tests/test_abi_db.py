@@ -82,3 +82,18 @@ def test_plan_strategy_uses_db(tmp_path):
     with pytest.raises(be.BEError) as ex:
         be.plan_strategy(None, mm, be.make_config(be.STRAT_ELEMENT))
     assert ex.value.code == be.EUNSUPPORTED
+
+
+@pytest.mark.parametrize("order", [1, 4])
+def test_plan_strategy_stacked_element_form(order):
+    """The DG divergence (select producer over x) and the face mass plan as
+    the element strategy's stacked form; letters summed outside the
+    operator, or two stacking letters, do not."""
+    for text in (W.dg_divergence_spec(E=1000, order=order, rows=3), W.face_mass_spec(E=1000, order=order, rows=2)):
+        assert be.plan_strategy(None, be.Einsum(text)) == be.STRAT_ELEMENT
+    # y is summed in A and B but also appears nowhere in D: two stacking letters
+    two = be.Einsum("xye,ij,xyej->ei | A,D,B ; A:f64[2,2,50] ; D:f64[6,6] ; B:f64[2,2,50,6]")
+    assert be.plan_strategy(None, two) == be.STRAT_GENERIC
+    # a letter of A alone (summed outside the operator)
+    lone = be.Einsum("ze,ij,ej->ei | A,D,B ; A:f64[3,50] ; D:f64[6,6] ; B:f64[50,6]")
+    assert be.plan_strategy(None, lone) == be.STRAT_GENERIC

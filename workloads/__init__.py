@@ -111,6 +111,85 @@ def dg_gradient_spec(E: int = 262144, ndof: int = 35, dim: int = 3, producer: st
 
 
 # --------------------------------------------------------------------------
+# DG local divergence and face mass: b einsums sharing the operator
+# --------------------------------------------------------------------------
+
+
+def tet_dofs(order: int) -> int:
+    """Nodal dofs of a Pk tetrahedron, (k+1)(k+2)(k+3)/6."""
+    return (order + 1) * (order + 2) * (order + 3) // 6
+
+
+def tri_dofs(order: int) -> int:
+    """Nodal dofs of a Pk triangle (one face of the tetrahedron), (k+1)(k+2)/2."""
+    return (order + 1) * (order + 2) // 2
+
+
+def dg_divergence(E: int = 100000, order: int = 4, rows: int = 1, ints: bool = False):
+    """Shared D[r,i,j] (3 x N x N) and per row k the metric terms J_k[x,r,e]
+    (3 x 3 x E) and the vector field's components u_k, v_k, w_k (E x N),
+    N = tet_dofs(order); N(0,1) FP64, or small integers when ``ints``."""
+    N = tet_dofs(order)
+    f = small_ints if ints else normal
+    D = f(6, 0, (3, N, N))
+    data = []
+    for k in range(rows):
+        data.append(dict(J=f(6, 1 + 4 * k, (3, 3, E)), u=f(6, 2 + 4 * k, (E, N)),
+                         v=f(6, 3 + 4 * k, (E, N)), w=f(6, 4 + 4 * k, (E, N))))
+    return D, data
+
+
+def dg_divergence_spec(E: int = 100000, order: int = 4, rows: int = 1) -> str:
+    """Text of the DG local divergence, one einsum per field:
+    R_k[e,i] = sum_{x,r,j} J_k[x,r,e] D[r,i,j] F_k[x,e,j], with F_k selecting
+    the component u_k, v_k or w_k by x."""
+    N = tet_dofs(order)
+    decls = [f"D:f64[3,{N},{N}]"]
+    for k in range(rows):
+        decls += [f"J{k}:f64[3,3,{E}]", f"u{k}:f64[{E},{N}]", f"v{k}:f64[{E},{N}]", f"w{k}:f64[{E},{N}]",
+                  f"F{k}(x,e,j):f64[3,{E},{N}] := x==0 ? u{k}[e,j] : (x==1 ? v{k}[e,j] : w{k}[e,j])"]
+    body = " | ".join(f"J{k},D,F{k}" for k in range(rows))
+    return f"xre,rij,xej->ei | {body} ; " + " ; ".join(decls)
+
+
+def dg_divergence_arrays(D, data) -> dict:
+    arrs = {"D": D}
+    for k, d in enumerate(data):
+        for name in ("J", "u", "v", "w"):
+            arrs[f"{name}{k}"] = d[name]
+    return arrs
+
+
+def face_mass(E: int = 100000, order: int = 4, rows: int = 1, ints: bool = False):
+    """Shared face lift M[i,f,j] (N x 4 x NF) and per row k the face
+    Jacobians J_k[f,e] (4 x E) and face values U_k[f,e,j] (4 x E x NF),
+    N = tet_dofs(order), NF = tri_dofs(order); N(0,1) FP64 or small ints."""
+    N, NF = tet_dofs(order), tri_dofs(order)
+    f = small_ints if ints else normal
+    M = f(7, 0, (N, 4, NF))
+    data = [dict(J=f(7, 1 + 2 * k, (4, E)), U=f(7, 2 + 2 * k, (4, E, NF))) for k in range(rows)]
+    return M, data
+
+
+def face_mass_spec(E: int = 100000, order: int = 4, rows: int = 1) -> str:
+    """Text of the face mass term R_k[e,i] = sum_{f,j} J_k[f,e] M[i,f,j] U_k[f,e,j]."""
+    N, NF = tet_dofs(order), tri_dofs(order)
+    decls = [f"M:f64[{N},4,{NF}]"]
+    for k in range(rows):
+        decls += [f"J{k}:f64[4,{E}]", f"U{k}:f64[4,{E},{NF}]"]
+    body = " | ".join(f"J{k},M,U{k}" for k in range(rows))
+    return f"fe,ifj,fej->ei | {body} ; " + " ; ".join(decls)
+
+
+def face_mass_arrays(M, data) -> dict:
+    arrs = {"M": M}
+    for k, d in enumerate(data):
+        arrs[f"J{k}"] = d["J"]
+        arrs[f"U{k}"] = d["U"]
+    return arrs
+
+
+# --------------------------------------------------------------------------
 # Workload 3: dense chemistry-style contraction 'abef,efij->abij'
 # --------------------------------------------------------------------------
 
