@@ -426,7 +426,7 @@ static int do_execute(be_ctx *x, const be_einsum *hc, const be_config *cfg, int3
   if (strategy == BE_STRAT_DENSE_SPLIT) {
     if (!x) return fail(BE_EARG, "the dense split strategy needs a context (workspace)");
     DensePlan dp;
-    st = plan_dense(e, bi, bo, dp, err);
+    st = plan_dense(e, bi, bo, dp, err, &sc);
     if (st) return fail(st, err);
     if (dp.M == 0 || dp.N == 0) return BE_OK;
     std::lock_guard<std::mutex> g(x->mu);
@@ -438,12 +438,12 @@ static int do_execute(be_ctx *x, const be_einsum *hc, const be_config *cfg, int3
       } else {
         if (r.argB != prevB) {
           KernelMark km(x, BE_KERNEL_SPLIT, s);
-          ce = dense_split_b(DenseB{r.B, dp.K, dp.N, r.ldb, r.snb, dp.M}, x->ws, s);
+          ce = dense_split_b(DenseB{r.B, dp.K, dp.N, r.ldb, r.snb, dp.M, r.alB, r.beB}, x->ws, s);
           prevB = r.argB;
         }
         if (ce == cudaSuccess) {
           KernelMark km(x, BE_KERNEL_SPLIT, s);
-          ce = dense_split_a(DenseA{r.A, dp.M, r.lda, r.ska}, dp.K, dp.M, dp.N, x->ws, s);
+          ce = dense_split_a(DenseA{r.A, dp.M, r.lda, r.ska, r.alA, r.beA}, dp.K, dp.M, dp.N, x->ws, s);
         }
         if (ce == cudaSuccess) {
           KernelMark km(x, BE_KERNEL_DENSE_GEMM, s);

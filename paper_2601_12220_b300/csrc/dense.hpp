@@ -8,16 +8,19 @@
 
 namespace be {
 
-// A (M x K) of one row, element (m, k) at A[m * lda + k * ska]
+// A (M x K) of one row, element (m, k) at alpha * A[m * lda + k * ska] + beta
 struct DenseA {
   const double *A;
   int64_t M, lda, ska;
+  double alpha = 1.0, beta = 0.0;
 };
 
-// B (K x N), element (k, n) at B[k * ldb + n * snb]; M_max sizes the workspace
+// B (K x N), element (k, n) at alpha * B[k * ldb + n * snb] + beta; M_max
+// sizes the workspace
 struct DenseB {
   const double *B;
   int64_t K, N, ldb, snb, M_max;
+  double alpha = 1.0, beta = 0.0;
 };
 
 // workspace carve-up: split operands (TF32, K-major, zero-padded to the

@@ -3,7 +3,8 @@
 // introduction, M = ab, K = ef, N = ij) evaluated on the tcgen05 tensor
 // cores.
 //
-//  1. split_rows / split_cols: each FP64 operand is scaled by a power of two
+//  1. split_rows / split_cols: each FP64 operand (or its affine producer
+//     alpha * x + beta, evaluated here) is scaled by a power of two
 //     per row of A (per column of B) so that its largest entry lies in
 //     [2^13, 2^14), then written as two TF32 parts hi = tf32(x),
 //     lo = tf32(x - hi) (11 significant bits each) into a zero-padded
@@ -374,12 +375,20 @@ __device__ __forceinline__ void split_scaled(double x, int s, bool fp32_ok, floa
   }
 }
 
+// the operand value of an affine producer, alpha * x + beta (AFF), else x
+template <bool AFF>
+__device__ __forceinline__ double affine(double x, double alpha, double beta) {
+  return AFF ? fma(alpha, x, beta) : x;
+}
+
 // A (M x K): A[m*lda + k*ska] -> TF32 hi/lo [Mp x Kp], zero-padded; sa[m].
 // Rows with unit stride and 16-byte alignment are read as double2, four in
-// flight per thread, and written as float2.
+// flight per thread, and written as float2.  AFF: the operand is
+// alpha * A + beta (an affine producer fused into the split).
+template <bool AFF>
 __global__ void __launch_bounds__(256) split_rows(const double *__restrict__ A, int64_t M, int64_t K, int64_t lda,
                                                   int64_t ska, float *__restrict__ hi, float *__restrict__ lo,
-                                                  int64_t Kp, int *__restrict__ sa) {
+                                                  int64_t Kp, int *__restrict__ sa, double alpha, double beta) {
   __shared__ double red[32];
   const int64_t m = blockIdx.x;
   const double *row = A + m * lda;
@@ -397,18 +406,18 @@ __global__ void __launch_bounds__(256) split_rows(const double *__restrict__ A, 
         for (int u = 0; u < 4; ++u) v[u] = r2[k + u * blockDim.x];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          bits = max(bits, (unsigned long long)__double_as_longlong(v[u].x) & 0x7fffffffffffffffull);
-          bits = max(bits, (unsigned long long)__double_as_longlong(v[u].y) & 0x7fffffffffffffffull);
+          bits = max(bits, (unsigned long long)__double_as_longlong(affine<AFF>(v[u].x, alpha, beta)) & 0x7fffffffffffffffull);
+          bits = max(bits, (unsigned long long)__double_as_longlong(affine<AFF>(v[u].y, alpha, beta)) & 0x7fffffffffffffffull);
         }
       }
       for (; k < K2; k += blockDim.x) {
         const double2 v = r2[k];
-        bits = max(bits, (unsigned long long)__double_as_longlong(v.x) & 0x7fffffffffffffffull);
-        bits = max(bits, (unsigned long long)__double_as_longlong(v.y) & 0x7fffffffffffffffull);
+        bits = max(bits, (unsigned long long)__double_as_longlong(affine<AFF>(v.x, alpha, beta)) & 0x7fffffffffffffffull);
+        bits = max(bits, (unsigned long long)__double_as_longlong(affine<AFF>(v.y, alpha, beta)) & 0x7fffffffffffffffull);
       }
     } else {
       for (int64_t k = threadIdx.x; k < K; k += blockDim.x)
-        bits = max(bits, (unsigned long long)__double_as_longlong(row[k * ska]) & 0x7fffffffffffffffull);
+        bits = max(bits, (unsigned long long)__double_as_longlong(affine<AFF>(row[k * ska], alpha, beta)) & 0x7fffffffffffffffull);
     }
   }
   double mx = block_max(__longlong_as_double((long long)bits), red);
@@ -429,8 +438,8 @@ __global__ void __launch_bounds__(256) split_rows(const double *__restrict__ A, 
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         float ha, la, hb, lb;
-        split_scaled(v[u].x, s, fp32_ok, ha, la);
-        split_scaled(v[u].y, s, fp32_ok, hb, lb);
+        split_scaled(affine<AFF>(v[u].x, alpha, beta), s, fp32_ok, ha, la);
+        split_scaled(affine<AFF>(v[u].y, alpha, beta), s, fp32_ok, hb, lb);
         h2[k + u * blockDim.x] = make_float2(ha, hb);
         l2[k + u * blockDim.x] = make_float2(la, lb);
       }
@@ -439,8 +448,8 @@ __global__ void __launch_bounds__(256) split_rows(const double *__restrict__ A, 
       float ha = 0.f, la = 0.f, hb = 0.f, lb = 0.f;
       if (k < K2) {
         const double2 v = r2[k];
-        split_scaled(v.x, s, fp32_ok, ha, la);
-        split_scaled(v.y, s, fp32_ok, hb, lb);
+        split_scaled(affine<AFF>(v.x, alpha, beta), s, fp32_ok, ha, la);
+        split_scaled(affine<AFF>(v.y, alpha, beta), s, fp32_ok, hb, lb);
       }
       h2[k] = make_float2(ha, hb);
       l2[k] = make_float2(la, lb);
@@ -449,7 +458,7 @@ __global__ void __launch_bounds__(256) split_rows(const double *__restrict__ A, 
   }
   for (int64_t k = threadIdx.x; k < Kp; k += blockDim.x) {
     float h = 0.f, l = 0.f;
-    if (m < M && k < K) split_scaled(row[k * ska], s, fp32_ok, h, l);
+    if (m < M && k < K) split_scaled(affine<AFF>(row[k * ska], alpha, beta), s, fp32_ok, h, l);
     hrow[k] = h;
     lrow[k] = l;
   }
@@ -457,23 +466,29 @@ __global__ void __launch_bounds__(256) split_rows(const double *__restrict__ A, 
 
 // per-column max |B| of B (K x N), B[k*ldb + n*snb]; K split over blockIdx.y,
 // combined with an integer max on the (non-negative) double bit patterns
+template <bool AFF>
 __global__ void __launch_bounds__(256) col_max(const double *__restrict__ B, int64_t K, int64_t N, int64_t ldb,
-                                               int64_t snb, unsigned long long *__restrict__ bmax) {
+                                               int64_t snb, unsigned long long *__restrict__ bmax, double alpha,
+                                               double beta) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const int64_t kper = (K + gridDim.y - 1) / gridDim.y;
   const int64_t k0 = (int64_t)blockIdx.y * kper, k1 = min(K, k0 + kper);
   unsigned long long bits = 0;
   for (int64_t k = k0; k < k1; ++k)
-    bits = max(bits, (unsigned long long)__double_as_longlong(B[k * ldb + n * snb]) & 0x7fffffffffffffffull);
+    bits = max(bits, (unsigned long long)__double_as_longlong(affine<AFF>(B[k * ldb + n * snb], alpha, beta)) &
+                         0x7fffffffffffffffull);
   atomicMax(&bmax[n], bits);
 }
 
-// B (K x N) -> transposed TF32 hi/lo [Np x Kp] (K-major), zero-padded
+// B (K x N) -> transposed TF32 hi/lo [Np x Kp] (K-major), zero-padded;
+// AFF: the operand is alpha * B + beta
+template <bool AFF>
 __global__ void __launch_bounds__(256) split_cols_t(const double *__restrict__ B, int64_t K, int64_t N, int64_t ldb,
                                                    int64_t snb, const unsigned long long *__restrict__ bmax,
                                                    int *__restrict__ sb, float *__restrict__ hi,
-                                                   float *__restrict__ lo, int64_t Kp, int64_t Np) {
+                                                   float *__restrict__ lo, int64_t Kp, int64_t Np, double alpha,
+                                                   double beta) {
   __shared__ double tile[32][33];
   const int64_t k0 = (int64_t)blockIdx.x * 32, nb = (int64_t)blockIdx.y * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
@@ -482,7 +497,7 @@ __global__ void __launch_bounds__(256) split_cols_t(const double *__restrict__ B
   if (blockIdx.x == 0 && ty == 0 && nn < N) sb[nn] = scl;
   for (int r = ty; r < 32; r += 8) {
     const int64_t k = k0 + r;
-    tile[r][tx] = (k < K && nn < N) ? ldexp(B[k * ldb + nn * snb], scl) : 0.0;
+    tile[r][tx] = (k < K && nn < N) ? ldexp(affine<AFF>(B[k * ldb + nn * snb], alpha, beta), scl) : 0.0;
   }
   __syncthreads();
   for (int r = ty; r < 32; r += 8) {
@@ -535,19 +550,27 @@ cudaError_t dense_split_b(const DenseB &b, void *ws, cudaStream_t s) {
   DenseWs w = dense_ws_layout(ws, b.M_max, b.N, b.K);
   cudaError_t e = cudaMemsetAsync(w.bmax, 0, sizeof(unsigned long long) * (size_t)b.N, s);
   if (e != cudaSuccess) return e;
+  const bool aff = b.alpha != 1.0 || b.beta != 0.0;
   if (b.N > 0 && b.K > 0) {
     dim3 gm((unsigned)((b.N + 255) / 256), (unsigned)std::min<int64_t>(64, b.K));
-    col_max<<<gm, 256, 0, s>>>(b.B, b.K, b.N, b.ldb, b.snb, w.bmax);
+    if (aff) col_max<true><<<gm, 256, 0, s>>>(b.B, b.K, b.N, b.ldb, b.snb, w.bmax, b.alpha, b.beta);
+    else col_max<false><<<gm, 256, 0, s>>>(b.B, b.K, b.N, b.ldb, b.snb, w.bmax, 1.0, 0.0);
   }
   dim3 g((unsigned)(Kp / 32), (unsigned)(Np / 32));
-  split_cols_t<<<g, 256, 0, s>>>(b.B, b.K, b.N, b.ldb, b.snb, w.bmax, w.sb, w.bh, w.bl, Kp, Np);
+  if (aff)
+    split_cols_t<true><<<g, 256, 0, s>>>(b.B, b.K, b.N, b.ldb, b.snb, w.bmax, w.sb, w.bh, w.bl, Kp, Np, b.alpha, b.beta);
+  else
+    split_cols_t<false><<<g, 256, 0, s>>>(b.B, b.K, b.N, b.ldb, b.snb, w.bmax, w.sb, w.bh, w.bl, Kp, Np, 1.0, 0.0);
   return cudaGetLastError();
 }
 
 cudaError_t dense_split_a(const DenseA &a, int64_t K, int64_t M_max, int64_t N, void *ws, cudaStream_t s) {
   const int64_t Mp = (a.M + BM - 1) / BM * BM, Kp = (K + BK - 1) / BK * BK;
   DenseWs w = dense_ws_layout(ws, M_max, N, K);
-  split_rows<<<(unsigned)Mp, 256, 0, s>>>(a.A, a.M, K, a.lda, a.ska, w.ah, w.al, Kp, w.sa);
+  if (a.alpha != 1.0 || a.beta != 0.0)
+    split_rows<true><<<(unsigned)Mp, 256, 0, s>>>(a.A, a.M, K, a.lda, a.ska, w.ah, w.al, Kp, w.sa, a.alpha, a.beta);
+  else
+    split_rows<false><<<(unsigned)Mp, 256, 0, s>>>(a.A, a.M, K, a.lda, a.ska, w.ah, w.al, Kp, w.sa, 1.0, 0.0);
   return cudaGetLastError();
 }
 

@@ -531,8 +531,74 @@ static int64_t flat_stride(const Einsum &e, const View &v, const std::vector<int
   return st;
 }
 
+// A functional body that is affine in a single buffer reference,
+// f(x) = alpha * x + beta, with alpha and beta built from numbers and runtime
+// scalars by + - * and division by a constant (the producers
+// (alpha_1 A + beta_1)(alpha_2 B + beta_2) of Sec. "Evaluation", TCCG
+// experiment).  ref receives the reference node; false for anything else.
+static bool affine_of(const Arg &A, int node, const std::vector<double> *sc, double &alpha, double &beta, int &ref) {
+  const XNode &n = A.nodes[node];
+  switch (n.op) {
+    case X_NUM: alpha = 0.0; beta = n.num; return true;
+    case X_SCALAR:
+      alpha = 0.0;
+      beta = sc ? (n.id < (int)sc->size() ? (*sc)[n.id] : 0.0) : 1.0;
+      return true;
+    case X_REF:
+      if (ref >= 0) return false;               // a second reference
+      ref = node;
+      alpha = 1.0;
+      beta = 0.0;
+      return true;
+    case X_NEG: {
+      if (!affine_of(A, n.kids[0], sc, alpha, beta, ref)) return false;
+      alpha = -alpha;
+      beta = -beta;
+      return true;
+    }
+    case X_ADD: case X_SUB: case X_MUL: case X_DIV: {
+      double a0, b0, a1, b1;
+      const int r0 = ref;
+      if (!affine_of(A, n.kids[0], sc, a0, b0, ref)) return false;
+      const bool left_ref = ref != r0;
+      const int r1 = ref;
+      if (!affine_of(A, n.kids[1], sc, a1, b1, ref)) return false;
+      const bool right_ref = ref != r1;
+      if (n.op == X_ADD) { alpha = a0 + a1; beta = b0 + b1; return true; }
+      if (n.op == X_SUB) { alpha = a0 - a1; beta = b0 - b1; return true; }
+      if (n.op == X_MUL) {
+        if (left_ref && right_ref) return false;
+        if (right_ref) { alpha = b0 * a1; beta = b0 * b1; }
+        else { alpha = a0 * b1; beta = b0 * b1; }
+        return true;
+      }
+      if (right_ref) return false;              // division by the reference
+      if (sc && b1 == 0.0) return false;
+      const double d = sc ? b1 : 1.0;
+      alpha = a0 / d;
+      beta = b0 / d;
+      return true;
+    }
+    default: return false;
+  }
+}
+
+// view of operand position pos of argument arg, directly or through an
+// affine producer (coefficients in alpha, beta)
+static bool dense_operand(const Einsum &e, int arg, int pos, const std::vector<BufIn> &bufs,
+                          const std::vector<double> *sc, View &v, double &alpha, double &beta) {
+  alpha = 1.0;
+  beta = 0.0;
+  if (arg_view(e, arg, pos, bufs, v)) return true;
+  const Arg &A = e.args[arg];
+  int ref = -1;
+  if (!affine_of(A, A.root, sc, alpha, beta, ref) || ref < 0) return false;
+  ref_view(e, A.nodes[ref], pos, bufs, v);
+  return v.dtype == F64;
+}
+
 int plan_dense(const Einsum &e, const std::vector<BufIn> &bufs, const std::vector<BufIn> &outs, DensePlan &p,
-               std::string &why) {
+               std::string &why, const std::vector<double> *scalars) {
   p = DensePlan();
   if (e.n != 2) { why = "dense strategy needs two operands"; return EUNSUPPORTED; }
   if (e.out_dtype != F64) { why = "dense strategy evaluates float64"; return EUNSUPPORTED; }
@@ -575,11 +641,12 @@ int plan_dense(const Einsum &e, const std::vector<BufIn> &bufs, const std::vecto
   p.rows.clear();
   for (int i = 0; i < e.b; ++i) {
     View va, vb;
-    if (!arg_view(e, e.rows[i][0], 0, bufs, va) || !arg_view(e, e.rows[i][1], 1, bufs, vb)) {
-      why = "dense operands must be plain views";
+    DenseRow r;
+    if (!dense_operand(e, e.rows[i][0], 0, bufs, scalars, va, r.alA, r.beA) ||
+        !dense_operand(e, e.rows[i][1], 1, bufs, scalars, vb, r.alB, r.beB)) {
+      why = "dense operands must be views or affine producers of one view";
       return EUNSUPPORTED;
     }
-    DenseRow r;
     r.argA = e.rows[i][0];
     r.argB = e.rows[i][1];
     r.A = (const double *)va.ptr;

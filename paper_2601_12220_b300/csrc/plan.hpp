@@ -40,6 +40,8 @@ struct DenseRow {
   const double *A, *B;
   int64_t lda, ska, ldb, snb;
   double *C;
+  // affine producers: the operands are alA * A + beA and alB * B + beB
+  double alA = 1.0, beA = 0.0, alB = 1.0, beB = 0.0;
 };
 struct DensePlan {
   int64_t M = 0, N = 0, K = 0;
@@ -53,7 +55,9 @@ int plan_generic_row(const Einsum &e, int row, const std::vector<BufIn> &bufs, c
                      const std::vector<double> &scalars, GParams &p, std::string &err);
 int plan_element(const Einsum &e, const std::vector<BufIn> &bufs, const std::vector<BufIn> &outs,
                  const be_config_t &cfg, EParams &p, std::string &why);
+// scalars: the call's runtime scalars for the affine producers' coefficients,
+// or nullptr when only the form is checked
 int plan_dense(const Einsum &e, const std::vector<BufIn> &bufs, const std::vector<BufIn> &outs, DensePlan &p,
-               std::string &why);
+               std::string &why, const std::vector<double> *scalars = nullptr);
 
 }  // namespace be

@@ -97,3 +97,14 @@ def test_plan_strategy_stacked_element_form(order):
     # a letter of A alone (summed outside the operator)
     lone = be.Einsum("ze,ij,ej->ei | A,D,B ; A:f64[3,50] ; D:f64[6,6] ; B:f64[50,6]")
     assert be.plan_strategy(None, lone) == be.STRAT_GENERIC
+
+
+def test_plan_dense_affine_producers():
+    """Operands that are affine in one buffer reference plan as the dense
+    split strategy; other producers do not."""
+    ok = ["P(i,k) := $a*A[i,k]+$b", "P(i,k) := 2.0*A[i,k]-1.0", "P(i,k) := -(A[i,k]/3.0)", "P(i,k) := ($a+1)*A[i,k]"]
+    bad = ["P(i,k) := A[i,k]*A[i,k]", "P(i,k) := sin(A[i,k])", "P(i,k) := 1.0/A[i,k]", "P(i,k) := A[i,k]+i"]
+    for body in ok + bad:
+        e = be.Einsum(f"ik,kj->ij | P,B ; A:f64[64,48] ; B:f64[48,40] ; {body}")
+        want = be.STRAT_DENSE_SPLIT if body in ok else be.STRAT_GENERIC
+        assert be.plan_strategy(None, e, precision=be.PREC_SPLIT) == want, body

@@ -125,3 +125,59 @@ def test_chem_full_size_sampled(ctx):
         worst = max(worst, r.max())
     print(f"split-precision max error / S over samples: {worst:.3e}")
     assert worst <= 1e-6
+
+
+def run_split_sc(ctx, text, arrs, scalars=()):
+    e = be.Einsum(text)
+    assert be.plan_strategy(ctx, e, precision=be.PREC_SPLIT) == be.STRAT_DENSE_SPLIT
+    outs = [torch.full(e.out_shape, float("nan"), dtype=torch.float64, device=DEV) for _ in range(e.b)]
+    be.execute(ctx, e, {k: torch.from_numpy(np.ascontiguousarray(v)).to(DEV) for k, v in arrs.items()}, outs,
+               precision=be.PREC_SPLIT, scalars=scalars)
+    assert ctx.status() == be.OK
+    return [o.cpu().numpy() for o in outs]
+
+
+@pytest.mark.parametrize("M,N,K", [(300, 260, 200), (129, 5, 65), (256, 384, 2048)])
+def test_affine_producers_runtime_scalars(ctx, M, N, K):
+    """(alpha1 A + beta1)(alpha2 B + beta2) with runtime scalars, fused into
+    the split of both operands."""
+    g = np.random.default_rng(M + N + K)
+    A, B = g.standard_normal((M, K)), g.standard_normal((K, N))
+    text = (f"ik,kj->ij | P,Q ; A:f64[{M},{K}] ; B:f64[{K},{N}] ; P(i,k) := $a1*A[i,k]+$b1 ; "
+            f"Q(k,j) := $a2*B[k,j]+$b2")
+    sc = (0.5, -1.25, 2.0, 0.75)
+    got, = run_split_sc(ctx, text, dict(A=A, B=B), sc)
+    (ref, S), = ev.evaluate(text, dict(A=A, B=B), scalars=dict(a1=sc[0], b1=sc[1], a2=sc[2], b2=sc[3]))
+    assert rel_err(got, ref, S).max() <= 1e-6
+
+
+def test_affine_tccg_shape_literals(ctx):
+    """A TCCG-shaped contraction 'abcd,cdef->abef' (M = ab, K = cd, N = ef)
+    with literal coefficients, a subtraction and a division by a constant,
+    two rows sharing the second operand."""
+    g = np.random.default_rng(5)
+    a, b, c, d, e_, f = 12, 20, 9, 30, 14, 10
+    A0, A1 = g.standard_normal((a, b, c, d)), g.standard_normal((a, b, c, d))
+    B = g.standard_normal((c, d, e_, f))
+    text = (f"abcd,cdef->abef | P0,Q | P1,Q ; A0:f64[{a},{b},{c},{d}] ; A1:f64[{a},{b},{c},{d}] ; "
+            f"B:f64[{c},{d},{e_},{f}] ; P0(a,b,c,d) := 0.5*A0[a,b,c,d] - 2.0 ; "
+            f"P1(a,b,c,d) := -(A1[a,b,c,d] + 1.5) ; Q(c,d,e,f) := B[c,d,e,f]/4.0 + 0.25")
+    arrs = dict(A0=A0, A1=A1, B=B)
+    got = run_split_sc(ctx, text, arrs)
+    ref = ev.evaluate(text, arrs)
+    for k in range(2):
+        assert rel_err(got[k], ref[k][0], ref[k][1]).max() <= 1e-6
+
+
+def test_affine_integers_bit_exact(ctx):
+    """Small-integer operands and integer coefficients stay exact in every
+    TF32 part and partial sum: bit-exact against the oracle."""
+    g = np.random.default_rng(9)
+    M, N, K = 200, 150, 1500
+    A = g.integers(-3, 4, (M, K)).astype(np.float64)
+    B = g.integers(-3, 4, (K, N)).astype(np.float64)
+    text = (f"ik,kj->ij | P,Q ; A:f64[{M},{K}] ; B:f64[{K},{N}] ; P(i,k) := 2*A[i,k]-1 ; "
+            f"Q(k,j) := $s*B[k,j]+$t")
+    got, = run_split_sc(ctx, text, dict(A=A, B=B), (-2.0, 3.0))
+    (ref, S), = ev.evaluate(text, dict(A=A, B=B), scalars=dict(s=-2.0, t=3.0))
+    assert np.array_equal(got, ref)
