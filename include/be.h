@@ -174,6 +174,37 @@ int be_graph_check(int32_t n_nodes, const int32_t *colors, const int32_t *edges,
 int be_identify(const be_einsum *ref, const be_einsum *target, char *buf, size_t len, size_t *needed);
 
 /*
+ * be_raise -- RaiseToBatchedEinsum, the first step of Alg. 2 (Sec.
+ * "Integration with other frameworks"): read a loop-nest kernel back as
+ * the functional batched einsum it computes.  kernel: lines of
+ *   "{ [i0,i1,..] : 0<=i0<N0 and 0<=i1<N1 .. }"   loop domain
+ *   "name:dtype[d0,d1,..]"                         input array
+ *   "name(p,q,..) := expr"                         substitution rule (expr as in be_parse)
+ *   "for i0" ... "end"                             loop nesting
+ *   "y[i0,..] = sum([i1,..], f(..)*g(..)*..)"      statement (or a plain product)
+ * ('#' starts a comment).  A factor is a rule call r(i0,..) or an array
+ * access A[i0,..] with loop names as subscripts; output subscripts are
+ * enclosing loops, the others are summed.  Each statement is one row; all
+ * rows must share one index structure up to a renaming of their loop names
+ * and the order of their factors.  Index letters are the loop names of the
+ * first statement in order of first appearance (output, then factors).
+ *   out: new handle (free with be_free_einsum), usable wherever a parsed
+ *        einsum is: canonicalize, lookup, identify, execute (one buffer per
+ *        declared array, declaration order).
+ * Errors: BE_EPARSE (kernel grammar), BE_EINVALID (unknown names, bad
+ * subscripts, statements that do not form one batched einsum), BE_ETOOMANY
+ * (> 26 loop indices), and the errors of be_parse on the raised text.
+ */
+int be_raise(const char *kernel, be_einsum **out);
+
+#define BE_RAISED_SPEC 0     /* the be_parse text the kernel was raised to       */
+#define BE_RAISED_LOOP 1     /* k: loop name of index letter 'a' + k            */
+#define BE_RAISED_OUTPUT 2   /* k: output array of row k                         */
+/* Names kept by be_raise (BE_ENOTFOUND for an einsum that was parsed, or
+ * k out of range); the string goes to buf like the other string calls. */
+int be_raised_name(const be_einsum *e, int32_t kind, int32_t k, char *buf, size_t len, size_t *needed);
+
+/*
  * Tuning database keyed by (normal form, device name, precision mode),
  * the paper's database of performance facts (Introduction, Fig. "The
  * Feinsum approach").  db_path: append-only text file, created if missing;

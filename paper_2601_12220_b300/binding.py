@@ -34,7 +34,7 @@ EXPORTS = [
     "be_plan_strategy", "be_status", "be_ctx_set_timing", "be_ctx_timing", "be_gemm_split_noalloc",
     "be_batch_create", "be_batch_run", "be_batch_info", "be_batch_destroy", "be_tune",
     "be_server_create", "be_server_submit", "be_server_wait", "be_server_drain", "be_server_stats",
-    "be_server_reset_stats", "be_server_destroy",
+    "be_server_reset_stats", "be_server_destroy", "be_raise", "be_raised_name",
 ]
 KERNEL_ELEMENT, KERNEL_GENERIC, KERNEL_DENSE_GEMM, KERNEL_SPLIT, KERNEL_PERSISTENT = 0, 1, 2, 3, 4
 
@@ -74,7 +74,7 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError(f"{LIB_PATH} is missing: build it with python -m paper_2601_12220_b300.build")
+            raise ImportError(f"{LIB_PATH} is missing: build it with python paper_2601_12220_b300/build.py")
         L = ctypes.CDLL(LIB_PATH)
         vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
         P = ctypes.POINTER
@@ -94,6 +94,8 @@ def lib():
             "be_induced_graph": (ctypes.c_int, [vp, P(i32), P(i32), i32, P(i32), i64, P(i64)]),
             "be_graph_check": (ctypes.c_int, [i32, P(i32), P(i32), i64, P(i32)]),
             "be_identify": (ctypes.c_int, [vp, vp, ctypes.c_char_p, sz, P(sz)]),
+            "be_raise": (ctypes.c_int, [ctypes.c_char_p, P(vp)]),
+            "be_raised_name": (ctypes.c_int, [vp, i32, i32, ctypes.c_char_p, sz, P(sz)]),
             "be_ctx_create": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_char_p, i32, sz, P(vp)]),
             "be_ctx_destroy": (None, [vp]),
             "be_lookup": (ctypes.c_int, [vp, vp, i32, P(Config), P(ctypes.c_double)]),
@@ -148,11 +150,14 @@ def _string(fn, *args):
 # ---------------------------------------------------------------- IR
 
 class Einsum:
-    """be_parse handle."""
+    """be_parse handle (or, through raise_kernel, a be_raise handle)."""
 
-    def __init__(self, text: str):
-        h = ctypes.c_void_p()
-        check(lib().be_parse(text.encode(), ctypes.byref(h)))
+    def __init__(self, text: str, _handle=None):
+        if _handle is None:
+            h = ctypes.c_void_p()
+            check(lib().be_parse(text.encode(), ctypes.byref(h)))
+        else:
+            h = _handle
         self._h = h
         self.text = text
         v = [ctypes.c_int32() for _ in range(7)]
@@ -194,6 +199,39 @@ class Einsum:
         colors = np.array(cols[:n.value], dtype=np.int32)
         edges = np.array(eds[:2 * ne.value], dtype=np.int32).reshape(-1, 2)
         return colors, edges
+
+
+RAISED_SPEC, RAISED_LOOP, RAISED_OUTPUT = 0, 1, 2
+
+
+def raise_kernel(kernel: str) -> Einsum:
+    """be_raise: the functional batched einsum a loop-nest kernel computes.
+    The result carries ``loop_names`` (index letter -> loop name) and
+    ``outputs`` (row -> output array); ``text`` is the raised be_parse text."""
+    h = ctypes.c_void_p()
+    check(lib().be_raise(kernel.encode(), ctypes.byref(h)))
+    spec = _string(lib().be_raised_name, h, RAISED_SPEC, 0)
+    e = Einsum(spec, _handle=h)
+    e.kernel = kernel
+    e.loop_names = {}
+    k = 0
+    while True:
+        need = ctypes.c_size_t(0)
+        if lib().be_raised_name(h, RAISED_LOOP, k, None, 0, ctypes.byref(need)) != OK:
+            break
+        e.loop_names[chr(ord("a") + k)] = _string(lib().be_raised_name, h, RAISED_LOOP, k)
+        k += 1
+    e.outputs = [_string(lib().be_raised_name, h, RAISED_OUTPUT, r) for r in range(e.b)]
+    return e
+
+
+def identify_kernel(ref: "Einsum", kernel: "Einsum") -> dict:
+    """Alg. 2 against a raised kernel: ref's index letters and argument names
+    -> the kernel's loop names and argument names."""
+    pairs = [kv.split("=") for kv in _string(lib().be_identify, ref.handle, kernel.handle).split(";") if kv]
+    names = getattr(kernel, "loop_names", {})
+    n_idx = len(names)                 # be_identify lists the indices first
+    return {k: (names.get(v, v) if q < n_idx else v) for q, (k, v) in enumerate(pairs)}
 
 
 def graph_check(colors, edges) -> int:

@@ -16,6 +16,7 @@
 
 #include "dense.hpp"
 #include "handles.hpp"
+#include "raise.hpp"
 
 using namespace be;
 
@@ -93,6 +94,46 @@ int be_parse(const char *text, be_einsum **out) {
 }
 
 void be_free_einsum(be_einsum *e) { delete e; }
+
+int be_raise(const char *kernel, be_einsum **out) {
+  if (!kernel || !out) return fail(BE_EARG, "NULL argument");
+  Raised r;
+  std::string err;
+  int st = raise_kernel(kernel, r, err);
+  if (st) return fail(st, "raise: " + err);
+  auto h = std::make_unique<be_einsum>();
+  st = parse(r.spec, h->e, err);
+  if (st) return fail(st, "raised einsum '" + r.spec + "': " + err);
+  h->raised_spec = r.spec;
+  h->loop_names = r.loop_names;
+  h->outputs = r.outputs;
+  *out = h.release();
+  return BE_OK;
+}
+
+int be_raised_name(const be_einsum *h, int32_t kind, int32_t k, char *buf, size_t len, size_t *needed) {
+  if (!h) return fail(BE_EARG, "NULL einsum");
+  if (h->raised_spec.empty()) return fail(BE_ENOTFOUND, "einsum was not raised from a kernel");
+  std::string s;
+  if (kind == BE_RAISED_SPEC) {
+    s = h->raised_spec;
+  } else if (kind == BE_RAISED_LOOP) {
+    if (k < 0 || k >= (int32_t)h->loop_names.size()) return fail(BE_ENOTFOUND, "no such index letter");
+    s = h->loop_names[k];
+  } else if (kind == BE_RAISED_OUTPUT) {
+    if (k < 0 || k >= (int32_t)h->outputs.size()) return fail(BE_ENOTFOUND, "no such row");
+    s = h->outputs[k];
+  } else {
+    return fail(BE_EARG, "unknown kind");
+  }
+  if (needed) *needed = s.size() + 1;
+  if (buf && len > 0) {
+    const size_t n = std::min(len - 1, s.size());
+    std::memcpy(buf, s.data(), n);
+    buf[n] = 0;
+  }
+  return BE_OK;
+}
 
 int be_einsum_info(const be_einsum *h, int32_t *b, int32_t *n, int32_t *n_buffers, int32_t *n_args,
                    int32_t *n_scalars, int32_t *out_ndim, int32_t *out_dtype) {

@@ -21,6 +21,10 @@ struct be_einsum {
   Einsum e;
   std::mutex mu;
   std::unique_ptr<Canon> canon;   // cached C(e) for lookups
+  // raised from a loop-nest kernel (be_raise): the text it was written as,
+  // the loop name of each index letter and the output array of each row
+  std::string raised_spec;
+  std::vector<std::string> loop_names, outputs;
 };
 
 struct be_canon {
