@@ -197,6 +197,32 @@ int be_identify(const be_einsum *ref, const be_einsum *target, char *buf, size_t
  */
 int be_raise(const char *kernel, be_einsum **out);
 
+/*
+ * be_record_facts -- record_facts of the transformation writer's view (Sec.
+ * "Integration with other frameworks"): time cfg on the idealized reference
+ * einsum ref -- device operands of its declared shapes filled with
+ * synthetic values (floating types uniform in [-1, 1), integers -3..3),
+ * every runtime scalar 1 -- after `warmup` untimed runs, average `reps`
+ * timed runs (CUDA events on the default stream), and store the time with
+ * be_record under ref's normal form.  The library allocates and frees the
+ * synthetic operands itself.  *seconds (may be NULL) receives the time.
+ * Errors: BE_EARG, the errors of be_execute for a cfg that does not fit ref,
+ * BE_ECUDA (allocation, launch), BE_EDB.
+ */
+int be_record_facts(be_ctx *x, const be_einsum *ref, const be_config *cfg, int32_t precision, int32_t warmup,
+                    int32_t reps, double *seconds);
+
+/*
+ * be_load_transforms -- a user-supplied transform library: one registration
+ * per line, "<reference in be_parse text> => <strategy> <tile0> <tile1>
+ * <tile2> <tile3> [<stages> <stage_mask> <vec> <split> [<precision>]]"
+ * ('#' starts a comment line).  Every line is parsed first (BE_EPARSE or the
+ * be_parse error of the reference, with its line number, and nothing is
+ * timed); then each is recorded with be_record_facts.  *n_recorded (may be
+ * NULL) counts the registrations stored.
+ */
+int be_load_transforms(be_ctx *x, const char *text, int32_t warmup, int32_t reps, int32_t *n_recorded);
+
 #define BE_RAISED_SPEC 0     /* the be_parse text the kernel was raised to       */
 #define BE_RAISED_LOOP 1     /* k: loop name of index letter 'a' + k            */
 #define BE_RAISED_OUTPUT 2   /* k: output array of row k                         */

@@ -34,7 +34,8 @@ EXPORTS = [
     "be_plan_strategy", "be_status", "be_ctx_set_timing", "be_ctx_timing", "be_gemm_split_noalloc",
     "be_batch_create", "be_batch_run", "be_batch_info", "be_batch_destroy", "be_tune",
     "be_server_create", "be_server_submit", "be_server_wait", "be_server_drain", "be_server_stats",
-    "be_server_reset_stats", "be_server_destroy", "be_raise", "be_raised_name",
+    "be_server_reset_stats", "be_server_destroy", "be_raise", "be_raised_name", "be_record_facts",
+    "be_load_transforms",
 ]
 KERNEL_ELEMENT, KERNEL_GENERIC, KERNEL_DENSE_GEMM, KERNEL_SPLIT, KERNEL_PERSISTENT = 0, 1, 2, 3, 4
 
@@ -95,6 +96,8 @@ def lib():
             "be_graph_check": (ctypes.c_int, [i32, P(i32), P(i32), i64, P(i32)]),
             "be_identify": (ctypes.c_int, [vp, vp, ctypes.c_char_p, sz, P(sz)]),
             "be_raise": (ctypes.c_int, [ctypes.c_char_p, P(vp)]),
+            "be_record_facts": (ctypes.c_int, [vp, vp, P(Config), i32, i32, i32, P(ctypes.c_double)]),
+            "be_load_transforms": (ctypes.c_int, [vp, ctypes.c_char_p, i32, i32, P(i32)]),
             "be_raised_name": (ctypes.c_int, [vp, i32, i32, ctypes.c_char_p, sz, P(sz)]),
             "be_ctx_create": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_char_p, i32, sz, P(vp)]),
             "be_ctx_destroy": (None, [vp]),
@@ -302,6 +305,21 @@ class Context:
 
     def record(self, canon: Canon, cfg: Config, seconds: float, precision=PREC_FP64):
         check(lib().be_record(self._h, canon.handle, precision, ctypes.byref(cfg), seconds))
+
+    def record_facts(self, ref: "Einsum", cfg: Config, precision=PREC_FP64, warmup=3, reps=10) -> float:
+        """Time cfg on synthetic operands of ref's shapes and store it under
+        ref's normal form; returns the seconds per run."""
+        sec = ctypes.c_double()
+        check(lib().be_record_facts(self._h, ref.handle, ctypes.byref(cfg), precision, warmup, reps,
+                                    ctypes.byref(sec)))
+        return sec.value
+
+    def load_transforms(self, text: str, warmup=3, reps=10) -> int:
+        """Register a transform library (lines '<reference> => <config>');
+        returns the number of registrations recorded."""
+        n = ctypes.c_int32()
+        check(lib().be_load_transforms(self._h, text.encode(), warmup, reps, ctypes.byref(n)))
+        return n.value
 
     def db_size(self) -> int:
         n = ctypes.c_int64()

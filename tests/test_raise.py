@@ -100,3 +100,19 @@ def test_parsed_einsum_has_no_raised_names():
     e = be.Einsum("ij,j->i | A,B ; A:f64[3,2] ; B:f64[2]")
     need = ctypes.c_size_t(0)
     assert be.lib().be_raised_name(e.handle, 1, 0, None, 0, ctypes.byref(need)) == be.ENOTFOUND
+
+
+@pytest.mark.parametrize("text,code", [
+    ("ij,j->i | A,B ; A:f64[4,3] ; B:f64[3]", be.EPARSE),                  # no '=>'
+    ("ij,j->i | A,B ; A:f64[4,3] ; B:f64[3] => 2 32", be.EPARSE),          # too few config fields
+    ("ij,j->i | A,B ; A:f64[4,3] ; B:f64[3] => 2 0 0 0 0 1", be.EPARSE),   # stages without the rest
+    ("ij,jk->i | A,B ; A:f64[4,3] ; B:f64[3] => 1 0 0 0 0", be.EINVALID),  # reference fails be_parse
+])
+def test_transform_library_errors_before_timing(text, code):
+    """A malformed transform library is refused while it is read, before
+    anything is timed (so on any host)."""
+    ctx = be.Context(None, device_name="dev", device=-1)
+    with pytest.raises(be.BEError) as ex:
+        ctx.load_transforms("# header comment\n" + text + "\n")
+    assert ex.value.code == code
+    assert ctx.db_size() == 0
