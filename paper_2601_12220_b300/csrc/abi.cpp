@@ -346,6 +346,9 @@ void be_ctx_destroy(be_ctx *x) {
   if (!x) return;
   for (void *p : x->stage)
     if (p) cudaFree(p);
+  for (cudaStream_t q : x->pipe)
+    if (q) cudaStreamDestroy(q);
+  for (cudaEvent_t ev : x->pipe_ev) cudaEventDestroy(ev);
   if (x->ws) cudaFree(x->ws);
   if (x->status) cudaFree(x->status);
   for (auto &m : x->marks) {
@@ -582,6 +585,65 @@ static size_t dense_bytes(const Buffer &b) {
   return n;
 }
 
+// Chunking of be_execute_host along the output's outermost letter L: every
+// buffer must either not involve L (copied whole) or have L as its outermost
+// dimension in every access and nowhere else (a chunk of L is then one
+// contiguous slice).  kind[k]: 0 whole, 1 sliced; false if any buffer fails.
+static bool host_chunking(const Einsum &e, std::vector<int> &kind) {
+  if (e.out.empty()) return false;
+  const int L = e.out[0];
+  kind.assign(e.buffers.size(), 0);
+  std::vector<int> seen(e.buffers.size(), 0);   // bit 0: L outermost, bit 1: L elsewhere or outermost not L
+  for (int i = 0; i < e.b; ++i)
+    for (int j = 0; j < e.n; ++j) {
+      const Arg &A = e.args[e.rows[i][j]];
+      const auto &letters = e.in[j];
+      if (!A.functional()) {
+        int &f = seen[A.buffer];
+        for (size_t d = 0; d < letters.size(); ++d)
+          if (letters[d] == L) f |= d == 0 ? 1 : 2;
+        if (!letters.empty() && letters[0] != L && std::find(letters.begin(), letters.end(), L) != letters.end()) f |= 2;
+        continue;
+      }
+      for (const XNode &nd : A.nodes) {
+        if (nd.op != X_REF) continue;
+        int &f = seen[nd.id];
+        bool has_l = false, outer_l = false;
+        for (size_t d = 0; d < nd.sub.size(); ++d)
+          if (nd.sub[d] >= 0 && letters[nd.sub[d]] == L) {
+            has_l = true;
+            if (d == 0) outer_l = true;
+            else f |= 2;
+          }
+        if (has_l && outer_l) f |= 1;
+        if (!has_l && (f & 1)) f |= 2;   // the same buffer also read without L
+        if (!has_l) f |= 4;
+      }
+    }
+  for (size_t k = 0; k < e.buffers.size(); ++k) {
+    const int f = seen[k];
+    if (f & 2) return false;
+    if ((f & 1) && (f & 4)) return false;
+    kind[k] = (f & 1) ? 1 : 0;
+  }
+  return true;
+}
+
+// the einsum with the extent of the output's outermost letter set to n
+static void resize_outer(const Einsum &src, const std::vector<int> &kind, int64_t n, Einsum &dst) {
+  dst = src;
+  const int L = src.out[0];
+  dst.len[L] = n;
+  for (size_t k = 0; k < dst.buffers.size(); ++k)
+    if (kind[k] == 1) dst.buffers[k].shape[0] = n;
+  for (int i = 0; i < src.b; ++i)
+    for (int j = 0; j < src.n; ++j) {
+      Arg &A = dst.args[src.rows[i][j]];
+      for (size_t d = 0; d < src.in[j].size() && d < A.shape.size(); ++d)
+        if (src.in[j][d] == L) A.shape[d] = n;
+    }
+}
+
 int be_execute_host(be_ctx *x, const be_einsum *h, const be_config *cfg, int32_t precision, const be_buf *bufs,
                     int32_t n_bufs, const be_buf *outs, int32_t n_outs, const double *scalars, int32_t n_scalars,
                     void *stream) {
@@ -616,6 +678,69 @@ int be_execute_host(be_ctx *x, const be_einsum *h, const be_config *cfg, int32_t
   }
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<be_buf> db(n_bufs), dout(n_outs);
+  // Large inputs stream through in chunks of the output's outermost letter:
+  // copy-in of chunk c + 1, the kernels of chunk c and copy-out of chunk
+  // c - 1 run on three streams, so both PCIe directions and the GPU overlap.
+  size_t total = 0;
+  for (size_t v : need) total += v;
+  std::vector<int> kind;
+  const int64_t L_ext = e.out.empty() ? 0 : e.len[e.out[0]];
+  const int n_chunks = (int)std::min<int64_t>(8, L_ext);
+  if (total >= ((size_t)64 << 20) && n_chunks >= 2 && host_chunking(e, kind)) {
+    for (int q = 0; q < 3; ++q)
+      if (!x->pipe[q] && (ce = cudaStreamCreateWithFlags(&x->pipe[q], cudaStreamNonBlocking)) != cudaSuccess)
+        return fail(BE_ECUDA, std::string("stream: ") + cudaGetErrorString(ce));
+    while ((int)x->pipe_ev.size() < 2 * n_chunks + 1) {
+      cudaEvent_t ev;
+      if ((ce = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+        return fail(BE_ECUDA, std::string("event: ") + cudaGetErrorString(ce));
+      x->pipe_ev.push_back(ev);
+    }
+    cudaStream_t s_in = x->pipe[0], s_run = x->pipe[1], s_out = x->pipe[2];
+    // after the caller's earlier work on `stream`
+    cudaEventRecord(x->pipe_ev[2 * n_chunks], s);
+    cudaStreamWaitEvent(s_in, x->pipe_ev[2 * n_chunks], 0);
+    for (int k = 0; k < n_bufs; ++k)
+      if (kind[k] == 0 && need[k] &&
+          (ce = cudaMemcpyAsync(x->stage[k], bufs[k].ptr, need[k], cudaMemcpyHostToDevice, s_in)) != cudaSuccess)
+        return fail(BE_ECUDA, std::string("H2D: ") + cudaGetErrorString(ce));
+    const int64_t chunk = (L_ext + n_chunks - 1) / n_chunks;
+    const size_t out_row = L_ext ? out_bytes / (size_t)L_ext : 0;
+    for (int ch = 0; ch < n_chunks; ++ch) {
+      const int64_t e0 = ch * chunk, n = std::min<int64_t>(chunk, L_ext - e0);
+      if (n <= 0) break;
+      for (int k = 0; k < n_bufs; ++k) {
+        const size_t row = need[k] / (size_t)L_ext;
+        if (kind[k] == 1) {
+          ce = cudaMemcpyAsync((char *)x->stage[k] + e0 * row, (const char *)bufs[k].ptr + e0 * row, n * row,
+                               cudaMemcpyHostToDevice, s_in);
+          if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("H2D: ") + cudaGetErrorString(ce));
+        }
+        db[k] = be_buf{(char *)x->stage[k] + (kind[k] == 1 ? e0 * row : 0), nullptr, bufs[k].ndim, bufs[k].dtype};
+      }
+      for (int k = 0; k < n_outs; ++k)
+        dout[k] = be_buf{(char *)x->stage[n_bufs + k] + e0 * out_row, nullptr, outs[k].ndim, outs[k].dtype};
+      cudaEventRecord(x->pipe_ev[2 * ch], s_in);
+      cudaStreamWaitEvent(s_run, x->pipe_ev[2 * ch], 0);
+      be_einsum part;
+      resize_outer(e, kind, n, part.e);
+      int st = do_execute(nullptr, &part, reinterpret_cast<const be_config *>(&c), precision, db.data(), n_bufs,
+                          dout.data(), n_outs, scalars, n_scalars, s_run);
+      if (st) return st;
+      cudaEventRecord(x->pipe_ev[2 * ch + 1], s_run);
+      cudaStreamWaitEvent(s_out, x->pipe_ev[2 * ch + 1], 0);
+      for (int k = 0; k < n_outs; ++k)
+        if (n * out_row &&
+            (ce = cudaMemcpyAsync((char *)outs[k].ptr + e0 * out_row, (char *)x->stage[n_bufs + k] + e0 * out_row,
+                                  n * out_row, cudaMemcpyDeviceToHost, s_out)) != cudaSuccess)
+          return fail(BE_ECUDA, std::string("D2H: ") + cudaGetErrorString(ce));
+    }
+    ce = cudaStreamSynchronize(s_out);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s_run);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s_in);
+    if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("sync: ") + cudaGetErrorString(ce));
+    return BE_OK;
+  }
   for (int k = 0; k < n_bufs; ++k) {
     if (need[k]) ce = cudaMemcpyAsync(x->stage[k], bufs[k].ptr, need[k], cudaMemcpyHostToDevice, s);
     if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("H2D: ") + cudaGetErrorString(ce));

@@ -42,9 +42,12 @@ struct be_ctx {
   size_t hbm_budget = 0;
   std::mutex mu;
   std::unordered_map<std::string, DbEntry> db;
-  // staging memory of be_execute_host
+  // staging memory of be_execute_host, and its copy-in / compute / copy-out
+  // streams and per-chunk events (created on first use)
   std::vector<void *> stage;
   std::vector<size_t> stage_size;
+  cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};
+  std::vector<cudaEvent_t> pipe_ev;
   // workspace of the dense split strategy and the device status word
   void *ws = nullptr;
   size_t ws_size = 0;

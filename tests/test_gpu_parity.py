@@ -249,6 +249,43 @@ def test_execute_host_matches_device():
         assert np.array_equal(outs[x], dev[x])
 
 
+@pytest.mark.parametrize("E", [60001, 100000])
+def test_execute_host_chunked_matches_device(E):
+    """Above 64 MB the host path streams element chunks through three
+    streams; every chunk's results equal the device run bit for bit."""
+    D, G, a, b = W.dg_gradient(E=E)
+    arrs = dict(D=D, G=G, a=a, b=b)
+    text = W.dg_gradient_spec(E=E)
+    ctx = be.Context(None, device=0)
+    outs = [np.full((E, 35), np.nan) for _ in range(3)]
+    be.execute_host(ctx, be.Einsum(text), arrs, outs)
+    dev, _ = run(text, arrs)
+    for x in range(3):
+        assert np.array_equal(outs[x], dev[x])
+
+
+def test_execute_host_unchunkable_layout_and_stacked_form():
+    """A field stored with the element letter inside (not outermost) keeps
+    the one-piece host path; the stacked divergence form streams in chunks."""
+    E, N = 300000, 35
+    g = np.random.default_rng(4)
+    U = g.standard_normal((N, E))
+    Dm = g.standard_normal((N, N))
+    text = f"je,ij->ei | U,D ; U:f64[{N},{E}] ; D:f64[{N},{N}]"
+    ctx = be.Context(None, device=0)
+    out = [np.full((E, N), np.nan)]
+    be.execute_host(ctx, be.Einsum(text), dict(U=U, D=Dm), out)
+    dev, _ = run(text, dict(U=U, D=Dm))
+    assert np.array_equal(out[0], dev[0])
+    D, data = W.dg_divergence(E=100000, order=4, rows=1)
+    arrs = W.dg_divergence_arrays(D, data)
+    text = W.dg_divergence_spec(E=100000, order=4, rows=1)
+    out = [np.full((100000, 35), np.nan)]
+    be.execute_host(ctx, be.Einsum(text), arrs, out)
+    dev, _ = run(text, arrs)
+    assert np.array_equal(out[0], dev[0])
+
+
 def test_deterministic():
     E = 3001
     D, G, a, b = W.dg_gradient(E=E)
