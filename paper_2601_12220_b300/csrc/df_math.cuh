@@ -128,6 +128,26 @@ __device__ __forceinline__ df df_from_double(double x) {
   return df{hi, (int)hw < 0 ? -lo : lo};
 }
 
+// the same without the range test, for callers that tested the range
+// beforehand (df_fast_ok): valid for zero and 2^-70 <= |x| < 2^101; zero is
+// handled by selects, so the code has no branch
+__device__ __forceinline__ df df_from_double_fast(double x) {
+  const uint32_t hw = (uint32_t)__double2hiint(x), lw = (uint32_t)__double2loint(x);
+  const uint32_t ax = hw & 0x7FFFFFFFu;
+  const uint32_t rnd = (lw >> 28) & 1u;
+  const uint32_t hb = ((ax - (896u << 20)) << 3) + (lw >> 29) + rnd;
+  const float hi = __uint_as_float(hb | (hw & 0x80000000u));
+  const int rem = (int)(lw & 0x1FFFFFFFu) - (int)(rnd << 29);
+  const float lo = (float)rem * __uint_as_float((uint32_t)((int)(ax >> 20) - 948) << 23);
+  const bool z = ax == 0u;
+  return df{z ? 0.f : hi, z ? 0.f : ((int)hw < 0 ? -lo : lo)};
+}
+// x is zero or in df_from_double's exact range
+__device__ __forceinline__ bool df_fast_ok(double x) {
+  const uint32_t ax = (uint32_t)__double2hiint(x) & 0x7FFFFFFFu;
+  return ax == 0u || ax - ((1023u - 70u) << 20) < (171u << 20);
+}
+
 // sin(x) as df; |x| < 2^20 (the reduction's exact range), else FP64 sin
 __device__ __forceinline__ df df_sin(double x) {
   // |x| < 2^20 (and finite), tested on the exponent bits
@@ -229,6 +249,30 @@ __device__ __forceinline__ df df_sin_tab2(double x, const float2 *tab) {
   const df cd = fast_two_sum(c1.hi, c1.lo + fmaf(-d.hi, d.lo, fmaf(p.hi, p.hi * (1.f / 24.f), -0.5f * p.lo)));
   const float2 s0 = tab[n & (SIN2_N - 1)], c0 = tab[(n + SIN2_N / 4) & (SIN2_N - 1)];
   return df_add(df_mul(df{s0.x, s0.y}, cd), df_mul(df{c0.x, c0.y}, sd));
+}
+
+// df_sin_tab2 without the range test: |x| < 2^20 (sin_fast_ok), and the
+// reduced argument converted without its range test (it is zero or at least
+// 2^-70 whenever it matters: a reduced argument below 2^-70 is replaced by
+// zero, an absolute change far below the result's rounding)
+__device__ __forceinline__ df df_sin_tab2_fast(double x, const float2 *tab) {
+  const double nm = fma(x, 162.97466172610083, 6755399441055744.0);
+  const int n = __double2loint(nm);
+  const double nd = nm - 6755399441055744.0;
+  const double dr = fma(-nd, PI512_LO, fma(-nd, PI512_HI, x));
+  const uint32_t adr = (uint32_t)__double2hiint(dr) & 0x7FFFFFFFu;
+  const df d = df_from_double_fast(adr < ((1023u - 70u) << 20) ? 0.0 : dr);
+  const float d2 = d.hi * d.hi;
+  const df sd = fast_two_sum(d.hi, fmaf(d.hi * d2, fmaf(d2, 1.f / 120.f, -1.f / 6.f), d.lo));
+  const df p = two_prod(d.hi, d.hi);
+  const df c1 = fast_two_sum(1.f, -0.5f * p.hi);
+  const df cd = fast_two_sum(c1.hi, c1.lo + fmaf(-d.hi, d.lo, fmaf(p.hi, p.hi * (1.f / 24.f), -0.5f * p.lo)));
+  const float2 s0 = tab[n & (SIN2_N - 1)], c0 = tab[(n + SIN2_N / 4) & (SIN2_N - 1)];
+  return df_add(df_mul(df{s0.x, s0.y}, cd), df_mul(df{c0.x, c0.y}, sd));
+}
+// |x| < 2^20 (and finite): the range of df_sin_tab2_fast
+__device__ __forceinline__ bool sin_fast_ok(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7FF) < 1023 + 20;
 }
 
 // sin(x) as df using the table (|x| < 2^20, else FP64 sin)

@@ -190,3 +190,18 @@ def test_default_is_tensor_core_and_unsupported_shape_is_refused():
     assert exc.value.code == be.EUNSUPPORTED
     be.execute(None, e, bufs, out)   # the default takes another strategy
     torch.cuda.synchronize()
+
+
+def test_out_of_range_operands_take_the_tested_path():
+    """Sine arguments beyond 2^20 and operands below 2^-70 fail the batch
+    range test, so their batches run the tested producer (FP64 sine and
+    conversion through FP64); neighbouring batches keep the fast one."""
+    E = 700
+    D, G, a, b = W.dg_gradient(E=E)
+    a, b = a.copy(), b.copy()
+    a[5, 3] = 3.0e6
+    a[100, :] *= 2.0 ** 25
+    a[400, 0] = -2.0 ** 21
+    b[200, 7] = 2.0 ** -80
+    b[300, :] = 0.0
+    check(W.dg_gradient_spec(E=E), dict(D=D, G=G, a=a, b=b))
