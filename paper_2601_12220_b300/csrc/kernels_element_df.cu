@@ -6,7 +6,7 @@
 // double-float (df) arithmetic: D, u and g are held as float pairs, the dot
 // products accumulate exactly through TwoSum with the cross terms in a
 // second float, and the fused producer u = sin(a) * b is evaluated with the
-// df sine.  Results reach FP64 accuracy (about 2^-46 of the absolute
+// df sine (full-circle table).  Results reach FP64 accuracy (about 2^-46 of the absolute
 // contraction) while the FP64 pipe only adds the two halves of each output.
 #include <algorithm>
 
@@ -19,20 +19,43 @@ namespace {
 
 using dfm::df;
 
-__device__ __forceinline__ df prod_df(const EProd &q, int64_t e, int k, int NJ0, const float4 *sin_tab) {
+// the producer's value at (e, k) in double-float.  The operands are loaded
+// first and range-tested together; when all pass (the usual case) the
+// conversions and the sine run without tests or out-of-line calls.
+__device__ __forceinline__ df prod_df(const EProd &q, int64_t e, int k, int NJ0, const float2 *sin_tab) {
   if (q.kind == 3) {   // stacked: sum_x A_x[e, s, j] * B_x[e, s, j] at k = s * NJ0 + j, in df
     const int s = k / NJ0, j = k - s * NJ0;
+    double av[EM_MAXX], bv[EM_MAXX];
+    bool ok = true;
+#pragma unroll
+    for (int x = 0; x < EM_MAXX; ++x) {
+      av[x] = x < q.X ? q.A[x].ptr[e * q.A[x].se + s * q.A[x].ss + j * q.A[x].sj] : 0.0;
+      bv[x] = x < q.X ? q.B[x].ptr[e * q.B[x].se + s * q.B[x].ss + j * q.B[x].sj] : 0.0;
+      ok = ok && dfm::df_fast_ok(av[x]) && dfm::df_fast_ok(bv[x]);
+    }
     float sh = 0.f, sl = 0.f;
-    for (int x = 0; x < q.X; ++x)
-      dfm::dot_acc(sh, sl, dfm::df_from_double(q.A[x].ptr[e * q.A[x].se + s * q.A[x].ss + j * q.A[x].sj]),
-                   dfm::df_from_double(q.B[x].ptr[e * q.B[x].se + s * q.B[x].ss + j * q.B[x].sj]));
+    if (ok) {
+#pragma unroll
+      for (int x = 0; x < EM_MAXX; ++x)
+        if (x < q.X) dfm::dot_acc(sh, sl, dfm::df_from_double_fast(av[x]), dfm::df_from_double_fast(bv[x]));
+    } else {
+#pragma unroll
+      for (int x = 0; x < EM_MAXX; ++x)
+        if (x < q.X) dfm::dot_acc(sh, sl, dfm::df_from_double(av[x]), dfm::df_from_double(bv[x]));
+    }
     return dfm::two_sum(sh, sl);
   }
   const double a = q.a.ptr[e * q.a.se + k * q.a.sk];
-  if (q.kind == 0) return dfm::df_from_double(a);
+  if (q.kind == 0) return dfm::df_fast_ok(a) ? dfm::df_from_double_fast(a) : dfm::df_from_double(a);
   const double b = q.b.ptr[e * q.b.se + k * q.b.sk];
-  if (q.kind == 2) return dfm::df_mul(dfm::df_from_double(a), dfm::df_from_double(b));
-  return dfm::df_mul(dfm::df_sin_tab(a, sin_tab), dfm::df_from_double(b));
+  if (q.kind == 2) {
+    if (dfm::df_fast_ok(a) && dfm::df_fast_ok(b))
+      return dfm::df_mul(dfm::df_from_double_fast(a), dfm::df_from_double_fast(b));
+    return dfm::df_mul(dfm::df_from_double(a), dfm::df_from_double(b));
+  }
+  if (dfm::sin_fast_ok(a) && dfm::df_fast_ok(b))
+    return dfm::df_mul(dfm::df_sin_tab2_fast(a, sin_tab), dfm::df_from_double_fast(b));
+  return dfm::df_mul(dfm::df_sin_tab2(a, sin_tab), dfm::df_from_double(b));
 }
 
 constexpr int DF_EPT = 4;   // elements per thread in the contraction phase
@@ -44,9 +67,9 @@ __global__ void __launch_bounds__(512, 2) element_df_kernel(const __grid_constan
   float2 *Us = Ds + R * NI * NJ;                      // [TE][NJ], one producer group at a time
   float2 *Gs = Us + TE * NJ;                          // [rows][TE][R]
   const int n_f2 = R * NI * NJ + TE * NJ + p.n_rows * TE * R;
-  float4 *sin_tab = (float4 *)(smf + n_f2 + (n_f2 & 1));              // 16-byte aligned
+  float2 *sin_tab = smf + n_f2;                       // full-circle sine table
   const int tid = threadIdx.x, nt = blockDim.x;
-  dfm::sin_table_fill(sin_tab);
+  dfm::sin2_table_fill(sin_tab);
 
   for (int idx = tid; idx < R * NI * NJ; idx += nt) {
     const int r = idx / (NI * NJ), rem = idx % (NI * NJ);
@@ -138,7 +161,7 @@ int element_df_block(const EParams &p) {
 
 cudaError_t launch_element_df(const EParams &p, int grid, int block, cudaStream_t s) {
   if (p.tile_e % DF_EPT) return cudaErrorInvalidValue;          // element groups never straddle a tile
-  const size_t smem = sizeof(float2) * (element_smem_words(p) + 1) + sizeof(float4) * dfm::SIN_TAB_N;
+  const size_t smem = sizeof(float2) * (element_smem_words(p) + dfm::SIN2_N);
   if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
   static bool attr = false;
   if (!attr) {
