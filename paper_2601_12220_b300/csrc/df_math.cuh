@@ -6,11 +6,14 @@
 // Building blocks (published error-free transformations): TwoSum (Knuth),
 // Fast2Sum (Dekker, 1971) for |a| >= |b|, and TwoProd through a fused
 // multiply-add (the product's rounding error is exactly fma(a, b, -p)).
-// sine: Cody-Waite reduction by pi/2 (pi/2 held in three floats; x - k*p1
-// with one FP64 fma, k*p2 formed exactly with TwoProd) followed by the Taylor series of sin or
-// cos on |r| <= pi/4, the small high-order terms in plain float and the
-// leading ones in df.  The constants are 1/k! and pi/2 rounded into float
-// pairs (hex literals, derived with exact rational arithmetic).
+// Sine (df_sin, used to fill the tables): Cody-Waite reduction by pi/2
+// (pi/2 held in three floats; x - k*p1 with one FP64 fma, k*p2 formed
+// exactly with TwoProd) followed by the Taylor series of sin or cos on
+// |r| <= pi/4, the small high-order terms in plain float and the leading
+// ones in df.  The constants are 1/k! and pi/2 rounded into float pairs
+// (hex literals, derived with exact rational arithmetic).  The kernels use
+// df_sin_tab2: reduction to a grid of pi/512 and the angle-addition formula
+// with a full-circle table of sin(n pi/512).
 #pragma once
 
 #include <cstdint>
@@ -176,39 +179,6 @@ __device__ __forceinline__ df df_sin(double x) {
   return (q & 2) ? df_neg(p) : p;
 }
 
-// ---- table-driven sine: sin(x0 + d) = sin x0 cos d + cos x0 sin d ----
-// x0 = k / 256, k in [-SIN_TAB_K, SIN_TAB_K] covers the reduced range |r| <= pi/4;
-// the table holds sin x0, cos x0 as df (s.hi, s.lo, c.hi, c.lo), filled once
-// per CTA with df_sin (exact argument k / 256).  |d| <= 2^-9, so
-// sin d = d - d^3/6 and cos d = 1 - d^2/2 + d^4/24 leave terms below 2^-51.
-constexpr int SIN_TAB_K = 202;
-constexpr int SIN_TAB_N = 2 * SIN_TAB_K + 1;
-
-__device__ __forceinline__ void sin_table_fill(float4 *tab) {
-  for (int k = threadIdx.x; k < SIN_TAB_N; k += blockDim.x) {
-    const double x0 = (double)(k - SIN_TAB_K) / 256.0;
-    const df s = df_sin(x0);
-    // cos x0 by its series directly (|x0| <= 0.79)
-    const df xr = df_from_double(x0);
-    const df x2 = df_mul(xr, xr);
-    float t = COS_C[11][0];
-    for (int n = 10; n >= 6; --n) t = fmaf(t, x2.hi, COS_C[n][0]);
-    df cc{t, 0.f};
-    for (int n = 5; n >= 0; --n) cc = df_add(df_mul(cc, x2), df{COS_C[n][0], COS_C[n][1]});
-    tab[k] = make_float4(s.hi, s.lo, cc.hi, cc.lo);
-  }
-}
-
-// an integer-valued double with |v| < 2^31 as an int, by bit moves
-__device__ __forceinline__ int kd_to_int(double v) {
-  const long long b = __double_as_longlong(v);
-  const int e = (int)((b >> 52) & 0x7FF) - 1023;              // v = 0 or |v| in [2^e, 2^(e+1))
-  if (e < 0) return 0;
-  const long long m = (b & 0xFFFFFFFFFFFFFll) | (1ll << 52);
-  const int n = (int)(m >> (52 - e));
-  return b < 0 ? -n : n;
-}
-
 // FP64 sine of an argument outside the double-float range, kept out of line
 // so that the callers' hot code stays small
 static __device__ __noinline__ df sin_far(double x) { return df_from_double(sin(x)); }
@@ -273,33 +243,6 @@ __device__ __forceinline__ df df_sin_tab2_fast(double x, const float2 *tab) {
 // |x| < 2^20 (and finite): the range of df_sin_tab2_fast
 __device__ __forceinline__ bool sin_fast_ok(double x) {
   return (int)((__double_as_longlong(x) >> 52) & 0x7FF) < 1023 + 20;
-}
-
-// sin(x) as df using the table (|x| < 2^20, else FP64 sin)
-__device__ __forceinline__ df df_sin_tab(double x, const float4 *tab) {
-  if ((int)((__double_as_longlong(x) >> 52) & 0x7FF) >= 1023 + 20) return df_from_double(sin(x));
-  // the quadrant from x in FP64 (error far below 1/2 for |x| < 2^20, so
-  // |r| <= pi/4 + 2^-30 and the table index stays inside); x - k * PIO2_1 is
-  // exact in one fma (k * PIO2_1 has at most 44 bits)
-  const double kd = rint(x * 0.63661977236758134308);
-  const float k = __double2float_rn(kd);
-  df r = df_from_double(fma(-kd, (double)PIO2_1, x));
-  r = df_add(r, df_neg(two_prod(k, PIO2_2)));
-  r = df_add(r, df{-k * PIO2_3, 0.f});
-  const float fk = rintf(r.hi * 256.f);
-  const df d = df_add(r, df{-fk * 0.00390625f, 0.f});             // r - k/256, exact grid point
-  const float4 t = tab[min(max((int)fk + SIN_TAB_K, 0), SIN_TAB_N - 1)];   // |r| <= pi/4: always inside
-  const float d3 = d.hi * d.hi * d.hi;
-  const df sd = df_add(d, df{-d3 * (1.f / 6.f), 0.f});
-  df d2 = two_prod(d.hi, d.hi);
-  d2.lo = fmaf(2.f * d.hi, d.lo, d2.lo);
-  const df cd = df_add(df_add(df{1.f, 0.f}, df{-0.5f * d2.hi, -0.5f * d2.lo}), df{d2.hi * d2.hi * (1.f / 24.f), 0.f});
-  const df s0{t.x, t.y}, c0{t.z, t.w};
-  const int q = ((int)k) & 3;
-  df res;
-  if (q & 1) res = df_add(df_mul(c0, cd), df_neg(df_mul(s0, sd)));   // cos r
-  else res = df_add(df_mul(s0, cd), df_mul(c0, sd));                   // sin r
-  return (q & 2) ? df_neg(res) : res;
 }
 
 }  // namespace dfm
