@@ -345,6 +345,90 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
+# ---------------------------------------------------------------- FEM action
+
+def run_fem(args):
+    """FEM action 'ij,ej->ei', b = 4 rows sharing D (4 x 4), E = 4096: time per
+    batched einsum through be_execute and as a CUDA-graph replay of a batch,
+    plus canonicalization of 200 copies under random renames, row and
+    operand permutations (latency p50 / p99 and one key for all)."""
+    import torch
+    import paper_2601_12220_b300 as be
+
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    E = 4096
+    D, us = W.fem_action(E=E)
+    host = {"D": D, **{f"u{k}": u for k, u in enumerate(us)}}
+    bufs = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
+    outs = [torch.empty((E, 4), dtype=torch.float64, device=dev) for _ in range(4)]
+    text = W.fem_action_spec(E=E)
+    ctx = be.Context(None, device=local)
+    stream = torch.cuda.current_stream(dev)
+    byts = 8.0 * (sum(v.size for v in host.values()) + 4 * E * 4)
+
+    def step():
+        e = be.Einsum(text)
+        c = e.canonicalize()
+        hit = ctx.lookup(c)
+        be.execute(ctx, e, bufs, outs, cfg=hit[0] if hit else None, stream=stream)
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / steps
+
+    steps = max(args.steps, 100)
+    ctx.set_timing(True)
+    with Clocks(local) as clk:
+        ms = timed(step, steps)
+    ctx.set_timing(False)
+    n_k, t_k = ctx.timing(be.KERNEL_ELEMENT)
+    batch = be.Batch(ctx, [(be.Einsum(text), bufs, outs)])
+    ms_graph = timed(lambda: batch.run(stream), steps)
+    # canonicalization of 200 relabeled copies
+    ins, out = ["ij", "ej"], "ei"
+    rows = [["D", f"u{k}"] for k in range(4)]
+    g = W.rng(1, 77)
+    lat, keys = [], set()
+    for _ in range(200):
+        r = W.relabel(out, ins, rows, g)
+        lens = {r.rename["i"]: 4, r.rename["j"]: 4, r.rename["e"]: E}
+        decl = {}
+        for row in r.rows:
+            for q, a in enumerate(row):
+                decl[a] = ",".join(str(lens[c]) for c in r.ins[q])
+        t = (f"{','.join(r.ins)}->{r.out} | " + " | ".join(",".join(x) for x in r.rows) + " ; " +
+             " ; ".join(f"{a}:f64[{sh}]" for a, sh in decl.items()))
+        e = be.Einsum(t)
+        a0 = time.perf_counter()
+        c = e.canonicalize()
+        lat.append(time.perf_counter() - a0)
+        keys.add(c.key)
+    lat = np.sort(np.asarray(lat)) * 1e6
+    line = {"metric": METRIC, "value": world * 1e3 / ms, "unit": "batched einsums/s", "n_gpus": world,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"fem_action: b=4 'ij,ej->ei', D 4x4 shared, E={E}, U[-1,1]",
+                       "parallelism": f"replicas x{world}", "l2": "inputs in L2 (0.5 MB)"},
+            "einsums_per_s": world * 4e3 / ms, "gb_s": world * byts / (ms * 1e-3) / 1e9,
+            "kernel_ms": t_k / max(1, n_k),
+            "graph_replay": {"ms_per_step": ms_graph, "batched_einsums_per_s": world * 1e3 / ms_graph},
+            "canonicalize_200_copies": {"p50_us": float(lat[len(lat) // 2]), "p99_us": float(lat[int(0.99 * len(lat))]),
+                                        "distinct_keys": len(keys), "key": sorted(keys)[0]},
+            "clocks": clk.summary(), "gpu_launches": n_k}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------- DG divergence and face mass
 
 def run_stacked(args):
@@ -772,7 +856,7 @@ def main():
                     help="0 default (double-float on the FP32 pipe), 1 FP64 pipe")
     ap.add_argument("--workload", default="dg_gradient",
                     choices=["dg_gradient", "chem_dense", "uneven_mix", "serving", "dg_divergence", "face_mass",
-                             "dense_affine"])
+                             "dense_affine", "fem_action"])
     ap.add_argument("--affine-n", type=int, default=64, help="every extent of the dense_affine contraction")
     ap.add_argument("--order", type=int, default=4, help="polynomial order of dg_divergence / face_mass")
     ap.add_argument("--rows", type=int, default=1, help="einsums b of dg_divergence / face_mass")
@@ -801,6 +885,8 @@ def main():
         run_stacked(args)
     elif args.workload == "dense_affine":
         run_affine(args)
+    elif args.workload == "fem_action":
+        run_fem(args)
     else:
         run_ours(args)
 
