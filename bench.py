@@ -693,8 +693,14 @@ def run_mix(args):
     dev = torch.device("cuda", local)
     g = W.rng(4, 0)
     items, byts, n_rows = [], 0, 0
+    fl64, fl32 = 0.0, 0.0          # loop-nest flops of the f64 and f32 instances
     for _ in range(args.mix_n):
         inst = W.mix_instance(g, max_operand=1 << args.mix_operand_log2, max_flops=1 << args.mix_flops_log2)
+        f = len(inst.rows) * W._flops(inst.out, inst.ins, inst.lens)
+        if "64" in str(inst.dtype):
+            fl64 += f
+        else:
+            fl32 += f
         arrs = W.instance_arrays(inst, g)
         e = be.Einsum(W.instance_spec(inst))
         dt = torch.float64 if e.out_dtype == be.F64 else torch.float32
@@ -745,9 +751,16 @@ def run_mix(args):
             "one_launch_per_einsum": {"ms_per_step": ms_single, "einsums_per_s": args.mix_n / (ms_single * 1e-3)},
             "speedup_vs_one_launch_per_einsum": ms_single / ms_batch,
             "gb_s": world * byts / (ms_batch * 1e-3) / 1e9,
-            "roofline": {"kernel": "persistent_kernel", "bound": "hbm", "achieved": byts / (kms * 1e-3) / 1e9,
-                         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": byts / (kms * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                         "traffic": None, "algorithmic_bytes": byts},
+            "roofline": {"kernel": "persistent_kernel", "bound": "alu",
+                         "achieved": (fl64 + fl32) / (kms * 1e-3) / 1e12,
+                         "peak": (fl64 + fl32) / (fl64 / (FP64_PEAK_TFLOPS * 1e12) + fl32 / (FP32_PEAK_TFLOPS * 1e12)) / 1e12,
+                         "unit": "TFLOP/s",
+                         "frac": (fl64 / (FP64_PEAK_TFLOPS * 1e12) + fl32 / (FP32_PEAK_TFLOPS * 1e12)) / (kms * 1e-3),
+                         "counts": "loop-nest flops (2 x iteration volume x (operands - 1) per row); peak: the time "
+                                   "at nominal FP64 (1.25 TFLOP/s) for the f64 instances plus FP32 for the f32 ones",
+                         "traffic": None, "algorithmic_bytes": byts,
+                         "hbm": {"achieved": byts / (kms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                 "frac": byts / (kms * 1e-3) / 1e9 / peaks["hbm_gbs"]}},
             "clocks": clk.summary(), "gpu_launches": n_k}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -822,6 +835,17 @@ def run_serving(args):
         lat.append(fin - t)
     lat = np.sort(np.asarray(lat))
     single_rate = len(arrivals) / (fin - arrivals[0])
+    # kernel launches of the served sequence: each template's count (the same
+    # on every execution), summed over the requests
+    kinds = (be.KERNEL_ELEMENT, be.KERNEL_GENERIC, be.KERNEL_DENSE_GEMM, be.KERNEL_SPLIT, be.KERNEL_PERSISTENT)
+    per_template = np.zeros(len(templates), dtype=np.int64)
+    ctx.set_timing(True)
+    for k, (e, bufs, outs) in enumerate(templates):
+        be.execute(ctx, e, bufs, outs)
+        torch.cuda.synchronize()
+        per_template[k] = sum(ctx.timing(kd)[0] for kd in kinds)
+    ctx.set_timing(False)
+    launches = int(per_template[pick].sum())
     line = {"metric": METRIC, "value": world * st["throughput"], "unit": "einsums/s", "n_gpus": world,
             "steps": 1, "warmup": 1, "ms_per_step": 1e3 / max(st["throughput"], 1e-9), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32 mix", "data": "synthetic",
@@ -836,7 +860,7 @@ def run_serving(args):
             "one_launch_per_einsum": {"einsums_per_s": single_rate,
                                       "latency_p50_ms": float(lat[len(lat) // 2]) * 1e3,
                                       "latency_p99_ms": float(lat[int(0.99 * (len(lat) - 1))]) * 1e3},
-            "clocks": clk.summary()}
+            "clocks": clk.summary(), "gpu_launches": launches}
     srv.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
