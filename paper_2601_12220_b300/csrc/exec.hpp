@@ -45,6 +45,8 @@ struct alignas(16) GParams {
   void *out;
   int32_t out_dtype;
   int32_t mode;         // 0 thread, 1 warp, 2 CTA per output (by contraction length)
+  int32_t fast;         // 1: <= 4 operands, all views of the output's dtype, <= 4 contracted letters
+  int32_t pad_fast;
   double scalars[8];
   GOp ops[GMAXOPS];
   GIns ins[GMAXINS];

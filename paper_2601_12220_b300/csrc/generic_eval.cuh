@@ -142,6 +142,77 @@ __device__ T contract(const GParams &p, int64_t o, int64_t first, int64_t stride
   return acc;
 }
 
+// Sum of the terms of output o over the contiguous iterations [lo, hi) for a
+// row whose operands are all plain views of type T (GParams::fast): the
+// offset of each operand is kept running -- the output letters give its
+// base, and the contracted odometer adds the letter's coefficient on each
+// step and takes len * coefficient off when the letter wraps -- so a term
+// costs a typed load per operand and a few integer adds.  Iterations run in
+// the same order as contract() with stride 1.
+template <typename T>
+__device__ T contract_fast(const GParams &p, int64_t o, int64_t lo, int64_t hi) {
+  if (lo >= hi) return (T)0;
+  int64_t off[4] = {0, 0, 0, 0};
+  int64_t rem = o;
+  for (int d = p.n_out - 1; d >= 0; --d) {
+    const int L = p.out_letter[d];
+    const int64_t q = rem / p.len[L], v = rem - q * p.len[L];
+    rem = q;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < p.n_ops) off[k] += p.ops[k].coef[L] * v;
+  }
+  // contracted letters: digit, length and per-operand step (innermost last)
+  int64_t dig[4] = {0, 0, 0, 0}, ln[4] = {1, 1, 1, 1}, st[4][4], wrap[4][4];
+  int64_t it = lo;
+#pragma unroll
+  for (int t = 3; t >= 0; --t) {
+    if (t < p.n_con) {
+      const int L = p.con_letter[t];
+      ln[t] = p.len[L];
+      const int64_t q = it / ln[t];
+      dig[t] = it - q * ln[t];
+      it = q;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      st[t][k] = (t < p.n_con && k < p.n_ops) ? p.ops[k].coef[p.con_letter[t]] : 0;
+      wrap[t][k] = st[t][k] * ln[t];
+      off[k] += st[t][k] * dig[t];
+    }
+  }
+  const T *ptr[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) ptr[k] = (const T *)p.ops[k < p.n_ops ? k : 0].ptr;
+  T acc = (T)0;
+  for (int64_t i = lo; i < hi; ++i) {
+    T prod = ptr[0][off[0]];
+#pragma unroll
+    for (int k = 1; k < 4; ++k)
+      if (k < p.n_ops) prod *= ptr[k][off[k]];
+    acc += prod;
+#pragma unroll
+    for (int t = 3; t >= 0; --t) {
+      if (t >= p.n_con) continue;
+      ++dig[t];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) off[k] += st[t][k];
+      if (dig[t] < ln[t]) break;
+      dig[t] = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) off[k] -= wrap[t][k];
+    }
+  }
+  return acc;
+}
+
+// iterations [lo, hi) of lane v of nv: contiguous chunks
+__device__ __forceinline__ void chunk_of(int64_t total, int v, int nv, int64_t &lo, int64_t &hi) {
+  const int64_t c = (total + nv - 1) / nv;
+  lo = min(total, (int64_t)v * c);
+  hi = min(total, lo + c);
+}
+
 // One output, evaluated the same way by every kernel that uses the row:
 //   mode 0: one thread, iterations in order;
 //   mode 1: one warp, lane l takes iterations l, l+32, ..., then a fixed
@@ -150,22 +221,40 @@ __device__ T contract(const GParams &p, int64_t o, int64_t first, int64_t stride
 //           fixed tree over the 256 partials in shared memory.
 // Modes 1 and 2 must be called by the whole warp / CTA; the result is valid
 // in lane 0 / thread 0.
+// (rows with GParams::fast give each lane or virtual lane a contiguous
+// chunk of the iterations instead of every 32nd / 256th one; the chunks are
+// fixed, so the result is still deterministic)
 template <typename T>
 __device__ __forceinline__ T out_thread(const GParams &p, int64_t o) {
-  return contract<T>(p, o, 0, 1);
+  return p.fast ? contract_fast<T>(p, o, 0, p.total_con) : contract<T>(p, o, 0, 1);
 }
 
 template <typename T>
 __device__ __forceinline__ T out_warp(const GParams &p, int64_t o) {
   const int lane = threadIdx.x & 31;
-  T v = contract<T>(p, o, lane, 32);
+  T v;
+  if (p.fast) {
+    int64_t lo, hi;
+    chunk_of(p.total_con, lane, 32, lo, hi);
+    v = contract_fast<T>(p, o, lo, hi);
+  } else {
+    v = contract<T>(p, o, lane, 32);
+  }
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   return v;
 }
 
 template <typename T>
 __device__ __forceinline__ T out_block(const GParams &p, int64_t o, double *red) {
-  for (int v = threadIdx.x; v < 256; v += blockDim.x) red[v] = (double)contract<T>(p, o, v, 256);
+  for (int v = threadIdx.x; v < 256; v += blockDim.x) {
+    if (p.fast) {
+      int64_t lo, hi;
+      chunk_of(p.total_con, v, 256, lo, hi);
+      red[v] = (double)contract_fast<T>(p, o, lo, hi);
+    } else {
+      red[v] = (double)contract<T>(p, o, v, 256);
+    }
+  }
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     for (int v = threadIdx.x; v < w; v += blockDim.x) red[v] = (double)((T)red[v] + (T)red[v + w]);

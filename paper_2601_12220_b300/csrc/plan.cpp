@@ -203,6 +203,10 @@ int plan_generic_row(const Einsum &e, int row, const std::vector<BufIn> &bufs, c
     op.prog_len = n_ins - op.prog_begin;
     op.dtype = arg.dtype;
   }
+  // the running-offset evaluator: plain views of the output's dtype only
+  p.fast = p.n_ops <= 4 && p.n_con <= 4 && p.total_con < ((int64_t)1 << 31);
+  for (int j = 0; j < p.n_ops; ++j)
+    if (p.ops[j].kind != 0 || p.ops[j].dtype != p.out_dtype) p.fast = 0;
   return OK;
 }
 
