@@ -318,3 +318,38 @@ def test_lookup_transfer_same_bits():
     got2, _ = run(text2, arrs, ctx=ctx)
     for x in range(3):
         assert np.array_equal(got[x], got2[2 - x])
+
+
+GEN = be.make_config(be.STRAT_GENERIC)
+
+
+@pytest.mark.parametrize("text_fmt,shapes", [
+    # mode 0 (contraction < 64), one and two contracted letters
+    ("ij,j->i", {"A": (70, 9), "B": (9,)}),
+    ("ijk,jk->i", {"A": (50, 3, 5), "B": (3, 5)}),
+    # mode 1 (warp per output), ragged chunks (1000 = 32 * 31 + 8)
+    ("ik,kj->ij", {"A": (33, 1000), "B": (1000, 17)}),
+    # mode 2 (CTA per output), four contracted letters
+    ("iabcd,abcd->i", {"A": (5, 9, 10, 11, 23), "B": (9, 10, 11, 23)}),
+    # four operands, no contracted letter; and an empty contraction
+    ("ij,ij,i,j->ij", {"A": (40, 30), "B": (40, 30), "C": (40,), "D": (30,)}),
+    ("ik,kj->ij", {"A": (6, 0), "B": (0, 7)}),
+])
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_generic_running_offsets(text_fmt, shapes, dt):
+    """Rows of plain views take the generic evaluator's running-offset path in
+    all three modes; results match the oracle (FP32 within its gamma bound)."""
+    g = np.random.default_rng(len(text_fmt) + 7)
+    names = list(shapes)
+    arrs = {n: g.standard_normal(sh).astype(np.float32 if dt == "f32" else np.float64) for n, sh in shapes.items()}
+    decl = " ; ".join(f"{n}:{dt}[{','.join(str(d) for d in sh)}]" for n, sh in shapes.items())
+    text = f"{text_fmt} | {','.join(names)} ; {decl}"
+    got, e = run(text, arrs, cfg=GEN)
+    ref, S = ev.evaluate(text, arrs)[0]
+    ins, out = text_fmt.split("->")
+    lens = {c: d for op, n in zip(ins.split(","), names) for c, d in zip(op, shapes[n])}
+    K = int(np.prod([lens[c] for c in lens if c not in out])) if any(c not in out for c in lens) else 1
+    u = 2.0 ** -24
+    tol = 1e-12 if dt == "f64" else max(K * u / (1 - K * u), 1e-6)    # gamma_K for FP32 accumulation
+    assert got[0].shape == ref.shape
+    assert np.all(np.abs(got[0] - ref) <= tol * S)
