@@ -163,7 +163,7 @@ __device__ T contract_fast(const GParams &p, int64_t o, int64_t lo, int64_t hi) 
       if (k < p.n_ops) off[k] += p.ops[k].coef[L] * v;
   }
   // contracted letters: digit, length and per-operand step (innermost last)
-  int64_t dig[4] = {0, 0, 0, 0}, ln[4] = {1, 1, 1, 1}, st[4][4], wrap[4][4];
+  int64_t dig[4] = {0, 0, 0, 0}, ln[4] = {1, 1, 1, 1}, st[4][4];
   int64_t it = lo;
 #pragma unroll
   for (int t = 3; t >= 0; --t) {
@@ -177,7 +177,6 @@ __device__ T contract_fast(const GParams &p, int64_t o, int64_t lo, int64_t hi) 
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       st[t][k] = (t < p.n_con && k < p.n_ops) ? p.ops[k].coef[p.con_letter[t]] : 0;
-      wrap[t][k] = st[t][k] * ln[t];
       off[k] += st[t][k] * dig[t];
     }
   }
@@ -200,7 +199,7 @@ __device__ T contract_fast(const GParams &p, int64_t o, int64_t lo, int64_t hi) 
       if (dig[t] < ln[t]) break;
       dig[t] = 0;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) off[k] -= wrap[t][k];
+      for (int k = 0; k < 4; ++k) off[k] -= st[t][k] * ln[t];
     }
   }
   return acc;

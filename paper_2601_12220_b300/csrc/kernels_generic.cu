@@ -10,7 +10,7 @@ namespace be {
 
 namespace {
 
-__global__ void __launch_bounds__(256) generic_kernel(const __grid_constant__ GParams p) {
+__global__ void __launch_bounds__(256, 3) generic_kernel(const __grid_constant__ GParams p) {
   __shared__ double red[256];
   // outputs per CTA per step: a thread, a warp or the whole CTA per output
   const int64_t per = p.mode == 0 ? blockDim.x : (p.mode == 1 ? (blockDim.x >> 5) : 1);
