@@ -393,8 +393,10 @@ __global__ void __launch_bounds__(256) split_rows(const double *__restrict__ A, 
   const int64_t m = blockIdx.x;
   const double *row = A + m * lda;
   const bool vec = ska == 1 && ((uintptr_t)row & 15) == 0 && (K & 1) == 0 && (Kp & 1) == 0;
-  // |x| compared as integers on the sign-cleared bit pattern (no FP64 pipe work)
-  unsigned long long bits = 0;
+  // |x| compared as integers on the sign-cleared high word (32-bit: a 64-bit
+  // integer max issues on the FP64 pipe); the scale needs only the largest
+  // exponent, which the high word carries
+  uint32_t bits = 0;
   if (m < M) {
     if (vec) {
       const double2 *r2 = (const double2 *)row;
@@ -406,21 +408,23 @@ __global__ void __launch_bounds__(256) split_rows(const double *__restrict__ A, 
         for (int u = 0; u < 4; ++u) v[u] = r2[k + u * blockDim.x];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          bits = max(bits, (unsigned long long)__double_as_longlong(affine<AFF>(v[u].x, alpha, beta)) & 0x7fffffffffffffffull);
-          bits = max(bits, (unsigned long long)__double_as_longlong(affine<AFF>(v[u].y, alpha, beta)) & 0x7fffffffffffffffull);
+          bits = max(bits, (uint32_t)__double2hiint(affine<AFF>(v[u].x, alpha, beta)) & 0x7fffffffu);
+          bits = max(bits, (uint32_t)__double2hiint(affine<AFF>(v[u].y, alpha, beta)) & 0x7fffffffu);
         }
       }
       for (; k < K2; k += blockDim.x) {
         const double2 v = r2[k];
-        bits = max(bits, (unsigned long long)__double_as_longlong(affine<AFF>(v.x, alpha, beta)) & 0x7fffffffffffffffull);
-        bits = max(bits, (unsigned long long)__double_as_longlong(affine<AFF>(v.y, alpha, beta)) & 0x7fffffffffffffffull);
+        bits = max(bits, (uint32_t)__double2hiint(affine<AFF>(v.x, alpha, beta)) & 0x7fffffffu);
+        bits = max(bits, (uint32_t)__double2hiint(affine<AFF>(v.y, alpha, beta)) & 0x7fffffffu);
       }
     } else {
       for (int64_t k = threadIdx.x; k < K; k += blockDim.x)
-        bits = max(bits, (unsigned long long)__double_as_longlong(affine<AFF>(row[k * ska], alpha, beta)) & 0x7fffffffffffffffull);
+        bits = max(bits, (uint32_t)__double2hiint(affine<AFF>(row[k * ska], alpha, beta)) & 0x7fffffffu);
     }
   }
-  double mx = block_max(__longlong_as_double((long long)bits), red);
+  // the row maximum rounded down to its high word (same exponent, hence the
+  // same power-of-two scale)
+  double mx = block_max(__hiloint2double((int)bits, 0), red);
   const int s = scale_for(mx);
   // the scaled row max is below 2^14; FP32 scaling is exact while |x| >= 2^-100 * max
   const bool fp32_ok = mx == 0.0 || (mx > 0x1p-26 && mx < 0x1p+100 && s > -120 && s < 120);
@@ -464,7 +468,8 @@ __global__ void __launch_bounds__(256) split_rows(const double *__restrict__ A, 
   }
 }
 
-// per-column max |B| of B (K x N), B[k*ldb + n*snb]; K split over blockIdx.y,
+// per-column max |B| of B (K x N), B[k*ldb + n*snb], rounded down to its high
+// word (the scale needs only the exponent); K split over blockIdx.y,
 // combined with an integer max on the (non-negative) double bit patterns
 template <bool AFF>
 __global__ void __launch_bounds__(256) col_max(const double *__restrict__ B, int64_t K, int64_t N, int64_t ldb,
@@ -474,11 +479,10 @@ __global__ void __launch_bounds__(256) col_max(const double *__restrict__ B, int
   if (n >= N) return;
   const int64_t kper = (K + gridDim.y - 1) / gridDim.y;
   const int64_t k0 = (int64_t)blockIdx.y * kper, k1 = min(K, k0 + kper);
-  unsigned long long bits = 0;
+  uint32_t bits = 0;
   for (int64_t k = k0; k < k1; ++k)
-    bits = max(bits, (unsigned long long)__double_as_longlong(affine<AFF>(B[k * ldb + n * snb], alpha, beta)) &
-                         0x7fffffffffffffffull);
-  atomicMax(&bmax[n], bits);
+    bits = max(bits, (uint32_t)__double2hiint(affine<AFF>(B[k * ldb + n * snb], alpha, beta)) & 0x7fffffffu);
+  atomicMax(&bmax[n], (unsigned long long)bits << 32);
 }
 
 // B (K x N) -> transposed TF32 hi/lo [Np x Kp] (K-major), zero-padded;
