@@ -162,22 +162,35 @@ __device__ T contract_fast(const GParams &p, int64_t o, int64_t lo, int64_t hi) 
     for (int k = 0; k < 4; ++k)
       if (k < p.n_ops) off[k] += p.ops[k].coef[L] * v;
   }
-  // contracted letters: digit, length and per-operand step (innermost last)
-  int64_t dig[4] = {0, 0, 0, 0}, ln[4] = {1, 1, 1, 1}, st[4][4];
+  // the innermost contracted letter in scalars, its steps in registers; the
+  // outer letters' steps are read from the row on a carry
+  int64_t din = 0, lin = 1, s_in[4] = {0, 0, 0, 0};
+  int64_t dig[3] = {0, 0, 0}, ln[3] = {1, 1, 1};
+  int cl[3] = {0, 0, 0};
   int64_t it = lo;
+  if (p.n_con > 0) {
+    const int L = p.con_letter[p.n_con - 1];
+    lin = p.len[L];
+    const int64_t q = it / lin;
+    din = it - q * lin;
+    it = q;
 #pragma unroll
-  for (int t = 3; t >= 0; --t) {
-    if (t < p.n_con) {
-      const int L = p.con_letter[t];
-      ln[t] = p.len[L];
+    for (int k = 0; k < 4; ++k) {
+      s_in[k] = k < p.n_ops ? p.ops[k].coef[L] : 0;
+      off[k] += s_in[k] * din;
+    }
+  }
+#pragma unroll
+  for (int t = 2; t >= 0; --t) {
+    if (t < p.n_con - 1) {
+      cl[t] = p.con_letter[t];
+      ln[t] = p.len[cl[t]];
       const int64_t q = it / ln[t];
       dig[t] = it - q * ln[t];
       it = q;
-    }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      st[t][k] = (t < p.n_con && k < p.n_ops) ? p.ops[k].coef[p.con_letter[t]] : 0;
-      off[k] += st[t][k] * dig[t];
+      for (int k = 0; k < 4; ++k)
+        if (k < p.n_ops) off[k] += p.ops[k].coef[cl[t]] * dig[t];
     }
   }
   const T *ptr[4];
@@ -190,16 +203,26 @@ __device__ T contract_fast(const GParams &p, int64_t o, int64_t lo, int64_t hi) 
     for (int k = 1; k < 4; ++k)
       if (k < p.n_ops) prod *= ptr[k][off[k]];
     acc += prod;
+    if (p.n_con == 0) continue;
+    ++din;
 #pragma unroll
-    for (int t = 3; t >= 0; --t) {
-      if (t >= p.n_con) continue;
+    for (int k = 0; k < 4; ++k) off[k] += s_in[k];
+    if (din < lin) continue;
+    din = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) off[k] -= s_in[k] * lin;
+#pragma unroll
+    for (int t = 2; t >= 0; --t) {
+      if (t >= p.n_con - 1) continue;
       ++dig[t];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) off[k] += st[t][k];
+      for (int k = 0; k < 4; ++k)
+        if (k < p.n_ops) off[k] += p.ops[k].coef[cl[t]];
       if (dig[t] < ln[t]) break;
       dig[t] = 0;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) off[k] -= st[t][k] * ln[t];
+      for (int k = 0; k < 4; ++k)
+        if (k < p.n_ops) off[k] -= p.ops[k].coef[cl[t]] * ln[t];
     }
   }
   return acc;
