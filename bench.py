@@ -811,14 +811,33 @@ def run_serving(args):
         srv.submit(p)
     srv.drain(60.0)
     srv.reset_stats()
-    with Clocks(local) as clk:
+
+    def serve(arr, pk):
         t0 = time.perf_counter()
-        for t, k in zip(arrivals, pick):
+        for t, k in zip(arr, pk):
             while time.perf_counter() - t0 < t:
                 pass
             srv.submit(prepared[k])
+        submitted = time.perf_counter() - t0
         srv.drain(300.0)
+        return submitted
+
+    with Clocks(local) as clk:
+        serve(arrivals, pick)
     st = srv.stats()
+    # arrival-rate sweep: the same template mix at each offered rate, to
+    # the rate where throughput stops following the offer (saturation)
+    sweep = []
+    for r in (float(x) for x in args.serve_sweep.split(",") if x.strip()):
+        arr = W.poisson_arrivals(r, args.serve_sweep_seconds, seed_offset=3)
+        pk = W.rng(5, 4).integers(0, len(templates), size=len(arr))
+        srv.reset_stats()
+        sub = serve(arr, pk)
+        s2 = srv.stats()
+        sweep.append({"offered_per_s": r, "submitted_per_s": len(arr) / max(sub, 1e-9),
+                      "einsums_per_s": s2["throughput"], "latency_p50_ms": s2["p50_s"] * 1e3,
+                      "latency_p99_ms": s2["p99_s"] * 1e3, "completed": s2["completed"],
+                      "failed": s2["failed"], "max_inflight": s2["max_inflight"]})
     # one launch per einsum, same sequence: measured service times, FIFO replay
     service = np.zeros(len(templates))
     for k, (e, bufs, outs) in enumerate(templates):
@@ -861,6 +880,8 @@ def run_serving(args):
                                       "latency_p50_ms": float(lat[len(lat) // 2]) * 1e3,
                                       "latency_p99_ms": float(lat[int(0.99 * (len(lat) - 1))]) * 1e3},
             "clocks": clk.summary(), "gpu_launches": launches}
+    if sweep:
+        line["rate_sweep"] = sweep
     srv.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -886,6 +907,9 @@ def main():
     ap.add_argument("--rows", type=int, default=1, help="einsums b of dg_divergence / face_mass")
     ap.add_argument("--stacked-elements", type=int, default=100000)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
+    ap.add_argument("--serve-sweep", default="",
+                    help="comma-separated offered rates (requests/s) served after the main run, e.g. 5000,20000,80000")
+    ap.add_argument("--serve-sweep-seconds", type=float, default=3.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-templates", type=int, default=256)
     ap.add_argument("--serve-streams", type=int, default=8)

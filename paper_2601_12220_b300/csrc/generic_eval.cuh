@@ -143,89 +143,99 @@ __device__ T contract(const GParams &p, int64_t o, int64_t first, int64_t stride
 }
 
 // Sum of the terms of output o over the contiguous iterations [lo, hi) for a
-// row whose operands are all plain views of type T (GParams::fast): the
-// offset of each operand is kept running -- the output letters give its
-// base, and the contracted odometer adds the letter's coefficient on each
-// step and takes len * coefficient off when the letter wraps -- so a term
-// costs a typed load per operand and a few integer adds.  Iterations run in
-// the same order as contract() with stride 1.
-template <typename T>
-__device__ T contract_fast(const GParams &p, int64_t o, int64_t lo, int64_t hi) {
-  if (lo >= hi) return (T)0;
-  int64_t off[4] = {0, 0, 0, 0};
+// row whose operands are all plain views of type T (GParams::fast), with
+// NOPS operands.  The output letters give each operand's base; the
+// iterations then run as runs of the innermost contracted letter: a run is
+// a tight loop of typed loads at a 32-bit stride and one multiply-add per
+// term, and the outer letters advance (an odometer) between runs, adding a
+// letter's coefficient on each step and taking len * coefficient off when
+// it wraps.  GParams::fast guarantees that the contraction count and every
+// in-operand offset fit in 32 bits.  Iterations run in the same order as
+// contract() with stride 1.
+template <typename T, int NOPS>
+__device__ T contract_runs(const GParams &p, int64_t o, int lo, int hi) {
+  const T *q[NOPS];
+#pragma unroll
+  for (int k = 0; k < NOPS; ++k) q[k] = (const T *)p.ops[k].ptr;
   int64_t rem = o;
   for (int d = p.n_out - 1; d >= 0; --d) {
     const int L = p.out_letter[d];
-    const int64_t q = rem / p.len[L], v = rem - q * p.len[L];
-    rem = q;
+    const int64_t t = rem / p.len[L], v = rem - t * p.len[L];
+    rem = t;
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (k < p.n_ops) off[k] += p.ops[k].coef[L] * v;
+    for (int k = 0; k < NOPS; ++k) q[k] += p.ops[k].coef[L] * v;
   }
-  // the innermost contracted letter in scalars, its steps in registers; the
-  // outer letters' steps are read from the row on a carry
-  int64_t din = 0, lin = 1, s_in[4] = {0, 0, 0, 0};
-  int64_t dig[3] = {0, 0, 0}, ln[3] = {1, 1, 1};
-  int cl[3] = {0, 0, 0};
-  int64_t it = lo;
+  // innermost contracted letter: digit din of lin, stride s[k]; outer
+  // letters cl[t]: digit dig[t] of ln[t]
+  int din = 0, lin = 1, s[NOPS];
+  int dig[3] = {0, 0, 0}, ln[3] = {1, 1, 1}, cl[3] = {0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < NOPS; ++k) s[k] = 0;
+  int it = lo;
   if (p.n_con > 0) {
     const int L = p.con_letter[p.n_con - 1];
-    lin = p.len[L];
-    const int64_t q = it / lin;
-    din = it - q * lin;
-    it = q;
+    lin = (int)p.len[L];
+    din = it % lin;
+    it /= lin;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      s_in[k] = k < p.n_ops ? p.ops[k].coef[L] : 0;
-      off[k] += s_in[k] * din;
+    for (int k = 0; k < NOPS; ++k) {
+      s[k] = (int)p.ops[k].coef[L];
+      q[k] += (int64_t)s[k] * din;
     }
   }
 #pragma unroll
   for (int t = 2; t >= 0; --t) {
     if (t < p.n_con - 1) {
       cl[t] = p.con_letter[t];
-      ln[t] = p.len[cl[t]];
-      const int64_t q = it / ln[t];
-      dig[t] = it - q * ln[t];
-      it = q;
+      ln[t] = (int)p.len[cl[t]];
+      dig[t] = it % ln[t];
+      it /= ln[t];
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (k < p.n_ops) off[k] += p.ops[k].coef[cl[t]] * dig[t];
+      for (int k = 0; k < NOPS; ++k) q[k] += p.ops[k].coef[cl[t]] * dig[t];
     }
   }
-  const T *ptr[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) ptr[k] = (const T *)p.ops[k < p.n_ops ? k : 0].ptr;
   T acc = (T)0;
-  for (int64_t i = lo; i < hi; ++i) {
-    T prod = ptr[0][off[0]];
+  int i = lo;
+  while (i < hi) {
+    const int n = min(lin - din, hi - i);
+#pragma unroll 4
+    for (int c = 0; c < n; ++c) {
+      T prod = q[0][c * s[0]];
 #pragma unroll
-    for (int k = 1; k < 4; ++k)
-      if (k < p.n_ops) prod *= ptr[k][off[k]];
-    acc += prod;
-    if (p.n_con == 0) continue;
-    ++din;
+      for (int k = 1; k < NOPS; ++k) prod *= q[k][c * s[k]];
+      acc += prod;
+    }
+    i += n;
+    if (i >= hi) break;
+    // the innermost letter wrapped (the run started at digit din): back to
+    // its digit 0, carry outward
 #pragma unroll
-    for (int k = 0; k < 4; ++k) off[k] += s_in[k];
-    if (din < lin) continue;
+    for (int k = 0; k < NOPS; ++k) q[k] -= (int64_t)s[k] * din;
     din = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) off[k] -= s_in[k] * lin;
 #pragma unroll
     for (int t = 2; t >= 0; --t) {
       if (t >= p.n_con - 1) continue;
       ++dig[t];
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (k < p.n_ops) off[k] += p.ops[k].coef[cl[t]];
+      for (int k = 0; k < NOPS; ++k) q[k] += p.ops[k].coef[cl[t]];
       if (dig[t] < ln[t]) break;
       dig[t] = 0;
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (k < p.n_ops) off[k] -= p.ops[k].coef[cl[t]] * ln[t];
+      for (int k = 0; k < NOPS; ++k) q[k] -= p.ops[k].coef[cl[t]] * ln[t];
     }
   }
   return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ T contract_fast(const GParams &p, int64_t o, int64_t lo, int64_t hi) {
+  if (lo >= hi) return (T)0;
+  switch (p.n_ops) {
+    case 1: return contract_runs<T, 1>(p, o, (int)lo, (int)hi);
+    case 2: return contract_runs<T, 2>(p, o, (int)lo, (int)hi);
+    case 3: return contract_runs<T, 3>(p, o, (int)lo, (int)hi);
+    default: return contract_runs<T, 4>(p, o, (int)lo, (int)hi);
+  }
 }
 
 // iterations [lo, hi) of lane v of nv: contiguous chunks

@@ -8,6 +8,7 @@
 // elementwise producers run inside the operand loads (Def. "Functional
 // Batched Einstein Summation"; the fused listing of the Feinsum section).
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 #include "plan.hpp"
@@ -142,7 +143,10 @@ int plan_generic_row(const Einsum &e, int row, const std::vector<BufIn> &bufs, c
     }
   p.out = out.ptr;
   p.out_dtype = e.out_dtype;
-  p.mode = p.total_con < 64 ? 0 : (p.total_con < 16384 ? 1 : 2);
+  // a thread per output for short contractions, a warp for medium ones and
+  // a CTA for long ones, or for medium ones with too few outputs to fill the
+  // GPU with warps (each virtual lane still takes at least 8 terms)
+  p.mode = p.total_con < 64 ? 0 : ((p.total_con >= 16384 || (p.total_con >= 2048 && p.total_out < 1024)) ? 2 : 1);
   for (size_t k = 0; k < scalars.size(); ++k) p.scalars[k] = scalars[k];
   int n_ins = 0;
   for (int j = 0; j < e.n; ++j) {
@@ -204,9 +208,14 @@ int plan_generic_row(const Einsum &e, int row, const std::vector<BufIn> &bufs, c
     op.dtype = arg.dtype;
   }
   // the running-offset evaluator: plain views of the output's dtype only
-  p.fast = p.n_ops <= 4 && p.n_con <= 4 && p.total_con < ((int64_t)1 << 31);
-  for (int j = 0; j < p.n_ops; ++j)
+  // (the contraction count and each operand's largest offset fit in 32 bits)
+  p.fast = p.n_ops >= 1 && p.n_ops <= 4 && p.n_con <= 4 && p.total_con < ((int64_t)1 << 31);
+  for (int j = 0; j < p.n_ops; ++j) {
     if (p.ops[j].kind != 0 || p.ops[j].dtype != p.out_dtype) p.fast = 0;
+    int64_t span = 0;
+    for (int L = 0; L < p.n_letters; ++L) span += std::abs(p.ops[j].coef[L]) * std::max<int64_t>(0, p.len[L] - 1);
+    if (span >= ((int64_t)1 << 31)) p.fast = 0;
+  }
   return OK;
 }
 

@@ -6,12 +6,17 @@
 // arrival order as long as the bytes pinned by requests in flight (their
 // declared buffers and outputs) stay within the HBM budget, and launches each
 // admitted request at once on one of several streams, so requests that
-// arrive while others run overlap with them on the device.  A host callback
-// queued behind each request's kernels stamps its completion time, releases
-// its budget and wakes the worker, which then admits what was waiting.
+// arrive while others run overlap with them on the device.  An event is
+// recorded behind each request's kernels; a completion thread polls the
+// oldest event of every stream (events of one stream complete in order),
+// stamps the completion time, releases the budget and wakes the worker,
+// which then admits what was waiting.  Events do not hold the stream the
+// way a host callback does, so a stream's next request starts as soon as
+// the previous one's kernels finish.
 // The configuration of each request comes from the tuning database under its
 // normal form (Alg. 1 + lookup), memoized by the request's text.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -45,8 +50,11 @@ struct be_server {
   int64_t inflight = 0, max_inflight = 0;
   std::vector<cudaStream_t> streams;
   size_t next_stream = 0;
+  std::vector<std::deque<std::pair<ServeReq *, cudaEvent_t>>> running;   // per stream, launch order
+  std::vector<cudaEvent_t> free_events;
+  std::atomic<uint64_t> launched{0};   // requests handed to the completion thread
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
+  std::condition_variable cv_work, cv_done, cv_reap;
   std::deque<ServeReq *> pending;
   std::unordered_map<int64_t, std::unique_ptr<ServeReq>> reqs;
   int64_t next_id = 1;
@@ -56,7 +64,7 @@ struct be_server {
   std::unordered_map<std::string, be_config> cfg_memo;
   std::unordered_map<std::string, bool> cfg_have;
   bool stop = false;
-  std::thread worker;
+  std::thread worker, reaper;
 };
 
 struct ServeReq {
@@ -72,20 +80,70 @@ struct ServeReq {
   int status = BE_OK;
 };
 
-static void CUDART_CB on_done(void *arg) {
-  ServeReq *r = (ServeReq *)arg;
-  be_server *s = r->srv;
-  const double t = now_s();
-  std::lock_guard<std::mutex> g(s->mu);
+// completion of a running request (the server's lock held)
+static void finish(be_server *s, ServeReq *r, double t, int status) {
   r->t_done = t;
   r->state = 2;
+  r->status = status;
   s->inflight_bytes -= r->bytes;
   s->inflight -= 1;
-  s->latencies.push_back(t - r->t_submit);
-  s->completed += 1;
-  s->last_done = std::max(s->last_done, t);
-  s->cv_work.notify_one();
-  s->cv_done.notify_all();
+  if (status == BE_OK) {
+    s->latencies.push_back(t - r->t_submit);
+    s->completed += 1;
+    s->last_done = std::max(s->last_done, t);
+  } else {
+    s->failed += 1;
+  }
+}
+
+// Completion thread: snapshots the oldest running request of each stream,
+// then queries their events without the lock until one has finished or the
+// worker has launched more, and retires every finished head under the
+// lock.  While requests are in flight it spins (yielding) and falls back to
+// short sleeps after a while without progress; with nothing in flight it
+// waits for the worker.
+static void reaper_loop(be_server *s) {
+  cudaSetDevice(s->device);
+  using Head = std::pair<ServeReq *, cudaEvent_t>;
+  std::vector<Head> heads(s->streams.size());
+  std::vector<cudaError_t> res(s->streams.size());
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (true) {
+    bool any = false;
+    for (size_t k = 0; k < heads.size(); ++k) {
+      heads[k] = s->running[k].empty() ? Head{nullptr, nullptr} : s->running[k].front();
+      any |= heads[k].first != nullptr;
+    }
+    if (!any) {
+      if (s->stop && s->pending.empty() && s->inflight == 0) break;
+      s->cv_reap.wait(lk);
+      continue;
+    }
+    const uint64_t seen = s->launched.load(std::memory_order_relaxed);
+    lk.unlock();
+    int idle = 0;
+    bool progress = false;
+    while (true) {
+      for (size_t k = 0; k < heads.size(); ++k) {
+        res[k] = heads[k].first ? cudaEventQuery(heads[k].second) : cudaErrorNotReady;
+        progress |= res[k] != cudaErrorNotReady;
+      }
+      if (progress || s->launched.load(std::memory_order_relaxed) != seen) break;
+      if (++idle < 4096) std::this_thread::yield();
+      else std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    const double t = now_s();
+    lk.lock();
+    if (!progress) continue;
+    for (size_t k = 0; k < heads.size(); ++k) {
+      if (res[k] == cudaErrorNotReady) continue;
+      s->running[k].pop_front();
+      s->free_events.push_back(heads[k].second);
+      finish(s, heads[k].first, t, res[k] == cudaSuccess ? BE_OK : BE_ECUDA);
+    }
+    s->cv_work.notify_one();
+    s->cv_done.notify_all();
+  }
 }
 
 static void worker_loop(be_server *s) {
@@ -128,8 +186,16 @@ static void worker_loop(be_server *s) {
         if (have) s->cfg_memo[r->e->e.text] = cfg;
       }
       // the dense split strategy shares its context's workspace: keep it on one stream
-      cudaStream_t st = s->streams[s->precision == BE_PREC_SPLIT ? 0 : s->next_stream];
+      const size_t si = s->precision == BE_PREC_SPLIT ? 0 : s->next_stream;
+      cudaStream_t st = s->streams[si];
       s->next_stream = (s->next_stream + 1) % s->streams.size();
+      cudaEvent_t ev = nullptr;
+      if (!s->free_events.empty()) {
+        ev = s->free_events.back();
+        s->free_events.pop_back();
+      } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        ev = nullptr;
+      }
       r->t_admit = now_s();
       r->state = 1;
       s->inflight_bytes += r->bytes;
@@ -140,17 +206,16 @@ static void worker_loop(be_server *s) {
       int rc = be::execute_internal(s->x, r->e, have ? &cfg : nullptr, s->precision, r->bufs.data(),
                                     (int32_t)r->bufs.size(), r->outs.data(), (int32_t)r->outs.size(),
                                     r->scalars.data(), (int32_t)r->scalars.size(), st);
-      if (rc == BE_OK && cudaLaunchHostFunc(st, on_done, r) == cudaSuccess) {
+      if (rc == BE_OK && ev && cudaEventRecord(ev, st) == cudaSuccess) {
         lk.lock();
+        s->running[si].emplace_back(r, ev);
+        s->launched.fetch_add(1, std::memory_order_relaxed);
+        s->cv_reap.notify_one();
         continue;
       }
       lk.lock();
-      r->status = rc ? rc : BE_ECUDA;
-      r->state = 2;
-      r->t_done = now_s();
-      s->inflight_bytes -= r->bytes;
-      s->inflight -= 1;
-      s->failed += 1;
+      if (ev) s->free_events.push_back(ev);
+      finish(s, r, now_s(), rc ? rc : BE_ECUDA);
       s->cv_done.notify_all();
     }
     if (s->stop && s->pending.empty() && s->inflight == 0) break;
@@ -188,8 +253,10 @@ int be_server_create(be_ctx *x, int32_t precision, int32_t n_streams, size_t hbm
     }
     s->streams.push_back(st);
   }
+  s->running.resize(s->streams.size());
   be_server *raw = s.get();
   raw->worker = std::thread(worker_loop, raw);
+  raw->reaper = std::thread(reaper_loop, raw);
   *out = s.release();
   return BE_OK;
 }
@@ -286,12 +353,19 @@ void be_server_destroy(be_server *s) {
     std::lock_guard<std::mutex> g(s->mu);
     s->stop = true;
     s->cv_work.notify_one();
+    s->cv_reap.notify_one();
   }
   s->worker.join();
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->cv_reap.notify_one();
+  }
+  s->reaper.join();
   for (auto st : s->streams) {
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
   }
+  for (auto ev : s->free_events) cudaEventDestroy(ev);
   delete s;
 }
 

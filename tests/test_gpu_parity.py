@@ -331,6 +331,12 @@ GEN = be.make_config(be.STRAT_GENERIC)
     ("ik,kj->ij", {"A": (33, 1000), "B": (1000, 17)}),
     # mode 2 (CTA per output), four contracted letters
     ("iabcd,abcd->i", {"A": (5, 9, 10, 11, 23), "B": (9, 10, 11, 23)}),
+    # a medium contraction: a CTA per output when there are few outputs (15),
+    # a warp per output when there are many (1088)
+    ("ik,kj->ij", {"A": (3, 3001), "B": (3001, 5)}),
+    ("ik,kj->ij", {"A": (34, 2500), "B": (2500, 32)}),
+    # three operands, the innermost contracted letter shorter than a chunk
+    ("ab,bc,cd->ad", {"A": (7, 300), "B": (300, 9), "C": (9, 6)}),
     # four operands, no contracted letter; and an empty contraction
     ("ij,ij,i,j->ij", {"A": (40, 30), "B": (40, 30), "C": (40,), "D": (30,)}),
     ("ik,kj->ij", {"A": (6, 0), "B": (0, 7)}),
