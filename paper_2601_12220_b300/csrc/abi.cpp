@@ -892,6 +892,14 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
       b->rows.push_back(p);
       // outputs per tile so that each tile costs about cost_target operand terms
       const double per_out = (double)std::max<int64_t>(1, p.total_con) * std::max(1, p.n_ops);
+      if (p.mode == 3) {   // units are GEMM tiles of tile x tile outputs
+        const double per_tile = per_out * p.gemm.tile * p.gemm.tile;
+        const int64_t tile = std::max<int64_t>(1, std::min<int64_t>((int64_t)(cost_target / per_tile), 65536));
+        for (int64_t s0 = 0; s0 < p.gemm.tiles; s0 += tile)
+          b->tiles.push_back(PTile{row, 0, s0, std::min(tile, p.gemm.tiles - s0)});
+        b->terms += per_out * (double)p.total_out;
+        continue;
+      }
       int64_t tile = (int64_t)(cost_target / per_out);
       if (p.mode == 0) {
         tile = std::max<int64_t>(32, std::min<int64_t>(tile, 65536));
@@ -908,7 +916,8 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
   std::vector<double> cost(b->tiles.size());
   for (size_t t = 0; t < b->tiles.size(); ++t) {
     const GParams &p = b->rows[b->tiles[t].row];
-    cost[t] = (double)b->tiles[t].count * (double)std::max<int64_t>(1, p.total_con) * std::max(1, p.n_ops);
+    cost[t] = (double)b->tiles[t].count * (double)std::max<int64_t>(1, p.total_con) * std::max(1, p.n_ops) *
+              (p.mode == 3 ? (double)p.gemm.tile * p.gemm.tile : 1.0);
   }
   std::vector<size_t> order(b->tiles.size());
   for (size_t t = 0; t < order.size(); ++t) order[t] = t;

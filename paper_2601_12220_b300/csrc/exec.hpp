@@ -36,6 +36,36 @@ struct GOp {
   int64_t coef[GMAXL];
 };
 
+// Tiled form of a two-operand row (mode 3): C[b, m, n] = sum_k A[b, m, k] B[b, k, n]
+// over a GEMM view of the letters -- M: output letters only A's offset
+// depends on, N: output letters only B's offset depends on, batch: output
+// letters both depend on, K: every contracted letter.  Each list runs
+// outermost first; a CTA computes a tile x tile block of one batch value.
+// Every output sums its terms in increasing k, whatever the tile, so the
+// launcher may pick the side: large tiles reuse staged operands more, small
+// ones give more CTAs (FP64, whose pipe is the bound, wants many).
+#define GT_MAX 64
+#define GT_K 16
+
+struct GGemm {
+  int32_t nm, nn, nk, nb;           // letters per role
+  int32_t m[GMAXL], n[GMAXL], k[GMAXL], b[GMAXL];
+  int64_t M, N, K, B;               // extents
+  int64_t tiles_m, tiles_n, tiles;  // tiles per batch value along M, N; all tiles
+  int64_t out_coef[GMAXL];          // dense output offset per letter
+  int32_t a_kmajor, b_kmajor;       // consecutive threads load along K (else along M / N)
+  int32_t tile;                     // 32 or 64 outputs per side
+  int32_t pad;
+};
+
+// tile side (16, 32 or 64; 64 for FP32 only) and the tile counts it gives
+inline void set_gemm_tile(GGemm &g, int tile) {
+  g.tile = tile;
+  g.tiles_m = (g.M + tile - 1) / tile;
+  g.tiles_n = (g.N + tile - 1) / tile;
+  g.tiles = g.B * g.tiles_m * g.tiles_n;
+}
+
 struct alignas(16) GParams {
   int32_t n_ops, n_letters, n_out, n_con;
   int64_t len[GMAXL];
@@ -44,9 +74,10 @@ struct alignas(16) GParams {
   int64_t total_out, total_con;
   void *out;
   int32_t out_dtype;
-  int32_t mode;         // 0 thread, 1 warp, 2 CTA per output (by contraction length)
+  int32_t mode;         // 0 thread, 1 warp, 2 CTA per output (by contraction length), 3 GEMM tiles
   int32_t fast;         // 1: <= 4 operands, all views of the output's dtype, <= 4 contracted letters
-  int32_t pad_fast;
+  int32_t n_hoist;      // fast rows: the last n_hoist operands do not depend on a contracted letter
+  GGemm gemm;           // mode 3 only
   double scalars[8];
   GOp ops[GMAXOPS];
   GIns ins[GMAXINS];

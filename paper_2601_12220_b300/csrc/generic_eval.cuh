@@ -227,15 +227,35 @@ __device__ T contract_runs(const GParams &p, int64_t o, int lo, int hi) {
   return acc;
 }
 
+// acc times the hoisted operands (GParams::n_hoist, constant over the sum) at output o
+template <typename T>
+__device__ __forceinline__ T times_hoisted(const GParams &p, int64_t o, T acc) {
+  for (int k = p.n_ops - p.n_hoist; k < p.n_ops; ++k) {
+    int64_t off = 0, rem = o;
+    for (int d = p.n_out - 1; d >= 0; --d) {
+      const int L = p.out_letter[d];
+      const int64_t t = rem / p.len[L];
+      off += p.ops[k].coef[L] * (rem - t * p.len[L]);
+      rem = t;
+    }
+    acc *= ((const T *)p.ops[k].ptr)[off];
+  }
+  return acc;
+}
+
+// The sum over [lo, hi) of the operands that move with the contraction,
+// times the hoisted operands.
 template <typename T>
 __device__ __forceinline__ T contract_fast(const GParams &p, int64_t o, int64_t lo, int64_t hi) {
   if (lo >= hi) return (T)0;
-  switch (p.n_ops) {
-    case 1: return contract_runs<T, 1>(p, o, (int)lo, (int)hi);
-    case 2: return contract_runs<T, 2>(p, o, (int)lo, (int)hi);
-    case 3: return contract_runs<T, 3>(p, o, (int)lo, (int)hi);
-    default: return contract_runs<T, 4>(p, o, (int)lo, (int)hi);
+  T acc;
+  switch (p.n_ops - p.n_hoist) {
+    case 1: acc = contract_runs<T, 1>(p, o, (int)lo, (int)hi); break;
+    case 2: acc = contract_runs<T, 2>(p, o, (int)lo, (int)hi); break;
+    case 3: acc = contract_runs<T, 3>(p, o, (int)lo, (int)hi); break;
+    default: acc = contract_runs<T, 4>(p, o, (int)lo, (int)hi); break;
   }
+  return times_hoisted<T>(p, o, acc);
 }
 
 // iterations [lo, hi) of lane v of nv: contiguous chunks
@@ -297,10 +317,166 @@ __device__ __forceinline__ T out_block(const GParams &p, int64_t o, double *red)
   return r;
 }
 
-// every output of [start, start + count) of row p, by the row's mode
-__device__ __forceinline__ void eval_range(const GParams &p, int64_t start, int64_t count, double *red) {
+// Mode 3: one TM x TM tile of the GEMM view (GGemm) of a two-operand row.
+// Per K-slice of 16, the CTA stages A[m, k] and B[k, n] in shared memory
+// (loaded along the role in which the operand is contiguous), with the
+// offsets of the slice's m, n and k values computed once from the letters'
+// digits; each of the 16 x 16 threads then accumulates an R x R block of
+// outputs (R = TM / 16), every output summing its terms in increasing k (so
+// the result does not depend on which kernel runs the tile).  Must be called
+// by the whole CTA.
+constexpr int GEMM_SMEM = 2 * GT_K * (GT_MAX + 2) * 8 + (4 * GT_MAX + 2 * GT_K) * 8;
+
+template <typename T, int TM>
+__device__ void gemm_tile(const GParams &p, int64_t tile, unsigned char *sm) {
+  constexpr int R = TM / 16;                        // outputs per thread along each side
+  constexpr int S = TM + 16 / (int)sizeof(T);       // padded row of a staged slice
+  constexpr int PER = TM * GT_K / 256;              // staged values per thread and operand
+  const GGemm &g = p.gemm;
+  if (tile >= g.tiles) return;                      // uniform over the CTA
+  T *As = (T *)sm;                                  // [GT_K][S]
+  T *Bs = As + GT_K * S;                            // [GT_K][S]
+  int64_t *offAm = (int64_t *)(sm + 2 * GT_K * (GT_MAX + 2) * 8);
+  int64_t *offCm = offAm + GT_MAX, *offBn = offCm + GT_MAX, *offCn = offBn + GT_MAX;
+  int64_t *offAk = offCn + GT_MAX, *offBk = offAk + GT_K;
+  const int tid = threadIdx.x;
+  const int64_t *ca = p.ops[0].coef, *cb = p.ops[1].coef;
+  int64_t r = tile;
+  const int64_t nt = r % g.tiles_n;
+  r /= g.tiles_n;
+  const int64_t mt = r % g.tiles_m;
+  r /= g.tiles_m;
+  int64_t baseA = 0, baseB = 0, baseC = 0;
+  for (int d = g.nb - 1; d >= 0; --d) {
+    const int L = g.b[d];
+    const int64_t v = r % p.len[L];
+    r /= p.len[L];
+    baseA += ca[L] * v;
+    baseB += cb[L] * v;
+    baseC += g.out_coef[L] * v;
+  }
+  const int64_t m0 = mt * TM, n0 = nt * TM;
+  const int vm = (int)min((int64_t)TM, g.M - m0), vn = (int)min((int64_t)TM, g.N - n0);
+  if (tid < TM) {
+    int64_t x = m0 + tid, oa = 0, oc = 0;
+    if (tid < vm)
+      for (int d = g.nm - 1; d >= 0; --d) {
+        const int L = g.m[d];
+        const int64_t v = x % p.len[L];
+        x /= p.len[L];
+        oa += ca[L] * v;
+        oc += g.out_coef[L] * v;
+      }
+    offAm[tid] = oa;
+    offCm[tid] = oc;
+  } else if (tid >= 64 && tid < 64 + TM) {
+    const int t = tid - 64;
+    int64_t x = n0 + t, ob = 0, oc = 0;
+    if (t < vn)
+      for (int d = g.nn - 1; d >= 0; --d) {
+        const int L = g.n[d];
+        const int64_t v = x % p.len[L];
+        x /= p.len[L];
+        ob += cb[L] * v;
+        oc += g.out_coef[L] * v;
+      }
+    offBn[t] = ob;
+    offCn[t] = oc;
+  }
+  const T *A = (const T *)p.ops[0].ptr + baseA, *B = (const T *)p.ops[1].ptr + baseB;
+  const int tm = tid >> 4, tn = tid & 15;
+  // threads whose whole block lies outside the tile skip the arithmetic
+  const bool active = tm * R < vm && tn * R < vn;
+  T acc[R][R];
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int j = 0; j < R; ++j) acc[i][j] = (T)0;
+  for (int64_t k0 = 0; k0 < g.K; k0 += GT_K) {
+    const int vk = (int)min((int64_t)GT_K, g.K - k0);
+    __syncthreads();   // the previous slice is consumed; the m / n tables are written
+    if (tid >= 128 && tid < 128 + GT_K) {
+      const int t = tid - 128;
+      int64_t x = k0 + t, oa = 0, ob = 0;
+      if (t < vk)
+        for (int d = g.nk - 1; d >= 0; --d) {
+          const int L = g.k[d];
+          const int64_t v = x % p.len[L];
+          x /= p.len[L];
+          oa += ca[L] * v;
+          ob += cb[L] * v;
+        }
+      offAk[t] = oa;
+      offBk[t] = ob;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + 256 * q;
+      const int kk = g.a_kmajor ? e % GT_K : e / TM, mm = g.a_kmajor ? e / GT_K : e % TM;
+      As[kk * S + mm] = (kk < vk && mm < vm) ? A[offAm[mm] + offAk[kk]] : (T)0;
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + 256 * q;
+      const int kk = g.b_kmajor ? e % GT_K : e / TM, nn = g.b_kmajor ? e / GT_K : e % TM;
+      Bs[kk * S + nn] = (kk < vk && nn < vn) ? B[offBn[nn] + offBk[kk]] : (T)0;
+    }
+    __syncthreads();
+    if (!active) continue;
+    for (int kk = 0; kk < vk; ++kk) {
+      T a[R], b[R];
+      if constexpr (sizeof(T) * R >= 16) {          // 16-byte loads (the rows are 16-byte aligned)
+#pragma unroll
+        for (int i = 0; i < R; i += 16 / (int)sizeof(T)) {
+          const float4 av = *(const float4 *)&As[kk * S + tm * R + i], bv = *(const float4 *)&Bs[kk * S + tn * R + i];
+          memcpy(a + i, &av, 16);
+          memcpy(b + i, &bv, 16);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          a[i] = As[kk * S + tm * R + i];
+          b[i] = Bs[kk * S + tn * R + i];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < R; ++j) acc[i][j] += a[i] * b[j];
+    }
+  }
+  T *C = (T *)p.out + baseC;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int m = tm * R + i;
+    if (m >= vm) continue;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int n = tn * R + j;
+      if (n < vn) C[offCm[m] + offCn[n]] = acc[i][j];
+    }
+  }
+  __syncthreads();   // the tables and slices are free for the next tile
+}
+
+// every output of [start, start + count) of row p, by the row's mode (GEMM
+// tiles [start, start + count) in mode 3)
+__device__ __forceinline__ void eval_range(const GParams &p, int64_t start, int64_t count, double *red,
+                                           unsigned char *gsm) {
   const int64_t end = start + count;
-  if (p.mode == 0) {
+  if (p.mode == 3) {   // [start, end) are GEMM tiles
+    for (int64_t t = start; t < end; ++t) {
+      if (p.out_dtype == F64) {
+        if (p.gemm.tile == 16) gemm_tile<double, 16>(p, t, gsm);
+        else gemm_tile<double, 32>(p, t, gsm);
+      } else {
+        if (p.gemm.tile == 16) gemm_tile<float, 16>(p, t, gsm);
+        else if (p.gemm.tile == 32) gemm_tile<float, 32>(p, t, gsm);
+        else gemm_tile<float, 64>(p, t, gsm);
+      }
+    }
+  } else if (p.mode == 0) {
     for (int64_t o = start + threadIdx.x; o < end; o += blockDim.x) {
       if (p.out_dtype == F64) ((double *)p.out)[o] = out_thread<double>(p, o);
       else ((float *)p.out)[o] = out_thread<float>(p, o);

@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(256, 3) persistent_kernel(const GParams *__res
                                                          unsigned long long *__restrict__ counter) {
   __shared__ GParams sp;
   __shared__ double red[256];
+  __shared__ __align__(16) unsigned char gsm[gen::GEMM_SMEM];
   __shared__ long long tile_id;
   __shared__ int cur_row;
   if (threadIdx.x == 0) cur_row = -1;
@@ -38,7 +39,7 @@ __global__ void __launch_bounds__(256, 3) persistent_kernel(const GParams *__res
     }
     __syncthreads();
     if (threadIdx.x == 0) cur_row = tl.row;
-    gen::eval_range(sp, tl.start, tl.count, red);
+    gen::eval_range(sp, tl.start, tl.count, red, gsm);
     __syncthreads();   // tile consumed before tile_id and sp are rewritten
   }
 }

@@ -114,6 +114,78 @@ int check_buffers(const Einsum &e, const std::vector<BufIn> &bufs, const std::ve
 
 // ------------------------------------------------------------ generic
 
+// Operands of a fast row that no contracted letter moves are constant over
+// the whole sum: they go last (n_hoist of them) and multiply the sum once
+// instead of every term (one multiply per term fewer for each).
+static void hoist_invariants(GParams &p) {
+  if (!p.fast || p.n_ops < 3 || p.n_con == 0) return;
+  auto invariant = [&](const GOp &op) {
+    for (int c = 0; c < p.n_con; ++c) {
+      const int L = p.con_letter[c];
+      if (p.len[L] > 1 && op.coef[L] != 0) return false;
+    }
+    return true;
+  };
+  GOp run[4], inv[4];
+  int nr = 0, ni = 0;
+  for (int k = 0; k < p.n_ops; ++k) (invariant(p.ops[k]) ? inv[ni++] : run[nr++]) = p.ops[k];
+  if (nr == 0 || ni == 0) return;
+  for (int k = 0; k < nr; ++k) p.ops[k] = run[k];
+  for (int k = 0; k < ni; ++k) p.ops[nr + k] = inv[k];
+  p.n_hoist = ni;
+}
+
+// Mode 3: the GEMM view of a fast two-operand row whose M, N and K extents
+// are all large enough to fill its tiles.  Letters within a role run
+// outermost first, ordered by decreasing stride, so the fastest-varying
+// letter of each role has the smallest stride; each operand is then loaded
+// along the role (K or M / N) in which it is contiguous.
+static void plan_gemm_view(GParams &p) {
+  if (!p.fast || p.n_ops != 2) return;
+  GGemm g{};
+  const int64_t *ca = p.ops[0].coef, *cb = p.ops[1].coef;
+  int64_t oc = 1;
+  for (int d = p.n_out - 1; d >= 0; --d) {
+    g.out_coef[p.out_letter[d]] = oc;
+    oc *= p.len[p.out_letter[d]];
+  }
+  std::vector<int> M, N, K, Bt;
+  for (int d = 0; d < p.n_out; ++d) {
+    const int L = p.out_letter[d];
+    if (cb[L] == 0) M.push_back(L);
+    else if (ca[L] == 0) N.push_back(L);
+    else Bt.push_back(L);
+  }
+  for (int c = 0; c < p.n_con; ++c) K.push_back(p.con_letter[c]);
+  auto ext = [&](const std::vector<int> &v) {
+    int64_t n = 1;
+    for (int L : v) n *= p.len[L];
+    return n;
+  };
+  g.M = ext(M), g.N = ext(N), g.K = ext(K), g.B = ext(Bt);
+  if (g.M < 32 || g.N < 32 || g.K < 8) return;
+  auto by = [&](std::vector<int> &v, auto key) {
+    std::stable_sort(v.begin(), v.end(), [&](int x, int y) { return key(x) > key(y); });
+  };
+  by(M, [&](int L) { return std::abs(ca[L]); });
+  by(N, [&](int L) { return std::abs(cb[L]); });
+  by(K, [&](int L) { return std::abs(ca[L]) + std::abs(cb[L]); });
+  g.nm = (int)M.size(), g.nn = (int)N.size(), g.nk = (int)K.size(), g.nb = (int)Bt.size();
+  for (int q = 0; q < g.nm; ++q) g.m[q] = M[q];
+  for (int q = 0; q < g.nn; ++q) g.n[q] = N[q];
+  for (int q = 0; q < g.nk; ++q) g.k[q] = K[q];
+  for (int q = 0; q < g.nb; ++q) g.b[q] = Bt[q];
+  // the tile side is a launch choice (every output sums its terms in
+  // increasing k whatever the tile): 64 for FP32, 32 for FP64 by default
+  set_gemm_tile(g, p.out_dtype == F64 ? 32 : 64);
+  const int lk = K.back(), lm = M.back(), ln = N.back();
+  g.a_kmajor = std::abs(ca[lk]) < std::abs(ca[lm]);
+  g.b_kmajor = std::abs(cb[lk]) < std::abs(cb[ln]);
+  p.gemm = g;
+  p.mode = 3;
+}
+
+
 int plan_generic_row(const Einsum &e, int row, const std::vector<BufIn> &bufs, const BufIn &out,
                      const std::vector<double> &scalars, GParams &p, std::string &err) {
   std::memset(&p, 0, sizeof(p));
@@ -216,6 +288,8 @@ int plan_generic_row(const Einsum &e, int row, const std::vector<BufIn> &bufs, c
     for (int L = 0; L < p.n_letters; ++L) span += std::abs(p.ops[j].coef[L]) * std::max<int64_t>(0, p.len[L] - 1);
     if (span >= ((int64_t)1 << 31)) p.fast = 0;
   }
+  hoist_invariants(p);
+  plan_gemm_view(p);
   return OK;
 }
 

@@ -122,3 +122,29 @@ def test_empty_batch_and_empty_rows():
     b.run()
     torch.cuda.synchronize()
     assert b.info()["tiles"] == 0
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_gemm_tiles_same_bits_at_any_tile_side(dt):
+    """Two-operand rows run as GEMM tiles.  The persistent executor uses the
+    default side (32 for FP64, 64 for FP32) while a lone launch of a small
+    row picks a smaller one to fill the SMs; every output still sums its
+    terms in increasing k, so the bits agree."""
+    g = np.random.default_rng(3)
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    specs = [("ik,kj->ij", (70, 33), (33, 90)), ("ki,kj->ij", (40, 64), (40, 33)),
+             ("ijcd,cdab->ijab", (5, 9, 6, 7), (6, 7, 8, 5)), ("ik,kj->ij", (600, 40), (40, 700))]
+    items = []
+    for text, sa, sb in specs:
+        spec = f"{text} | A,B ; A:{dt}[{','.join(map(str, sa))}] ; B:{dt}[{','.join(map(str, sb))}]"
+        e = be.Einsum(spec)
+        bufs = {"A": torch.from_numpy(g.standard_normal(sa)).to(tdt).to(DEV),
+                "B": torch.from_numpy(g.standard_normal(sb)).to(tdt).to(DEV)}
+        items.append((e, bufs, [torch.full(e.out_shape, float("nan"), dtype=tdt, device=DEV)]))
+    ctx = be.Context(None, device=0)
+    be.Batch(ctx, items).run()
+    torch.cuda.synchronize()
+    for e, bufs, outs in items:
+        alone = generic_alone(e, bufs)
+        torch.cuda.synchronize()
+        assert torch.equal(outs[0], alone[0])

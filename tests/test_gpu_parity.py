@@ -337,6 +337,17 @@ GEN = be.make_config(be.STRAT_GENERIC)
     ("ik,kj->ij", {"A": (34, 2500), "B": (2500, 32)}),
     # three operands, the innermost contracted letter shorter than a chunk
     ("ab,bc,cd->ad", {"A": (7, 300), "B": (300, 9), "C": (9, 6)}),
+    # lanes sharing the runs of the innermost letter: a warp over 5 runs of
+    # 160; 8 CTA groups of 32 lanes over 12 runs of 300; 2 groups of 128
+    # lanes over 2 runs of 1100 (ragged last passes)
+    ("ijk,jk->i", {"A": (1100, 5, 160), "B": (5, 160)}),
+    ("ijk,jk->i", {"A": (10, 12, 300), "B": (12, 300)}),
+    ("ijk,jk->i", {"A": (6, 2, 1100), "B": (2, 1100)}),
+    # operands no contracted letter moves multiply the sum once (hoisted):
+    # one, two, and the third of Fig. 1's operands
+    ("ij,j,i->i", {"A": (45, 700), "B": (700,), "C": (45,)}),
+    ("ij,i,j,i->i", {"A": (20, 90), "B": (20,), "C": (90,), "D": (20,)}),
+    ("mnj,mni,kli->ijkl", {"A": (9, 11, 5), "B": (9, 11, 6), "C": (4, 3, 6)}),
     # four operands, no contracted letter; and an empty contraction
     ("ij,ij,i,j->ij", {"A": (40, 30), "B": (40, 30), "C": (40,), "D": (30,)}),
     ("ik,kj->ij", {"A": (6, 0), "B": (0, 7)}),
@@ -359,3 +370,35 @@ def test_generic_running_offsets(text_fmt, shapes, dt):
     tol = 1e-12 if dt == "f64" else max(K * u / (1 - K * u), 1e-6)    # gamma_K for FP32 accumulation
     assert got[0].shape == ref.shape
     assert np.all(np.abs(got[0] - ref) <= tol * S)
+
+
+@pytest.mark.parametrize("text_fmt,shapes", [
+    # ragged M, N and K (K = 33: slices of 16, 16 and 1)
+    ("ik,kj->ij", {"A": (70, 33), "B": (33, 90)}),
+    # the first operand holds the output's second letter
+    ("kj,ik->ij", {"A": (20, 48), "B": (65, 20)}),
+    # several letters per role, K-major and N-major loads
+    ("ijcd,cdab->ijab", {"A": (5, 9, 6, 7), "B": (6, 7, 8, 5)}),
+    ("ki,kj->ij", {"A": (40, 64), "B": (40, 33)}),
+    ("ik,jk->ij", {"A": (100, 24), "B": (37, 24)}),
+    # a batch letter in both operands and the output
+    ("bik,bkj->bij", {"A": (3, 40, 20), "B": (3, 20, 50)}),
+    # a contracted letter only one operand has
+    ("ikl,kj->ij", {"A": (33, 9, 4), "B": (9, 40)}),
+])
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_generic_gemm_tiles(text_fmt, shapes, dt):
+    """Two-operand rows with large enough M, N and K run as 64 x 64 GEMM
+    tiles staged in shared memory; each output sums its terms in increasing
+    k, so the oracle bound is gamma_K (FP32) or 1e-12 (FP64)."""
+    g = np.random.default_rng(len(text_fmt) + 11)
+    names = list(shapes)
+    arrs = {n: g.standard_normal(sh).astype(np.float32 if dt == "f32" else np.float64) for n, sh in shapes.items()}
+    decl = " ; ".join(f"{n}:{dt}[{','.join(str(d) for d in sh)}]" for n, sh in shapes.items())
+    text = f"{text_fmt} | {','.join(names)} ; {decl}"
+    got, e = run(text, arrs, cfg=GEN)
+    ref, S = ev.evaluate(text, arrs)[0]
+    ins, out = text_fmt.split("->")
+    lens = {c: d for op, n in zip(ins.split(","), names) for c, d in zip(op, shapes[n])}
+    K = int(np.prod([lens[c] for c in lens if c not in out]))
+    assert_close(got[0], ref, S, 1e-12 if dt == "f64" else max(gamma(K), 1e-6))
