@@ -77,6 +77,9 @@ struct alignas(16) GParams {
   int32_t mode;         // 0 thread, 1 warp, 2 CTA per output (by contraction length), 3 GEMM tiles
   int32_t fast;         // 1: <= 4 operands, all views of the output's dtype, <= 4 contracted letters
   int32_t n_hoist;      // fast rows: the last n_hoist operands do not depend on a contracted letter
+  int32_t n_inv;        // fast rows, modes 0-2: the n_inv operands before those do not depend on
+                        // the innermost contracted letter
+  int32_t pad_inv;
   GGemm gemm;           // mode 3 only
   double scalars[8];
   GOp ops[GMAXOPS];

@@ -144,7 +144,9 @@ __device__ T contract(const GParams &p, int64_t o, int64_t first, int64_t stride
 
 // Sum of the terms of output o over the contiguous iterations [lo, hi) for a
 // row whose operands are all plain views of type T (GParams::fast), with
-// NOPS operands.  The output letters give each operand's base; the
+// NV operands that move along the innermost contracted letter followed by NI
+// that do not (GParams::n_inv): within a run the NV operands' products are
+// summed and the run's sum is multiplied once by the NI operands' product.  The output letters give each operand's base; the
 // iterations then run as runs of the innermost contracted letter: a run is
 // a tight loop of typed loads at a 32-bit stride and one multiply-add per
 // term, and the outer letters advance (an odometer) between runs, adding a
@@ -152,8 +154,9 @@ __device__ T contract(const GParams &p, int64_t o, int64_t first, int64_t stride
 // it wraps.  GParams::fast guarantees that the contraction count and every
 // in-operand offset fit in 32 bits.  Iterations run in the same order as
 // contract() with stride 1.
-template <typename T, int NOPS>
+template <typename T, int NV, int NI>
 __device__ T contract_runs(const GParams &p, int64_t o, int lo, int hi) {
+  constexpr int NOPS = NV + NI;
   const T *q[NOPS];
 #pragma unroll
   for (int k = 0; k < NOPS; ++k) q[k] = (const T *)p.ops[k].ptr;
@@ -198,12 +201,27 @@ __device__ T contract_runs(const GParams &p, int64_t o, int lo, int hi) {
   int i = lo;
   while (i < hi) {
     const int n = min(lin - din, hi - i);
+    if constexpr (NI == 0) {
 #pragma unroll 4
-    for (int c = 0; c < n; ++c) {
-      T prod = q[0][c * s[0]];
+      for (int c = 0; c < n; ++c) {
+        T prod = q[0][c * s[0]];
 #pragma unroll
-      for (int k = 1; k < NOPS; ++k) prod *= q[k][c * s[k]];
-      acc += prod;
+        for (int k = 1; k < NV; ++k) prod *= q[k][c * s[k]];
+        acc += prod;
+      }
+    } else {
+      T run = (T)0;
+#pragma unroll 4
+      for (int c = 0; c < n; ++c) {
+        T prod = q[0][c * s[0]];
+#pragma unroll
+        for (int k = 1; k < NV; ++k) prod *= q[k][c * s[k]];
+        run += prod;
+      }
+      T inv = q[NV][0];
+#pragma unroll
+      for (int k = NV + 1; k < NOPS; ++k) inv *= q[k][0];
+      acc += inv * run;
     }
     i += n;
     if (i >= hi) break;
@@ -249,11 +267,18 @@ template <typename T>
 __device__ __forceinline__ T contract_fast(const GParams &p, int64_t o, int64_t lo, int64_t hi) {
   if (lo >= hi) return (T)0;
   T acc;
-  switch (p.n_ops - p.n_hoist) {
-    case 1: acc = contract_runs<T, 1>(p, o, (int)lo, (int)hi); break;
-    case 2: acc = contract_runs<T, 2>(p, o, (int)lo, (int)hi); break;
-    case 3: acc = contract_runs<T, 3>(p, o, (int)lo, (int)hi); break;
-    default: acc = contract_runs<T, 4>(p, o, (int)lo, (int)hi); break;
+  const int l = (int)lo, h = (int)hi;
+  switch ((p.n_ops - p.n_hoist) * 4 + p.n_inv) {   // (run operands, of them constant within a run)
+    case 4: acc = contract_runs<T, 1, 0>(p, o, l, h); break;
+    case 8: acc = contract_runs<T, 2, 0>(p, o, l, h); break;
+    case 9: acc = contract_runs<T, 1, 1>(p, o, l, h); break;
+    case 12: acc = contract_runs<T, 3, 0>(p, o, l, h); break;
+    case 13: acc = contract_runs<T, 2, 1>(p, o, l, h); break;
+    case 14: acc = contract_runs<T, 1, 2>(p, o, l, h); break;
+    case 17: acc = contract_runs<T, 3, 1>(p, o, l, h); break;
+    case 18: acc = contract_runs<T, 2, 2>(p, o, l, h); break;
+    case 19: acc = contract_runs<T, 1, 3>(p, o, l, h); break;
+    default: acc = contract_runs<T, 4, 0>(p, o, l, h); break;
   }
   return times_hoisted<T>(p, o, acc);
 }

@@ -135,6 +135,25 @@ static void hoist_invariants(GParams &p) {
   p.n_hoist = ni;
 }
 
+// Of the operands left in the sum of a fast row (modes 0-2), those that the
+// innermost contracted letter does not move are constant within each run of
+// it: they go after the others (n_inv of them) and multiply each run's sum
+// once instead of every term (rows with at least three such operands).
+static void split_run_invariants(GParams &p) {
+  if (!p.fast || p.mode == 3 || p.n_con == 0) return;
+  const int L = p.con_letter[p.n_con - 1];
+  if (p.len[L] < 2) return;
+  const int nr = p.n_ops - p.n_hoist;
+  if (nr < 3) return;   // with two operands a term costs one multiply-add either way
+  GOp var[4], inv[4];
+  int nv = 0, ni = 0;
+  for (int k = 0; k < nr; ++k) (p.ops[k].coef[L] == 0 ? inv[ni++] : var[nv++]) = p.ops[k];
+  if (nv == 0 || ni == 0) return;
+  for (int k = 0; k < nv; ++k) p.ops[k] = var[k];
+  for (int k = 0; k < ni; ++k) p.ops[nv + k] = inv[k];
+  p.n_inv = ni;
+}
+
 // Mode 3: the GEMM view of a fast two-operand row whose M, N and K extents
 // are all large enough to fill its tiles.  Letters within a role run
 // outermost first, ordered by decreasing stride, so the fastest-varying
@@ -290,6 +309,7 @@ int plan_generic_row(const Einsum &e, int row, const std::vector<BufIn> &bufs, c
   }
   hoist_invariants(p);
   plan_gemm_view(p);
+  split_run_invariants(p);
   return OK;
 }
 

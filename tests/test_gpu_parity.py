@@ -343,6 +343,13 @@ GEN = be.make_config(be.STRAT_GENERIC)
     ("ijk,jk->i", {"A": (1100, 5, 160), "B": (5, 160)}),
     ("ijk,jk->i", {"A": (10, 12, 300), "B": (12, 300)}),
     ("ijk,jk->i", {"A": (6, 2, 1100), "B": (2, 1100)}),
+    # operands the innermost contracted letter does not move multiply each
+    # run's sum once: one (triple product), two (the isomorphism example),
+    # none with two operands, and two beside a fully hoisted one
+    ("ik,kl,lj->ij", {"A": (9, 40), "B": (40, 70), "C": (70, 11)}),
+    ("ijk,ik,ij,ij->i", {"A": (30, 40, 50), "B": (30, 50), "C": (30, 40), "D": (30, 40)}),
+    ("ij,ik->i", {"A": (50, 60), "B": (50, 70)}),
+    ("il,j,k,i->i", {"A": (25, 33), "B": (7,), "C": (9,), "D": (25,)}),
     # operands no contracted letter moves multiply the sum once (hoisted):
     # one, two, and the third of Fig. 1's operands
     ("ij,j,i->i", {"A": (45, 700), "B": (700,), "C": (45,)}),
