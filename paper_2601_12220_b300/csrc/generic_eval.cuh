@@ -155,19 +155,11 @@ __device__ T contract(const GParams &p, int64_t o, int64_t first, int64_t stride
 // in-operand offset fit in 32 bits.  Iterations run in the same order as
 // contract() with stride 1.
 template <typename T, int NV, int NI>
-__device__ T contract_runs(const GParams &p, int64_t o, int lo, int hi) {
+__device__ T contract_runs(const GParams &p, const int64_t *base, int lo, int hi) {
   constexpr int NOPS = NV + NI;
   const T *q[NOPS];
 #pragma unroll
-  for (int k = 0; k < NOPS; ++k) q[k] = (const T *)p.ops[k].ptr;
-  int64_t rem = o;
-  for (int d = p.n_out - 1; d >= 0; --d) {
-    const int L = p.out_letter[d];
-    const int64_t t = rem / p.len[L], v = rem - t * p.len[L];
-    rem = t;
-#pragma unroll
-    for (int k = 0; k < NOPS; ++k) q[k] += p.ops[k].coef[L] * v;
-  }
+  for (int k = 0; k < NOPS; ++k) q[k] = (const T *)p.ops[k].ptr + base[k];
   // innermost contracted letter: digit din of lin, stride s[k]; outer
   // letters cl[t]: digit dig[t] of ln[t]
   int din = 0, lin = 1, s[NOPS];
@@ -245,47 +237,64 @@ __device__ T contract_runs(const GParams &p, int64_t o, int lo, int hi) {
   return acc;
 }
 
-// acc times the hoisted operands (GParams::n_hoist, constant over the sum) at output o
-template <typename T>
-__device__ __forceinline__ T times_hoisted(const GParams &p, int64_t o, T acc) {
-  for (int k = p.n_ops - p.n_hoist; k < p.n_ops; ++k) {
-    int64_t off = 0, rem = o;
+// Offsets of output o's element in each operand of a fast row (output
+// letters only), with 32-bit divisions when the output count fits.
+__device__ __forceinline__ void out_offsets(const GParams &p, int64_t o, int64_t off[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) off[k] = 0;
+  if (p.total_out < ((int64_t)1 << 31)) {
+    uint32_t rem = (uint32_t)o;
     for (int d = p.n_out - 1; d >= 0; --d) {
       const int L = p.out_letter[d];
-      const int64_t t = rem / p.len[L];
-      off += p.ops[k].coef[L] * (rem - t * p.len[L]);
+      const uint32_t n = (uint32_t)p.len[L], t = rem / n, v = rem - t * n;
       rem = t;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (k < p.n_ops) off[k] += p.ops[k].coef[L] * (int64_t)v;
     }
-    acc *= ((const T *)p.ops[k].ptr)[off];
+  } else {
+    int64_t rem = o;
+    for (int d = p.n_out - 1; d >= 0; --d) {
+      const int L = p.out_letter[d];
+      const int64_t t = rem / p.len[L], v = rem - t * p.len[L];
+      rem = t;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (k < p.n_ops) off[k] += p.ops[k].coef[L] * v;
+    }
   }
-  return acc;
 }
 
 // The sum over [lo, hi) of the operands that move with the contraction,
-// times the hoisted operands.
+// times the hoisted operands (GParams::n_hoist, constant over the sum).
 template <typename T>
 __device__ __forceinline__ T contract_fast(const GParams &p, int64_t o, int64_t lo, int64_t hi) {
   if (lo >= hi) return (T)0;
+  int64_t base[4];
+  out_offsets(p, o, base);
   T acc;
   const int l = (int)lo, h = (int)hi;
   switch ((p.n_ops - p.n_hoist) * 4 + p.n_inv) {   // (run operands, of them constant within a run)
-    case 4: acc = contract_runs<T, 1, 0>(p, o, l, h); break;
-    case 8: acc = contract_runs<T, 2, 0>(p, o, l, h); break;
-    case 9: acc = contract_runs<T, 1, 1>(p, o, l, h); break;
-    case 12: acc = contract_runs<T, 3, 0>(p, o, l, h); break;
-    case 13: acc = contract_runs<T, 2, 1>(p, o, l, h); break;
-    case 14: acc = contract_runs<T, 1, 2>(p, o, l, h); break;
-    case 17: acc = contract_runs<T, 3, 1>(p, o, l, h); break;
-    case 18: acc = contract_runs<T, 2, 2>(p, o, l, h); break;
-    case 19: acc = contract_runs<T, 1, 3>(p, o, l, h); break;
-    default: acc = contract_runs<T, 4, 0>(p, o, l, h); break;
+    case 4: acc = contract_runs<T, 1, 0>(p, base, l, h); break;
+    case 8: acc = contract_runs<T, 2, 0>(p, base, l, h); break;
+    case 9: acc = contract_runs<T, 1, 1>(p, base, l, h); break;
+    case 12: acc = contract_runs<T, 3, 0>(p, base, l, h); break;
+    case 13: acc = contract_runs<T, 2, 1>(p, base, l, h); break;
+    case 14: acc = contract_runs<T, 1, 2>(p, base, l, h); break;
+    case 17: acc = contract_runs<T, 3, 1>(p, base, l, h); break;
+    case 18: acc = contract_runs<T, 2, 2>(p, base, l, h); break;
+    case 19: acc = contract_runs<T, 1, 3>(p, base, l, h); break;
+    default: acc = contract_runs<T, 4, 0>(p, base, l, h); break;
   }
-  return times_hoisted<T>(p, o, acc);
+#pragma unroll
+  for (int k = 1; k < 4; ++k)
+    if (k >= p.n_ops - p.n_hoist && k < p.n_ops) acc *= ((const T *)p.ops[k].ptr)[base[k]];
+  return acc;
 }
 
-// iterations [lo, hi) of lane v of nv: contiguous chunks
+// iterations [lo, hi) of lane v of nv (32 or 256): contiguous chunks
 __device__ __forceinline__ void chunk_of(int64_t total, int v, int nv, int64_t &lo, int64_t &hi) {
-  const int64_t c = (total + nv - 1) / nv;
+  const int64_t c = nv == 32 ? (total + 31) >> 5 : (total + 255) >> 8;
   lo = min(total, (int64_t)v * c);
   hi = min(total, lo + c);
 }
