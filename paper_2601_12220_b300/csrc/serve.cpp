@@ -185,10 +185,20 @@ static void worker_loop(be_server *s) {
         s->cfg_have[r->e->e.text] = have;
         if (have) s->cfg_memo[r->e->e.text] = cfg;
       }
-      // the dense split strategy shares its context's workspace: keep it on one stream
-      const size_t si = s->precision == BE_PREC_SPLIT ? 0 : s->next_stream;
+      // the stream with the fewest requests in flight (from a rotating start,
+      // so ties spread); the dense split strategy shares its context's
+      // workspace: keep it on one stream
+      size_t si = 0;
+      if (s->precision != BE_PREC_SPLIT) {
+        const size_t ns = s->streams.size();
+        si = s->next_stream;
+        for (size_t j = 1; j < ns; ++j) {
+          const size_t c = (s->next_stream + j) % ns;
+          if (s->running[c].size() < s->running[si].size()) si = c;
+        }
+        s->next_stream = (si + 1) % ns;
+      }
       cudaStream_t st = s->streams[si];
-      s->next_stream = (s->next_stream + 1) % s->streams.size();
       cudaEvent_t ev = nullptr;
       if (!s->free_events.empty()) {
         ev = s->free_events.back();
