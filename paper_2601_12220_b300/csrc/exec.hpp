@@ -153,7 +153,10 @@ struct EParams {
 // element kernels: the operator, one producer group's operand tile (groups
 // are staged one after another) and every row's geometric factors
 inline size_t element_smem_words(const EParams &p) {
-  return (size_t)p.R * p.NI * p.NJ + (size_t)p.tile_e * p.NJ + (size_t)p.n_rows * p.tile_e * p.R;
+  // D, the produced operand of one tile, g per row, and in the stacked form
+  // the tile's A_x[e, s] when they do not depend on j (converted once)
+  const size_t stacked = p.NJ0 > 0 ? (size_t)p.tile_e * EM_MAXX * (p.NJ / p.NJ0) : 0;
+  return (size_t)p.R * p.NI * p.NJ + (size_t)p.tile_e * p.NJ + (size_t)p.n_rows * p.tile_e * p.R + stacked;
 }
 // budget for those words: 200 KB less the double-float kernel's sine table
 #define EM_SMEM_BUDGET (190 * 1024)

@@ -66,7 +66,8 @@ __global__ void __launch_bounds__(512, 2) element_df_kernel(const __grid_constan
   float2 *Ds = smf;                                   // [R][NI][NJ]
   float2 *Us = Ds + R * NI * NJ;                      // [TE][NJ], one producer group at a time
   float2 *Gs = Us + TE * NJ;                          // [rows][TE][R]
-  const int n_f2 = R * NI * NJ + TE * NJ + p.n_rows * TE * R;
+  float2 *Ac = Gs + p.n_rows * TE * R;                // stacked form: [TE][EM_MAXX][S]
+  const int n_f2 = (int)element_smem_words(p);
   float2 *sin_tab = smf + n_f2;                       // full-circle sine table
   const int tid = threadIdx.x, nt = blockDim.x;
   dfm::sin2_table_fill(sin_tab);
@@ -97,10 +98,62 @@ __global__ void __launch_bounds__(512, 2) element_df_kernel(const __grid_constan
     const int groups_e = (te + DF_EPT - 1) / DF_EPT;
     for (int g = 0; g < p.n_groups; ++g) {
       if (g > 0) __syncthreads();   // the previous group's operand consumed
-      for (int idx = tid; idx < te * NJ; idx += nt) {
-        const int el = idx / NJ, j = idx % NJ;
-        const df u = prod_df(p.groups[g], e0 + el, j, p.NJ0, sin_tab);
-        Us[el * NJ + j] = make_float2(u.hi, u.lo);
+      const EProd &q = p.groups[g];
+      bool a_no_j = q.kind == 3, b_no_s = q.kind == 3;
+      for (int x = 0; x < EM_MAXX; ++x)
+        if (x < q.X) {
+          a_no_j = a_no_j && q.A[x].sj == 0;
+          b_no_s = b_no_s && q.B[x].ss == 0;
+        }
+      if (a_no_j) {
+        // stacked form whose A_x[e, s] do not depend on j (the metric terms
+        // of the divergence, the face Jacobians of the face mass): each is
+        // converted once per tile; a thread then forms v[e, s, j] for every
+        // s of one (e, j), converting B_x[e, j] once when it does not depend
+        // on s.  The same df operations as prod_df, in the same order.
+        const int NJ0 = p.NJ0, S = NJ / NJ0;
+        for (int idx = tid; idx < te * q.X * S; idx += nt) {
+          const int el = idx / (q.X * S), rem = idx % (q.X * S), x = rem / S, sx = rem % S;
+          const double a = q.A[x].ptr[(e0 + el) * q.A[x].se + sx * q.A[x].ss];
+          const df d = dfm::df_fast_ok(a) ? dfm::df_from_double_fast(a) : dfm::df_from_double(a);
+          Ac[(el * EM_MAXX + x) * S + sx] = make_float2(d.hi, d.lo);
+        }
+        __syncthreads();
+        for (int idx = tid; idx < te * NJ0; idx += nt) {
+          const int el = idx / NJ0, j = idx % NJ0;
+          const int64_t e = e0 + el;
+          df bx[EM_MAXX];
+#pragma unroll
+          for (int x = 0; x < EM_MAXX; ++x) {
+            bx[x] = df{0.f, 0.f};
+            if (b_no_s && x < q.X) {
+              const double b = q.B[x].ptr[e * q.B[x].se + j * q.B[x].sj];
+              bx[x] = dfm::df_fast_ok(b) ? dfm::df_from_double_fast(b) : dfm::df_from_double(b);
+            }
+          }
+          for (int sx = 0; sx < S; ++sx) {
+            float sh = 0.f, sl = 0.f;
+#pragma unroll
+            for (int x = 0; x < EM_MAXX; ++x) {
+              if (x >= q.X) continue;
+              df b = bx[x];
+              if (!b_no_s) {
+                const double bv = q.B[x].ptr[e * q.B[x].se + sx * q.B[x].ss + j * q.B[x].sj];
+                b = dfm::df_fast_ok(bv) ? dfm::df_from_double_fast(bv) : dfm::df_from_double(bv);
+              }
+              const float2 a = Ac[(el * EM_MAXX + x) * S + sx];
+              dfm::dot_acc(sh, sl, df{a.x, a.y}, b);
+            }
+            const df v = dfm::two_sum(sh, sl);
+            Us[el * NJ + sx * NJ0 + j] = make_float2(v.hi, v.lo);
+          }
+        }
+      } else {
+        for (int idx = tid; idx < te * NJ; idx += nt) {
+          const int el = idx / NJ, j = idx % NJ;
+          const df u = prod_df(q, e0 + el, j, p.NJ0, sin_tab);
+          Us[el * NJ + j] = make_float2(u.hi, u.lo);
+        }
       }
       __syncthreads();
       for (int item = tid; item < groups_e * NI; item += nt) {
