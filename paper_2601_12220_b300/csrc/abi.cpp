@@ -528,7 +528,9 @@ static int do_execute(be_ctx *x, const be_einsum *hc, const be_config *cfg, int3
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * per_sm));
     if (ep.E > 0) {
       KernelMark km(x, BE_KERNEL_ELEMENT, s);
-      ce = variant == 1 ? launch_element(ep, grid, block, s) : launch_element_df(ep, grid, block, s);
+      if (variant == 1) ce = launch_element(ep, grid, block, s);
+      else if (element_df_small(ep) && c.tile[1] <= 0) ce = launch_element_df_small(ep, s);
+      else ce = launch_element_df(ep, grid, block, s);
     }
   } else {
     for (int i = 0; i < e.b && ce == cudaSuccess; ++i) {

@@ -152,7 +152,7 @@ struct EParams {
 // shared-memory doubles (or float pairs) of the FP64 and double-float
 // element kernels: the operator, one producer group's operand tile (groups
 // are staged one after another) and every row's geometric factors
-inline size_t element_smem_words(const EParams &p) {
+__host__ __device__ inline size_t element_smem_words(const EParams &p) {
   // D, the produced operand of one tile, g per row, and in the stacked form
   // the tile's A_x[e, s] when they do not depend on j (converted once)
   const size_t stacked = p.NJ0 > 0 ? (size_t)p.tile_e * EM_MAXX * (p.NJ / p.NJ0) : 0;
@@ -173,6 +173,9 @@ __host__ __device__ inline int64_t d_offset(const EParams &p, int r, int i, int 
 cudaError_t launch_element(const EParams &p, int grid, int block, cudaStream_t s);
 // same strategy in double-float arithmetic on the FP32 pipe (FP64 accuracy)
 cudaError_t launch_element_df(const EParams &p, int grid, int block, cudaStream_t s);
+// the double-float variant for small operators (NI, NJ <= 8, not stacked): one thread per element
+bool element_df_small(const EParams &p);
+cudaError_t launch_element_df_small(const EParams &p, cudaStream_t s);
 int element_df_block(const EParams &p);   // block size matching one tile's work items
 // same strategy with t = u D^T as a digit-split GEMM on the tcgen05 tensor
 // cores (FP64 accuracy); status receives BE_ETIMEOUT if a bounded wait expires

@@ -205,7 +205,88 @@ __global__ void __launch_bounds__(512, 2) element_df_kernel(const __grid_constan
   }
 }
 
+// Small operators (NI, NJ <= NB, R <= 4; e.g. the FEM action's 4 x 4 D):
+// one thread per (producer group, element) keeps u[e, :] and t[r, i] in
+// registers, so the streamed operands are read and the outputs written once,
+// coalesced across the warp, with no tile staging.  Entries beyond NI / NJ
+// are zero, which adds nothing to a compensated sum, so every output is the
+// same sequence of df operations as in element_df_kernel.
+template <int NB>
+__global__ void __launch_bounds__(256) element_df_small_kernel(const __grid_constant__ EParams p) {
+  __shared__ float2 Ds[EM_MAXR * NB * NB];   // [r][i][j]
+  __shared__ float2 sin_tab[dfm::SIN2_N];
+  const int R = p.R, NI = p.NI, NJ = p.NJ;
+  dfm::sin2_table_fill(sin_tab);
+  for (int idx = threadIdx.x; idx < EM_MAXR * NB * NB; idx += blockDim.x) {
+    const int r = idx / (NB * NB), i = (idx / NB) % NB, j = idx % NB;
+    df d{0.f, 0.f};
+    if (r < R && i < NI && j < NJ) d = dfm::df_from_double(p.D[d_offset(p, r, i, j)]);
+    Ds[idx] = make_float2(d.hi, d.lo);
+  }
+  __syncthreads();
+  const int64_t total = (int64_t)p.n_groups * p.E;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
+    const int g = (int)(w / p.E);
+    const int64_t e = w - (int64_t)g * p.E;
+    df u[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) u[j] = j < NJ ? prod_df(p.groups[g], e, j, 0, sin_tab) : df{0.f, 0.f};
+    df t[EM_MAXR][NB];
+#pragma unroll
+    for (int r = 0; r < EM_MAXR; ++r) {
+      if (r >= R) break;
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        float sh = 0.f, sl = 0.f;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          const float2 d = Ds[(r * NB + i) * NB + j];
+          dfm::dot_acc(sh, sl, df{d.x, d.y}, u[j]);
+        }
+        t[r][i] = dfm::fast_two_sum(sh, sl);
+      }
+    }
+    for (int k = 0; k < p.n_rows; ++k) {
+      if (p.rows[k].group != g) continue;
+      df gk[EM_MAXR];
+      if (p.has_g) {
+        const EView &v = p.rows[k].g;
+#pragma unroll
+        for (int r = 0; r < EM_MAXR; ++r)
+          if (r < R) gk[r] = dfm::df_from_double(v.ptr[e * v.se + r * v.sk]);
+      }
+      double *out = p.rows[k].out + e * NI;
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        if (i >= NI) break;
+        df acc = t[0][i];
+        if (p.has_g) {
+          float sh = 0.f, sl = 0.f;
+#pragma unroll
+          for (int r = 0; r < EM_MAXR; ++r)
+            if (r < R) dfm::dot_acc(sh, sl, gk[r], t[r][i]);
+          acc = dfm::fast_two_sum(sh, sl);
+        }
+        out[i] = dfm::df_to_double(acc);
+      }
+    }
+  }
+}
+
 }  // namespace
+
+bool element_df_small(const EParams &p) { return p.NJ0 == 0 && p.R <= EM_MAXR && p.NI <= 8 && p.NJ <= 8; }
+
+cudaError_t launch_element_df_small(const EParams &p, cudaStream_t s) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t blocks = ((int64_t)p.n_groups * p.E + 255) / 256;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sms * 8));
+  if (p.NI <= 4 && p.NJ <= 4) element_df_small_kernel<4><<<grid, 256, 0, s>>>(p);
+  else element_df_small_kernel<8><<<grid, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
 
 int element_df_block(const EParams &p) {
   const int items = (p.tile_e + DF_EPT - 1) / DF_EPT * p.NI;
