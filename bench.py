@@ -358,7 +358,8 @@ def run_fem(args):
     world, rank, local = dist_setup(args.gpus)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    E = 4096
+    E = args.fem_e
+    peaks = load_peaks()
     D, us = W.fem_action(E=E)
     host = {"D": D, **{f"u{k}": u for k, u in enumerate(us)}}
     bufs = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
@@ -418,9 +419,16 @@ def run_fem(args):
             "steps": steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"fem_action: b=4 'ij,ej->ei', D 4x4 shared, E={E}, U[-1,1]",
-                       "parallelism": f"replicas x{world}", "l2": "inputs in L2 (0.5 MB)"},
+                       "parallelism": f"replicas x{world}",
+                       "l2": f"inputs in L2 ({byts / 2**20:.1f} MB)" if byts < 100e6
+                       else f"inputs larger than L2 ({byts / 1e9:.2f} GB per step), no flush"},
             "einsums_per_s": world * 4e3 / ms, "gb_s": world * byts / (ms * 1e-3) / 1e9,
             "kernel_ms": t_k / max(1, n_k),
+            "roofline": {"kernel": "element kernel", "bound": "hbm",
+                         "achieved": byts / (t_k / max(1, n_k) * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": byts / (t_k / max(1, n_k) * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                         "peak_source": peaks["source"],
+                         "traffic": None},
             "graph_replay": {"ms_per_step": ms_graph, "batched_einsums_per_s": world * 1e3 / ms_graph},
             "canonicalize_200_copies": {"p50_us": float(lat[len(lat) // 2]), "p99_us": float(lat[int(0.99 * len(lat))]),
                                         "distinct_keys": len(keys), "key": sorted(keys)[0]},
@@ -906,6 +914,7 @@ def main():
     ap.add_argument("--order", type=int, default=4, help="polynomial order of dg_divergence / face_mass")
     ap.add_argument("--rows", type=int, default=1, help="einsums b of dg_divergence / face_mass")
     ap.add_argument("--stacked-elements", type=int, default=100000)
+    ap.add_argument("--fem-e", type=int, default=4096, help="elements of the fem_action workload")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-sweep", default="",
                     help="comma-separated offered rates (requests/s) served after the main run, e.g. 5000,20000,80000")

@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(512, 2) element_df_kernel(const __grid_constan
 }
 
 // Small operators (NI, NJ <= NB, R <= 4; e.g. the FEM action's 4 x 4 D):
-// one thread per (producer group, element) keeps u[e, :] and t[r, i] in
+// one thread per (producer group: blockIdx.y, element) keeps u[e, :] and t[r, i] in
 // registers, so the streamed operands are read and the outputs written once,
 // coalesced across the warp, with no tile staging.  Entries beyond NI / NJ
 // are zero, which adds nothing to a compensated sum, so every output is the
@@ -224,13 +224,12 @@ __global__ void __launch_bounds__(256) element_df_small_kernel(const __grid_cons
     Ds[idx] = make_float2(d.hi, d.lo);
   }
   __syncthreads();
-  const int64_t total = (int64_t)p.n_groups * p.E;
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
-    const int g = (int)(w / p.E);
-    const int64_t e = w - (int64_t)g * p.E;
+  const int g = blockIdx.y;                     // producer group
+  const EProd &q = p.groups[g];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < p.E; e += (int64_t)gridDim.x * blockDim.x) {
     df u[NB];
 #pragma unroll
-    for (int j = 0; j < NB; ++j) u[j] = j < NJ ? prod_df(p.groups[g], e, j, 0, sin_tab) : df{0.f, 0.f};
+    for (int j = 0; j < NB; ++j) u[j] = j < NJ ? prod_df(q, e, j, 0, sin_tab) : df{0.f, 0.f};
     df t[EM_MAXR][NB];
 #pragma unroll
     for (int r = 0; r < EM_MAXR; ++r) {
@@ -281,8 +280,10 @@ cudaError_t launch_element_df_small(const EParams &p, cudaStream_t s) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t blocks = ((int64_t)p.n_groups * p.E + 255) / 256;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sms * 8));
+  // x: elements (grid-stride), y: producer groups
+  const int64_t blocks = (p.E + 255) / 256;
+  const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sms * 8 / std::max(1, p.n_groups) + 1)),
+                  (unsigned)p.n_groups);
   if (p.NI <= 4 && p.NJ <= 4) element_df_small_kernel<4><<<grid, 256, 0, s>>>(p);
   else element_df_small_kernel<8><<<grid, 256, 0, s>>>(p);
   return cudaGetLastError();
