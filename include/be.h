@@ -62,7 +62,14 @@ extern "C" {
 /* ---- evaluation strategies (be_config.strategy) ---- */
 #define BE_STRAT_AUTO 0        /* pick by pattern: ELEMENT, DENSE_SPLIT, else GENERIC   */
 #define BE_STRAT_GENERIC 1     /* one thread per output element, any notation           */
-#define BE_STRAT_ELEMENT 2     /* shared small operators x streamed per-element operands */
+#define BE_STRAT_ELEMENT 2     /* shared small operators x streamed per-element operands;
+                                  tile[0] elements per tile, tile[1] threads per CTA,
+                                  tile[2] variant (1 FP64 pipe, 2 double-float on the FP32
+                                  pipe, 3 tensor-core digit split; 0 = tensor cores where
+                                  the shape allows, else double-float), tile[3] for small
+                                  operators (at most 8 x 8) on the double-float variant:
+                                  1 + the share of the elements, in sixteenths, that run
+                                  on the FP64 pipe beside the double-float ones (0 = 8/16) */
 #define BE_STRAT_DENSE_SPLIT 3 /* FP64 contraction as split FP16 products on tcgen05;
                                   needs a context (its workspace holds the split operands) */
 

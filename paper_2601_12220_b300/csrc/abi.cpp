@@ -529,7 +529,8 @@ static int do_execute(be_ctx *x, const be_einsum *hc, const be_config *cfg, int3
     if (ep.E > 0) {
       KernelMark km(x, BE_KERNEL_ELEMENT, s);
       if (variant == 1) ce = launch_element(ep, grid, block, s);
-      else if (element_df_small(ep) && c.tile[1] <= 0) ce = launch_element_df_small(ep, s);
+      else if (element_df_small(ep) && c.tile[1] <= 0)
+        ce = launch_element_df_small(ep, c.tile[3] > 0 ? c.tile[3] - 1 : SMALL_FP64_SHARE16, s);
       else ce = launch_element_df(ep, grid, block, s);
     }
   } else {

@@ -173,9 +173,14 @@ __host__ __device__ inline int64_t d_offset(const EParams &p, int r, int i, int 
 cudaError_t launch_element(const EParams &p, int grid, int block, cudaStream_t s);
 // same strategy in double-float arithmetic on the FP32 pipe (FP64 accuracy)
 cudaError_t launch_element_df(const EParams &p, int grid, int block, cudaStream_t s);
-// the double-float variant for small operators (NI, NJ <= 8, not stacked): one thread per element
+// the double-float variant for small operators (NI, NJ <= 8, not stacked):
+// one thread per element; fp64_share16 / 16 of the elements run on the FP64
+// pipe beside the double-float ones
+// default FP64 share of the small-operator kernel, in sixteenths (measured on
+// the FEM action at E = 2^24)
+#define SMALL_FP64_SHARE16 8
 bool element_df_small(const EParams &p);
-cudaError_t launch_element_df_small(const EParams &p, cudaStream_t s);
+cudaError_t launch_element_df_small(const EParams &p, int fp64_share16, cudaStream_t s);
 int element_df_block(const EParams &p);   // block size matching one tile's work items
 // same strategy with t = u D^T as a digit-split GEMM on the tcgen05 tensor
 // cores (FP64 accuracy); status receives BE_ETIMEOUT if a bounded wait expires

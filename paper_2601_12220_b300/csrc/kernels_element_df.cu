@@ -58,6 +58,16 @@ __device__ __forceinline__ df prod_df(const EProd &q, int64_t e, int k, int NJ0,
   return dfm::df_mul(dfm::df_sin_tab2(a, sin_tab), dfm::df_from_double(b));
 }
 
+// the producer's value at (e, k) in FP64 (the small-operator kernel's FP64
+// share): a view, a * b, or sin(a) * b with the df sine rounded to FP64
+__device__ __forceinline__ double prod_fp64(const EProd &q, int64_t e, int k, const float2 *sin_tab) {
+  const double a = q.a.ptr[e * q.a.se + k * q.a.sk];
+  if (q.kind == 0) return a;
+  const double b = q.b.ptr[e * q.b.se + k * q.b.sk];
+  if (q.kind == 2) return a * b;
+  return dfm::df_to_double(dfm::sin_fast_ok(a) ? dfm::df_sin_tab2_fast(a, sin_tab) : dfm::df_sin_tab2(a, sin_tab)) * b;
+}
+
 constexpr int DF_EPT = 4;   // elements per thread in the contraction phase
 
 __global__ void __launch_bounds__(512, 2) element_df_kernel(const __grid_constant__ EParams p) {
@@ -205,34 +215,80 @@ __global__ void __launch_bounds__(512, 2) element_df_kernel(const __grid_constan
   }
 }
 
-// Small operators (NI, NJ <= NB, R <= 4; e.g. the FEM action's 4 x 4 D):
-// one thread per (producer group: blockIdx.y, element) keeps u[e, :] and t[r, i] in
-// registers, so the streamed operands are read and the outputs written once,
-// coalesced across the warp, with no tile staging.  Entries beyond NI / NJ
-// are zero, which adds nothing to a compensated sum, so every output is the
-// same sequence of df operations as in element_df_kernel.
-template <int NB>
-__global__ void __launch_bounds__(256) element_df_small_kernel(const __grid_constant__ EParams p) {
-  __shared__ float2 Ds[EM_MAXR * NB * NB];   // [r][i][j]
+// Small operators (NI, NJ <= NB, R <= RM <= 4; e.g. the FEM action's 4 x 4
+// D): one thread per (producer group: blockIdx.y, element) keeps u[e, :] and
+// t[r, i] in registers, so the streamed operands are read and the outputs
+// written once, coalesced across the warp, with no tile staging.  B300's
+// FP64 pipe and its FP32 pipe work side by side: the first blocks64 blocks
+// of each group evaluate the elements [0, E64) as FP64 multiply-add chains,
+// the others the elements [E64, E) in double-float; block dispatch
+// interleaves the two kinds on every SM.  In the double-float part, entries
+// beyond NI / NJ are zero, which adds nothing to a compensated sum, so every
+// output is the same sequence of df operations as in element_df_kernel.
+template <int NB, int RM>
+__global__ void __launch_bounds__(256, (NB == 4 && RM == 1) ? 4 : 2)
+    element_df_small_kernel(const __grid_constant__ EParams p, int64_t E64, int blocks64) {
+  __shared__ float2 Ds[RM * NB * NB];   // [r][i][j] as df
+  __shared__ double Dd[RM * NB * NB];   // the same in FP64
   __shared__ float2 sin_tab[dfm::SIN2_N];
   const int R = p.R, NI = p.NI, NJ = p.NJ;
   dfm::sin2_table_fill(sin_tab);
-  for (int idx = threadIdx.x; idx < EM_MAXR * NB * NB; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < RM * NB * NB; idx += blockDim.x) {
     const int r = idx / (NB * NB), i = (idx / NB) % NB, j = idx % NB;
-    df d{0.f, 0.f};
-    if (r < R && i < NI && j < NJ) d = dfm::df_from_double(p.D[d_offset(p, r, i, j)]);
+    const double v = (r < R && i < NI && j < NJ) ? p.D[d_offset(p, r, i, j)] : 0.0;
+    const df d = dfm::df_from_double(v);
     Ds[idx] = make_float2(d.hi, d.lo);
+    Dd[idx] = v;
   }
   __syncthreads();
   const int g = blockIdx.y;                     // producer group
   const EProd &q = p.groups[g];
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < p.E; e += (int64_t)gridDim.x * blockDim.x) {
+  const bool fp64 = (int)blockIdx.x < blocks64;
+  const int64_t lo = fp64 ? 0 : E64, hi = fp64 ? E64 : p.E;
+  const int64_t b0 = fp64 ? blockIdx.x : blockIdx.x - blocks64;
+  const int64_t nb = fp64 ? blocks64 : (int64_t)gridDim.x - blocks64;
+  for (int64_t e = lo + b0 * blockDim.x + threadIdx.x; e < hi; e += nb * blockDim.x) {
+    if (fp64) {
+      double u[NB], t[RM][NB];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) u[j] = j < NJ ? prod_fp64(q, e, j, sin_tab) : 0.0;
+#pragma unroll
+      for (int r = 0; r < RM; ++r) {
+        if (r >= R) break;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+          double acc = 0.0;
+#pragma unroll
+          for (int j = 0; j < NB; ++j)
+            if (j < NJ) acc = fma(Dd[(r * NB + i) * NB + j], u[j], acc);
+          t[r][i] = acc;
+        }
+      }
+      for (int k = 0; k < p.n_rows; ++k) {
+        if (p.rows[k].group != g) continue;
+        const EView &v = p.rows[k].g;
+        double *out = p.rows[k].out + e * NI;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+          if (i >= NI) break;
+          double acc = t[0][i];
+          if (p.has_g) {
+            acc = 0.0;
+#pragma unroll
+            for (int r = 0; r < RM; ++r)
+              if (r < R) acc = fma(v.ptr[e * v.se + r * v.sk], t[r][i], acc);
+          }
+          out[i] = acc;
+        }
+      }
+      continue;
+    }
     df u[NB];
 #pragma unroll
     for (int j = 0; j < NB; ++j) u[j] = j < NJ ? prod_df(q, e, j, 0, sin_tab) : df{0.f, 0.f};
-    df t[EM_MAXR][NB];
+    df t[RM][NB];
 #pragma unroll
-    for (int r = 0; r < EM_MAXR; ++r) {
+    for (int r = 0; r < RM; ++r) {
       if (r >= R) break;
 #pragma unroll
       for (int i = 0; i < NB; ++i) {
@@ -247,11 +303,11 @@ __global__ void __launch_bounds__(256) element_df_small_kernel(const __grid_cons
     }
     for (int k = 0; k < p.n_rows; ++k) {
       if (p.rows[k].group != g) continue;
-      df gk[EM_MAXR];
+      df gk[RM];
       if (p.has_g) {
         const EView &v = p.rows[k].g;
 #pragma unroll
-        for (int r = 0; r < EM_MAXR; ++r)
+        for (int r = 0; r < RM; ++r)
           if (r < R) gk[r] = dfm::df_from_double(v.ptr[e * v.se + r * v.sk]);
       }
       double *out = p.rows[k].out + e * NI;
@@ -262,7 +318,7 @@ __global__ void __launch_bounds__(256) element_df_small_kernel(const __grid_cons
         if (p.has_g) {
           float sh = 0.f, sl = 0.f;
 #pragma unroll
-          for (int r = 0; r < EM_MAXR; ++r)
+          for (int r = 0; r < RM; ++r)
             if (r < R) dfm::dot_acc(sh, sl, gk[r], t[r][i]);
           acc = dfm::fast_two_sum(sh, sl);
         }
@@ -276,16 +332,27 @@ __global__ void __launch_bounds__(256) element_df_small_kernel(const __grid_cons
 
 bool element_df_small(const EParams &p) { return p.NJ0 == 0 && p.R <= EM_MAXR && p.NI <= 8 && p.NJ <= 8; }
 
-cudaError_t launch_element_df_small(const EParams &p, cudaStream_t s) {
+cudaError_t launch_element_df_small(const EParams &p, int fp64_share16, cudaStream_t s) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // x: elements (grid-stride), y: producer groups
-  const int64_t blocks = (p.E + 255) / 256;
-  const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sms * 8 / std::max(1, p.n_groups) + 1)),
-                  (unsigned)p.n_groups);
-  if (p.NI <= 4 && p.NJ <= 4) element_df_small_kernel<4><<<grid, 256, 0, s>>>(p);
-  else element_df_small_kernel<8><<<grid, 256, 0, s>>>(p);
+  // x: elements (grid-stride; the first b64 blocks take the FP64 share,
+  // fp64_share16 / 16 of the elements), y: producer groups
+  fp64_share16 = std::max(0, std::min(16, fp64_share16));
+  const int64_t per_group = std::max<int64_t>(2, (int64_t)sms * 8 / std::max(1, p.n_groups) + 1);
+  const int64_t E64 = std::min(p.E, (p.E * fp64_share16 / 16 + 255) / 256 * 256);
+  const int64_t need64 = (E64 + 255) / 256, needdf = (p.E - E64 + 255) / 256;
+  const int64_t b64 = E64 > 0 ? std::max<int64_t>(1, std::min<int64_t>(need64, per_group * fp64_share16 / 16)) : 0;
+  const int64_t bdf = E64 < p.E ? std::max<int64_t>(1, std::min<int64_t>(needdf, per_group - b64)) : 0;
+  const dim3 grid((unsigned)std::max<int64_t>(1, b64 + bdf), (unsigned)p.n_groups);
+  const bool r1 = p.R == 1;
+  if (p.NI <= 4 && p.NJ <= 4) {
+    if (r1) element_df_small_kernel<4, 1><<<grid, 256, 0, s>>>(p, E64, (int)b64);
+    else element_df_small_kernel<4, EM_MAXR><<<grid, 256, 0, s>>>(p, E64, (int)b64);
+  } else {
+    if (r1) element_df_small_kernel<8, 1><<<grid, 256, 0, s>>>(p, E64, (int)b64);
+    else element_df_small_kernel<8, EM_MAXR><<<grid, 256, 0, s>>>(p, E64, (int)b64);
+  }
   return cudaGetLastError();
 }
 

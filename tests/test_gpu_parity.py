@@ -320,6 +320,31 @@ def test_lookup_transfer_same_bits():
         assert np.array_equal(got[x], got2[2 - x])
 
 
+@pytest.mark.parametrize("share", [1, 10, 17, 0], ids=["df", "mixed", "fp64", "default"])
+def test_small_operator_kernel_fp64_share(share):
+    """Small operators (NI, NJ <= 8) run one element per thread, a share of
+    the elements as FP64 multiply-adds and the rest in double-float
+    (tile[3] = 1 + sixteenths on the FP64 pipe): FEM action (4 x 4, four
+    fields), a P1-sized gradient (R = 3 with G and the sine producer) and a
+    7 x 7 operator, with element counts that leave ragged blocks."""
+    cfg = be.make_config(be.STRAT_ELEMENT, (0, 0, 2, share))
+    E = 5003
+    D, us = W.fem_action(E=E)
+    text = W.fem_action_spec(E=E)
+    arrs = {"D": D, **{f"u{k}": u for k, u in enumerate(us)}}
+    got, _ = run(text, arrs, cfg=cfg)
+    for k, (r, S) in enumerate(ev.evaluate(text, arrs)):
+        assert_close(got[k], r, S, 1e-12)
+    for ndof in (4, 7):
+        E = 3001
+        D, G, a, b = W.dg_gradient(E=E, ndof=ndof)
+        text = W.dg_gradient_spec(E=E, ndof=ndof)
+        arrs = dict(D=D, G=G, a=a, b=b)
+        got, _ = run(text, arrs, cfg=cfg)
+        for k, (r, S) in enumerate(ev.evaluate(text, arrs)):
+            assert_close(got[k], r, S, 1e-12)
+
+
 GEN = be.make_config(be.STRAT_GENERIC)
 
 
