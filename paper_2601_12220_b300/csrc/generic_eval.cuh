@@ -351,7 +351,8 @@ __device__ __forceinline__ T out_block(const GParams &p, int64_t o, double *red)
   return r;
 }
 
-// Mode 3: one TM x TM tile of the GEMM view (GGemm) of a two-operand row.
+// Mode 3: one TM x TM tile of the GEMM view (GGemm) of a row with two
+// operands in its sum (a hoisted third operand multiplies each finished sum).
 // Per K-slice of 16, the CTA stages A[m, k] and B[k, n] in shared memory
 // (loaded along the role in which the operand is contiguous), with the
 // offsets of the slice's m, n and k values computed once from the letters'
@@ -359,7 +360,7 @@ __device__ __forceinline__ T out_block(const GParams &p, int64_t o, double *red)
 // outputs (R = TM / 16), every output summing its terms in increasing k (so
 // the result does not depend on which kernel runs the tile).  Must be called
 // by the whole CTA.
-constexpr int GEMM_SMEM = 2 * GT_K * (GT_MAX + 2) * 8 + (4 * GT_MAX + 2 * GT_K) * 8;
+constexpr int GEMM_SMEM = 2 * GT_K * (GT_MAX + 2) * 8 + (6 * GT_MAX + 2 * GT_K) * 8;
 
 template <typename T, int TM>
 __device__ void gemm_tile(const GParams &p, int64_t tile, unsigned char *sm) {
@@ -373,14 +374,17 @@ __device__ void gemm_tile(const GParams &p, int64_t tile, unsigned char *sm) {
   int64_t *offAm = (int64_t *)(sm + 2 * GT_K * (GT_MAX + 2) * 8);
   int64_t *offCm = offAm + GT_MAX, *offBn = offCm + GT_MAX, *offCn = offBn + GT_MAX;
   int64_t *offAk = offCn + GT_MAX, *offBk = offAk + GT_K;
+  int64_t *offHm = offBk + GT_K, *offHn = offHm + GT_MAX;   // the hoisted operand, if any
   const int tid = threadIdx.x;
   const int64_t *ca = p.ops[0].coef, *cb = p.ops[1].coef;
+  const bool hoist = p.n_hoist > 0;
+  const int64_t *ch = p.ops[hoist ? 2 : 0].coef;
   int64_t r = tile;
   const int64_t nt = r % g.tiles_n;
   r /= g.tiles_n;
   const int64_t mt = r % g.tiles_m;
   r /= g.tiles_m;
-  int64_t baseA = 0, baseB = 0, baseC = 0;
+  int64_t baseA = 0, baseB = 0, baseC = 0, baseH = 0;
   for (int d = g.nb - 1; d >= 0; --d) {
     const int L = g.b[d];
     const int64_t v = r % p.len[L];
@@ -388,11 +392,12 @@ __device__ void gemm_tile(const GParams &p, int64_t tile, unsigned char *sm) {
     baseA += ca[L] * v;
     baseB += cb[L] * v;
     baseC += g.out_coef[L] * v;
+    baseH += ch[L] * v;
   }
   const int64_t m0 = mt * TM, n0 = nt * TM;
   const int vm = (int)min((int64_t)TM, g.M - m0), vn = (int)min((int64_t)TM, g.N - n0);
   if (tid < TM) {
-    int64_t x = m0 + tid, oa = 0, oc = 0;
+    int64_t x = m0 + tid, oa = 0, oc = 0, oh = 0;
     if (tid < vm)
       for (int d = g.nm - 1; d >= 0; --d) {
         const int L = g.m[d];
@@ -400,12 +405,14 @@ __device__ void gemm_tile(const GParams &p, int64_t tile, unsigned char *sm) {
         x /= p.len[L];
         oa += ca[L] * v;
         oc += g.out_coef[L] * v;
+        oh += ch[L] * v;
       }
     offAm[tid] = oa;
     offCm[tid] = oc;
+    offHm[tid] = oh;
   } else if (tid >= 64 && tid < 64 + TM) {
     const int t = tid - 64;
-    int64_t x = n0 + t, ob = 0, oc = 0;
+    int64_t x = n0 + t, ob = 0, oc = 0, oh = 0;
     if (t < vn)
       for (int d = g.nn - 1; d >= 0; --d) {
         const int L = g.n[d];
@@ -413,9 +420,11 @@ __device__ void gemm_tile(const GParams &p, int64_t tile, unsigned char *sm) {
         x /= p.len[L];
         ob += cb[L] * v;
         oc += g.out_coef[L] * v;
+        oh += ch[L] * v;
       }
     offBn[t] = ob;
     offCn[t] = oc;
+    offHn[t] = oh;
   }
   const T *A = (const T *)p.ops[0].ptr + baseA, *B = (const T *)p.ops[1].ptr + baseB;
   const int tm = tid >> 4, tn = tid & 15;
@@ -488,7 +497,9 @@ __device__ void gemm_tile(const GParams &p, int64_t tile, unsigned char *sm) {
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       const int n = tn * R + j;
-      if (n < vn) C[offCm[m] + offCn[n]] = acc[i][j];
+      if (n >= vn) continue;
+      // the hoisted operand multiplies the finished sum
+      C[offCm[m] + offCn[n]] = hoist ? acc[i][j] * ((const T *)p.ops[2].ptr)[baseH + offHm[m] + offHn[n]] : acc[i][j];
     }
   }
   __syncthreads();   // the tables and slices are free for the next tile

@@ -154,13 +154,16 @@ static void split_run_invariants(GParams &p) {
   p.n_inv = ni;
 }
 
-// Mode 3: the GEMM view of a fast two-operand row whose M, N and K extents
+// Mode 3: the GEMM view of a fast row with two operands in its sum (plus at
+// most one hoisted operand) whose M, N and K extents
 // are all large enough to fill its tiles.  Letters within a role run
 // outermost first, ordered by decreasing stride, so the fastest-varying
 // letter of each role has the smallest stride; each operand is then loaded
 // along the role (K or M / N) in which it is contiguous.
 static void plan_gemm_view(GParams &p) {
-  if (!p.fast || p.n_ops != 2) return;
+  // two operands in the sum, and at most one hoisted operand (it multiplies
+  // each output once, after its sum)
+  if (!p.fast || p.n_ops - p.n_hoist != 2 || p.n_hoist > 1) return;
   GGemm g{};
   const int64_t *ca = p.ops[0].coef, *cb = p.ops[1].coef;
   int64_t oc = 1;

@@ -417,6 +417,9 @@ def test_generic_running_offsets(text_fmt, shapes, dt):
     ("bik,bkj->bij", {"A": (3, 40, 20), "B": (3, 20, 50)}),
     # a contracted letter only one operand has
     ("ikl,kj->ij", {"A": (33, 9, 4), "B": (9, 40)}),
+    # Fig. 1's notation: the third operand, which no contracted letter moves,
+    # multiplies each finished sum of the first two
+    ("mnj,mni,kli->ijkl", {"A": (9, 11, 40), "B": (9, 11, 36), "C": (2, 3, 36)}),
 ])
 @pytest.mark.parametrize("dt", ["f64", "f32"])
 def test_generic_gemm_tiles(text_fmt, shapes, dt):
