@@ -237,10 +237,15 @@ int plan_generic_row(const Einsum &e, int row, const std::vector<BufIn> &bufs, c
     }
   p.out = out.ptr;
   p.out_dtype = e.out_dtype;
-  // a thread per output for short contractions, a warp for medium ones and
-  // a CTA for long ones, or for medium ones with too few outputs to fill the
-  // GPU with warps (each virtual lane still takes at least 8 terms)
-  p.mode = p.total_con < 64 ? 0 : ((p.total_con >= 16384 || (p.total_con >= 2048 && p.total_out < 1024)) ? 2 : 1);
+  // a thread per output for short contractions (under 512 terms when there
+  // are at least 32768 outputs, enough threads to fill the GPU, else under
+  // 64: a warp's butterfly sum would cost more FP64 adds than its terms), a
+  // warp for medium ones and a CTA for long ones, or for medium ones with too
+  // few outputs to fill the GPU with warps (each virtual lane still takes at
+  // least 8 terms)
+  p.mode = (p.total_con < 64 || (p.total_con < 512 && p.total_out >= 32768))
+               ? 0
+               : ((p.total_con >= 16384 || (p.total_con >= 2048 && p.total_out < 1024)) ? 2 : 1);
   for (size_t k = 0; k < scalars.size(); ++k) p.scalars[k] = scalars[k];
   int n_ins = 0;
   for (int j = 0; j < e.n; ++j) {

@@ -349,6 +349,9 @@ GEN = be.make_config(be.STRAT_GENERIC)
 
 
 @pytest.mark.parametrize("text_fmt,shapes", [
+    # mode 0 for a 100-term contraction with 40000 outputs (thread per output
+    # up to 512 terms once there are 32768 outputs)
+    ("ik,kj,k->ij", {"A": (200, 100), "B": (100, 200), "C": (100,)}),
     # mode 0 (contraction < 64), one and two contracted letters
     ("ij,j->i", {"A": (70, 9), "B": (9,)}),
     ("ijk,jk->i", {"A": (50, 3, 5), "B": (3, 5)}),
