@@ -16,7 +16,7 @@ namespace be {
 
 namespace {
 
-__global__ void __launch_bounds__(256, 3) persistent_kernel(const GParams *__restrict__ rows,
+__global__ void __launch_bounds__(256, 4) persistent_kernel(const GParams *__restrict__ rows,
                                                          const PTile *__restrict__ tiles, int64_t n_tiles,
                                                          unsigned long long *__restrict__ counter) {
   __shared__ GParams sp;
