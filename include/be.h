@@ -311,7 +311,7 @@ int be_tune(be_ctx *x, const be_einsum *e, int32_t precision, const be_buf *bufs
  *   pointers, as for be_execute) and runtime scalars scalars[k] (may be
  *   NULL when n_scalars is NULL or 0).  Every row becomes a descriptor; its
  *   outputs are cut into tiles of about 2^tile[1] operand terms (default
- *   18); cfg->tile[0] is the block size (default 256), cfg->tile[2] CTAs per
+ *   20); cfg->tile[0] is the block size (default 256), cfg->tile[2] CTAs per
  *   SM (default 4); cfg may be NULL.  The buffers are borrowed and must stay
  *   valid while the batch is used; their CONTENTS may change between runs.
  *   Device memory for descriptors and tiles is allocated here.

@@ -870,7 +870,7 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
   if (cfg) std::memcpy(&c, cfg, sizeof(c));
   b->block = c.tile[0] > 0 ? c.tile[0] : 256;
   if (b->block % 32 || b->block > 256) return fail(BE_EARG, "block size must be a multiple of 32 up to 256");
-  const int cost_log2 = c.tile[1] > 0 ? c.tile[1] : 18;
+  const int cost_log2 = c.tile[1] > 0 ? c.tile[1] : 20;
   const int per_sm = c.tile[2] > 0 ? c.tile[2] : 4;
   const double cost_target = std::ldexp(1.0, cost_log2);
   std::string err;
