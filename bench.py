@@ -74,11 +74,28 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # 3*35*35 + 3*3*35 terms, plus 3 per normalisation of 2*105 results (the
 # sine and the conversions are not counted, so this is a lower bound)
 DF_FLOPS_PER_ELEMENT = 15 * (3 * 35 * 35 + 3 * 3 * 35) + 3 * 2 * 105
-# bf16 MMA flops the tensor-core variant issues per element: 21 digit
-# products x 3 K-steps of 16 x 112 accumulator columns (blocks of 32, 32, 32
-# and 16: halves of 16 columns holding 5 dofs x 3 terms and one padding
-# column) x 2
-TC_MMA_FLOPS_PER_ELEMENT = 21 * 3 * 16 * 112 * 2
+# bf16 MMA flops the tensor-core variant issues per element: per column
+# block of 32 and K-slice of 16, u's digit q = 0..5 times D's digit planes
+# p = 0..min(5, 6 - q) in one MMA of N = 32 (number of planes): 6 + 6 + 5 +
+# 4 + 3 + 2 = 26 planes (832 columns); 3 K-slices, 4 column blocks, x 2
+TC_MMA_FLOPS_PER_ELEMENT = 2 * 16 * 3 * 4 * 32 * (6 + 6 + 5 + 4 + 3 + 2)
+# headers whose code is compiled into each kernel: the committed profile of a
+# kernel stays valid only while the kernel source and these hash as recorded
+KERNEL_HEADERS = {"kernels_element_tc.cu": ["df_math.cuh", "tc_common.cuh", "exec.hpp"],
+                  "kernels_element_df.cu": ["df_math.cuh", "exec.hpp"],
+                  "kernels_element.cu": ["exec.hpp"],
+                  "kernels_dense.cu": ["dense.hpp", "tc_common.cuh"],
+                  "kernels_persistent.cu": ["generic_eval.cuh", "exec.hpp"]}
+
+
+def source_hash(source):
+    """sha256 (first 16 hex digits) of a kernel source file followed by the
+    headers compiled into it."""
+    d = os.path.join(ROOT, "paper_2601_12220_b300", "csrc")
+    h = hashlib.sha256()
+    for f in [source] + KERNEL_HEADERS.get(source, []):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def kernel_traffic(kernel):
@@ -88,7 +105,7 @@ def kernel_traffic(kernel):
     summ = os.path.join(ROOT, "profiles", kernel["profile"])
     if not (os.path.exists(src) and os.path.exists(summ)):
         return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = source_hash(kernel["source"])
     got = {}
     for line in open(summ):
         if ":" in line:

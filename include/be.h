@@ -369,6 +369,18 @@ void be_server_destroy(be_server *s);
  */
 int be_status(be_ctx *x, int32_t *device_status);
 
+/*
+ * be_ctx_set_wait_limit -- limit, in SM clock cycles, of every pipeline
+ * wait of the tensor-core kernels (the element strategy's digit-split GEMM
+ * and the dense split GEMM) launched through x; 0 restores the default of
+ * about one second.  A wait that runs out stops its kernel early (outputs
+ * not valid), frees the kernel's tensor memory after its issued work has
+ * completed, and leaves BE_ETIMEOUT for be_status.  A limit of a few
+ * thousand cycles makes the waits run out on purpose (failure-path tests);
+ * the paper has no counterpart.  Errors: BE_EARG.
+ */
+int be_ctx_set_wait_limit(be_ctx *x, int64_t cycles);
+
 /* ---- per-kernel timing (CUDA events on the launching stream) ---- */
 #define BE_KERNEL_ELEMENT 0     /* element-streaming kernel              */
 #define BE_KERNEL_GENERIC 1     /* generic loop-nest kernel              */
@@ -393,19 +405,34 @@ int be_ctx_timing(be_ctx *x, int32_t kernel, int64_t *launches, double *total_ms
  * and stall their other streams.
  *
  * Scratch: a fixed 64 MiB array compiled into the library (plus one status
- * word), resident on every GPU that loads the library until the process
- * exits.  The call fails with BE_ETOOMANY (nothing launched) when the
+ * word), held on every GPU where the library's device code is loaded until
+ * the process exits.  With CUDA's default lazy module loading the driver
+ * reserves the array on a device only when the first call there looks up
+ * its address, so that first call (a warm-up) is where the 64 MiB are
+ * taken, and it can fail with BE_ECUDA if the device is already full: make
+ * it before the caller sets up its memory pool and before any stream
+ * capture.  The call fails with BE_ETOOMANY (nothing launched) when the
  * problem needs more: about (M + N) * K * 8 bytes with M and N padded to
- * 128 and K to 32 (e.g. M = N = 1024, K = 3968 fits).  The first call on a
- * device looks up the array's device address with that device current; make
- * that first call before any stream capture.  Every call reuses the same
- * array (the call clears what must start at zero), so calls whose GPU work
- * overlaps -- on different streams or devices sharing a context -- race; issue
- * them in order on one stream.  Errors: BE_EARG, BE_ETOOMANY, BE_ECUDA,
- * message in be_last_error().
+ * 128 and K to 32 (e.g. M = N = 1024, K = 3968 fits).  Every call reuses the
+ * same array (the call clears what must start at zero), so calls whose GPU
+ * work overlaps -- on different streams or devices sharing a context -- race;
+ * issue them in order on one stream.  Errors: BE_EARG, BE_ETOOMANY,
+ * BE_ECUDA, message in be_last_error().  A kernel whose bounded wait ran
+ * out leaves BE_ETIMEOUT in the array's status word; read it with
+ * be_gemm_split_noalloc_status.
  */
 int be_gemm_split_noalloc(const double *A, int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc,
                           int64_t M, int64_t N, int64_t K, void *stream);
+
+/*
+ * be_gemm_split_noalloc_status -- read and clear the status word of the
+ * current device's fixed array: BE_OK, or BE_ETIMEOUT when a call since the
+ * last read stopped early (its C is then not valid).  Allocates nothing; it
+ * copies one word synchronously with the device, so call it after the
+ * stream that ran the calls has been synchronized.  The paper has no
+ * counterpart.  Errors: BE_EARG, BE_ECUDA.
+ */
+int be_gemm_split_noalloc_status(int32_t *status);
 
 /* Strategy the engine would run for e under cfg (after AUTO resolution). */
 int be_plan_strategy(be_ctx *x, const be_einsum *e, const be_config *cfg, int32_t precision,

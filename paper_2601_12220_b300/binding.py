@@ -32,6 +32,7 @@ EXPORTS = [
     "be_canon_tokens", "be_induced_graph", "be_graph_check", "be_identify", "be_ctx_create",
     "be_ctx_destroy", "be_lookup", "be_record", "be_db_size", "be_execute", "be_execute_host",
     "be_plan_strategy", "be_status", "be_ctx_set_timing", "be_ctx_timing", "be_gemm_split_noalloc",
+    "be_gemm_split_noalloc_status", "be_ctx_set_wait_limit",
     "be_batch_create", "be_batch_run", "be_batch_info", "be_batch_destroy", "be_tune",
     "be_server_create", "be_server_submit", "be_server_wait", "be_server_drain", "be_server_stats",
     "be_server_reset_stats", "be_server_destroy", "be_raise", "be_raised_name", "be_record_facts",
@@ -112,6 +113,8 @@ def lib():
             "be_status": (ctypes.c_int, [vp, P(i32)]),
             "be_ctx_set_timing": (ctypes.c_int, [vp, i32]),
             "be_gemm_split_noalloc": (ctypes.c_int, [vp, i64, vp, i64, vp, i64, i64, i64, i64, vp]),
+            "be_gemm_split_noalloc_status": (ctypes.c_int, [P(i32)]),
+            "be_ctx_set_wait_limit": (ctypes.c_int, [vp, i64]),
             "be_batch_create": (ctypes.c_int, [vp, i32, P(vp), P(P(Buf)), P(i32), P(P(Buf)), P(i32),
                                                P(P(ctypes.c_double)), P(i32), P(Config), P(vp)]),
             "be_batch_run": (ctypes.c_int, [vp, vp]),
@@ -334,6 +337,10 @@ class Context:
 
     def set_timing(self, enable=True):
         check(lib().be_ctx_set_timing(self._h, 1 if enable else 0))
+
+    def set_wait_limit(self, cycles: int = 0):
+        """Limit (SM cycles) of the tensor-core kernels' pipeline waits; 0 = default."""
+        check(lib().be_ctx_set_wait_limit(self._h, int(cycles)))
 
     def timing(self, kernel: int):
         """(launches, total ms) of kernel id since the last read."""

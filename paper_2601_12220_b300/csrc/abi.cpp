@@ -492,7 +492,7 @@ static int do_execute(be_ctx *x, const be_einsum *hc, const be_config *cfg, int3
         if (ce == cudaSuccess) {
           KernelMark km(x, BE_KERNEL_DENSE_GEMM, s);
           ce = dense_split_gemm(DenseA{r.A, dp.M, r.lda, r.ska}, dp.N, dp.K, dp.M, r.C, dp.N, x->ws, c.split >= 4,
-                                c.tile[2] > 0 ? c.tile[2] : 2, x->status, s);
+                                c.tile[2] > 0 ? c.tile[2] : 2, x->status, x->wait_limit, s);
         }
       }
       if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("dense split: ") + cudaGetErrorString(ce));
@@ -514,7 +514,7 @@ static int do_execute(be_ctx *x, const be_einsum *hc, const be_config *cfg, int3
         status = x->status;
       }
       KernelMark km(x, BE_KERNEL_ELEMENT, s);
-      ce = launch_element_tc(ep, status, s);
+      ce = launch_element_tc(ep, status, x ? x->wait_limit : 0, s);
       if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("launch: ") + cudaGetErrorString(ce));
       return BE_OK;
     }
@@ -1046,6 +1046,14 @@ int be_tune(be_ctx *x, const be_einsum *hc, int32_t precision, const be_buf *buf
   cudaEventDestroy(b);
   if (best_t < 0) return fail(BE_EUNSUPPORTED, "no candidate configuration ran");
   if (best_seconds) *best_seconds = best_t;
+  return BE_OK;
+}
+
+int be_ctx_set_wait_limit(be_ctx *x, int64_t cycles) {
+  if (!x) return fail(BE_EARG, "NULL context");
+  if (cycles < 0) return fail(BE_EARG, "negative wait limit");
+  std::lock_guard<std::mutex> g(x->mu);
+  x->wait_limit = cycles;
   return BE_OK;
 }
 

@@ -38,8 +38,10 @@ cudaError_t dense_split_b(const DenseB &b, void *ws, cudaStream_t s);
 // split A (one row of the batch) into the workspace
 cudaError_t dense_split_a(const DenseA &a, int64_t K, int64_t M_max, int64_t N, void *ws, cudaStream_t s);
 // tensor-core GEMM of the split operands into C (M x N, row stride ldc)
-// lolo adds the lo*lo product (tighter bound, one more MMA per k-step)
+// lolo adds the lo*lo product (tighter bound, one more MMA per k-step);
+// wait_limit: SM cycles before a pipeline wait gives up and records
+// BE_ETIMEOUT in *status (0: about one second)
 cudaError_t dense_split_gemm(const DenseA &a, int64_t N, int64_t K, int64_t M_max, double *C, int64_t ldc,
-                             void *ws, bool lolo, int hdrain, int *status, cudaStream_t s);
+                             void *ws, bool lolo, int hdrain, int *status, long long wait_limit, cudaStream_t s);
 
 }  // namespace be

@@ -240,6 +240,67 @@ __device__ __forceinline__ df df_sin_tab2_fast(double x, const float2 *tab) {
   const float2 s0 = tab[n & (SIN2_N - 1)], c0 = tab[(n + SIN2_N / 4) & (SIN2_N - 1)];
   return df_add(df_mul(df{s0.x, s0.y}, cd), df_mul(df{c0.x, c0.y}, sd));
 }
+// Half-circle table: sin(n pi / 512) for n = 0..511 as (hi, lo); an index
+// n of the full circle reads entry n mod 512 and negates it when bit 9 of n
+// is set (sin(x + pi) = -sin x).  Half the shared memory of the full table
+// for two extra logic operations per lookup.
+constexpr int SINH_N = 512;
+__device__ __forceinline__ void sin_half_table_fill(float2 *tab, int tid, int nthreads) {
+  for (int n = tid; n < SINH_N; n += nthreads) {
+    const int mm = n <= 256 ? n : 512 - n;
+    const df s = df_sin((double)mm * PI512_HI);
+    tab[n] = make_float2(s.hi, s.lo);
+  }
+}
+__device__ __forceinline__ df sin_half_entry(const float2 *tab, int n) {
+  const float2 v = tab[n & (SINH_N - 1)];
+  const uint32_t sg = ((uint32_t)n << 22) & 0x80000000u;   // bit 9 of n -> sign
+  return df{__uint_as_float(__float_as_uint(v.x) ^ sg), __uint_as_float(__float_as_uint(v.y) ^ sg)};
+}
+// df_sin_tab2_fast on the half-circle table (|x| < 2^20, sin_fast_ok)
+__device__ __forceinline__ df df_sin_half_fast(double x, const float2 *tab) {
+  const double nm = fma(x, 162.97466172610083, 6755399441055744.0);
+  const int n = __double2loint(nm);
+  const double nd = nm - 6755399441055744.0;
+  const double dr = fma(-nd, PI512_LO, fma(-nd, PI512_HI, x));
+  const uint32_t adr = (uint32_t)__double2hiint(dr) & 0x7FFFFFFFu;
+  const df d = df_from_double_fast(adr < ((1023u - 70u) << 20) ? 0.0 : dr);
+  const float d2 = d.hi * d.hi;
+  const df sd = fast_two_sum(d.hi, fmaf(d.hi * d2, fmaf(d2, 1.f / 120.f, -1.f / 6.f), d.lo));
+  const df p = two_prod(d.hi, d.hi);
+  const df c1 = fast_two_sum(1.f, -0.5f * p.hi);
+  const df cd = fast_two_sum(c1.hi, c1.lo + fmaf(-d.hi, d.lo, fmaf(p.hi, p.hi * (1.f / 24.f), -0.5f * p.lo)));
+  const df s0 = sin_half_entry(tab, n), c0 = sin_half_entry(tab, n + SINH_N / 2);
+  return df_add(df_mul(s0, cd), df_mul(c0, sd));
+}
+// the tested form: FP64 sine beyond the reduction's exact range
+__device__ __forceinline__ df df_sin_half(double x, const float2 *tab) {
+  if ((int)((__double_as_longlong(x) >> 52) & 0x7FF) >= 1023 + 20) return sin_far(x);
+  const double nm = fma(x, 162.97466172610083, 6755399441055744.0);
+  const int n = __double2loint(nm);
+  const double nd = nm - 6755399441055744.0;
+  const double dr = fma(-nd, PI512_LO, fma(-nd, PI512_HI, x));
+  const df d = df_from_double(dr);
+  const float d2 = d.hi * d.hi;
+  const df sd = fast_two_sum(d.hi, fmaf(d.hi * d2, fmaf(d2, 1.f / 120.f, -1.f / 6.f), d.lo));
+  const df p = two_prod(d.hi, d.hi);
+  const df c1 = fast_two_sum(1.f, -0.5f * p.hi);
+  const df cd = fast_two_sum(c1.hi, c1.lo + fmaf(-d.hi, d.lo, fmaf(p.hi, p.hi * (1.f / 24.f), -0.5f * p.lo)));
+  const df s0 = sin_half_entry(tab, n), c0 = sin_half_entry(tab, n + SINH_N / 2);
+  return df_add(df_mul(s0, cd), df_mul(c0, sd));
+}
+
+// exact float -> double of a normal float or zero by integer operations
+// (the 8-bit exponent rebased by 1023 - 127 = 896 in the high word, the
+// significand's low 3 bits moved to the top of the low word); subnormal,
+// infinite and NaN floats take the hardware conversion
+__device__ __forceinline__ double f2d_bits(float f) {
+  const uint32_t u = __float_as_uint(f), a = u & 0x7FFFFFFFu;
+  const uint32_t ef = a >> 23;
+  if (ef == 0u || ef == 0xFFu) return a == 0u ? __hiloint2double((int)(u & 0x80000000u), 0) : (double)f;
+  return __hiloint2double((int)((u & 0x80000000u) | ((a >> 3) + (896u << 20))), (int)(u << 29));
+}
+
 // |x| < 2^20 (and finite): the range of df_sin_tab2_fast
 __device__ __forceinline__ bool sin_fast_ok(double x) {
   return (int)((__double_as_longlong(x) >> 52) & 0x7FF) < 1023 + 20;

@@ -183,8 +183,10 @@ bool element_df_small(const EParams &p);
 cudaError_t launch_element_df_small(const EParams &p, int fp64_share16, cudaStream_t s);
 int element_df_block(const EParams &p);   // block size matching one tile's work items
 // same strategy with t = u D^T as a digit-split GEMM on the tcgen05 tensor
-// cores (FP64 accuracy); status receives BE_ETIMEOUT if a bounded wait expires
+// cores (every output certified within 1e-12 S, the rest recomputed in
+// FP64); status receives BE_ETIMEOUT if a bounded wait expires, wait_limit
+// is in SM cycles (0: about one second)
 bool element_tc_supported(const EParams &p, std::string &why);
-cudaError_t launch_element_tc(const EParams &p, int *status, cudaStream_t s);
+cudaError_t launch_element_tc(const EParams &p, int *status, long long wait_limit, cudaStream_t s);
 
 }  // namespace be

@@ -52,6 +52,9 @@ struct be_ctx {
   void *ws = nullptr;
   size_t ws_size = 0;
   int *status = nullptr;
+  // limit of the tensor-core kernels' pipeline waits in SM cycles (0: about
+  // one second); lowered only to exercise the BE_ETIMEOUT path
+  long long wait_limit = 0;
   // optional per-kernel timing: (kernel id, start, stop) event pairs
   bool timing = false;
   std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> marks;

@@ -35,6 +35,8 @@
 #include <cuda_runtime.h>
 
 #include "dense.hpp"
+#include "launch_attr.hpp"
+#include "tc_common.cuh"
 
 namespace be {
 
@@ -70,18 +72,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait; false when it gave up (or another thread already did)
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *status) {
-  long long start = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort_flag) return false;
-    if (clock64() - start > TIMEOUT_CYCLES) {
-      *abort_flag = 1;
-      atomicExch(status, 9);  // BE_ETIMEOUT
-      return false;
-    }
-  }
-  return true;
+// bounded wait (tc::mbar_wait: suspended between tries, the clock read
+// every eighth try); false when it gave up (or another thread already did)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *status,
+                                          long long limit) {
+  return tc::mbar_wait(bar, parity, abort_flag, status, limit);
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
@@ -165,7 +160,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     gemm_split_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                       const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
                       const int *__restrict__ sa, const int *__restrict__ sb, double *__restrict__ C, int64_t M,
-                      int64_t N, int64_t ldc, int nkb, int lolo, int hdrain, int *status) {
+                      int64_t N, int64_t ldc, int nkb, int lolo, int hdrain, int *status, long long limit) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *bars = (uint64_t *)(smem + STAGES * STAGE_BYTES);
@@ -204,16 +199,32 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
+      int last_kb[STAGES];
+      for (int s = 0; s < STAGES; ++s) last_kb[s] = -1;
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % STAGES;
         const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, status)) break;
+        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, status, limit)) break;
         uint8_t *st = smem + s * STAGE_BYTES;
         mbar_expect_tx(&full[s], STAGE_BYTES);
         tma_load_2d(st, &tmAh, &full[s], kb * BK, m0);
         tma_load_2d(st + TILE_BYTES, &tmAl, &full[s], kb * BK, m0);
         tma_load_2d(st + 2 * TILE_BYTES, &tmBh, &full[s], kb * BK, n0);
         tma_load_2d(st + 3 * TILE_BYTES, &tmBl, &full[s], kb * BK, n0);
+        last_kb[s] = kb;
+      }
+      // on an abort the MMA thread may not have consumed every stage: wait
+      // (bounded by the full limit, not the caller's) until the last copies
+      // issued into each stage have landed, so that none is outstanding when
+      // the CTA leaves
+      if (*abort_flag) {
+        for (int s = 0; s < STAGES; ++s) {
+          if (last_kb[s] < 0) continue;
+          const uint32_t par = (uint32_t)(last_kb[s] / STAGES) & 1u;
+          const long long t0 = clock64();
+          while (!mbar_try_wait(&full[s], par) && clock64() - t0 < TIMEOUT_CYCLES) {
+          }
+        }
       }
     }
   } else if (warp == 1) {
@@ -224,10 +235,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const bool hlast = (kb % hdrain) == hdrain - 1 || kb == nkb - 1;
         const bool lfirst = (kb % L_CHUNK) == 0;
         const bool llast = (kb % L_CHUNK) == L_CHUNK - 1 || kb == nkb - 1;
-        if (hfirst && !mbar_wait(&he[hb], ((uint32_t)(hc >> 1) & 1u) ^ 1u, abort_flag, status)) break;
-        if (lfirst && !mbar_wait(&le[lb], ((uint32_t)(lc >> 1) & 1u) ^ 1u, abort_flag, status)) break;
+        if (hfirst && !mbar_wait(&he[hb], ((uint32_t)(hc >> 1) & 1u) ^ 1u, abort_flag, status, limit)) break;
+        if (lfirst && !mbar_wait(&le[lb], ((uint32_t)(lc >> 1) & 1u) ^ 1u, abort_flag, status, limit)) break;
         const int s = kb % STAGES;
-        if (!mbar_wait(&full[s], (uint32_t)(kb / STAGES) & 1u, abort_flag, status)) break;
+        if (!mbar_wait(&full[s], (uint32_t)(kb / STAGES) & 1u, abort_flag, status, limit)) break;
         tc_fence_after();
         const uint32_t dh = tmem + (uint32_t)(hb * BN), dl = tmem + (uint32_t)(2 * BN + lb * BN);
         const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
@@ -264,7 +275,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const bool hlast = (kb % hdrain) == hdrain - 1 || kb == nkb - 1;
       const bool llast = (kb % L_CHUNK) == L_CHUNK - 1 || kb == nkb - 1;
       if (hlast) {
-        const bool got = mbar_wait(&hf[hb], (uint32_t)(hc >> 1) & 1u, abort_flag, status);
+        const bool got = mbar_wait(&hf[hb], (uint32_t)(hc >> 1) & 1u, abort_flag, status, limit);
         if (!__all_sync(0xffffffffu, got)) { ok = false; break; }   // warp-uniform before tcgen05.ld
         tc_fence_after();
         drain32(lane_base + (uint32_t)(hb * BN), hi, lo);
@@ -272,7 +283,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_arrive(&he[hb]);
       }
       if (llast) {
-        const bool gl = mbar_wait(&lf[lb], (uint32_t)(lc >> 1) & 1u, abort_flag, status);
+        const bool gl = mbar_wait(&lf[lb], (uint32_t)(lc >> 1) & 1u, abort_flag, status, limit);
         if (!__all_sync(0xffffffffu, gl)) { ok = false; break; }
         tc_fence_after();
         drain32(lane_base + (uint32_t)(2 * BN + lb * BN), hi, lo);
@@ -292,16 +303,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   }
 
-  // teardown: on an abort, wait (bounded) for this CTA's outstanding copies
-  // before the tensor memory is released
-  __syncthreads();
-  if (*abort_flag && threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      long long t0 = clock64();
-      while (!mbar_try_wait(&full[s], 0) && !mbar_try_wait(&full[s], 1) && clock64() - t0 < TIMEOUT_CYCLES / 4) {
-      }
-    }
-  }
+  // teardown: the copy thread has waited for its outstanding copies and the
+  // MMA thread for its MMAs (fin) before the tensor memory is released
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
@@ -579,7 +582,7 @@ cudaError_t dense_split_a(const DenseA &a, int64_t K, int64_t M_max, int64_t N, 
 }
 
 cudaError_t dense_split_gemm(const DenseA &a, int64_t N, int64_t K, int64_t M_max, double *C, int64_t ldc, void *ws,
-                             bool lolo, int hdrain, int *status, cudaStream_t s) {
+                             bool lolo, int hdrain, int *status, long long wait_limit, cudaStream_t s) {
   const int64_t Mp = (a.M + BM - 1) / BM * BM, Np = (N + BN - 1) / BN * BN, Kp = (K + BK - 1) / BK * BK;
   DenseWs w = dense_ws_layout(ws, M_max, N, K);
   cudaError_t e = cudaSuccess;
@@ -589,15 +592,13 @@ cudaError_t dense_split_gemm(const DenseA &a, int64_t N, int64_t K, int64_t M_ma
   if (!make_map(&mah, w.ah, Kp, Mp) || !make_map(&mal, w.al, Kp, Mp) || !make_map(&mbh, w.bh, Kp, Np) ||
       !make_map(&mbl, w.bl, Kp, Np))
     return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    e = cudaFuncSetAttribute(gemm_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  e = smem_limit_once((const void *)gemm_split_kernel, SMEM_BYTES, attr);
+  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)(Np / BN), (unsigned)(Mp / BM));
   gemm_split_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(mah, mal, mbh, mbl, w.sa, w.sb, C, a.M, N, ldc,
-                                                       (int)(Kp / BK), lolo ? 1 : 0, hdrain, status);
+                                                       (int)(Kp / BK), lolo ? 1 : 0, hdrain, status,
+                                                       wait_limit > 0 ? wait_limit : TIMEOUT_CYCLES);
   return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@
 // threads own (e, i) output points, so the stores of R_k[e, i] are
 // contiguous.
 #include "exec.hpp"
+#include "launch_attr.hpp"
 
 namespace be {
 
@@ -105,12 +106,9 @@ __global__ void __launch_bounds__(256) element_kernel(const __grid_constant__ EP
 cudaError_t launch_element(const EParams &p, int grid, int block, cudaStream_t s) {
   size_t smem = sizeof(double) * element_smem_words(p);
   if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t st = cudaFuncSetAttribute(element_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (st != cudaSuccess) return st;
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  cudaError_t st = smem_limit_once((const void *)element_kernel, 200 * 1024, attr);
+  if (st != cudaSuccess) return st;
   element_kernel<<<grid, block, smem, s>>>(p);
   return cudaGetLastError();
 }

@@ -12,6 +12,7 @@
 
 #include "df_math.cuh"
 #include "exec.hpp"
+#include "launch_attr.hpp"
 
 namespace be {
 
@@ -365,12 +366,9 @@ cudaError_t launch_element_df(const EParams &p, int grid, int block, cudaStream_
   if (p.tile_e % DF_EPT) return cudaErrorInvalidValue;          // element groups never straddle a tile
   const size_t smem = sizeof(float2) * (element_smem_words(p) + dfm::SIN2_N);
   if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t st = cudaFuncSetAttribute(element_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (st != cudaSuccess) return st;
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  cudaError_t st = smem_limit_once((const void *)element_df_kernel, 200 * 1024, attr);
+  if (st != cudaSuccess) return st;
   element_df_kernel<<<grid, block, smem, s>>>(p);
   return cudaGetLastError();
 }

@@ -2,8 +2,11 @@
 // element_kernel (R_k[e,i] = sum_{r,j} D[r,i,j] g_k[e,r] u[e,j], D shared by
 // all elements, Sec. "Batched einsums in DG-FEM Operators"), with the hoisted
 // contraction t[e,r,i] = sum_j D[r,i,j] u[e,j] evaluated as a GEMM on
-// tcgen05 (M = 128 elements, N = (i, r) pairs, K = j) to FP64 accuracy by
-// an error-free split of both operands into small integer digits:
+// tcgen05 (M = 128 elements, N = (i, r) columns, K = j) to FP64 accuracy by
+// an error-free split of both operands into small integer digits, and a
+// per-output check that sends the rare output it cannot certify to an FP64
+// recomputation, so that every result is within 1e-12 of the absolute
+// contraction S = sum |D| |g| |u| of Eq. (1).
 //
 //  * u[e, :] (one element, produced by the fused producer in double-float)
 //    is scaled by 2^-k_e so that every |v_j| <= 1 and written as six
@@ -12,22 +15,36 @@
 //    own 2^-k_n and digits c_p (D 2^-k_n = 2^-8 sum_p c_p 2^-9p, c_p 2^-9p
 //    stored), from the FP64 bits once per CTA.
 //  * sum_j D[n,j] u[e,j] = 2^(k_e + k_n - 8) sum_{p,q} sum_j (c_p 2^-9p)(d_q 2^(-8-9q)).
-//    The digit products are grouped by level L = p + q.  Levels 0..3 each
-//    accumulate in their own FP32 tensor-memory accumulator: every partial
-//    sum is an integer multiple of 2^(-8-9L) below 2^24 times that (at most 4 pairs
-//    x 64 terms x 2^16), so the tensor core adds them exactly.  Levels 4 and
-//    5 share a fifth accumulator (its truncation stays below 2^-49 of
-//    NJ max|u| max|D|); levels 6 and up are dropped (below 2^-50 of the same).
-//  * The epilogue adds the five accumulators of each column in double-float,
-//    applies the scales, contracts with g_k[e, :] in double-float and stores
-//    FP64.
-// Bound per output: |err| <= 2^-48 NJ max_j|u_j| sum_r |g_r| max_j|D_rij|
-// plus double-float rounding (about 2^-46 of the absolute contraction S).
-// The bound is normwise (the digits share one exponent per row): on dense
-// data of moderate dynamic range it is far below 1e-12 S (about 2e-15 S on
-// the DG workload), but for rows whose entries span many orders of
-// magnitude it can exceed 1e-12 S; element_df_kernel is the componentwise
-// path for such data.
+//    The digit products are grouped by level L = p + q <= 6, one FP32
+//    accumulator in tensor memory per level.  Levels 0..3 are exact (every
+//    partial sum is an integer multiple of 2^(-8-9L) below 2^24 of that
+//    unit: at most 4 pairs x 64 terms x 2^16), levels 4..6 are exact up to
+//    K = 42 and nearly so beyond; levels 7 and up are dropped (below
+//    2^-52 K of the scale).
+//  * Stacked issue: the six planes of D's digits of a column block are
+//    contiguous in shared memory, so one MMA with A = u's digit q and
+//    B = planes p = 0..P adds d_q c_p into the accumulators of levels
+//    q .. q + P at once (its N is (P + 1) x 32 columns, the accumulators of
+//    a block sit 32 columns apart).  A block takes 6 MMAs per K-slice of 16
+//    (plus one that starts the level-6 accumulator) instead of one per pair.
+//  * The epilogue adds the seven accumulators of each column in
+//    double-float, applies the scales, contracts with g_k[e, :] in
+//    double-float and stores FP64.
+//
+// Error and the check.  With every level exact, what remains is the
+// representation of the operands by six digits (2^-54 of the scale per
+// factor), the dropped levels and the double-float roundings: per column,
+// |t - t~| <= 2^(k_e+k_n-8) E_n with E_n = 2^-46 (sum_j |D_nj| 2^-k_n + K)
+// + 2^-42, plus relative roundings far below 1e-12.  Since
+// S >= sum_r |g_r| |t_r|, an output is certified when
+//     sum_r |g_r| (F E_n(r) 2^(k_e + k_n - 8) - |t~_r|) <= 0,
+// F = (1e-12 - 2^-43)^-1 with margins; the epilogue evaluates this sum for
+// every output.  On dense data of moderate range practically every output
+// passes (the margin is a factor of about 100 on N(0,1) data).  An element
+// with an output that fails, or whose scales leave the window |k| <= 24
+// where double-float keeps full precision, is recomputed in FP64 by the
+// epilogue warps at the end of its tile (one thread per u_j, per t_ri and
+// per output).  Elements that are all zero are exact and never flagged.
 //
 // Warp roles (512 threads, one CTA per SM, persistent over tiles of 128
 // elements):
@@ -35,25 +52,27 @@
 //    is produced while the MMAs of tile t run) in the 32-byte-swizzle
 //    K-major layout, reading a and b with coalesced loads and prefetching
 //    the next tile's rows into L2;
-//  * warp 7 issues the MMAs (one thread) into three tensor-memory slots of
-//    5 accumulators x 32 columns, one column block (two 16-column halves of
-//    16 / R values of i with their R terms) per slot.  Every accumulator
-//    starts on a 32-column boundary: with accumulators at 48-column offsets,
-//    MMAs issued back to back into neighbouring accumulators gave wrong sums
-//    on B300 (correct when the issue was slowed down);
+//  * warp 7 issues the MMAs (one thread) into two tensor-memory slots of
+//    7 accumulators x 32 columns (every accumulator on a 32-column
+//    boundary), one column block (two 16-column halves of 16 / R values of
+//    i with their R terms) per slot;
 //  * warps 8-15 drain a slot (two warps per TMEM lane quarter, one per half
-//    of the block) while the next blocks accumulate, and write the outputs.
-// D's digit planes are built once per CTA with integer arithmetic on the
-// FP64 bits (no FP64 instruction).  Every wait is bounded: on expiry the
-// CTA records BE_ETIMEOUT, stops issuing and frees its tensor memory after
-// its MMAs complete.
+//    of the block) while the next block accumulates, write the outputs and
+//    run the per-output check.
+// Every wait is bounded (a limit in SM cycles that the caller may lower):
+// on expiry the CTA records BE_ETIMEOUT, every role leaves its loop
+// collectively, and the tensor memory is freed only after all issued MMAs
+// have completed.
 #include <algorithm>
+#include <atomic>
+#include <cmath>
 #include <type_traits>
 
 #include <cuda_bf16.h>
 
 #include "df_math.cuh"
 #include "exec.hpp"
+#include "launch_attr.hpp"
 #include "tc_common.cuh"
 
 namespace be {
@@ -64,32 +83,60 @@ using dfm::df;
 
 constexpr int TC_M = 128;                       // elements per tile
 constexpr int TC_P = 6;                         // digits per operand
-constexpr int TC_LEV = 5;                       // accumulators per column block
-constexpr int TC_NCOL = 32;                     // accumulator columns per level (32-column aligned)
-constexpr int TC_SLOT = TC_LEV * TC_NCOL;       // 160 columns per slot
-constexpr int TC_NSLOT = 3;                     // 480 of the 512 tensor-memory columns
-constexpr int TC_KU = 8;                        // buffers of per-element row scales
+constexpr int TC_LEV = 7;                       // levels 0..6, one accumulator each
+constexpr int TC_NCOL = 32;                     // columns of a block (and of an accumulator)
+constexpr int TC_SLOT = TC_LEV * TC_NCOL;       // 224 columns per slot
+constexpr int TC_NSLOT = 2;                     // 448 of the 512 tensor-memory columns
+constexpr int TC_KU = 4;                        // buffers of per-element row scales
 constexpr int NPROD = 224, NEPI = 256;
 constexpr int MMA_WARP = NPROD / 32;            // 7
 constexpr int TC_THREADS = NPROD + 32 + NEPI;   // producer warps 0-6, MMA warp 7, epilogue warps 8-15
 constexpr int TC_MAXROWS = 4;                   // einsums (rows) per launch
-constexpr int TC_MAXNB = 160;                   // B rows (all column blocks)
+constexpr int TC_MAXCB = 8;                     // column blocks
+constexpr int TC_BPLANE = TC_NCOL * 32;         // bytes of one digit plane of a block and K-slice
+constexpr int KU_ZERO = -126;                   // row-scale code of an element that is all zero
+constexpr int TC_WIN = 24;                      // scale window |k| <= TC_WIN of the certified path
+constexpr size_t TC_SMEM_LIMIT = 227 * 1024;
 
-// the 21 digit products (level, digit of D, digit of u) with level <= 5, in
-// accumulator order: levels 0..3 alone, levels 4 and 5 into accumulator 4
 struct TcParams {
   EParams p;
   int *status;
-  int ncb, IB, NBtot, KS, NG;                   // column blocks, i per block, B rows, K steps, j groups of 8
-  int ncol[8], n0[8];                           // per block: MMA N and first B row
+  long long wait_limit;                         // SM cycles before a wait gives up
+  int ncb, IB, KS, NG, NB;                      // column blocks, i per block, K-slices of 16, j groups of 8, B rows
+  double fcheck;                                // F of the per-output check (margins included)
 };
 
-// scale exponent k with |x| < 2^k for the largest |x| of a row, clamped so
-// that the scaled values stay in FP32's normal range
-__device__ __forceinline__ int row_exp(double mx) {
-  const int ex = (int)((__double_as_longlong(mx) >> 52) & 0x7FF);
+// byte offsets of the shared-memory regions (from a 256-byte aligned base)
+struct TcSmem {
+  uint32_t b, a, sin, kD, kDs, zc, kU, mxw, fm, fu, ft, bars, misc, total;
+};
+__host__ __device__ inline TcSmem tc_smem(const TcParams &tp) {
+  TcSmem s;
+  uint32_t o = 0;
+  s.b = o;    o += (uint32_t)(tp.ncb * tp.KS * TC_P * TC_BPLANE);
+  s.a = o;    o += (uint32_t)(2 * TC_P * tp.KS * TC_M * 32);
+  s.sin = o;  o += (uint32_t)(sizeof(float2) * dfm::SINH_N);
+  s.kD = o;   o += 4u * tp.NB;
+  s.kDs = o;  o += 4u * tp.NB;
+  s.zc = o;   o += 4u * tp.NB;
+  s.kU = o;   o += 4u * TC_KU * TC_M;
+  s.mxw = o;  o += 4u * TC_M;
+  s.fm = o;   o += 4u * 8;                      // two 128-bit masks of flagged elements
+  s.fu = o;   o += 8u * (uint32_t)((tp.p.NJ + 1) & ~1);
+  s.ft = o;   o += 8u * (uint32_t)(tp.p.R * tp.p.NI);
+  s.bars = o; o += 8u * 9;
+  s.misc = o; o += 16;
+  s.total = o;
+  return s;
+}
+
+// scale exponent k with |x| < 2^k for a row maximum given by the high word
+// of its FP64 bits, clamped to [-100, 100] (the scaled values stay in
+// FP32's normal range)
+__device__ __forceinline__ int row_exp_hw(int hw) {
+  const int ex = (hw >> 20) & 0x7FF;
   if (ex == 0) return -100;
-  return min(100, max(-100, ex - 1023 + 1));
+  return min(100, max(-100, ex - 1022));
 }
 __device__ __forceinline__ float pow2f(int k) { return __uint_as_float((uint32_t)(k + 127) << 23); }   // |k| <= 126
 
@@ -123,13 +170,15 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 
 // Operand planes are K-major in the 32-byte-swizzle layout: for each slice
 // of 16 values of K (one MMA K-step) the rows are 32 bytes long and packed,
-// 8-row groups 256 bytes apart, slices rows * 32 bytes apart; within an
-// 8-row group the two 16-byte halves of a row swap places when the row's
-// bit 2 is set.  One MMA K-step thus reads one contiguous block.
-// Byte offset of the 16-byte chunk g (values 8g .. 8g+7 of K) of row m in a
-// plane of `rows` rows (256-byte aligned):
+// 8-row groups 256 bytes apart; within an 8-row group the two 16-byte halves
+// of a row swap places when the row's bit 2 is set.  Byte offset of the
+// 16-byte chunk h (values 8h .. 8h+7 of the slice) of row m:
+__device__ __forceinline__ uint32_t sw32_row(int m, int h) {
+  return (uint32_t)((m >> 3) * 256 + (m & 7) * 32 + (((h & 1) ^ ((m >> 2) & 1)) << 4));
+}
+// u's planes: plane q holds KS slices of 128 rows; chunk g of row m
 __device__ __forceinline__ uint32_t sw32(int rows, int m, int g) {
-  return (uint32_t)((g >> 1) * rows * 32 + (m >> 3) * 256 + (m & 7) * 32 + (((g & 1) ^ ((m >> 2) & 1)) << 4));
+  return (uint32_t)((g >> 1) * rows * 32) + sw32_row(m, g);
 }
 
 // high word of a bound on |u| for the row scale (|sin a| <= 1); for a
@@ -173,15 +222,17 @@ __device__ __forceinline__ void prefetch_rows(const EView &v, int64_t e1, int te
 
 // six balanced base-512 digits of x * 2^-k (|x| < 2^k), each times 2^-9q,
 // by integer arithmetic on the bits of x: X = round(x * 2^(53 - k)) is split
-// from the bottom, d = ((X + 256) mod 512) - 256, X = (X - d) / 512
+// from the bottom, d = ((X + 256) mod 512) - 256, X = (X - d) / 512.  A value
+// at or above 2^k (possible only in a row whose scale was clamped; such rows
+// never reach a certified output) gives digits of zero.
 __device__ __forceinline__ void digits_bits(double x, int k, float *d) {
   const long long b = __double_as_longlong(x);
   int ex = (int)((b >> 52) & 0x7FF);
   long long m = b & 0xFFFFFFFFFFFFFll;
   if (ex == 0) ex = 1;
   else m |= 1ll << 52;
-  const int sh = 1022 + k - ex;                          // >= 0 since |x| < 2^k
-  long long X = sh >= 63 ? 0 : (sh == 0 ? m : ((m >> (sh - 1)) + 1) >> 1);
+  const int sh = 1022 + k - ex;
+  long long X = (sh >= 63 || sh < 0) ? 0 : (sh == 0 ? m : ((m >> (sh - 1)) + 1) >> 1);
   if (b < 0) X = -X;
 #pragma unroll
   for (int q = TC_P - 1; q > 0; --q) {
@@ -193,23 +244,23 @@ __device__ __forceinline__ void digits_bits(double x, int k, float *d) {
 }
 
 // the fused producer's value in double-float: a, a * b or sin(a) * b (the
-// conversions stay off the FP64 pipe, which the epilogue's output sums use)
-__device__ __forceinline__ df produce(const EProd &q, double a, double b, const float2 *sin_tab) {
+// conversions stay off the FP64 pipe, which the output sums use); out of
+// line, since only batches with an operand outside the fast range take it
+static __device__ __noinline__ df produce(const EProd &q, double a, double b, const float2 *sin_tab) {
   if (q.kind == 0) return dfm::df_from_double(a);
   if (q.kind == 2) return dfm::df_mul(dfm::df_from_double(a), dfm::df_from_double(b));
-  return dfm::df_mul(dfm::df_sin_tab2(a, sin_tab), dfm::df_from_double(b));
+  return dfm::df_mul(dfm::df_sin_half(a, sin_tab), dfm::df_from_double(b));
 }
 
 // the producer without range tests or out-of-line calls, for operands that
 // produce_fast_ok accepted: a batch whose operands all pass runs as one
-// straight-line block (the tested variant's rare-case branches and calls
-// split the block and cost about a fifth of the kernel's time)
+// straight-line block
 template <bool FAST>
 __device__ __forceinline__ df produce_t(const EProd &q, double a, double b, const float2 *sin_tab) {
   if (!FAST) return produce(q, a, b, sin_tab);
   if (q.kind == 0) return dfm::df_from_double_fast(a);
   if (q.kind == 2) return dfm::df_mul(dfm::df_from_double_fast(a), dfm::df_from_double_fast(b));
-  return dfm::df_mul(dfm::df_sin_tab2_fast(a, sin_tab), dfm::df_from_double_fast(b));
+  return dfm::df_mul(dfm::df_sin_half_fast(a, sin_tab), dfm::df_from_double_fast(b));
 }
 __device__ __forceinline__ bool produce_fast_ok(const EProd &q, double a, double b) {
   if (q.kind == 0) return dfm::df_fast_ok(a);
@@ -217,8 +268,9 @@ __device__ __forceinline__ bool produce_fast_ok(const EProd &q, double a, double
   return dfm::sin_fast_ok(a) && dfm::df_fast_ok(b);
 }
 
-// named barrier of the producer warps, and the same barrier returning
-// the AND of a predicate over them (so that all of them leave together)
+// named barriers: 1 for the producer warps, 2 for the epilogue warps (the
+// .red forms return the AND / OR of a predicate over the participants, so
+// that a role leaves its loop together)
 __device__ __forceinline__ void prod_sync() { asm volatile("bar.sync 1, 224;" ::: "memory"); }
 __device__ __forceinline__ bool prod_all(bool v) {
   uint32_t r;
@@ -228,20 +280,68 @@ __device__ __forceinline__ bool prod_all(bool v) {
                : "memory");
   return r != 0;
 }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
+__device__ __forceinline__ bool epi_any(bool v) {
+  uint32_t r;
+  asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 2, 256, q;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(r)
+               : "r"((uint32_t)v)
+               : "memory");
+  return r != 0;
+}
 
 // Columns of a block: two halves of 16, each holding H0 = 16 / R values of
 // i with their R terms (column = il * R + r) and zero padding after them, so
-// that an epilogue thread's half never splits an i.  B row n -> (i, r).
+// that an epilogue thread's half never splits an i.  B row n (block n / 32,
+// column n mod 32) -> (i, r); false for a padding column.
 template <int R>
 __device__ __forceinline__ bool brow(const TcParams &tp, int n, int &i, int &r) {
   constexpr int H0 = 16 / R;
-  int cb = 0;
-  while (cb + 1 < tp.ncb && n >= tp.n0[cb + 1]) ++cb;
-  const int c = n - tp.n0[cb], h = c >> 4, cc = c & 15;
+  const int cb = n >> 5, c = n & 31, h = c >> 4, cc = c & 15;
   r = cc % R;
   const int il = cc / R;
   i = cb * 2 * H0 + h * H0 + il;
   return il < H0 && i < tp.p.NI;
+}
+
+// |k| of a scale outside the certified window
+__device__ __forceinline__ bool out_of_window(int k) { return k < -TC_WIN || k > TC_WIN; }
+
+// FP64 recomputation of every output of element e by the 256 epilogue
+// threads (et = 0..255): u_j, then t[r, i] = sum_j D[r, i, j] u_j, then
+// R_k[e, i] = sum_r g_k[e, r] t[r, i]; each value by one thread in FP64
+// (dot products of at most 64 terms, error far below 1e-12 S)
+static __device__ __noinline__ void fallback_element(const EParams &p, int64_t e, int et, double *fu, double *ft) {
+  const EProd &q = p.groups[0];
+  if (et < p.NJ) {
+    const double a = q.a.ptr[e * q.a.se + et * q.a.sk];
+    double u = a;
+    if (q.kind != 0) {
+      const double b = q.b.ptr[e * q.b.se + et * q.b.sk];
+      u = q.kind == 1 ? sin(a) * b : a * b;
+    }
+    fu[et] = u;
+  }
+  epi_sync();
+  for (int n = et; n < p.R * p.NI; n += NEPI) {
+    const int r = n / p.NI, i = n - r * p.NI;
+    const double *d = p.D + r * p.sr + i * p.si;
+    double s = 0.0;
+    for (int j = 0; j < p.NJ; ++j) s = fma(d[j * p.sj], fu[j], s);
+    ft[n] = s;
+  }
+  epi_sync();
+  for (int o = et; o < p.n_rows * p.NI; o += NEPI) {
+    const int k = o / p.NI, i = o - k * p.NI;
+    double v = ft[i];
+    if (p.has_g) {
+      const EView &g = p.rows[k].g;
+      v = 0.0;
+      for (int r = 0; r < p.R; ++r) v = fma(g.ptr[e * g.se + r * g.sk], ft[r * p.NI + i], v);
+    }
+    p.rows[k].out[e * p.NI + i] = v;
+  }
+  epi_sync();
 }
 
 // ROWS: the number of einsums when specialized, 0 for any count up to 4
@@ -252,39 +352,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
   constexpr int IB = 2 * H0;                    // i per column block
   const EParams &p = tp.p;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t *Bp = smem;                                       // TC_P planes x NBtot rows x 128 B
-  const int bplane = tp.KS * tp.NBtot * 32;                 // bytes per digit plane of D
-  const int aplane = tp.KS * TC_M * 32;                     // bytes per digit plane of u
-  uint8_t *Ap = Bp + TC_P * bplane;                         // 2 buffers x TC_P planes x KS slices x 128 rows x 32 B
-  float2 *sin_tab = (float2 *)(Ap + 2 * TC_P * aplane);     // full-circle sine table
-  int *kD = (int *)(sin_tab + dfm::SIN2_N);                 // [TC_MAXNB]
-  float *kDs = (float *)(kD + TC_MAXNB);                    // [TC_MAXNB] 2^kD
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 255) & ~(uintptr_t)255);
+  const TcSmem SL = tc_smem(tp);
+  uint8_t *Bp = smem + SL.b;                                // [cb][ks][plane p][32 rows][32 B]
+  uint8_t *Ap = smem + SL.a;                                // [buffer][plane q][ks][128 rows][32 B]
+  float2 *sin_tab = (float2 *)(smem + SL.sin);              // half-circle sine table
+  int *kD = (int *)(smem + SL.kD);                          // [NB] scale exponent of each row of D
+  float *kDs = (float *)(smem + SL.kDs);                    // [NB] 2^kD
+  float *zc = (float *)(smem + SL.zc);                      // [NB] check term F E_n 2^kD
   // Row scales of u for the last TC_KU tiles: the epilogue can trail the
-  // producer by up to 2 + ceil(3 / ncb) tiles (two digit buffers ahead of
-  // the MMAs, which run at most three column blocks ahead of the epilogue)
-  int *kU = (int *)(kDs + TC_MAXNB);                        // [TC_KU][TC_M]
-  int *mxw = kU + TC_KU * TC_M;                             // [TC_M] high words of the row bounds
-  uint64_t *bars = (uint64_t *)(mxw + TC_M);
-  uint64_t *a_full = bars, *a_empty = bars + 2, *s_full = bars + 4, *s_empty = bars + 4 + TC_NSLOT;
-  uint64_t *fin = bars + 4 + 2 * TC_NSLOT;
-  uint32_t *tmem_slot = (uint32_t *)(fin + 1);
+  // producer by up to 2 + ceil(2 / ncb) tiles (two digit buffers ahead of
+  // the MMAs, which run at most two column blocks ahead of the epilogue)
+  int *kU = (int *)(smem + SL.kU);                          // [TC_KU][TC_M]
+  int *mxw = (int *)(smem + SL.mxw);                        // [TC_M] high words of the row bounds
+  uint32_t *fmask = (uint32_t *)(smem + SL.fm);             // [2][4] flagged elements of a tile
+  double *fu = (double *)(smem + SL.fu);                    // [NJ] FP64 recomputation: u
+  double *ft = (double *)(smem + SL.ft);                    // [R * NI] FP64 recomputation: t
+  uint64_t *bars = (uint64_t *)(smem + SL.bars);
+  uint64_t *a_full = bars, *a_empty = bars + 2, *s_full = bars + 4, *s_empty = bars + 6, *fin = bars + 8;
+  uint32_t *tmem_slot = (uint32_t *)(smem + SL.misc);
   volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int NJ = p.NJ, NI = p.NI;
+  const int aplane = tp.KS * TC_M * 32;                     // bytes per digit plane of u
+  const long long limit = tp.wait_limit;
 
   if (tid == 0) {
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&a_full[b], NPROD);
       tc::mbar_init(&a_empty[b], 1);
-    }
-    for (int b = 0; b < TC_NSLOT; ++b) {
       tc::mbar_init(&s_full[b], 1);
       tc::mbar_init(&s_empty[b], NEPI);
     }
     tc::mbar_init(fin, 1);
     *abort_flag = 0;
+    for (int k = 0; k < 8; ++k) fmask[k] = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == MMA_WARP) {
@@ -294,39 +397,63 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
   // zero both operand regions (K padding and padding rows stay zero)
   {
     uint4 *z = (uint4 *)smem;
-    const int n16 = (TC_P * bplane + 2 * TC_P * aplane) / 16;
+    const int n16 = (int)(SL.a + 2 * TC_P * aplane) / 16;
     for (int k = tid; k < n16; k += TC_THREADS) z[k] = make_uint4(0u, 0u, 0u, 0u);
   }
-  dfm::sin2_table_fill(sin_tab);
-  // B row n -> (i, r); scale exponent per real row
-  for (int n = tid; n < tp.NBtot; n += TC_THREADS) {
+  dfm::sin_half_table_fill(sin_tab, tid, TC_THREADS);
+  // per row n of D: scale exponent, 2^k, and the check term
+  //   zc = F 2^k (2^-46 (sum_j |D_nj| 2^-k + K) + 2^-42) (1 + 2^-20)
+  // (0 for a row of zeros, which is exact; infinite for a row whose scale
+  // leaves the window, so that every output using it is recomputed)
+  for (int n = tid; n < tp.NB; n += TC_THREADS) {
     int i, r;
     int hw = 0;
-    if (brow<R>(tp, n, i, r))
-      for (int j = 0; j < NJ; ++j) hw = max(hw, __double2hiint(p.D[r * p.sr + i * p.si + j * p.sj]) & 0x7FFFFFFF);
-    kD[n] = row_exp(__hiloint2double(hw, 0));
-    kDs[n] = pow2f(kD[n]);
+    double sabs = 0.0;
+    if (brow<R>(tp, n, i, r)) {
+      const double *d = p.D + r * p.sr + i * p.si;
+      for (int j = 0; j < NJ; ++j) {
+        const double x = d[j * p.sj];
+        hw = max(hw, __double2hiint(x) & 0x7FFFFFFF);
+        sabs += fabs(x);
+      }
+    }
+    const int k = row_exp_hw(hw);
+    kD[n] = k;
+    kDs[n] = pow2f(k);
+    float z = 0.0f;
+    if (hw != 0) {
+      if (out_of_window(k)) {
+        z = __int_as_float(0x7F800000);
+      } else {
+        const double sd = sabs * ldexp(1.0, -k);
+        z = (float)(tp.fcheck * ldexp(1.0, k) * (ldexp(sd + NJ, -46) + ldexp(1.0, -42)) * (1.0 + ldexp(1.0, -20)));
+      }
+    }
+    zc[n] = z;
   }
   __syncthreads();
   // digit planes of D: item (row n, group g of 8 values of j)
-  for (int item = tid; item < tp.NBtot * tp.NG; item += TC_THREADS) {
+  for (int item = tid; item < tp.NB * tp.NG; item += TC_THREADS) {
     const int n = item / tp.NG, g = item % tp.NG;
     int i, r;
     if (!brow<R>(tp, n, i, r)) continue;
     const int kn = kD[n];
+    const double *d = p.D + r * p.sr + i * p.si;
     uint32_t w[TC_P][4];
 #pragma unroll
     for (int jp = 0; jp < 4; ++jp) {
       float d0[TC_P], d1[TC_P];
       const int j = g * 8 + 2 * jp;
-      digits_bits(j < NJ ? p.D[r * p.sr + i * p.si + j * p.sj] : 0.0, kn, d0);
-      digits_bits(j + 1 < NJ ? p.D[r * p.sr + i * p.si + (j + 1) * p.sj] : 0.0, kn, d1);
+      digits_bits(j < NJ ? d[j * p.sj] : 0.0, kn, d0);
+      digits_bits(j + 1 < NJ ? d[(j + 1) * p.sj] : 0.0, kn, d1);
 #pragma unroll
       for (int q = 0; q < TC_P; ++q) w[q][jp] = pack_bf16(d0[q], d1[q]);
     }
+    const int cb = n >> 5, nl = n & 31, ks = g >> 1;
+    const uint32_t base = (uint32_t)((cb * tp.KS + ks) * TC_P) * TC_BPLANE + sw32_row(nl, g & 1);
 #pragma unroll
     for (int q = 0; q < TC_P; ++q)
-      *(uint4 *)(Bp + q * bplane + sw32(tp.NBtot, n, g)) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+      *(uint4 *)(Bp + base + q * TC_BPLANE) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
   }
   tc::fence_proxy_async();
   tc::fence_before();
@@ -357,11 +484,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
       }
       if (tid < TC_M) mxw[tid] = 0;
       prod_sync();
-      constexpr int NPW = NPROD / 32;
-      for (int r0 = warp; r0 < te; r0 += NPW * 4) {
-        int hw[4];
+      // RB rows per warp per round (a larger round, 10, measured 7 % slower)
+      constexpr int NPW = NPROD / 32, RB = 4;
+      for (int r0 = warp; r0 < te; r0 += NPW * RB) {
+        int hw[RB];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < RB; ++u) {
           const int row = r0 + NPW * u;
           const bool okr = row < te;
           const int h0 = (okr && lane < NJ) ? bound_hw(q, e0 + row, lane) : 0;
@@ -369,16 +497,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
           hw[u] = max(h0, h1);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < RB; ++u) {
           const int h = __reduce_max_sync(0xffffffffu, hw[u]);
           if (lane == 0 && r0 + NPW * u < te) mxw[r0 + NPW * u] = h;
         }
       }
       const int ab = t & 1;
       const uint32_t use = (uint32_t)(t >> 1);
-      if (!prod_all(tc::mbar_wait(&a_empty[ab], (use & 1u) ^ 1u, abort_flag, status))) break;
+      if (!prod_all(tc::mbar_wait(&a_empty[ab], (use & 1u) ^ 1u, abort_flag, status, limit))) break;
       int *ku = kU + (t & (TC_KU - 1)) * TC_M;
-      if (tid < TC_M) ku[tid] = row_exp(__hiloint2double(mxw[tid], 0));
+      if (tid < TC_M) ku[tid] = mxw[tid] == 0 ? KU_ZERO : row_exp_hw(mxw[tid]);
       prod_sync();
       uint8_t *A = Ap + ab * TC_P * aplane;
       // pairs per row; g / JP as (g * jinv) >> 20, exact for g < 2^12, JP <= 32
@@ -433,46 +561,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
   } else if (warp == MMA_WARP) {
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
-      const uint32_t bbase = tc::smem_u32(Bp);
       const uint64_t adesc0 = tc::sdesc_sw32(tc::smem_u32(Ap));
+      const uint64_t bdesc0 = tc::sdesc_sw32(tc::smem_u32(Bp));
       int t = 0;
       int64_t cnt = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++t) {
         const int ab = t & 1;
-        if (!tc::mbar_wait(&a_full[ab], (uint32_t)(t >> 1) & 1u, abort_flag, status)) break;
+        if (!tc::mbar_wait(&a_full[ab], (uint32_t)(t >> 1) & 1u, abort_flag, status, limit)) break;
         const uint64_t adesc = adesc0 + (uint64_t)((ab * TC_P * aplane) >> 4);
         tc::fence_after();
         for (int cb = 0; cb < tp.ncb; ++cb, ++cnt) {
-          const int slot = (int)(cnt % TC_NSLOT);
-          const uint32_t use = (uint32_t)(cnt / TC_NSLOT);
-          if (!tc::mbar_wait(&s_empty[slot], (use & 1u) ^ 1u, abort_flag, status)) { ok = false; break; }
+          const int slot = (int)(cnt & 1);
+          const uint32_t use = (uint32_t)(cnt >> 1);
+          if (!tc::mbar_wait(&s_empty[slot], (use & 1u) ^ 1u, abort_flag, status, limit)) { ok = false; break; }
           tc::fence_after();
-          const uint32_t idesc = tc::idesc_bf16(TC_M, tp.ncol[cb]);
           const uint32_t dslot = tmem + (uint32_t)(slot * TC_SLOT);
           // descriptors differ only in the start-address field (bits 0-13,
           // address >> 4), which stays below 2^14 for every operand here
-          const uint64_t bblk = tc::sdesc_sw32(bbase + (uint32_t)(tp.n0[cb] * 32));
-          // the 21 digit products with p + q <= 5 (p digit of D, q digit of
-          // u): level L < 4 into accumulator L, levels 4 and 5 into
-          // accumulator 4; the pair filter is resolved at compile time
+          for (int ks = 0; ks < tp.KS; ++ks) {
+            const uint64_t bks = bdesc0 + (uint64_t)(((cb * tp.KS + ks) * TC_P * TC_BPLANE) >> 4);
+            const uint64_t aks = adesc + (uint64_t)((ks * TC_M * 32) >> 4);
+            // u's digit q times D's planes p = 0 .. min(5, 6 - q) into the
+            // accumulators of levels q .. q + p (32 columns apart); the first
+            // MMA of a block overwrites levels 0..5, the level-6 accumulator
+            // is started by its own MMA (q = 1, p = 5)
 #pragma unroll
-          for (int L = 0; L < TC_LEV; ++L) {
-#pragma unroll
-            for (int pd = 0; pd < TC_P; ++pd) {
-#pragma unroll
-              for (int qd = 0; qd < TC_P; ++qd) {
-                const int lev = pd + qd;
-                if (L < TC_LEV - 1 ? lev != L : (lev < TC_LEV - 1 || lev > TC_LEV)) continue;
-                const bool first = pd == 0 && qd == L;     // first pair of accumulator L
-                const uint32_t d = dslot + (uint32_t)(L * TC_NCOL);
-                const uint64_t da = adesc + (uint64_t)((qd * aplane) >> 4);
-                const uint64_t db = bblk + (uint64_t)((pd * bplane) >> 4);
-#pragma unroll
-                for (int ks = 0; ks < 4; ++ks)
-                  if (ks < tp.KS)
-                    tc::mma_bf16(d, da + (uint64_t)(ks * (TC_M * 32 >> 4)), db + (uint64_t)(ks * (tp.NBtot * 32 >> 4)), idesc,
-                                 (first && ks == 0) ? 0u : 1u);
+            for (int qd = 0; qd < TC_P; ++qd) {
+              const uint64_t aq = aks + (uint64_t)((qd * aplane) >> 4);
+              if (qd == 0) {
+                tc::mma_bf16(dslot, aq, bks, tc::idesc_bf16(TC_M, 6 * TC_NCOL), ks > 0 ? 1u : 0u);
+              } else if (qd == 1 && ks == 0) {
+                tc::mma_bf16(dslot + 6 * TC_NCOL, aq, bks + (uint64_t)((5 * TC_BPLANE) >> 4), tc::idesc_bf16(TC_M, TC_NCOL), 0u);
+                tc::mma_bf16(dslot + TC_NCOL, aq, bks, tc::idesc_bf16(TC_M, 5 * TC_NCOL), 1u);
+              } else {
+                const int np_ = qd == 1 ? 6 : 7 - qd;    // planes p = 0 .. np_ - 1
+                tc::mma_bf16(dslot + (uint32_t)(qd * TC_NCOL), aq, bks, tc::idesc_bf16(TC_M, np_ * TC_NCOL), 1u);
               }
             }
           }
@@ -490,31 +614,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
     // ------------------------------------------------------------ epilogue
     const int quarter = warp & 3, half = (warp - MMA_WARP - 1) >> 2;
     const int m = quarter * 32 + lane;
+    const int et = tid - (NPROD + 32);                      // 0..255
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * (TC_NCOL / 2));
     const int n_rows = p.n_rows;
     int t = 0;
     int64_t cnt = 0;
-    bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++t) {
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++t) {
       const int64_t e = tile * TC_M + m;
       const bool valid = e < p.E;
       // g_k[e, r] of this thread's element as double-float (scaled by
-      // 2^(k_e - 16) once the tile's exponents are known)
+      // 2^(k_e - 8) once the tile's exponents are known); g outside the
+      // window flags the element
       df gk[KR][R];
+      bool flag = false;
 #pragma unroll
       for (int k = 0; k < KR; ++k)
 #pragma unroll
-        for (int r = 0; r < R; ++r)
-          gk[k][r] = dfm::df_from_double(
-              (valid && (ROWS || k < n_rows)) ? (p.has_g ? p.rows[k].g.ptr[e * p.rows[k].g.se + r * p.rows[k].g.sk] : 1.0) : 0.0);
+        for (int r = 0; r < R; ++r) {
+          const double g =
+              (valid && (ROWS || k < n_rows)) ? (p.has_g ? p.rows[k].g.ptr[e * p.rows[k].g.se + r * p.rows[k].g.sk] : 1.0) : 0.0;
+          const int hg = __double2hiint(g) & 0x7FFFFFFF;
+          flag |= hg != 0 && out_of_window(((hg >> 20) & 0x7FF) - 1023);
+          gk[k][r] = dfm::df_from_double(g);
+        }
+      bool zero_el = false;
+      float mx = 0.0f;                                      // largest check value of this thread's outputs
+      bool ok = true;
       for (int cb = 0; cb < tp.ncb; ++cb, ++cnt) {
-        const int slot = (int)(cnt % TC_NSLOT);
-        const uint32_t use = (uint32_t)(cnt / TC_NSLOT);
-        const bool got = tc::mbar_wait(&s_full[slot], use & 1u, abort_flag, status);
-        if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+        const int slot = (int)(cnt & 1);
+        const uint32_t use = (uint32_t)(cnt >> 1);
+        if (ok) ok = __all_sync(0xffffffffu, tc::mbar_wait(&s_full[slot], use & 1u, abort_flag, status, limit));
+        if (!ok) continue;                                 // aborting: the tile-end barrier is still reached
         tc::fence_after();
         if (cb == 0) {
-          const float sg = pow2f(kU[(t & (TC_KU - 1)) * TC_M + m] - 8);
+          const int ke = kU[(t & (TC_KU - 1)) * TC_M + m];
+          zero_el = ke == KU_ZERO;
+          flag |= !zero_el && out_of_window(ke);
+          const float sg = pow2f(max(ke, -100) - 8);
 #pragma unroll
           for (int k = 0; k < KR; ++k)
 #pragma unroll
@@ -523,8 +659,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
         const int nI = min(IB, NI - cb * IB);
         const int nIh = max(0, min(H0, nI - half * H0));      // i of this half (warp-uniform)
         const int nch = (nIh * R + 7) >> 3;                      // 8-column chunks holding them
-        // t for this half's columns: 5 accumulators per column added in
-        // double-float, times 2^k_n of the column's row of D
+        const int nb = cb * TC_NCOL + half * (TC_NCOL / 2);      // first B row of this half
+        // t for this half's columns: the 7 level accumulators of a column
+        // added in double-float (levels 0-1 and 2-3 by TwoSum, the pairs
+        // combined, levels 4-6 into the low part), times 2^k_n
         float th[16], tl[16];
 #pragma unroll
         for (int ch = 0; ch < 2; ++ch) {
@@ -543,33 +681,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
             for (int c = 0; c < 8; ++c) {
               if (ch * 8 + c >= H0 * R) continue;              // padding column of the half
               const df s01 = dfm::two_sum(__uint_as_float(v[0][c]), __uint_as_float(v[1][c]));
-              df s23 = dfm::two_sum(__uint_as_float(v[2][c]), __uint_as_float(v[3][c]));
-              s23.lo += __uint_as_float(v[4][c]);
-              const df x = dfm::df_add(s01, s23);
-              const float sc = kDs[min(tp.n0[cb] + half * 16 + ch * 8 + c, tp.NBtot - 1)];
+              const df s23 = dfm::two_sum(__uint_as_float(v[2][c]), __uint_as_float(v[3][c]));
+              const float s46 = (__uint_as_float(v[4][c]) + __uint_as_float(v[5][c])) + __uint_as_float(v[6][c]);
+              df s = dfm::two_sum(s01.hi, s23.hi);
+              s.lo += (s01.lo + s23.lo) + s46;
+              const df x = dfm::fast_two_sum(s.hi, s.lo);
+              const float sc = kDs[nb + ch * 8 + c];
               th[ch * 8 + c] = x.hi * sc;
               tl[ch * 8 + c] = x.lo * sc;
-            }
-          }
-        }
-        if (valid) {
-#pragma unroll
-          for (int il = 0; il < H0; ++il) {
-            if (il < nIh) {
-              const int i = cb * IB + half * H0 + il;
-#pragma unroll
-              for (int k = 0; k < KR; ++k) {
-                if (ROWS || k < n_rows) {
-                  // first term: its exact product starts the pair (s, c)
-                  const df g0 = gk[k][0], t0{th[il * R], tl[il * R]};
-                  float s = g0.hi * t0.hi;
-                  float c = fmaf(g0.hi, t0.lo, fmaf(g0.lo, t0.hi, fmaf(g0.hi, t0.hi, -s)));
-#pragma unroll
-                  for (int r = 1; r < R; ++r) dfm::dot_acc(s, c, gk[k][r], df{th[il * R + r], tl[il * R + r]});
-                  // hi + lo on the FP64 pipe: 3 instructions
-                  p.rows[k].out[e * NI + i] = (double)s + (double)c;
-                }
-              }
             }
           }
         }
@@ -577,6 +696,60 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
           tc::fence_before();
           tc::mbar_arrive(&s_empty[slot]);
         }
+        if (valid) {
+#pragma unroll
+          for (int il = 0; il < H0; ++il) {
+            if (il < nIh) {
+              const int i = cb * IB + half * H0 + il;
+              // check terms of the R columns of this i
+              float z[R];
+#pragma unroll
+              for (int r = 0; r < R; ++r) z[r] = zero_el ? 0.0f : zc[nb + il * R + r] - fabsf(th[il * R + r]);
+#pragma unroll
+              for (int k = 0; k < KR; ++k) {
+                if (ROWS || k < n_rows) {
+                  // first term: its exact product starts the pair (s, c)
+                  const df g0 = gk[k][0], t0{th[il * R], tl[il * R]};
+                  float s = g0.hi * t0.hi;
+                  float c = fmaf(g0.hi, t0.lo, fmaf(g0.lo, t0.hi, fmaf(g0.hi, t0.hi, -s)));
+                  float chk = fabsf(g0.hi) * z[0];
+#pragma unroll
+                  for (int r = 1; r < R; ++r) {
+                    dfm::dot_acc(s, c, gk[k][r], df{th[il * R + r], tl[il * R + r]});
+                    chk = fmaf(fabsf(gk[k][r].hi), z[r], chk);
+                  }
+                  mx = fmaxf(mx, chk);
+                  // hi + lo on the FP64 pipe (two exact conversions and an
+                  // add: three issue slots, against about twenty for the same
+                  // from bit moves)
+                  p.rows[k].out[e * NI + i] = (double)s + (double)c;
+                }
+              }
+            }
+          }
+        }
+      }
+      // tile end: flagged elements of this tile into the mask, then one
+      // barrier of the epilogue warps (which also tells every warp whether
+      // one of them gave up waiting)
+      if (ok && valid && (flag || mx > 0.0f)) atomicOr(&fmask[(t & 1) * 4 + (m >> 5)], 1u << (m & 31));
+      if (epi_any(!ok)) break;
+      uint32_t fm[4];
+#pragma unroll
+      for (int w = 0; w < 4; ++w) fm[w] = fmask[(t & 1) * 4 + w];
+      if (fm[0] | fm[1] | fm[2] | fm[3]) {
+#pragma unroll 1
+        for (int w = 0; w < 4; ++w) {
+          while (fm[w]) {
+            const int b = __ffs(fm[w]) - 1;
+            fm[w] &= fm[w] - 1u;
+            fallback_element(p, tile * TC_M + w * 32 + b, et, fu, ft);
+          }
+        }
+        // cleared before this thread reaches the next tile-end barrier; the
+        // next writer of this mask is two tiles on, past that barrier
+        if (et == 0)
+          for (int w = 0; w < 4; ++w) fmask[(t & 1) * 4 + w] = 0u;
       }
     }
   }
@@ -612,35 +785,27 @@ bool build_params(const EParams &p, TcParams &tp, std::string &why) {
   const int h0 = 16 / p.R;
   tp.IB = 2 * h0;
   tp.ncb = (p.NI + tp.IB - 1) / tp.IB;
-  if (tp.ncb > 8) { why = "too many column blocks"; return false; }
-  int nb = 0;
-  for (int cb = 0; cb < tp.ncb; ++cb) {
-    const int nI = std::min(tp.IB, p.NI - cb * tp.IB);
-    tp.n0[cb] = nb;
-    tp.ncol[cb] = nI <= h0 ? 16 : 32;                    // one or two 16-column halves
-    nb += tp.ncol[cb];
-  }
-  if (nb > TC_MAXNB) { why = "R * NI too large for the shared D planes"; return false; }
-  tp.NBtot = nb;
+  if (tp.ncb > TC_MAXCB) { why = "too many column blocks"; return false; }
+  tp.NB = tp.ncb * TC_NCOL;
   tp.KS = (p.NJ + 15) / 16;
   tp.NG = (p.NJ + 7) / 8;
+  // F = (1e-12 - 2^-43)^-1 (2^-43 covers the relative roundings: the
+  // producer's double-float value of u, the level sums, the contraction
+  // with g and the final conversion) times 1 + 2^-19 for the check's own
+  // FP32 roundings and the df -> float view of g
+  tp.fcheck = (1.0 + 1e-9) / (1e-12 - std::ldexp(1.0, -43)) * (1.0 + std::ldexp(1.0, -19));
+  tp.wait_limit = tc::TIMEOUT_CYCLES;
+  tp.status = nullptr;
   return true;
 }
 
-size_t smem_bytes(const TcParams &tp) {
-  return 1024 + (size_t)TC_P * tp.KS * tp.NBtot * 32 + 2 * (size_t)TC_P * tp.KS * TC_M * 32 +
-         sizeof(float2) * dfm::SIN2_N + sizeof(int) * (2 * TC_MAXNB + (TC_KU + 1) * TC_M) + 8 * (5 + 2 * TC_NSLOT) + 16;
-}
+size_t smem_bytes(const TcParams &tp) { return 256 + (size_t)tc_smem(tp).total; }
 
 template <int R, int ROWS>
 cudaError_t launch_rr(const TcParams &tp, int grid, size_t smem, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t st =
-        cudaFuncSetAttribute(element_tc_kernel<R, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (st != cudaSuccess) return st;
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  const cudaError_t st = smem_limit_once((const void *)element_tc_kernel<R, ROWS>, (int)TC_SMEM_LIMIT, attr);
+  if (st != cudaSuccess) return st;
   element_tc_kernel<R, ROWS><<<grid, TC_THREADS, smem, s>>>(tp);
   return cudaGetLastError();
 }
@@ -656,17 +821,18 @@ cudaError_t launch_r(const TcParams &tp, int grid, size_t smem, cudaStream_t s) 
 bool element_tc_supported(const EParams &p, std::string &why) {
   TcParams tp;
   if (!build_params(p, tp, why)) return false;
-  if (smem_bytes(tp) > 227 * 1024) { why = "shared memory"; return false; }
+  if (smem_bytes(tp) > TC_SMEM_LIMIT) { why = "shared memory"; return false; }
   return true;
 }
 
-cudaError_t launch_element_tc(const EParams &p, int *status, cudaStream_t s) {
+cudaError_t launch_element_tc(const EParams &p, int *status, long long wait_limit, cudaStream_t s) {
   TcParams tp;
   std::string why;
   if (!build_params(p, tp, why)) return cudaErrorInvalidValue;
   tp.status = status;
+  if (wait_limit > 0) tp.wait_limit = wait_limit;
   const size_t smem = smem_bytes(tp);
-  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  if (smem > TC_SMEM_LIMIT) return cudaErrorInvalidConfiguration;
   if (p.E <= 0) return cudaSuccess;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);

@@ -9,11 +9,14 @@
 // streams.  They pass their own inputs and outputs; the library's scratch
 // comes from the array below.
 //
-// The array (NOALLOC_SCRATCH_BYTES + a status word) is held by every GPU that
-// loads this library until the process exits.  The first call on a device
-// looks up the array's device address with that device current (the array's
-// host-side name is only a stand-in and must never reach a kernel); make that
-// first call before any stream capture.  All calls share the one array and
+// The array (NOALLOC_SCRATCH_BYTES + a status word) is held by every GPU where
+// this library's device code is loaded until the process exits; with lazy
+// module loading the driver reserves it on a device when the first call
+// there looks up the array's device address (with that device current: the
+// array's host-side name is only a stand-in and must never reach a kernel).
+// Make that first call early, before the caller sets up its memory pool and
+// before any stream capture.  A kernel whose bounded wait ran out leaves
+// BE_ETIMEOUT in the status word until be_gemm_split_noalloc_status reads it.  All calls share the one array and
 // it keeps the previous call's contents, so calls whose work overlaps on the
 // GPU race with each other; run them in order on one stream.
 #include <cstdint>
@@ -83,9 +86,11 @@ int be_gemm_split_noalloc(const double *A, int64_t lda, const double *B, int64_t
   int st = scratch_address(&ws);
   if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  // the status word is not cleared here: it keeps BE_ETIMEOUT from any call
+  // until be_gemm_split_noalloc_status reads and clears it
   int *status = (int *)((unsigned char *)ws + NOALLOC_SCRATCH_BYTES);
-  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
-  if (e == cudaSuccess && K == 0) {
+  cudaError_t e = cudaSuccess;
+  if (K == 0) {
     e = cudaMemset2DAsync(C, (size_t)ldc * sizeof(double), 0, (size_t)N * sizeof(double), (size_t)M, s);
   } else if (e == cudaSuccess) {
     // the split kernels overwrite every workspace entry they use (padding
@@ -93,9 +98,24 @@ int be_gemm_split_noalloc(const double *A, int64_t lda, const double *B, int64_t
     e = be::dense_split_b(be::DenseB{B, K, N, ldb, 1, M}, ws, s);
     if (e == cudaSuccess) e = be::dense_split_a(be::DenseA{A, M, lda, 1}, K, M, N, ws, s);
     if (e == cudaSuccess)
-      e = be::dense_split_gemm(be::DenseA{A, M, lda, 1}, N, K, M, C, ldc, ws, false, 2, status, s);
+      e = be::dense_split_gemm(be::DenseA{A, M, lda, 1}, N, K, M, C, ldc, ws, false, 2, status, 0, s);
   }
   if (e != cudaSuccess) return noalloc_fail(BE_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
+  return BE_OK;
+}
+
+// the status word after the scratch bytes of the current device's array,
+// read and cleared by two synchronous one-word copies (no allocation)
+int be_gemm_split_noalloc_status(int32_t *status) {
+  if (!status) return noalloc_fail(BE_EARG, "NULL status");
+  int v = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_noalloc_scratch, sizeof(int), NOALLOC_SCRATCH_BYTES);
+  if (e == cudaSuccess) {
+    const int zero = 0;
+    e = cudaMemcpyToSymbol(g_noalloc_scratch, &zero, sizeof(int), NOALLOC_SCRATCH_BYTES);
+  }
+  if (e != cudaSuccess) return noalloc_fail(BE_ECUDA, std::string("status word: ") + cudaGetErrorString(e));
+  *status = v;
   return BE_OK;
 }
 

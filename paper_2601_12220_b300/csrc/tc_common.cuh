@@ -27,32 +27,64 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// wait with a suspend-time hint: the thread sleeps until the phase
-// completes or about 0.1 ms pass, instead of spinning on issue slots that
-// the working warps need
-__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity) {
+// non-blocking test of the phase (a plain try_wait may block for a
+// system-dependent time, longer than a short wait limit)
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 100000;\n selp.u32 %0, 1, 0, p;\n}"
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok)
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
   return ok != 0;
 }
+// wait with a suspend-time hint: the thread sleeps until the phase
+// completes or about hint_ns nanoseconds pass, instead of spinning on issue
+// slots that the working warps need
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t hint_ns = 100000u) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
 // bounded wait; false when it gave up (or another thread already did), in
-// which case the abort flag is set and BE_ETIMEOUT recorded in *status
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *status) {
-  if (mbar_try_wait(bar, parity)) return true;
+// which case the abort flag is set and BE_ETIMEOUT recorded in *status.
+// Between tries the thread is suspended (the suspend-time hint; the thread
+// wakes when the phase completes) and the abort flag and the clock are read
+// only every eighth try, so that waiting warps take few issue slots from the
+// working ones.  `limit` is in SM clock cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *status,
+                                          long long limit = TIMEOUT_CYCLES) {
+  if (mbar_test_wait(bar, parity)) return true;
   const long long start = clock64();
-  while (!mbar_try_wait_sleep(bar, parity)) {
-    if (*abort_flag) return false;
-    if (clock64() - start > TIMEOUT_CYCLES) {
-      *abort_flag = 1;
-      if (status) atomicExch(status, 9);   // BE_ETIMEOUT
-      return false;
+  if (limit < 1000000) {
+    // a short limit (failure-path tests): non-blocking tests, so that the
+    // limit is honoured even where a suspended try would outlast it
+    while (!mbar_test_wait(bar, parity)) {
+      if (*abort_flag) return false;
+      if (clock64() - start > limit) {
+        *abort_flag = 1;
+        if (status) atomicExch(status, 9);   // BE_ETIMEOUT
+        return false;
+      }
+    }
+    return true;
+  }
+  const uint32_t hint = 100000u;
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait_sleep(bar, parity, hint)) return true;
+    if ((it & 7u) == 0u) {
+      if (*abort_flag) return false;
+      if (clock64() - start > limit) {
+        *abort_flag = 1;
+        if (status) atomicExch(status, 9);   // BE_ETIMEOUT
+        return false;
+      }
     }
   }
-  return true;
 }
 
 // make this thread's generic-proxy shared-memory writes visible to the

@@ -132,14 +132,13 @@ def test_wide_magnitude_range():
     check(W.dg_gradient_spec(E=E), dict(D=D, G=G, a=a, b=b))
 
 
-def test_sparse_rows_normwise_bound():
+def test_sparse_rows_componentwise():
     """Rows of u with one large entry and the rest 1e-9 smaller, rows of D
-    likewise, and elements that are all zero.  The digits are scaled per row,
-    so the guarantee here is the normwise one,
-        |err| <= 2^-48 NJ max_j|u_j| sum_r |g_r| max_j|D_rij| + 1e-13 S,
-    and all-zero elements give exact zeros.  The double-float variant meets
-    the componentwise 1e-12 * S on the same data."""
-    E, NJ = 256, 35
+    likewise, and elements that are all zero.  The digits share one scale
+    per row, so many outputs here cannot be certified by the per-output
+    check; those elements are recomputed in FP64 and every output still
+    meets the componentwise 1e-12 * S.  All-zero elements are exact zeros."""
+    E = 256
     D, G, a, b = W.dg_gradient(E=E)
     b = b.copy()
     b[::3, 1:] *= 1e-9
@@ -148,16 +147,39 @@ def test_sparse_rows_normwise_bound():
     D[:, ::2, 1:] *= 1e-9
     arrs = dict(D=D, G=G, a=a, b=b)
     text = W.dg_gradient_spec(E=E)
-    got = run(text, arrs)
-    ref = ev.evaluate(text, arrs)
-    umax = np.max(np.abs(np.sin(a) * b), axis=1)                 # [E]
-    dmax = np.max(np.abs(D), axis=2)                             # [r, i]
+    got, _ = check(text, arrs)
     for x in range(3):
-        r, S = ref[x]
-        bound = 2.0 ** -48 * NJ * umax[:, None] * (np.abs(G[:, :, x]) @ dmax) + 1e-13 * S
-        assert np.all(np.abs(got[x] - r) <= bound)
         assert np.all(got[x][1::7] == 0.0)
     check(text, arrs, DF)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_random_wide_range_entries(seed):
+    """Every entry of b (hence u) and of D scaled by its own 2^U, U uniform
+    in [-40, 40]: the worst case for shared digit scales.  The default path
+    meets 1e-12 * S componentwise on every output."""
+    E = 1500
+    D, G, a, b = W.dg_gradient(E=E)
+    g = np.random.default_rng(500 + seed)
+    b = b * np.exp2(g.integers(-40, 41, size=b.shape).astype(np.float64))
+    D = D * np.exp2(g.integers(-40, 41, size=D.shape).astype(np.float64))
+    check(W.dg_gradient_spec(E=E), dict(D=D, G=G, a=a, b=b))
+    check(W.dg_gradient_spec(E=E), dict(D=D, G=G, a=a, b=b), be.make_config(be.STRAT_ELEMENT))
+
+
+def test_cancelling_outputs():
+    """Outputs that cancel almost exactly (G and D chosen so that
+    sum_r g_r t_r is tiny against S).  The check bounds the error against
+    sum_r |g_r| |t_r| <= S, not against |R|, so these outputs are certified
+    without recomputation, and they meet 1e-12 * S."""
+    E = 512
+    D, G, a, b = W.dg_gradient(E=E)
+    G = G.copy()
+    G[:, 2, :] = 0.0
+    G[:, 1, :] = -G[:, 0, :]
+    D = D.copy()
+    D[1] = D[0] * (1.0 + 2.0 ** -40)
+    check(W.dg_gradient_spec(E=E), dict(D=D, G=G, a=a, b=b))
 
 
 def test_matches_double_float_variant():

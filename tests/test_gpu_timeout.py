@@ -1,0 +1,82 @@
+"""Failure detection on the tensor-core kernels, tested without a GPU fault.
+
+A context's wait limit (be_ctx_set_wait_limit) of a hundred SM cycles makes
+the pipeline waits of the element strategy's digit-split GEMM and of the
+dense split GEMM run out on purpose: the first wait on data that is still
+being produced (a TMA copy from HBM, a tile of digits) gives up, the CTA
+stops issuing, lets its issued MMAs and copies complete, frees its tensor
+memory and leaves BE_ETIMEOUT in the context's status word.  The context
+stays usable: the next call with the default limit gives correct results
+and status BE_OK.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
+
+import paper_2601_12220_b300 as be  # noqa: E402
+from oracle import evaluate as ev  # noqa: E402
+import workloads as W  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def _dg(ctx, E, cfg):
+    D, G, a, b = W.dg_gradient(E=E)
+    arrs = dict(D=D, G=G, a=a, b=b)
+    text = W.dg_gradient_spec(E=E)
+    e = be.Einsum(text)
+    outs = [torch.full((E, 35), float("nan"), dtype=torch.float64, device=DEV) for _ in range(3)]
+    be.execute(ctx, e, {k: torch.from_numpy(v).to(DEV) for k, v in arrs.items()}, outs, cfg=cfg)
+    torch.cuda.synchronize()
+    return text, arrs, [o.cpu().numpy() for o in outs]
+
+
+def test_element_tc_wait_runs_out_then_recovers():
+    ctx = be.Context(None, device=0)
+    tc = be.make_config(be.STRAT_ELEMENT, (0, 0, 3))
+    assert ctx.status() == be.OK
+    ctx.set_wait_limit(100)
+    _dg(ctx, 40000, tc)
+    assert ctx.status() == be.ETIMEOUT
+    assert ctx.status() == be.OK            # read and cleared
+    ctx.set_wait_limit(0)
+    text, arrs, got = _dg(ctx, 3000, tc)
+    assert ctx.status() == be.OK
+    ref = ev.evaluate(text, arrs)
+    for x in range(3):
+        r, S = ref[x]
+        assert np.all(np.abs(got[x] - r) <= 1e-12 * S)
+
+
+def _dense(ctx, M, N, K, seed):
+    g = np.random.default_rng(seed)
+    A = g.standard_normal((M, K))
+    B = g.standard_normal((K, N))
+    e = be.Einsum(f"ik,kj->ij | A,B ; A:f64[{M},{K}] ; B:f64[{K},{N}]")
+    C = torch.full((M, N), float("nan"), dtype=torch.float64, device=DEV)
+    be.execute(ctx, e, {"A": torch.from_numpy(A).to(DEV), "B": torch.from_numpy(B).to(DEV)}, [C],
+               precision=be.PREC_SPLIT, cfg=be.make_config(be.STRAT_DENSE_SPLIT))
+    torch.cuda.synchronize()
+    return A, B, C.cpu().numpy()
+
+
+def test_dense_wait_runs_out_then_recovers():
+    ctx = be.Context(None, device=0)
+    ctx.set_wait_limit(100)
+    _dense(ctx, 512, 512, 4096, 1)
+    assert ctx.status() == be.ETIMEOUT
+    ctx.set_wait_limit(0)
+    A, B, C = _dense(ctx, 300, 257, 1000, 2)
+    assert ctx.status() == be.OK
+    S = np.abs(A) @ np.abs(B)
+    assert np.all(np.abs(C - A @ B) <= 1e-6 * S)
+
+
+def test_wait_limit_rejects_negative():
+    ctx = be.Context(None, device=0)
+    with pytest.raises(be.BEError) as exc:
+        ctx.set_wait_limit(-1)
+    assert exc.value.code == be.EARG
