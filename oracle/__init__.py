@@ -17,7 +17,6 @@ Contents
                tolerances; host libm for sin / cos / exp
   evaluate.py  Python driver for einsum_ref.c (materialises each lambda
                operand over its domain, then contracts)
-  split.py     exact-slice arithmetic for the split-precision error model
 
 Parity status per function is listed in each module's header.
 """

@@ -52,10 +52,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs.append(o)
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr):
             cmd = [_nvcc(), "-c", s, "-o", o] + ARCH + FLAGS
-            if s.endswith(".cu"):
-                cmd += ["-Xptxas", "-v"] if verbose else []
-            else:
-                cmd += ["-x", "cu"] if False else []
+            if s.endswith(".cu") and verbose:
+                cmd += ["-Xptxas", "-v"]
             jobs.append(cmd)
 
     def run(cmd):

@@ -13,6 +13,7 @@
 #include <unordered_map>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "dense.hpp"
 #include "handles.hpp"
@@ -21,6 +22,13 @@
 using namespace be;
 
 static thread_local std::string g_err;
+
+// NVTX range around one host step (parse, canonicalize, lookup, execute): a
+// no-op unless a profiler that collects NVTX ranges is attached
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 static int fail(int code, const std::string &msg) {
   g_err = msg;
@@ -84,6 +92,7 @@ int be_version(void) { return 10000; }
 const char *be_last_error(void) { return g_err.c_str(); }
 
 int be_parse(const char *text, be_einsum **out) {
+  NvtxRange nv("be_parse");
   if (!text || !out) return fail(BE_EARG, "NULL argument");
   auto h = std::make_unique<be_einsum>();
   std::string err;
@@ -170,6 +179,7 @@ int be_einsum_buffer(const be_einsum *h, int32_t k, char *name, size_t len, size
 }
 
 int be_canonicalize(const be_einsum *h, be_canon **out) {
+  NvtxRange nv("be_canonicalize");
   if (!h || !out) return fail(BE_EARG, "NULL argument");
   auto c = std::make_unique<be_canon>();
   std::string err;
@@ -359,6 +369,7 @@ void be_ctx_destroy(be_ctx *x) {
 }
 
 int be_lookup(be_ctx *x, const be_canon *c, int32_t precision, be_config *out, double *seconds) {
+  NvtxRange nv("be_lookup");
   if (!x || !c || !out) return fail(BE_EARG, "NULL argument");
   std::lock_guard<std::mutex> g(x->mu);
   auto it = x->db.find(db_key(c->c.key, x->device_name, precision));
@@ -549,6 +560,7 @@ static int do_execute(be_ctx *x, const be_einsum *hc, const be_config *cfg, int3
 int be_execute(be_ctx *x, const be_einsum *h, const be_config *cfg, int32_t precision, const be_buf *bufs,
                int32_t n_bufs, const be_buf *outs, int32_t n_outs, const double *scalars, int32_t n_scalars,
                void *stream) {
+  NvtxRange nv("be_execute");
   return do_execute(x, h, cfg, precision, bufs, n_bufs, outs, n_outs, scalars, n_scalars, stream);
 }
 
@@ -650,6 +662,7 @@ static void resize_outer(const Einsum &src, const std::vector<int> &kind, int64_
 int be_execute_host(be_ctx *x, const be_einsum *h, const be_config *cfg, int32_t precision, const be_buf *bufs,
                     int32_t n_bufs, const be_buf *outs, int32_t n_outs, const double *scalars, int32_t n_scalars,
                     void *stream) {
+  NvtxRange nv("be_execute_host");
   if (!x || !h) return fail(BE_EARG, "NULL argument");
   const Einsum &e = h->e;
   if (n_bufs != (int)e.buffers.size() || n_outs != e.b) return fail(BE_EARG, "buffer counts differ from the spec");
@@ -958,6 +971,7 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
 }
 
 int be_batch_run(be_batch *b, void *stream) {
+  NvtxRange nv("be_batch_run");
   if (!b) return fail(BE_EARG, "NULL batch");
   cudaStream_t s = (cudaStream_t)stream;
   KernelMark km(b->x, BE_KERNEL_PERSISTENT, s);

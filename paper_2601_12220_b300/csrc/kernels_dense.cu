@@ -17,13 +17,15 @@
 //     large term hi*hi into H, the small terms hi*lo + lo*hi (+ lo*lo when
 //     requested) into L, each double-buffered (4 x 128 columns).  The
 //     tensor core rounds its FP32 accumulator toward zero (about 2^-23 of
-//     the accumulator per MMA, measured), so H is drained every 32 values
-//     of K (4 MMAs) and L every 512; sixteen epilogue warps read them
+//     the accumulator per MMA, measured), so H is drained every hdrain
+//     k-blocks of 32 values (2 by default: 64 values, 8 MMAs) and L every
+//     512 values; sixteen epilogue warps read them
 //     (tcgen05.ld) and add them into an FP32 pair per output with an
 //     error-free two-sum (about 48 bits).  The result is scaled back and
 //     stored in FP64.
 //  Error per output, relative to S = sum |a||b|: split residuals 3 * 2^-22
-//  (2 * 2^-22 with lo*lo), H truncation 4 * 2^-23, L truncation below 2^-26.
+//  (2 * 2^-22 with lo*lo), H truncation about 2^-23 per MMA between drains
+//  (8 * 2^-23 at the default drain), L truncation below 2^-26.
 // Every mbarrier wait is bounded (about one second of clock cycles); on
 // expiry the CTA records BE_ETIMEOUT in a status word, stops issuing work,
 // waits (bounded) for its own copies and frees its tensor memory.
