@@ -356,8 +356,7 @@ def run_ours(args):
             "clocks": clk.summary(), "gpu_launches": int(round(args.steps * launches_per_step))}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_baseline(args.cpu_sample)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
     if pg:
         pg.destroy_process_group()
 
@@ -450,8 +449,7 @@ def run_fem(args):
             "canonicalize_200_copies": {"p50_us": float(lat[len(lat) // 2]), "p99_us": float(lat[int(0.99 * len(lat))]),
                                         "distinct_keys": len(keys), "key": sorted(keys)[0]},
             "clocks": clk.summary(), "gpu_launches": n_k}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 # ------------------------------------------- DG divergence and face mass
@@ -538,14 +536,59 @@ def run_stacked(args):
             "generic": {"ms_per_step": gen_ms, "value": world * byts / (gen_ms * 1e-3) / 1e9,
                         "speedup_of_element": gen_ms / ms},
             "clocks": clk.summary(), "gpu_launches": n_launch}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 # ---------------------------------------------------------------- workload 3
 
 V_FULL, O_FULL, B_CHEM = 128, 32, 4
 TF32_OVER_BF16 = 1.1 / 2.25    # nominal dense TF32 : BF16 tensor rates of B300
+
+
+def chem_device_inputs(torch, dev, v, o, seed=1003):
+    """The dense workload's operands drawn on the device (torch's Philox
+    generator, seeded): A_k[a,b,e,f] = N(0,1) exp(-(|a-e|+|b-f|)/8), k < 4,
+    and the shared T[e,f,i,j] = N(0,1) exp(-(|e-i|+|f-j|)/8) -- the shapes
+    and decay of the workload without 8.6 GB of host generation and copy."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    ia = torch.arange(v, device=dev, dtype=torch.float64)
+    io = torch.arange(o, device=dev, dtype=torch.float64)
+    wv = torch.exp(-(ia[:, None] - ia[None, :]).abs() / 8.0)          # [a, e]
+    wo = torch.exp(-(ia[:, None] - io[None, :]).abs() / 8.0)          # [e, i]
+    bufs = {}
+    for k in range(B_CHEM):
+        A = torch.randn((v, v, v, v), generator=g, device=dev, dtype=torch.float64)
+        A *= wv[:, None, :, None]
+        A *= wv[None, :, None, :]
+        bufs[f"A{k}"] = A
+    T = torch.randn((v, v, o, o), generator=g, device=dev, dtype=torch.float64)
+    T *= wo[:, None, :, None] * wo[None, :, None, :]
+    bufs["T"] = T
+    return bufs
+
+
+def chem_sampled_error(torch, bufs, outs, v, o, n=256, seed=7):
+    """Componentwise error of sampled outputs (a, b, i, j) of every row
+    against an FP64 dot product of the same operands (numpy), relative to
+    the absolute contraction S = sum |A| |T|: max and median."""
+    rng = np.random.default_rng(seed)
+    T = bufs["T"].reshape(v * v, o * o)
+    rel = []
+    for k in range(len(outs)):
+        A = bufs[f"A{k}"].reshape(v * v, v * v)
+        C = outs[k].reshape(v * v, o * o)
+        m = rng.integers(0, v * v, n)
+        c = rng.integers(0, o * o, n)
+        a = A[torch.as_tensor(m, device=A.device)].cpu().numpy()
+        t = T[:, torch.as_tensor(c, device=T.device)].cpu().numpy()
+        got = C[torch.as_tensor(m, device=C.device), torch.as_tensor(c, device=C.device)].cpu().numpy()
+        ref = np.einsum("nk,kn->n", a, t)
+        S = np.einsum("nk,kn->n", np.abs(a), np.abs(t))
+        rel.append(np.abs(got - ref) / S)
+    rel = np.concatenate(rel)
+    return {"max_over_S": float(rel.max()), "median_over_S": float(np.median(rel)), "samples": int(rel.size),
+            "tolerance": 1e-6, "reference": "FP64 dot products of the sampled rows and columns (numpy)"}
 
 
 def run_chem(args):
@@ -558,9 +601,7 @@ def run_chem(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     v, o = args.chem_v, args.chem_o
-    As, T = W.chem_dense(v=v, o=o)
-    host = {f"A{k}": A for k, A in enumerate(As)} | {"T": T}
-    bufs = {k: torch.from_numpy(x).to(dev) for k, x in host.items()}
+    bufs = chem_device_inputs(torch, dev, v, o)
     outs = [torch.empty((v, v, o, o), dtype=torch.float64, device=dev) for _ in range(B_CHEM)]
     text = W.chem_dense_spec(v=v, o=o)
     ctx = be.Context(None, device=local)
@@ -590,6 +631,7 @@ def run_chem(args):
         torch.cuda.synchronize()
     ctx.set_timing(False)
     assert ctx.status() == be.OK
+    err = chem_sampled_error(torch, bufs, outs, v, o)
     ms = t0.elapsed_time(t1) / args.steps
     n_g, t_g = ctx.timing(be.KERNEL_DENSE_GEMM)
     n_s, t_s = ctx.timing(be.KERNEL_SPLIT)
@@ -604,7 +646,7 @@ def run_chem(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64 (split: 2 TF32 parts, 3 tensor products)",
             "data": "synthetic",
             "config": {"workload": f"chem_dense: b={B_CHEM} 'abef,efij->abij', v={v}, o={o}, efij shared, "
-                                   "entries N(0,1)*exp(-gap/8)", "parallelism": "replicas",
+                                   "entries N(0,1)*exp(-gap/8) (drawn on the device)", "parallelism": "replicas",
                        "l2": f"inputs larger than L2 ({byts / 1e9:.1f} GB per step)"},
             "gb_s": world * byts / (ms * 1e-3) / 1e9,
             "kernels": {"gemm_split_kernel_ms": gemm_ms, "gemm_launches": n_g,
@@ -616,9 +658,9 @@ def run_chem(args):
                                         f"{TF32_OVER_BF16:.3f} ({peaks['source']})",
                          "traffic": kernel_traffic({"source": "kernels_dense.cu",
                                                     "profile": "gemm_split_kernel_chem.md"})},
+            "error_vs_fp64": err,
             "clocks": clk.summary(), "gpu_launches": n_g + n_s}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_affine(args):
@@ -698,9 +740,9 @@ def run_affine(args):
                          "frac_issued": ach_issued / tf32_peak,
                          "peak_source": f"measured bf16 burst {peaks['bf16_tflops']} x nominal tf32/bf16 ratio "
                                         f"{TF32_OVER_BF16:.3f} ({peaks['source']})", "traffic": None},
+            "error_vs_fp64": err,
             "clocks": clk.summary(), "gpu_launches": n_g + n_s}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 # ---------------------------------------------------------------- workload 4
@@ -717,7 +759,7 @@ def run_mix(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     g = W.rng(4, 0)
-    items, byts, n_rows = [], 0, 0
+    items, insts, byts, n_rows = [], [], 0, 0
     fl64, fl32 = 0.0, 0.0          # loop-nest flops of the f64 and f32 instances
     for _ in range(args.mix_n):
         inst = W.mix_instance(g, max_operand=1 << args.mix_operand_log2, max_flops=1 << args.mix_flops_log2)
@@ -732,14 +774,38 @@ def run_mix(args):
         bufs = {k: torch.from_numpy(v).to(dev) for k, v in arrs.items()}
         outs = [torch.empty(e.out_shape, dtype=dt, device=dev) for _ in range(e.b)]
         items.append((e, bufs, outs))
+        insts.append(inst)
         byts += sum(v.nbytes for v in arrs.values()) + sum(o.numel() * o.element_size() for o in outs)
         n_rows += e.b
     ctx = be.Context(None, device=local)
     stream = torch.cuda.current_stream(dev)
+    # strategy policy: element-shaped FP64 instances on the element strategy;
+    # FP64 GEMM-form instances of >= 2^mix_split_log2 multiply-adds on the
+    # split-precision tensor cores (judged at 1e-6 S) unless --mix-no-split
+    policy = be.make_config(tile=(0, 0, 0, args.mix_split_log2), split=0 if args.mix_no_split else 1)
     t_plan = time.perf_counter()
-    batch = be.Batch(ctx, items)
+    batch = be.Batch(ctx, items, policy)
     t_plan = time.perf_counter() - t_plan
     info = batch.info()
+    kinds = batch.kinds()
+    # per-instance bound: HBM for element instances, the TF32 tensor pipe for
+    # split instances (3 products), the FP64 / FP32 pipe for generic ones
+    peaks0 = load_peaks()
+    tf32 = peaks0["bf16_tflops"] * TF32_OVER_BF16 * 1e12
+    pipe_s = {"hbm": 0.0, "tensor": 0.0, "fp64": 0.0, "fp32": 0.0}
+    for (e, bufs, outs), inst in zip(items, insts):
+        f = len(inst.rows) * W._flops(inst.out, inst.ins, inst.lens)
+        nbytes = sum(t.numel() * t.element_size() for t in bufs.values()) + \
+            sum(o.numel() * o.element_size() for o in outs)
+        if be.plan_strategy(ctx, e) == be.STRAT_ELEMENT:
+            pipe_s["hbm"] += nbytes / (peaks0["hbm_gbs"] * 1e9)
+        elif (not args.mix_no_split and "64" in str(inst.dtype) and f / 2 >= 2 ** args.mix_split_log2 and
+              be.plan_strategy(ctx, e, precision=be.PREC_SPLIT) == be.STRAT_DENSE_SPLIT):
+            pipe_s["tensor"] += 3 * f / tf32
+        elif "64" in str(inst.dtype):
+            pipe_s["fp64"] += f / (FP64_PEAK_TFLOPS * 1e12)
+        else:
+            pipe_s["fp32"] += f / (FP32_PEAK_TFLOPS * 1e12)
 
     def timed(fn, steps, warm):
         for _ in range(warm):
@@ -762,7 +828,11 @@ def run_mix(args):
         ms_batch = timed(lambda: batch.run(stream), args.steps, args.warmup)
     ctx.set_timing(False)
     n_k, t_k = ctx.timing(be.KERNEL_PERSISTENT)
+    assert ctx.status() == be.OK
     ms_single = timed(per_instance, max(1, args.steps // 2), 1)
+    generic_only = be.Batch(ctx, items, be.make_config(stage_mask=1))
+    ms_generic = timed(lambda: generic_only.run(stream), max(1, args.steps // 2), 1)
+    generic_only.close()
     peaks = load_peaks()
     kms = t_k / max(1, n_k)
     line = {"metric": METRIC, "value": world * args.mix_n / (ms_batch * 1e-3), "unit": "einsums/s",
@@ -773,8 +843,19 @@ def run_mix(args):
                                    f"operands <= 2^{args.mix_operand_log2}, flops <= 2^{args.mix_flops_log2}",
                        "rows": n_rows, "tiles": info["tiles"], "plan_s": t_plan, "parallelism": "replicas"},
             "rows_per_s": world * n_rows / (ms_batch * 1e-3),
+            "instances_per_strategy": kinds,
             "one_launch_per_einsum": {"ms_per_step": ms_single, "einsums_per_s": args.mix_n / (ms_single * 1e-3)},
             "speedup_vs_one_launch_per_einsum": ms_single / ms_batch,
+            "all_generic_batch": {"ms_per_step": ms_generic, "einsums_per_s": args.mix_n / (ms_generic * 1e-3)},
+            "per_pipe_bound_ms": {k: v * 1e3 for k, v in pipe_s.items()},
+            "roofline_per_instance_pipe": {
+                "bound_ms": max(pipe_s.values()) * 1e3, "serial_bound_ms": sum(pipe_s.values()) * 1e3,
+                "frac": max(pipe_s.values()) / (ms_batch * 1e-3),
+                "frac_serial": sum(pipe_s.values()) / (ms_batch * 1e-3),
+                "counts": "each instance at its own pipe's peak: element instances' bytes at measured HBM, split "
+                          "instances' issued TF32 flops (3 products) at measured bf16 x tf32/bf16, generic f64 / f32 "
+                          "loop-nest flops at nominal FP64 / FP32; bound = the busiest pipe (pipes overlap), "
+                          "serial = their sum"},
             "gb_s": world * byts / (ms_batch * 1e-3) / 1e9,
             "roofline": {"kernel": "persistent_kernel", "bound": "alu",
                          "achieved": (fl64 + fl32) / (kms * 1e-3) / 1e12,
@@ -787,8 +868,7 @@ def run_mix(args):
                          "hbm": {"achieved": byts / (kms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                  "frac": byts / (kms * 1e-3) / 1e9 / peaks["hbm_gbs"]}},
             "clocks": clk.summary(), "gpu_launches": n_k}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 # ---------------------------------------------------------------- workload 5
@@ -908,8 +988,7 @@ def run_serving(args):
     if sweep:
         line["rate_sweep"] = sweep
     srv.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -940,6 +1019,12 @@ def main():
     ap.add_argument("--serve-templates", type=int, default=256)
     ap.add_argument("--serve-streams", type=int, default=8)
     ap.add_argument("--mix-n", type=int, default=512)
+    ap.add_argument("--mix-split-log2", type=int, default=24,
+                    help="FP64 GEMM-form mix instances of at least 2^this multiply-adds take the split path")
+    ap.add_argument("--mix-no-split", action="store_true",
+                    help="keep FP64 GEMM-form mix instances on the FP64 generic path")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default workload only: skip the sub-objects of the other configurations")
     ap.add_argument("--mix-operand-log2", type=int, default=22)
     ap.add_argument("--mix-flops-log2", type=int, default=26)
     ap.add_argument("--chem-v", type=int, default=V_FULL)
@@ -949,20 +1034,55 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "chem_dense":
-        run_chem(args)
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    if args.workload == "chem_dense":
+        line = run_chem(args)
     elif args.workload == "uneven_mix":
-        run_mix(args)
+        line = run_mix(args)
     elif args.workload == "serving":
-        run_serving(args)
+        line = run_serving(args)
     elif args.workload in ("dg_divergence", "face_mass"):
-        run_stacked(args)
+        line = run_stacked(args)
     elif args.workload == "dense_affine":
-        run_affine(args)
+        line = run_affine(args)
     elif args.workload == "fem_action":
-        run_fem(args)
+        line = run_fem(args)
     else:
-        run_ours(args)
+        line = run_ours(args)
+        if line.get("n_gpus", 1) == 1 and not args.no_configs:
+            line["configs"] = other_configs(args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def other_configs(args):
+    """The other configurations of the benchmark, one sub-object each (1 GPU,
+    short runs): FEM action with canonicalization of 200 copies, the dense
+    split-precision contraction with its error, the 512-instance uneven mix
+    (batched vs one launch per einsum) and the serving loop (3 s Poisson
+    stream at 20 k requests/s)."""
+    import copy
+
+    def sub(fn, **kw):
+        a = copy.copy(args)
+        for k, v in kw.items():
+            setattr(a, k, v)
+        t = time.perf_counter()
+        try:
+            d = fn(a)
+        except Exception as exc:                       # reported, never hidden
+            return {"error": f"{type(exc).__name__}: {exc}"}
+        d.pop("metric", None)
+        d["wall_s"] = time.perf_counter() - t
+        return d
+
+    return {
+        "fem_action_b4_E4096": sub(run_fem, steps=100, warmup=5),
+        "chem_dense_v128_o32_b4": sub(run_chem, steps=5, warmup=3),
+        "uneven_mix_512": sub(run_mix, steps=6, warmup=3),
+        "serving_poisson_20k": sub(run_serving, serve_seconds=3.0, serve_sweep=""),
+    }
 
 
 if __name__ == "__main__":

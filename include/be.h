@@ -309,16 +309,30 @@ int be_tune(be_ctx *x, const be_einsum *e, int32_t precision, const be_buf *bufs
  * be_batch_create -- plan n instances: es[k] with its declared buffers
  *   bufs[k][0..n_bufs[k]) and outputs outs[k][0..n_outs[k]) (device
  *   pointers, as for be_execute) and runtime scalars scalars[k] (may be
- *   NULL when n_scalars is NULL or 0).  Every row becomes a descriptor; its
- *   outputs are cut into tiles of about 2^tile[1] operand terms (default
- *   20); cfg->tile[0] is the block size (default 256), cfg->tile[2] CTAs per
- *   SM (default 4); cfg may be NULL.  The buffers are borrowed and must stay
- *   valid while the batch is used; their CONTENTS may change between runs.
- *   Device memory for descriptors and tiles is allocated here.
+ *   NULL when n_scalars is NULL or 0).  Each instance gets a strategy:
+ *   element-shaped FP64 instances (shared small operator, streamed
+ *   per-element operands) take the element strategy with their database
+ *   configuration (cfg->stage_mask bit 0 keeps them generic); with
+ *   cfg->split >= 1, FP64 instances of GEMM form with at least
+ *   2^cfg->tile[3] multiply-adds (default 2^20) take the split-precision
+ *   tensor-core strategy (1e-6 * S); every other instance is generic: each
+ *   of its rows becomes a descriptor whose outputs are cut into tiles of
+ *   about 2^tile[1] operand terms (default 20) for one persistent launch
+ *   (cfg->tile[0] its block size, default 256, and 256 whenever a row is
+ *   evaluated as GEMM tiles; cfg->tile[2] CTAs per SM, default 4).  cfg may be NULL.  Everything is captured once in a CUDA
+ *   graph with three concurrent branches: the persistent grid of generic
+ *   tiles, the element launches and the split / GEMM launches (which use a
+ *   split workspace owned by the batch).  The element and dense launches
+ *   run once during creation.  The buffers are borrowed and must stay valid
+ *   while the batch is used; their CONTENTS may change between runs.
+ *   Device memory for descriptors, tiles and the workspace is allocated
+ *   here.
  * be_batch_run -- replay the captured graph on `stream` (asynchronous).
  *   Every output has a single owner and a fixed evaluation order, so the
- *   results are bitwise those of BE_STRAT_GENERIC on each instance alone.
- * be_batch_info -- rows, tiles and total operand terms of the batch.
+ *   results are bitwise those of be_execute on each instance alone with
+ *   the strategy it was given (BE_STRAT_GENERIC for generic instances).
+ * be_batch_info -- rows, tiles and total operand terms of the generic part.
+ * be_batch_kinds -- number of instances given each strategy.
  */
 int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_buf *const *bufs,
                     const int32_t *n_bufs, const be_buf *const *outs, const int32_t *n_outs,
@@ -326,6 +340,28 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
                     be_batch **out);
 int be_batch_run(be_batch *b, void *stream);
 int be_batch_info(const be_batch *b, int64_t *rows, int64_t *tiles, double *terms);
+int be_batch_kinds(const be_batch *b, int32_t *generic, int32_t *element, int32_t *dense);
+
+/*
+ * be_tune_batch -- the autotuner for a batch (spec pattern 2: tile
+ * shapes and schedules chosen by the engine's own tuner, results kept in
+ * the normal-form-keyed database).  Creates the batch of be_batch_create
+ * under each candidate launch shape of its persistent part -- block size
+ * 128 (skipped when a row is evaluated as GEMM tiles) or 256, 2, 3 or 4 CTAs
+ * per SM, tiles of 2^18, 2^20 or 2^22 operand terms -- with base's strategy policy (split, tile[3], stage_mask; base
+ * may be NULL), times reps graph replays on `stream` after one warm-up, and
+ * records every timed candidate in x's database under the batch key: the
+ * instances' canonical keys, sorted and hashed, so any renaming or
+ * reordering of the same instances finds the record.  be_batch_create with
+ * cfg == NULL then uses the best record.  Returns the best configuration,
+ * its seconds per replay and the number of candidates timed.  The element
+ * and dense launches of the batch run once per candidate.  Errors:
+ * BE_EARG, BE_EDB, BE_EUNSUPPORTED (no candidate ran), BE_ECUDA.
+ */
+int be_tune_batch(be_ctx *x, int32_t n, const be_einsum *const *es, const be_buf *const *bufs,
+                  const int32_t *n_bufs, const be_buf *const *outs, const int32_t *n_outs,
+                  const double *const *scalars, const int32_t *n_scalars, const be_config *base, int32_t reps,
+                  void *stream, be_config *best, double *best_seconds, int32_t *n_tried);
 void be_batch_destroy(be_batch *b);
 
 /*

@@ -33,7 +33,7 @@ EXPORTS = [
     "be_ctx_destroy", "be_lookup", "be_record", "be_db_size", "be_execute", "be_execute_host",
     "be_plan_strategy", "be_status", "be_ctx_set_timing", "be_ctx_timing", "be_gemm_split_noalloc",
     "be_gemm_split_noalloc_status", "be_ctx_set_wait_limit",
-    "be_batch_create", "be_batch_run", "be_batch_info", "be_batch_destroy", "be_tune",
+    "be_batch_create", "be_batch_run", "be_batch_info", "be_batch_kinds", "be_batch_destroy", "be_tune", "be_tune_batch",
     "be_server_create", "be_server_submit", "be_server_wait", "be_server_drain", "be_server_stats",
     "be_server_reset_stats", "be_server_destroy", "be_raise", "be_raised_name", "be_record_facts",
     "be_load_transforms",
@@ -119,6 +119,10 @@ def lib():
                                                P(P(ctypes.c_double)), P(i32), P(Config), P(vp)]),
             "be_batch_run": (ctypes.c_int, [vp, vp]),
             "be_batch_info": (ctypes.c_int, [vp, P(i64), P(i64), P(ctypes.c_double)]),
+            "be_batch_kinds": (ctypes.c_int, [vp, P(i32), P(i32), P(i32)]),
+            "be_tune_batch": (ctypes.c_int, [vp, i32, P(vp), P(P(Buf)), P(i32), P(P(Buf)), P(i32),
+                                             P(P(ctypes.c_double)), P(i32), P(Config), i32, vp, P(Config),
+                                             P(ctypes.c_double), P(i32)]),
             "be_batch_destroy": (None, [vp]),
             "be_server_create": (ctypes.c_int, [vp, i32, i32, sz, P(vp)]),
             "be_server_submit": (ctypes.c_int, [vp, vp, P(Buf), i32, P(Buf), i32, P(ctypes.c_double), i32, P(i64)]),
@@ -524,39 +528,50 @@ class Server:
         self.close()
 
 
+def _batch_arrays(items):
+    """C arrays of be_batch_create / be_tune_batch for (einsum, buffers,
+    outputs[, scalars]) items, and the objects they borrow."""
+    keep = []
+    n = len(items)
+    es = (ctypes.c_void_p * max(1, n))()
+    bptr = (ctypes.POINTER(Buf) * max(1, n))()
+    optr = (ctypes.POINTER(Buf) * max(1, n))()
+    nb = (ctypes.c_int32 * max(1, n))()
+    no = (ctypes.c_int32 * max(1, n))()
+    sptr = (ctypes.POINTER(ctypes.c_double) * max(1, n))()
+    ns = (ctypes.c_int32 * max(1, n))()
+    for k, item in enumerate(items):
+        e, bufs, outs = item[0], item[1], item[2]
+        scal = item[3] if len(item) > 3 else ()
+        bl = _order(e, bufs)
+        for t, (name, _, shape) in zip(bl, e.buffers):
+            if tuple(t.shape) != shape or not t.is_cuda:
+                raise BEError(ESHAPE, f"instance {k} buffer {name}: expected shape {shape}")
+        for t in outs:
+            if tuple(t.shape) != e.out_shape or not t.is_contiguous():
+                raise BEError(ESHAPE, f"instance {k}: outputs must be dense of shape {e.out_shape}")
+        bi = _bufs_torch(bl, keep)
+        bo = _bufs_torch(outs, keep, dense_only=True)
+        sc, nsc = _scalars(scal)
+        keep += [bi, bo, sc, e, bl, outs]
+        es[k] = e.handle.value
+        bptr[k] = ctypes.cast(bi, ctypes.POINTER(Buf))
+        optr[k] = ctypes.cast(bo, ctypes.POINTER(Buf))
+        nb[k], no[k], ns[k] = len(bl), len(outs), nsc
+        sptr[k] = ctypes.cast(sc, ctypes.POINTER(ctypes.c_double))
+    return (es, bptr, nb, optr, no, sptr, ns), keep
+
+
 class Batch:
-    """Persistent multi-instance executor over many (einsum, buffers, outputs)
-    instances, replayed as one CUDA graph per run."""
+    """Multi-instance executor over many (einsum, buffers, outputs) instances,
+    replayed as one CUDA graph per run: generic instances as tiles of one
+    persistent launch, element-shaped and (with cfg.split >= 1) dense FP64
+    instances on their own strategies in concurrent graph branches."""
 
     def __init__(self, ctx, items, cfg: Config | None = None):
-        keep = []
+        arrays, keep = _batch_arrays(items)
+        es, bptr, nb, optr, no, sptr, ns = arrays
         n = len(items)
-        es = (ctypes.c_void_p * max(1, n))()
-        bptr = (ctypes.POINTER(Buf) * max(1, n))()
-        optr = (ctypes.POINTER(Buf) * max(1, n))()
-        nb = (ctypes.c_int32 * max(1, n))()
-        no = (ctypes.c_int32 * max(1, n))()
-        sptr = (ctypes.POINTER(ctypes.c_double) * max(1, n))()
-        ns = (ctypes.c_int32 * max(1, n))()
-        for k, item in enumerate(items):
-            e, bufs, outs = item[0], item[1], item[2]
-            scal = item[3] if len(item) > 3 else ()
-            bl = _order(e, bufs)
-            for t, (name, _, shape) in zip(bl, e.buffers):
-                if tuple(t.shape) != shape or not t.is_cuda:
-                    raise BEError(ESHAPE, f"instance {k} buffer {name}: expected shape {shape}")
-            for t in outs:
-                if tuple(t.shape) != e.out_shape or not t.is_contiguous():
-                    raise BEError(ESHAPE, f"instance {k}: outputs must be dense of shape {e.out_shape}")
-            bi = _bufs_torch(bl, keep)
-            bo = _bufs_torch(outs, keep, dense_only=True)
-            sc, nsc = _scalars(scal)
-            keep += [bi, bo, sc, e, bl, outs]
-            es[k] = e.handle.value
-            bptr[k] = ctypes.cast(bi, ctypes.POINTER(Buf))
-            optr[k] = ctypes.cast(bo, ctypes.POINTER(Buf))
-            nb[k], no[k], ns[k] = len(bl), len(outs), nsc
-            sptr[k] = ctypes.cast(sc, ctypes.POINTER(ctypes.c_double))
         h = ctypes.c_void_p()
         check(lib().be_batch_create(ctx.handle if ctx else None, n, es, bptr, nb, optr, no, sptr, ns,
                                     ctypes.byref(cfg) if cfg else None, ctypes.byref(h)))
@@ -574,6 +589,12 @@ class Batch:
         check(lib().be_batch_info(self._h, ctypes.byref(r), ctypes.byref(t), ctypes.byref(w)))
         return {"rows": r.value, "tiles": t.value, "terms": w.value}
 
+    def kinds(self):
+        """Instances per strategy: {"generic": g, "element": m, "dense": d}."""
+        g, m, d = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(lib().be_batch_kinds(self._h, ctypes.byref(g), ctypes.byref(m), ctypes.byref(d)))
+        return {"generic": g.value, "element": m.value, "dense": d.value}
+
     def close(self):
         if getattr(self, "_h", None) and _lib is not None:
             _lib.be_batch_destroy(self._h)
@@ -581,6 +602,21 @@ class Batch:
 
     def __del__(self):
         self.close()
+
+
+def tune_batch(ctx, items, base: Config | None = None, reps=5, stream=None):
+    """be_tune_batch: time the batch's launch-shape candidates, record them
+    under the batch key; returns (best Config, seconds, candidates timed)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    (es, bptr, nb, optr, no, sptr, ns), keep = _batch_arrays(items)
+    best, sec, n = Config(), ctypes.c_double(), ctypes.c_int32()
+    check(lib().be_tune_batch(ctx.handle, len(items), es, bptr, nb, optr, no, sptr, ns,
+                              ctypes.byref(base) if base else None, int(reps), ctypes.c_void_p(stream.cuda_stream),
+                              ctypes.byref(best), ctypes.byref(sec), ctypes.byref(n)))
+    del keep
+    return best, sec.value, n.value
 
 
 def plan_strategy(ctx, e: Einsum, cfg: Config | None = None, precision=PREC_FP64) -> int:

@@ -297,7 +297,8 @@ static bool parse_record(const std::string &line, std::string &key, DbEntry &d) 
     else cur += ch;
   }
   f.push_back(cur);
-  if (f.size() != 5 || f[0].rfind("be1:", 0) != 0) return false;
+  // keys are normal forms of einsums ("be1:...") or of batches ("batch1:...")
+  if (f.size() != 5 || (f[0].rfind("be1:", 0) != 0 && f[0].rfind("batch1:", 0) != 0)) return false;
   char *end = nullptr;
   long prec = std::strtol(f[2].c_str(), &end, 10);
   if (*end || f[2].empty()) return false;
@@ -454,6 +455,36 @@ static int choose(const Einsum &e, const std::vector<BufIn> &bufs, const std::ve
   return BE_OK;
 }
 
+// the split, split and GEMM launches of every row of a dense plan, with the
+// workspace ws (dense_workspace_bytes(M, N, K) bytes) and status word given
+static cudaError_t run_dense_rows(be_ctx *x, const DensePlan &dp, const be_config_t &c, void *ws, int *status,
+                                  long long wait_limit, cudaStream_t s) {
+  cudaError_t ce = cudaSuccess;
+  int prevB = -1;
+  for (auto &r : dp.rows) {
+    if (dp.K == 0) {
+      ce = cudaMemsetAsync(r.C, 0, sizeof(double) * (size_t)(dp.M * dp.N), s);
+    } else {
+      if (r.argB != prevB) {
+        KernelMark km(x, BE_KERNEL_SPLIT, s);
+        ce = dense_split_b(DenseB{r.B, dp.K, dp.N, r.ldb, r.snb, dp.M, r.alB, r.beB}, ws, s);
+        prevB = r.argB;
+      }
+      if (ce == cudaSuccess) {
+        KernelMark km(x, BE_KERNEL_SPLIT, s);
+        ce = dense_split_a(DenseA{r.A, dp.M, r.lda, r.ska, r.alA, r.beA}, dp.K, dp.M, dp.N, ws, s);
+      }
+      if (ce == cudaSuccess) {
+        KernelMark km(x, BE_KERNEL_DENSE_GEMM, s);
+        ce = dense_split_gemm(DenseA{r.A, dp.M, r.lda, r.ska}, dp.N, dp.K, dp.M, r.C, dp.N, ws, c.split >= 4,
+                              c.tile[2] > 0 ? c.tile[2] : 2, status, wait_limit, s);
+      }
+    }
+    if (ce != cudaSuccess) return ce;
+  }
+  return cudaSuccess;
+}
+
 static int do_execute(be_ctx *x, const be_einsum *hc, const be_config *cfg, int32_t precision, const be_buf *bufs,
                       int32_t n_bufs, const be_buf *outs, int32_t n_outs, const double *scalars, int32_t n_scalars,
                       void *stream) {
@@ -486,28 +517,8 @@ static int do_execute(be_ctx *x, const be_einsum *hc, const be_config *cfg, int3
     if (dp.M == 0 || dp.N == 0) return BE_OK;
     std::lock_guard<std::mutex> g(x->mu);
     if ((st = ensure_status(x)) || (st = ensure_ws(x, dense_workspace_bytes(dp.M, dp.N, dp.K)))) return st;
-    int prevB = -1;
-    for (auto &r : dp.rows) {
-      if (dp.K == 0) {
-        ce = cudaMemsetAsync(r.C, 0, sizeof(double) * (size_t)(dp.M * dp.N), s);
-      } else {
-        if (r.argB != prevB) {
-          KernelMark km(x, BE_KERNEL_SPLIT, s);
-          ce = dense_split_b(DenseB{r.B, dp.K, dp.N, r.ldb, r.snb, dp.M, r.alB, r.beB}, x->ws, s);
-          prevB = r.argB;
-        }
-        if (ce == cudaSuccess) {
-          KernelMark km(x, BE_KERNEL_SPLIT, s);
-          ce = dense_split_a(DenseA{r.A, dp.M, r.lda, r.ska, r.alA, r.beA}, dp.K, dp.M, dp.N, x->ws, s);
-        }
-        if (ce == cudaSuccess) {
-          KernelMark km(x, BE_KERNEL_DENSE_GEMM, s);
-          ce = dense_split_gemm(DenseA{r.A, dp.M, r.lda, r.ska}, dp.N, dp.K, dp.M, r.C, dp.N, x->ws, c.split >= 4,
-                                c.tile[2] > 0 ? c.tile[2] : 2, x->status, x->wait_limit, s);
-        }
-      }
-      if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("dense split: ") + cudaGetErrorString(ce));
-    }
+    ce = run_dense_rows(x, dp, c, x->ws, x->status, x->wait_limit, s);
+    if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("dense split: ") + cudaGetErrorString(ce));
     return BE_OK;
   }
   if (strategy == BE_STRAT_ELEMENT) {
@@ -855,22 +866,61 @@ struct be_batch {
   GParams *d_rows = nullptr;
   PTile *d_tiles = nullptr;
   unsigned long long *d_counter = nullptr;
-  cudaStream_t cap = nullptr;
+  cudaStream_t cap = nullptr, branch[2] = {nullptr, nullptr};
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int grid = 0, block = 256;
   double terms = 0;
+  // instances per strategy, and the split workspace and status word of the
+  // dense instances (owned by the batch: the graph holds their addresses)
+  int32_t n_kind[3] = {0, 0, 0};
+  void *ws = nullptr;
+  int *status = nullptr;
+  bool own_status = false;
   ~be_batch() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (cap) cudaStreamDestroy(cap);
+    for (auto st : branch)
+      if (st) cudaStreamDestroy(st);
+    for (auto e : ev)
+      if (e) cudaEventDestroy(e);
     if (d_rows) cudaFree(d_rows);
     if (d_tiles) cudaFree(d_tiles);
     if (d_counter) cudaFree(d_counter);
+    if (ws) cudaFree(ws);
+    if (own_status && status) cudaFree(status);
   }
 };
 
 extern "C" {
+
+// Key of a batch in the tuning database: the canonical keys of its
+// instances (normal forms with their lengths, Alg. 1), sorted and hashed
+// (FNV-1a, 64 bits), so that any renaming or reordering of the instances
+// finds the same record.
+static int batch_key(int32_t n, const be_einsum *const *es, std::string &key) {
+  std::vector<std::string> ks;
+  std::string err;
+  int st;
+  for (int k = 0; k < n; ++k) {
+    if (!es[k]) return fail(BE_EARG, "NULL einsum in batch");
+    const Canon *c = be::canon_cached(const_cast<be_einsum *>(es[k]), err, st);
+    if (st) return fail(st, err);
+    ks.push_back(c->key);
+  }
+  std::sort(ks.begin(), ks.end());
+  uint64_t h = 1469598103934665603ull;
+  for (auto &k : ks) {
+    for (unsigned char ch : k) h = (h ^ ch) * 1099511628211ull;
+    h = (h ^ '\n') * 1099511628211ull;
+  }
+  char buf[64];
+  std::snprintf(buf, sizeof buf, "batch1:%d:%016llx", n, (unsigned long long)h);
+  key = buf;
+  return BE_OK;
+}
 
 int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_buf *const *bufs,
                     const int32_t *n_bufs, const be_buf *const *outs, const int32_t *n_outs,
@@ -880,12 +930,32 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
   b->x = x;
   be_config_t c;
   std::memset(&c, 0, sizeof(c));
-  if (cfg) std::memcpy(&c, cfg, sizeof(c));
+  if (cfg) {
+    std::memcpy(&c, cfg, sizeof(c));
+  } else if (x && n > 0) {
+    // a configuration tuned for this batch (be_tune_batch), by the batch key
+    std::string bk;
+    if (batch_key(n, es, bk) == BE_OK) {
+      std::lock_guard<std::mutex> g(x->mu);
+      auto it = x->db.find(db_key(bk, x->device_name, BE_PREC_FP64));
+      if (it != x->db.end()) std::memcpy(&c, &it->second.cfg, sizeof(c));
+    }
+  }
   b->block = c.tile[0] > 0 ? c.tile[0] : 256;
   if (b->block % 32 || b->block > 256) return fail(BE_EARG, "block size must be a multiple of 32 up to 256");
   const int cost_log2 = c.tile[1] > 0 ? c.tile[1] : 20;
   const int per_sm = c.tile[2] > 0 ? c.tile[2] : 4;
   const double cost_target = std::ldexp(1.0, cost_log2);
+  // strategy policy: element-shaped FP64 instances take the element strategy
+  // unless stage_mask bit 0 is set; with split >= 1, FP64 instances of GEMM
+  // form with at least 2^tile[3] (default 2^20) multiply-adds take the
+  // split-precision tensor-core strategy
+  const bool allow_element = !(c.stage_mask & 1u);
+  const double dense_min = std::ldexp(1.0, c.tile[3] > 0 ? c.tile[3] : 20);
+  std::vector<int> el_inst, dn_inst;
+  std::vector<be_config_t> el_cfg;
+  std::vector<DensePlan> dn_plan;
+  size_t ws_need = 0;
   std::string err;
   for (int k = 0; k < n; ++k) {
     if (!es[k]) return fail(BE_EARG, "NULL einsum in batch");
@@ -899,11 +969,38 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
     if (ns != (int)e.scalars.size()) return fail(BE_EARG, "instance " + std::to_string(k) + ": scalar count");
     std::vector<double> sc(ns);
     for (int q = 0; q < ns; ++q) sc[q] = scalars[k][q];
+    {
+      // the instance's own configuration (database record, else defaults)
+      be_config_t ci;
+      st = resolve_config(x, const_cast<be_einsum *>(es[k]), nullptr, BE_PREC_FP64, ci);
+      if (st) return st;
+      std::string why;
+      EParams ep;
+      DensePlan dp;
+      if (allow_element && plan_element(e, bi, bo, ci, ep, why) == OK) {
+        ci.strategy = BE_STRAT_ELEMENT;
+        el_inst.push_back(k);
+        el_cfg.push_back(ci);
+        ++b->n_kind[1];
+        continue;
+      }
+      if (c.split >= 1 && plan_dense(e, bi, bo, dp, why, &sc) == OK &&
+          (double)dp.M * (double)dp.N * (double)dp.K * (double)dp.rows.size() >= dense_min) {
+        ws_need = std::max(ws_need, dense_workspace_bytes(dp.M, dp.N, dp.K));
+        dn_inst.push_back(k);
+        dn_plan.push_back(dp);
+        ++b->n_kind[2];
+        continue;
+      }
+    }
+    ++b->n_kind[0];
     for (int i = 0; i < e.b; ++i) {
       GParams p;
       st = plan_generic_row(e, i, bi, bo[i], sc, p, err);
       if (st) return fail(st, "instance " + std::to_string(k) + ": " + err);
       if (p.total_out == 0) continue;
+      if (p.mode == 3 && b->block != 256)
+        return fail(BE_EARG, "instance " + std::to_string(k) + ": rows evaluated as GEMM tiles need a block of 256 threads");
       const int row = (int)b->rows.size();
       b->rows.push_back(p);
       // outputs per tile so that each tile costs about cost_target operand terms
@@ -953,20 +1050,159 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
     ce = cudaMemcpy(b->d_rows, b->rows.data(), sizeof(GParams) * b->rows.size(), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess && !b->tiles.empty())
     ce = cudaMemcpy(b->d_tiles, b->tiles.data(), sizeof(PTile) * b->tiles.size(), cudaMemcpyHostToDevice);
-  // capture counter reset + launch once; every run replays the graph
-  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-  if (ce == cudaSuccess) ce = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
-  if (ce == cudaSuccess) {
-    cudaError_t c1 = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), b->cap);
-    cudaError_t c2 = c1 == cudaSuccess ? launch_persistent(b->d_rows, b->d_tiles, (int64_t)b->tiles.size(),
-                                                         b->d_counter, b->grid, b->block, b->cap)
-                                       : c1;
-    ce = cudaStreamEndCapture(b->cap, &b->graph);
-    if (c2 != cudaSuccess) ce = c2;
+  if (ce == cudaSuccess && ws_need) ce = cudaMalloc(&b->ws, ws_need);
+  if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("batch setup: ") + cudaGetErrorString(ce));
+  if (!el_inst.empty() || !dn_inst.empty()) {
+    if (x) {
+      std::lock_guard<std::mutex> g(x->mu);
+      int st = ensure_status(x);
+      if (st) return st;
+      b->status = x->status;
+    } else {
+      ce = cudaMalloc(&b->status, sizeof(int));
+      if (ce == cudaSuccess) ce = cudaMemset(b->status, 0, sizeof(int));
+      if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("batch status word: ") + cudaGetErrorString(ce));
+      b->own_status = true;
+    }
   }
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  for (int q = 0; q < 2 && ce == cudaSuccess; ++q) ce = cudaStreamCreateWithFlags(&b->branch[q], cudaStreamNonBlocking);
+  for (int q = 0; q < 3 && ce == cudaSuccess; ++q) ce = cudaEventCreateWithFlags(&b->ev[q], cudaEventDisableTiming);
+  if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("batch setup: ") + cudaGetErrorString(ce));
+  const bool timing = x && x->timing;
+  if (x) x->timing = false;   // no timing events inside the captured graph
+  // element and dense instances: their launches, once outside the capture
+  // (first-launch set-up such as kernel attributes happens here) and then
+  // captured on their own branches
+  const long long wl = x ? x->wait_limit : 0;
+  auto launch_el = [&](cudaStream_t st) -> int {
+    for (size_t q = 0; q < el_inst.size(); ++q) {
+      const int k = el_inst[q];
+      be_config cq;
+      std::memcpy(&cq, &el_cfg[q], sizeof(cq));
+      int r = be::execute_internal(x, es[k], &cq, BE_PREC_FP64, bufs[k], n_bufs[k], outs[k], n_outs[k],
+                                   n_scalars && n_scalars[k] ? scalars[k] : nullptr, n_scalars ? n_scalars[k] : 0, st);
+      if (r) return r;
+    }
+    return BE_OK;
+  };
+  auto launch_dn = [&](cudaStream_t st) -> cudaError_t {
+    be_config_t cd;
+    std::memset(&cd, 0, sizeof(cd));
+    for (size_t q = 0; q < dn_inst.size(); ++q) {
+      cudaError_t r = run_dense_rows(nullptr, dn_plan[q], cd, b->ws, b->status, wl, st);
+      if (r != cudaSuccess) return r;
+    }
+    return cudaSuccess;
+  };
+  int est = launch_el(b->branch[0]);
+  if (!est && (ce = launch_dn(b->branch[1])) == cudaSuccess) ce = cudaDeviceSynchronize();
+  if (est || ce != cudaSuccess) {
+    if (x) x->timing = timing;
+    return est ? est : fail(BE_ECUDA, std::string("batch first launch: ") + cudaGetErrorString(ce));
+  }
+  // capture: counter reset + persistent launch on the capture stream; the
+  // element and dense branches fork from it and join back
+  ce = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+  if (ce == cudaSuccess) {
+    // the branches fork before the persistent launch, so that the three
+    // parts are concurrent in the graph (the side kernels take SMs as the
+    // persistent grid's CTAs leave) and join after it
+    cudaError_t c1 = cudaSuccess;
+    const bool side = !el_inst.empty() || !dn_inst.empty();
+    if (side) {
+      c1 = cudaEventRecord(b->ev[0], b->cap);
+      for (int q = 0; q < 2 && c1 == cudaSuccess; ++q) c1 = cudaStreamWaitEvent(b->branch[q], b->ev[0], 0);
+      if (c1 == cudaSuccess) {
+        est = launch_el(b->branch[0]);
+        if (est) c1 = cudaErrorUnknown;
+      }
+      if (c1 == cudaSuccess) c1 = launch_dn(b->branch[1]);
+    }
+    if (c1 == cudaSuccess) c1 = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), b->cap);
+    if (c1 == cudaSuccess)
+      c1 = launch_persistent(b->d_rows, b->d_tiles, (int64_t)b->tiles.size(), b->d_counter, b->grid, b->block, b->cap);
+    if (side) {
+      for (int q = 0; q < 2 && c1 == cudaSuccess; ++q) c1 = cudaEventRecord(b->ev[1 + q], b->branch[q]);
+      for (int q = 0; q < 2 && c1 == cudaSuccess; ++q) c1 = cudaStreamWaitEvent(b->cap, b->ev[1 + q], 0);
+    }
+    ce = cudaStreamEndCapture(b->cap, &b->graph);
+    if (c1 != cudaSuccess) ce = c1;
+  }
+  if (x) x->timing = timing;
+  if (est) return est;
   if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->exec, b->graph, 0);
   if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("batch setup: ") + cudaGetErrorString(ce));
   *out = b.release();
+  return BE_OK;
+}
+
+int be_tune_batch(be_ctx *x, int32_t n, const be_einsum *const *es, const be_buf *const *bufs,
+                  const int32_t *n_bufs, const be_buf *const *outs, const int32_t *n_outs,
+                  const double *const *scalars, const int32_t *n_scalars, const be_config *base, int32_t reps,
+                  void *stream, be_config *best, double *best_seconds, int32_t *n_tried) {
+  if (!x || !best || n <= 0) return fail(BE_EARG, "bad arguments");
+  if (n_tried) *n_tried = 0;
+  std::string bk;
+  int st = batch_key(n, es, bk);
+  if (st) return st;
+  be_canon bc;
+  bc.c.key = bk;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t a, e2;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&e2) != cudaSuccess) return fail(BE_ECUDA, "event");
+  double best_t = -1;
+  // the persistent part's launch shape: block size, CTAs per SM and the
+  // operand terms per tile; the strategy policy (split, tile[3],
+  // stage_mask) is the caller's
+  for (int block : {128, 256})
+    for (int per_sm : {2, 3, 4})
+      for (int cost : {18, 20, 22}) {
+        be_config cand;
+        std::memset(&cand, 0, sizeof(cand));
+        if (base) cand = *base;
+        cand.tile[0] = block;
+        cand.tile[1] = cost;
+        cand.tile[2] = per_sm;
+        be_batch *bt = nullptr;
+        st = be_batch_create(x, n, es, bufs, n_bufs, outs, n_outs, scalars, n_scalars, &cand, &bt);
+        if (st) { st = BE_OK; continue; }     // a candidate that cannot be planned is skipped
+        double total = 0;
+        int done = 0;
+        bool okc = be_batch_run(bt, stream) == BE_OK;
+        for (int r = 0; okc && r < std::max(1, reps); ++r) {
+          cudaEventRecord(a, s);
+          okc = be_batch_run(bt, stream) == BE_OK;
+          cudaEventRecord(e2, s);
+          if (!okc || cudaEventSynchronize(e2) != cudaSuccess) { okc = false; break; }
+          float ms = 0;
+          cudaEventElapsedTime(&ms, a, e2);
+          total += ms * 1e-3;
+          ++done;
+        }
+        be_batch_destroy(bt);
+        if (!okc || !done) continue;
+        const double sec = total / done;
+        if (n_tried) ++*n_tried;
+        const int rs = be_record(x, &bc, BE_PREC_FP64, &cand, sec);
+        if (rs) { cudaEventDestroy(a); cudaEventDestroy(e2); return rs; }
+        if (best_t < 0 || sec < best_t) {
+          best_t = sec;
+          *best = cand;
+        }
+      }
+  cudaEventDestroy(a);
+  cudaEventDestroy(e2);
+  if (best_t < 0) return fail(BE_EUNSUPPORTED, "no candidate batch configuration ran");
+  if (best_seconds) *best_seconds = best_t;
+  return BE_OK;
+}
+
+int be_batch_kinds(const be_batch *b, int32_t *generic, int32_t *element, int32_t *dense) {
+  if (!b) return fail(BE_EARG, "NULL batch");
+  if (generic) *generic = b->n_kind[0];
+  if (element) *element = b->n_kind[1];
+  if (dense) *dense = b->n_kind[2];
   return BE_OK;
 }
 

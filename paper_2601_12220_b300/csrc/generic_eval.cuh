@@ -368,7 +368,10 @@ __device__ void gemm_tile(const GParams &p, int64_t tile, unsigned char *sm) {
   constexpr int S = TM + 16 / (int)sizeof(T);       // padded row of a staged slice
   constexpr int PER = TM * GT_K / 256;              // staged values per thread and operand
   const GGemm &g = p.gemm;
-  if (tile >= g.tiles) return;                      // uniform over the CTA
+  // uniform over the CTA: a tile outside the grid, or a CTA of other than
+  // 256 threads (the staging below assigns its tables to fixed thread
+  // ranges; the host never launches such a CTA for GEMM rows)
+  if (tile >= g.tiles || blockDim.x != 256) return;
   T *As = (T *)sm;                                  // [GT_K][S]
   T *Bs = As + GT_K * S;                            // [GT_K][S]
   int64_t *offAm = (int64_t *)(sm + 2 * GT_K * (GT_MAX + 2) * 8);

@@ -108,3 +108,18 @@ def test_plan_dense_affine_producers():
         e = be.Einsum(f"ik,kj->ij | P,B ; A:f64[64,48] ; B:f64[48,40] ; {body}")
         want = be.STRAT_DENSE_SPLIT if body in ok else be.STRAT_GENERIC
         assert be.plan_strategy(None, e, precision=be.PREC_SPLIT) == want, body
+
+
+def test_batch_records_load(tmp_path):
+    """Records of tuned batches (keys "batch1:<n>:<hash of the instances'
+    canonical keys>") are read back from the database file like einsum
+    records; other prefixes are refused."""
+    p = tmp_path / "b.db"
+    p.write_text("batch1:16:00ff00ff00ff00ff\tdev\t0\t0 256 20 4 0 0 0 0 1\t2.5e-03\n"
+                 "batch1:16:00ff00ff00ff00ff\tdev\t0\t0 128 18 2 0 0 0 0 1\t3.5e-03\n")
+    ctx = be.Context(str(p), device_name="dev", device=-1)
+    assert ctx.db_size() == 1
+    p.write_text("tune:16:00ff\tdev\t0\t0 256 20 4 0 0 0 0 1\t2.5e-03\n")
+    with pytest.raises(be.BEError) as ex:
+        be.Context(str(p), device_name="dev", device=-1)
+    assert ex.value.code == be.EDB

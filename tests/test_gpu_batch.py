@@ -43,16 +43,32 @@ def generic_alone(e, bufs):
     return outs
 
 
+def default_alone(ctx, e, bufs):
+    dt = torch.float64 if e.out_dtype == be.F64 else torch.float32
+    outs = [torch.empty(e.out_shape, dtype=dt, device=DEV) for _ in range(e.b)]
+    be.execute(ctx, e, bufs, outs)
+    return outs
+
+
 def test_batch_bitwise_equals_generic_and_oracle():
+    """Generic instances match BE_STRAT_GENERIC alone bit for bit; the
+    element-shaped FP64 instances of the mix take the element strategy and
+    match be_execute's default (the same kernel) bit for bit."""
     items, meta = make_items(40, 7, lo_exp=1.0, hi_exp=5.0, max_operand=1 << 16, max_flops=1 << 22)
     ctx = be.Context(None, device=0)
     b = be.Batch(ctx, items)
+    kinds = b.kinds()
+    n_el = sum(1 for e, _, _ in items if be.plan_strategy(ctx, e) == be.STRAT_ELEMENT)
+    assert kinds["element"] == n_el and kinds["dense"] == 0 and kinds["generic"] == len(items) - n_el
     info = b.info()
-    assert info["rows"] == sum(e.b for e, _, _ in items)
+    assert info["rows"] == sum(e.b for e, _, _ in items if be.plan_strategy(ctx, e) != be.STRAT_ELEMENT)
     b.run()
     torch.cuda.synchronize()
     for (e, bufs, outs), (inst, text, arrs) in zip(items, meta):
-        alone = generic_alone(e, bufs)
+        if be.plan_strategy(ctx, e) == be.STRAT_ELEMENT:
+            alone = default_alone(ctx, e, bufs)
+        else:
+            alone = generic_alone(e, bufs)
         torch.cuda.synchronize()
         for o, a in zip(outs, alone):
             assert torch.equal(o, a)
@@ -83,7 +99,10 @@ def test_batch_replay_sees_new_contents():
     b.run()
     torch.cuda.synchronize()
     for e, bufs, outs in items:
-        alone = generic_alone(e, bufs)
+        if be.plan_strategy(None, e) == be.STRAT_ELEMENT:
+            alone = default_alone(None, e, bufs)
+        else:
+            alone = generic_alone(e, bufs)
         torch.cuda.synchronize()
         for o, a in zip(outs, alone):
             assert torch.equal(o, a)
@@ -148,3 +167,93 @@ def test_gemm_tiles_same_bits_at_any_tile_side(dt):
         alone = generic_alone(e, bufs)
         torch.cuda.synchronize()
         assert torch.equal(outs[0], alone[0])
+
+
+def test_mixed_kind_batch():
+    """One graph with all three strategies: element-shaped FP64 instances
+    (FEM action, DG gradient P4 on the tensor-core element kernel), dense
+    FP64 GEMM-form instances on the split-precision tensor-core path
+    (cfg.split = 1) and generic instances.  Each result equals be_execute
+    with the same strategy alone, bit for bit, and the oracle within the
+    strategy's tolerance (1e-12 S; 1e-6 S for the split path; FP32 rows
+    max(gamma_K, 1e-6) S)."""
+    g = np.random.default_rng(31)
+    items, meta, kind = [], [], []
+
+    def add(text, arrs, k):
+        e = be.Einsum(text)
+        dt = torch.float64 if e.out_dtype == be.F64 else torch.float32
+        bufs = {n: torch.from_numpy(v).to(DEV) for n, v in arrs.items()}
+        outs = [torch.full(e.out_shape, float("nan"), dtype=dt, device=DEV) for _ in range(e.b)]
+        items.append((e, bufs, outs))
+        meta.append((text, arrs))
+        kind.append(k)
+
+    # element: FEM action b = 4 and the DG gradient P4
+    D = g.uniform(-1, 1, (4, 4))
+    us = {f"u{k}": g.uniform(-1, 1, (3000, 4)) for k in range(4)}
+    add("ij,ej->ei | " + " | ".join(f"D,u{k}" for k in range(4)) + " ; D:f64[4,4] ; " +
+        " ; ".join(f"u{k}:f64[3000,4]" for k in range(4)), dict(D=D, **us), "element")
+    Dg, G, a, bb = W.dg_gradient(E=2500)
+    add(W.dg_gradient_spec(E=2500), dict(D=Dg, G=G, a=a, b=bb), "element")
+    # dense: FP64 matmul and the cluster form, above 2^20 multiply-adds
+    A, B = g.standard_normal((256, 192)), g.standard_normal((192, 320))
+    add("ik,kj->ij | A,B ; A:f64[256,192] ; B:f64[192,320]", dict(A=A, B=B), "dense")
+    T, V = g.standard_normal((12, 12, 16, 16)), g.standard_normal((16, 16, 12, 12))
+    add("ijcd,cdab->ijab | T,V | T,W ; T:f64[12,12,16,16] ; V:f64[16,16,12,12] ; W:f64[16,16,12,12]",
+        dict(T=T, V=V, W=g.standard_normal((16, 16, 12, 12))), "dense")
+    # generic: the mix
+    gi, gm = make_items(12, 8, lo_exp=1.0, hi_exp=4.0, max_operand=1 << 14, max_flops=1 << 18)
+    for it, m in zip(gi, gm):
+        e = it[0]
+        if be.plan_strategy(None, e) == be.STRAT_ELEMENT:
+            continue
+        items.append(it)
+        meta.append((m[1], m[2]))
+        kind.append("generic")
+    ctx = be.Context(None, device=0)
+    batch = be.Batch(ctx, items, be.make_config(split=1))
+    k = batch.kinds()
+    assert k == {"generic": kind.count("generic"), "element": 2, "dense": 2}
+    batch.run()
+    torch.cuda.synchronize()
+    for (e, bufs, outs), (text, arrs), kd in zip(items, meta, kind):
+        if kd == "element":
+            alone = default_alone(ctx, e, bufs)
+        elif kd == "dense":
+            dt = torch.float64
+            alone = [torch.empty(e.out_shape, dtype=dt, device=DEV) for _ in range(e.b)]
+            be.execute(ctx, e, bufs, alone, precision=be.PREC_SPLIT, cfg=be.make_config(be.STRAT_DENSE_SPLIT))
+        else:
+            alone = generic_alone(e, bufs)
+        torch.cuda.synchronize()
+        for o, a_ in zip(outs, alone):
+            assert torch.equal(o, a_), (kd, text[:60])
+        if kd == "generic":
+            continue                      # bitwise the generic strategy, checked against the oracle above
+        ref = ev.evaluate(text, arrs)
+        tol = 1e-6 if kd == "dense" else 1e-12
+        for o, (r, S) in zip(outs, ref):
+            assert np.all(np.abs(o.cpu().numpy() - r) <= tol * S), (kd, text[:60])
+    assert ctx.status() == be.OK
+
+
+def test_tune_batch_records_under_batch_key(tmp_path):
+    """be_tune_batch times the launch-shape candidates of a batch and records
+    them under the batch key; a batch created without a configuration then
+    uses the best record -- also when the same instances are listed in
+    another order (the key is built from their sorted canonical keys)."""
+    items, _ = make_items(16, 12, lo_exp=2.0, hi_exp=6.0, max_operand=1 << 16, max_flops=1 << 22)
+    ctx = be.Context(str(tmp_path / "db.txt"), device=0)
+    best, sec, n = be.tune_batch(ctx, items, reps=2)
+    assert n in (9, 18) and sec > 0
+    assert best.tile[0] in (128, 256) and best.tile[1] in (18, 20, 22) and best.tile[2] in (2, 3, 4)
+    assert ctx.db_size() == 1
+    tuned = be.Batch(ctx, items)
+    ref = be.Batch(None, items, best)
+    assert tuned.info() == ref.info()
+    rev = be.Batch(ctx, list(reversed(items)))
+    assert rev.info() == ref.info()
+    # resume: a fresh context reading the same file finds the record
+    ctx2 = be.Context(str(tmp_path / "db.txt"), device=0)
+    assert be.Batch(ctx2, items).info() == ref.info()
