@@ -395,6 +395,15 @@ int be_server_drain(be_server *s, double timeout_s);
 int be_server_stats(be_server *s, int64_t *completed, int64_t *failed, double *p50_s, double *p99_s,
                     double *throughput, size_t *peak_bytes, int64_t *max_inflight);
 int be_server_reset_stats(be_server *s);
+/*
+ * be_server_trace -- the tracing view of the requests completed since the
+ * last reset: per request six doubles (id, submit, admit, launched, done,
+ * stream index), times in seconds of a steady clock; `launched` is when
+ * the request's launch calls returned on the worker thread, `done` when
+ * the completion thread saw its event.  Copies min(cap, n) rows into rows
+ * (6 doubles each, completion order) and returns n.  Errors: BE_EARG.
+ */
+int be_server_trace(be_server *s, double *rows, int64_t cap, int64_t *n);
 void be_server_destroy(be_server *s);
 
 /*

@@ -35,7 +35,7 @@ EXPORTS = [
     "be_gemm_split_noalloc_status", "be_ctx_set_wait_limit",
     "be_batch_create", "be_batch_run", "be_batch_info", "be_batch_kinds", "be_batch_destroy", "be_tune", "be_tune_batch",
     "be_server_create", "be_server_submit", "be_server_wait", "be_server_drain", "be_server_stats",
-    "be_server_reset_stats", "be_server_destroy", "be_raise", "be_raised_name", "be_record_facts",
+    "be_server_reset_stats", "be_server_trace", "be_server_destroy", "be_raise", "be_raised_name", "be_record_facts",
     "be_load_transforms",
 ]
 KERNEL_ELEMENT, KERNEL_GENERIC, KERNEL_DENSE_GEMM, KERNEL_SPLIT, KERNEL_PERSISTENT = 0, 1, 2, 3, 4
@@ -131,6 +131,7 @@ def lib():
             "be_server_stats": (ctypes.c_int, [vp, P(i64), P(i64), P(ctypes.c_double), P(ctypes.c_double),
                                                P(ctypes.c_double), P(sz), P(i64)]),
             "be_server_reset_stats": (ctypes.c_int, [vp]),
+            "be_server_trace": (ctypes.c_int, [vp, P(ctypes.c_double), i64, P(i64)]),
             "be_server_destroy": (None, [vp]),
             "be_tune": (ctypes.c_int, [vp, vp, i32, P(Buf), i32, P(Buf), i32, P(ctypes.c_double), i32, i32, i32,
                                        ctypes.c_double, i32, vp, P(Config), P(ctypes.c_double), P(i32)]),
@@ -515,6 +516,15 @@ class Server:
                                     ctypes.byref(thr), ctypes.byref(pk), ctypes.byref(mi)))
         return {"completed": c.value, "failed": f.value, "p50_s": p50.value, "p99_s": p99.value,
                 "throughput": thr.value, "peak_bytes": pk.value, "max_inflight": mi.value}
+
+    def trace(self):
+        """Completed requests since the last reset: array of rows (id, submit,
+        admit, launched, done, stream), seconds."""
+        n = ctypes.c_int64()
+        check(lib().be_server_trace(self._h, None, 0, ctypes.byref(n)))
+        rows = (ctypes.c_double * (6 * max(1, n.value)))()
+        check(lib().be_server_trace(self._h, rows, n.value, ctypes.byref(n)))
+        return np.frombuffer(rows, dtype=np.float64)[: 6 * n.value].reshape(-1, 6).copy()
 
     def reset_stats(self):
         check(lib().be_server_reset_stats(self._h))

@@ -16,6 +16,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "dense.hpp"
+#include "launch_rec.hpp"
 #include "handles.hpp"
 #include "raise.hpp"
 
@@ -38,6 +39,11 @@ static int fail(int code, const std::string &msg) {
 namespace be {
 // lets the other translation units of the library report through be_last_error()
 void set_last_error(const std::string &msg) { g_err = msg; }
+// the calling thread's launch recorder (launch_rec.hpp)
+LaunchRecorder *&launch_recorder() {
+  static thread_local LaunchRecorder *r = nullptr;
+  return r;
+}
 }  // namespace be
 
 static int ensure_status(be_ctx *x) {

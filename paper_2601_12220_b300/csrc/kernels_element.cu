@@ -19,6 +19,7 @@
 // contiguous.
 #include "exec.hpp"
 #include "launch_attr.hpp"
+#include "launch_rec.hpp"
 
 namespace be {
 
@@ -109,8 +110,7 @@ cudaError_t launch_element(const EParams &p, int grid, int block, cudaStream_t s
   static std::atomic<uint64_t> attr{0};
   cudaError_t st = smem_limit_once((const void *)element_kernel, 200 * 1024, attr);
   if (st != cudaSuccess) return st;
-  element_kernel<<<grid, block, smem, s>>>(p);
-  return cudaGetLastError();
+  return be_launch(element_kernel, dim3(grid), dim3(block), smem, s, p);
 }
 
 }  // namespace be

@@ -13,6 +13,7 @@
 #include "df_math.cuh"
 #include "exec.hpp"
 #include "launch_attr.hpp"
+#include "launch_rec.hpp"
 
 namespace be {
 
@@ -348,13 +349,12 @@ cudaError_t launch_element_df_small(const EParams &p, int fp64_share16, cudaStre
   const dim3 grid((unsigned)std::max<int64_t>(1, b64 + bdf), (unsigned)p.n_groups);
   const bool r1 = p.R == 1;
   if (p.NI <= 4 && p.NJ <= 4) {
-    if (r1) element_df_small_kernel<4, 1><<<grid, 256, 0, s>>>(p, E64, (int)b64);
-    else element_df_small_kernel<4, EM_MAXR><<<grid, 256, 0, s>>>(p, E64, (int)b64);
+    return r1 ? be_launch(element_df_small_kernel<4, 1>, grid, dim3(256), 0, s, p, E64, (int)b64)
+              : be_launch(element_df_small_kernel<4, EM_MAXR>, grid, dim3(256), 0, s, p, E64, (int)b64);
   } else {
-    if (r1) element_df_small_kernel<8, 1><<<grid, 256, 0, s>>>(p, E64, (int)b64);
-    else element_df_small_kernel<8, EM_MAXR><<<grid, 256, 0, s>>>(p, E64, (int)b64);
+    return r1 ? be_launch(element_df_small_kernel<8, 1>, grid, dim3(256), 0, s, p, E64, (int)b64)
+              : be_launch(element_df_small_kernel<8, EM_MAXR>, grid, dim3(256), 0, s, p, E64, (int)b64);
   }
-  return cudaGetLastError();
 }
 
 int element_df_block(const EParams &p) {
@@ -369,8 +369,7 @@ cudaError_t launch_element_df(const EParams &p, int grid, int block, cudaStream_
   static std::atomic<uint64_t> attr{0};
   cudaError_t st = smem_limit_once((const void *)element_df_kernel, 200 * 1024, attr);
   if (st != cudaSuccess) return st;
-  element_df_kernel<<<grid, block, smem, s>>>(p);
-  return cudaGetLastError();
+  return be_launch(element_df_kernel, dim3(grid), dim3(block), smem, s, p);
 }
 
 }  // namespace be

@@ -74,6 +74,7 @@
 #include "exec.hpp"
 #include "launch_attr.hpp"
 #include "tc_common.cuh"
+#include "launch_rec.hpp"
 
 namespace be {
 
@@ -806,8 +807,7 @@ cudaError_t launch_rr(const TcParams &tp, int grid, size_t smem, cudaStream_t s)
   static std::atomic<uint64_t> attr{0};
   const cudaError_t st = smem_limit_once((const void *)element_tc_kernel<R, ROWS>, (int)TC_SMEM_LIMIT, attr);
   if (st != cudaSuccess) return st;
-  element_tc_kernel<R, ROWS><<<grid, TC_THREADS, smem, s>>>(tp);
-  return cudaGetLastError();
+  return be_launch(element_tc_kernel<R, ROWS>, dim3(grid), dim3(TC_THREADS), smem, s, tp);
 }
 // one einsum per term direction (R einsums, as in a gradient) is
 // specialized; other counts take the generic row loop

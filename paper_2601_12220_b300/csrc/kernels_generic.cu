@@ -5,6 +5,7 @@
 // producer program (the lambda of a functional batched einsum, evaluated at
 // the access, i.e. fused into the load).  Accumulates in the output's type.
 #include "generic_eval.cuh"
+#include "launch_rec.hpp"
 
 namespace be {
 
@@ -42,8 +43,7 @@ cudaError_t launch_generic(const GParams &p0, cudaStream_t s) {
   const int64_t per = p.mode == 0 ? block : (p.mode == 1 ? block / 32 : 1);
   const int64_t blocks = p.mode == 3 ? p.gemm.tiles : (p.total_out + per - 1) / per;
   const int grid = (int)(blocks < 148 * 16 ? blocks : 148 * 16);
-  generic_kernel<<<grid, block, 0, s>>>(p);
-  return cudaGetLastError();
+  return be_launch(generic_kernel, dim3(grid), dim3(block), 0, s, p);
 }
 
 }  // namespace be

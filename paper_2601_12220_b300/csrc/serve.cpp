@@ -15,7 +15,19 @@
 // the previous one's kernels finish.
 // The configuration of each request comes from the tuning database under its
 // normal form (Alg. 1 + lookup), memoized by the request's text.
+// Requests repeat: the same einsum on the same resident buffers.  A request
+// whose template has no graph yet launches directly, and a capture thread
+// then records the template's launches into a CUDA graph, keyed by the
+// einsum, its buffers, scalars and configuration; later requests of the
+// template replay the graph (one launch call of a few microseconds instead of
+// one per row with its parameter block), which keeps the single worker thread
+// ahead of the arrivals.  The graph is built by recording the launches as
+// kernel nodes (no stream capture, which would make the caller's device
+// synchronizations fail while it lasts), on its own thread, so it never holds
+// up admission.  Split-precision requests use the
+// context's workspace, which can move, and always launch directly.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -24,6 +36,7 @@
 #include <thread>
 
 #include "handles.hpp"
+#include "launch_rec.hpp"
 
 namespace {
 
@@ -59,12 +72,32 @@ struct be_server {
   std::unordered_map<int64_t, std::unique_ptr<ServeReq>> reqs;
   int64_t next_id = 1;
   std::vector<double> latencies;
+  // per completed request: id, submit, admit, launched (the launch calls
+  // returned), done, stream -- the tracing view of the latency
+  std::vector<std::array<double, 6>> trace;
   int64_t completed = 0, failed = 0;
   double first_submit = -1, last_done = -1;
   std::unordered_map<std::string, be_config> cfg_memo;
   std::unordered_map<std::string, bool> cfg_have;
   bool stop = false;
   std::thread worker, reaper;
+  // captured launches of request templates, filled by the capture thread
+  struct CaptureJob {
+    std::string key, text;
+    bool have;
+    be_config cfg;
+    std::vector<be_buf> bufs, outs;
+    std::vector<std::vector<int64_t>> strides;
+    std::vector<double> scalars;
+  };
+  std::mutex gmu;
+  std::condition_variable gcv;
+  std::unordered_map<std::string, cudaGraphExec_t> graphs;
+  std::unordered_map<std::string, bool> queued;
+  std::deque<CaptureJob> jobs;
+  bool gstop = false;
+  cudaStream_t cap = nullptr;
+  std::thread capturer;
 };
 
 struct ServeReq {
@@ -75,7 +108,8 @@ struct ServeReq {
   std::vector<std::vector<int64_t>> strides;
   std::vector<double> scalars;
   size_t bytes = 0;
-  double t_submit = 0, t_admit = 0, t_done = 0;
+  double t_submit = 0, t_admit = 0, t_launched = 0, t_done = 0;
+  int stream = -1;
   int state = 0;      // 0 queued, 1 running, 2 done
   int status = BE_OK;
 };
@@ -89,6 +123,7 @@ static void finish(be_server *s, ServeReq *r, double t, int status) {
   s->inflight -= 1;
   if (status == BE_OK) {
     s->latencies.push_back(t - r->t_submit);
+    s->trace.push_back({(double)r->id, r->t_submit, r->t_admit, r->t_launched, t, (double)r->stream});
     s->completed += 1;
     s->last_done = std::max(s->last_done, t);
   } else {
@@ -143,6 +178,65 @@ static void reaper_loop(be_server *s) {
     }
     s->cv_work.notify_one();
     s->cv_done.notify_all();
+  }
+}
+
+// key of a request template: einsum text, configuration, buffers (pointer,
+// dtype, strides), outputs and scalars, as raw bytes
+static std::string template_key(const ServeReq *r, const be_config *cfg) {
+  std::string k = r->e->e.text;       // the einsum by its text: a handle's address can be reused
+  k.push_back('\0');
+  auto put = [&](const void *p, size_t n) { k.append((const char *)p, n); };
+  const char has = cfg != nullptr;
+  put(&has, 1);
+  if (cfg) put(cfg, sizeof(*cfg));
+  for (const auto *v : {&r->bufs, &r->outs}) {
+    const size_t n = v->size();
+    put(&n, sizeof(n));
+    for (const be_buf &b : *v) {
+      put(&b.ptr, sizeof(b.ptr));
+      put(&b.ndim, sizeof(b.ndim));
+      put(&b.dtype, sizeof(b.dtype));
+      if (b.strides) put(b.strides, sizeof(int64_t) * (size_t)b.ndim);
+    }
+  }
+  put(r->scalars.data(), sizeof(double) * r->scalars.size());
+  return k;
+}
+
+// Capture thread: records each queued template's launches into a graph
+// (launch_rec.hpp: the launches become kernel nodes, nothing runs and no
+// stream is captured, so the caller's synchronizations are never affected)
+// and publishes the instantiated graph
+static void capture_loop(be_server *s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->gmu);
+  while (true) {
+    s->gcv.wait(lk, [&] { return s->gstop || !s->jobs.empty(); });
+    if (s->gstop) break;
+    be_server::CaptureJob j = std::move(s->jobs.front());
+    s->jobs.pop_front();
+    lk.unlock();
+    cudaGraphExec_t exec = nullptr;
+    // a private parse of the template's text: the caller may free its handle
+    // once its request is done
+    be_einsum *e = nullptr;
+    LaunchRecorder rec;
+    if (be_parse(j.text.c_str(), &e) == BE_OK && cudaGraphCreate(&rec.graph, 0) == cudaSuccess) {
+      launch_recorder() = &rec;
+      const int rc = be::execute_internal(s->x, e, j.have ? &j.cfg : nullptr, s->precision, j.bufs.data(),
+                                          (int32_t)j.bufs.size(), j.outs.data(), (int32_t)j.outs.size(),
+                                          j.scalars.data(), (int32_t)j.scalars.size(), s->cap);
+      launch_recorder() = nullptr;
+      if (rc == BE_OK && rec.status == cudaSuccess && rec.nodes > 0 &&
+          cudaGraphInstantiate(&exec, rec.graph, 0) != cudaSuccess)
+        exec = nullptr;
+      cudaGraphDestroy(rec.graph);
+    }
+    be_free_einsum(e);
+    cudaGetLastError();   // a failed recording leaves no sticky error behind
+    lk.lock();
+    if (exec) s->graphs.emplace(j.key, exec);
   }
 }
 
@@ -213,9 +307,50 @@ static void worker_loop(be_server *s) {
       s->peak_bytes = std::max(s->peak_bytes, s->inflight_bytes);
       s->max_inflight = std::max(s->max_inflight, s->inflight);
       lk.unlock();
-      int rc = be::execute_internal(s->x, r->e, have ? &cfg : nullptr, s->precision, r->bufs.data(),
-                                    (int32_t)r->bufs.size(), r->outs.data(), (int32_t)r->outs.size(),
-                                    r->scalars.data(), (int32_t)r->scalars.size(), st);
+      int rc = BE_OK;
+      bool done_launch = false;
+      const bool graphable = s->precision != BE_PREC_SPLIT && s->cap && !(s->x && s->x->timing);
+      std::string key;
+      if (graphable) {
+        key = template_key(r, have ? &cfg : nullptr);
+        std::lock_guard<std::mutex> g(s->gmu);
+        auto it2 = s->graphs.find(key);
+        if (it2 != s->graphs.end()) {
+          rc = cudaGraphLaunch(it2->second, st) == cudaSuccess ? BE_OK : BE_ECUDA;
+          done_launch = true;
+        }
+      }
+      if (!done_launch) {
+        rc = be::execute_internal(s->x, r->e, have ? &cfg : nullptr, s->precision, r->bufs.data(),
+                                  (int32_t)r->bufs.size(), r->outs.data(), (int32_t)r->outs.size(),
+                                  r->scalars.data(), (int32_t)r->scalars.size(), st);
+        // queue the template for capture (once; at most 65536 templates)
+        if (rc == BE_OK && graphable) {
+          std::lock_guard<std::mutex> g(s->gmu);
+          if (!s->queued.count(key) && s->queued.size() < 65536) {
+            s->queued[key] = true;
+            be_server::CaptureJob j;
+            j.key = key;
+            j.text = r->e->e.text;
+            j.have = have;
+            if (have) j.cfg = cfg;
+            j.bufs = r->bufs;
+            j.outs = r->outs;
+            j.scalars = r->scalars;
+            j.strides.reserve(j.bufs.size() + j.outs.size());
+            for (auto *v : {&j.bufs, &j.outs})
+              for (auto &b : *v)
+                if (b.strides) {
+                  j.strides.emplace_back(b.strides, b.strides + b.ndim);
+                  b.strides = j.strides.back().data();
+                }
+            s->jobs.push_back(std::move(j));
+            s->gcv.notify_one();
+          }
+        }
+      }
+      r->t_launched = now_s();
+      r->stream = (int)si;
       if (rc == BE_OK && ev && cudaEventRecord(ev, st) == cudaSuccess) {
         lk.lock();
         s->running[si].emplace_back(r, ev);
@@ -264,9 +399,17 @@ int be_server_create(be_ctx *x, int32_t precision, int32_t n_streams, size_t hbm
     s->streams.push_back(st);
   }
   s->running.resize(s->streams.size());
+  if (cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess) s->cap = nullptr;
+  // room for many requests up front: growing these under the server's lock
+  // (a rehash of the request table, a copy of the latency records) stalled
+  // admission and completion for milliseconds at the growth points
+  s->reqs.reserve(1 << 20);
+  s->latencies.reserve(1 << 20);
+  s->trace.reserve(1 << 20);
   be_server *raw = s.get();
   raw->worker = std::thread(worker_loop, raw);
   raw->reaper = std::thread(reaper_loop, raw);
+  if (raw->cap) raw->capturer = std::thread(capture_loop, raw);
   *out = s.release();
   return BE_OK;
 }
@@ -346,10 +489,23 @@ int be_server_stats(be_server *s, int64_t *completed, int64_t *failed, double *p
   return BE_OK;
 }
 
+int be_server_trace(be_server *s, double *rows, int64_t cap, int64_t *n) {
+  if (!s || !n || (cap > 0 && !rows)) return sfail(BE_EARG, "bad arguments");
+  std::lock_guard<std::mutex> g(s->mu);
+  *n = (int64_t)s->trace.size();
+  const int64_t m = std::min<int64_t>(cap, *n);
+  for (int64_t k = 0; k < m; ++k)
+    for (int c = 0; c < 6; ++c) rows[k * 6 + c] = s->trace[(size_t)k][(size_t)c];
+  return BE_OK;
+}
+
 int be_server_reset_stats(be_server *s) {
   if (!s) return sfail(BE_EARG, "NULL server");
   std::lock_guard<std::mutex> g(s->mu);
   s->latencies.clear();
+  s->trace.clear();
+  s->latencies.reserve(1 << 20);
+  s->trace.reserve(1 << 20);
   s->completed = s->failed = 0;
   s->first_submit = s->last_done = -1;
   s->peak_bytes = s->inflight_bytes;
@@ -371,11 +527,21 @@ void be_server_destroy(be_server *s) {
     s->cv_reap.notify_one();
   }
   s->reaper.join();
+  if (s->capturer.joinable()) {
+    {
+      std::lock_guard<std::mutex> g(s->gmu);
+      s->gstop = true;
+    }
+    s->gcv.notify_one();
+    s->capturer.join();
+  }
   for (auto st : s->streams) {
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
   }
   for (auto ev : s->free_events) cudaEventDestroy(ev);
+  for (auto &g : s->graphs) cudaGraphExecDestroy(g.second);
+  if (s->cap) cudaStreamDestroy(s->cap);
   delete s;
 }
 

@@ -107,3 +107,36 @@ def test_server_budget():
     stats = srv.stats()
     assert stats["completed"] == len(ids) and stats["peak_bytes"] <= budget
     srv.close()
+
+
+def test_server_replays_repeated_templates():
+    """A request template (same einsum, same resident buffers) submitted
+    again is served from a captured graph after its second launch: every
+    repetition reads the buffers' current contents and gives the bits of a
+    direct be_execute, also in a mix with other templates; the trace shows
+    each request's submit <= admit <= launched <= done."""
+    ctx = be.Context(None, device=0)
+    reqs = make_requests(12, 21)
+    srv = be.Server(ctx, n_streams=4)
+    prepared = [srv.prepare(*r) for r in reqs]
+    g = torch.Generator(device=DEV)
+    g.manual_seed(5)
+    for rep in range(5):
+        for e, bufs, outs in reqs:                       # new contents every round
+            for t in bufs.values():
+                if t.dtype.is_floating_point:
+                    t.copy_(torch.randn(t.shape, generator=g, device=DEV, dtype=t.dtype))
+        ids = [srv.submit(p) for p in prepared]
+        for i in ids:
+            st, _ = srv.wait(i, timeout=120.0)
+            assert st == be.OK
+        for e, bufs, outs in reqs:
+            alone = [torch.empty_like(o) for o in outs]
+            be.execute(ctx, e, bufs, alone)
+            torch.cuda.synchronize()
+            for o, a in zip(outs, alone):
+                assert torch.equal(o, a), rep
+    tr = srv.trace()
+    assert len(tr) == 60
+    assert np.all(tr[:, 1] <= tr[:, 2]) and np.all(tr[:, 2] <= tr[:, 3]) and np.all(tr[:, 3] <= tr[:, 4])
+    srv.close()
