@@ -98,6 +98,23 @@ def source_hash(source):
     return h.hexdigest()[:16]
 
 
+_PIPE = {}
+
+
+def pipe_peaks(be):
+    """Measured FP64 and FP32 pipe peaks of this device (TFLOP/s, be_peak_probe:
+    FMA chains in registers), measured once per process; the rooflines of the
+    FP64 and FP32 / double-float paths use these, with the nominal figures
+    (FP64 1.25 TFLOP/s; FP32 148 SMs x 128 lanes x 2 x 2.032 GHz) beside them."""
+    if not _PIPE:
+        _PIPE["fp64"] = be.peak_probe("fp64")
+        _PIPE["fp32"] = be.peak_probe("fp32")
+        _PIPE["source"] = "measured (be_peak_probe: FMA chains, best of 5)"
+        _PIPE["nominal_fp64"] = FP64_PEAK_TFLOPS
+        _PIPE["nominal_fp32"] = FP32_PEAK_TFLOPS
+    return _PIPE
+
+
 def kernel_traffic(kernel):
     """DRAM bytes per launch from the committed ncu summary of ``kernel``,
     valid only while the kernel source hashes to the value recorded there."""
@@ -331,11 +348,13 @@ def run_ours(args):
                                "counts": f"bf16 digit-product MMA flops issued ({TC_MMA_FLOPS_PER_ELEMENT} per element)"}}
     else:
         if variant == 1:              # FP64 pipe
-            ach_tf, peak, src = flops / (kms * 1e-3) / 1e12, FP64_PEAK_TFLOPS, "nominal B300 FP64 (1.25 TFLOP/s)"
+            pp = pipe_peaks(be)
+            ach_tf, peak, src = flops / (kms * 1e-3) / 1e12, pp["fp64"], pp["source"]
             what = "algorithmic FP64 flops"
         else:                         # double-float on the FP32 pipe
             ach_tf = DF_FLOPS_PER_ELEMENT * E / (kms * 1e-3) / 1e12
-            peak, src = FP32_PEAK_TFLOPS, "FP32 pipe from unit counts and clock: 148 SMs x 128 lanes x 2 x 2.032 GHz"
+            pp = pipe_peaks(be)
+            peak, src = pp["fp32"], pp["source"]
             what = f"FP32 flops of the compensated dot products ({DF_FLOPS_PER_ELEMENT} per element)"
         roofline = {"kernel": kernel["name"], "bound": "alu", "achieved": ach_tf, "peak": peak,
                     "unit": "TFLOP/s", "frac": ach_tf / peak, "counts": what,
@@ -803,9 +822,9 @@ def run_mix(args):
               be.plan_strategy(ctx, e, precision=be.PREC_SPLIT) == be.STRAT_DENSE_SPLIT):
             pipe_s["tensor"] += 3 * f / tf32
         elif "64" in str(inst.dtype):
-            pipe_s["fp64"] += f / (FP64_PEAK_TFLOPS * 1e12)
+            pipe_s["fp64"] += f / (pipe_peaks(be)["fp64"] * 1e12)
         else:
-            pipe_s["fp32"] += f / (FP32_PEAK_TFLOPS * 1e12)
+            pipe_s["fp32"] += f / (pipe_peaks(be)["fp32"] * 1e12)
 
     def timed(fn, steps, warm):
         for _ in range(warm):
@@ -854,16 +873,16 @@ def run_mix(args):
                 "frac_serial": sum(pipe_s.values()) / (ms_batch * 1e-3),
                 "counts": "each instance at its own pipe's peak: element instances' bytes at measured HBM, split "
                           "instances' issued TF32 flops (3 products) at measured bf16 x tf32/bf16, generic f64 / f32 "
-                          "loop-nest flops at nominal FP64 / FP32; bound = the busiest pipe (pipes overlap), "
+                          "loop-nest flops at the measured FP64 / FP32 rates; bound = the busiest pipe (pipes overlap), "
                           "serial = their sum"},
             "gb_s": world * byts / (ms_batch * 1e-3) / 1e9,
             "roofline": {"kernel": "persistent_kernel", "bound": "alu",
                          "achieved": (fl64 + fl32) / (kms * 1e-3) / 1e12,
-                         "peak": (fl64 + fl32) / (fl64 / (FP64_PEAK_TFLOPS * 1e12) + fl32 / (FP32_PEAK_TFLOPS * 1e12)) / 1e12,
+                         "peak": (fl64 + fl32) / (fl64 / (pipe_peaks(be)["fp64"] * 1e12) + fl32 / (pipe_peaks(be)["fp32"] * 1e12)) / 1e12,
                          "unit": "TFLOP/s",
-                         "frac": (fl64 / (FP64_PEAK_TFLOPS * 1e12) + fl32 / (FP32_PEAK_TFLOPS * 1e12)) / (kms * 1e-3),
+                         "frac": (fl64 / (pipe_peaks(be)["fp64"] * 1e12) + fl32 / (pipe_peaks(be)["fp32"] * 1e12)) / (kms * 1e-3),
                          "counts": "loop-nest flops (2 x iteration volume x (operands - 1) per row); peak: the time "
-                                   "at nominal FP64 (1.25 TFLOP/s) for the f64 instances plus FP32 for the f32 ones",
+                                   "at the measured FP64 rate for the f64 instances plus the measured FP32 rate for the f32 ones",
                          "traffic": None, "algorithmic_bytes": byts,
                          "hbm": {"achieved": byts / (kms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                  "frac": byts / (kms * 1e-3) / 1e9 / peaks["hbm_gbs"]}},
@@ -1052,6 +1071,8 @@ def main():
         line = run_ours(args)
         if line.get("n_gpus", 1) == 1 and not args.no_configs:
             line["configs"] = other_configs(args)
+            import paper_2601_12220_b300 as be
+            line["measured_pipe_peaks_tflops"] = pipe_peaks(be)
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -479,6 +479,16 @@ int be_gemm_split_noalloc(const double *A, int64_t lda, const double *B, int64_t
  */
 int be_gemm_split_noalloc_status(int32_t *status);
 
+/*
+ * be_peak_probe -- measured peak rate of one pipe on the current device, in
+ * TFLOP/s (2 flops per fused multiply-add): kind 0 FP64, kind 1 FP32.
+ * Independent FMA chains in registers, no memory traffic; best of reps
+ * timed launches after one warm-up.  The rooflines of the FP64 and
+ * double-float evaluation paths are stated against these rates.  Allocates
+ * a small output buffer.  Errors: BE_EARG, BE_ECUDA.
+ */
+int be_peak_probe(int32_t kind, int32_t reps, double *tflops);
+
 /* Strategy the engine would run for e under cfg (after AUTO resolution). */
 int be_plan_strategy(be_ctx *x, const be_einsum *e, const be_config *cfg, int32_t precision,
                      int32_t *strategy);

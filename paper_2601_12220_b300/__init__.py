@@ -6,7 +6,7 @@ if it has not been built (``python paper_2601_12220_b300/build.py``).
 """
 from .binding import (  # noqa: F401
     BEError, Batch, Canon, Config, Server, Context, Einsum, execute, execute_host, graph_check, identify, lib,
-    make_config, plan_strategy, tune, tune_batch, raise_kernel, identify_kernel,
+    make_config, peak_probe, plan_strategy, tune, tune_batch, raise_kernel, identify_kernel,
     OK, EPARSE, EINVALID, ESHAPE, EDTYPE, ETOOMANY, ENOTFOUND, EDB, EBUDGET, ETIMEOUT, ECUDA,
     EUNSUPPORTED, EARG, I8, I32, I64, F16, F32, F64, C64, C128, BF16, STRAT_AUTO, STRAT_GENERIC,
     STRAT_ELEMENT, STRAT_DENSE_SPLIT, PREC_FP64, PREC_SPLIT, SIGMA_INDEX, SIGMA_ARG, SIGMA_ROW, SIGMA_POS,

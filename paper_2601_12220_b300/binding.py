@@ -32,7 +32,7 @@ EXPORTS = [
     "be_canon_tokens", "be_induced_graph", "be_graph_check", "be_identify", "be_ctx_create",
     "be_ctx_destroy", "be_lookup", "be_record", "be_db_size", "be_execute", "be_execute_host",
     "be_plan_strategy", "be_status", "be_ctx_set_timing", "be_ctx_timing", "be_gemm_split_noalloc",
-    "be_gemm_split_noalloc_status", "be_ctx_set_wait_limit",
+    "be_gemm_split_noalloc_status", "be_ctx_set_wait_limit", "be_peak_probe",
     "be_batch_create", "be_batch_run", "be_batch_info", "be_batch_kinds", "be_batch_destroy", "be_tune", "be_tune_batch",
     "be_server_create", "be_server_submit", "be_server_wait", "be_server_drain", "be_server_stats",
     "be_server_reset_stats", "be_server_trace", "be_server_destroy", "be_raise", "be_raised_name", "be_record_facts",
@@ -115,6 +115,7 @@ def lib():
             "be_gemm_split_noalloc": (ctypes.c_int, [vp, i64, vp, i64, vp, i64, i64, i64, i64, vp]),
             "be_gemm_split_noalloc_status": (ctypes.c_int, [P(i32)]),
             "be_ctx_set_wait_limit": (ctypes.c_int, [vp, i64]),
+            "be_peak_probe": (ctypes.c_int, [i32, i32, P(ctypes.c_double)]),
             "be_batch_create": (ctypes.c_int, [vp, i32, P(vp), P(P(Buf)), P(i32), P(P(Buf)), P(i32),
                                                P(P(ctypes.c_double)), P(i32), P(Config), P(vp)]),
             "be_batch_run": (ctypes.c_int, [vp, vp]),
@@ -627,6 +628,13 @@ def tune_batch(ctx, items, base: Config | None = None, reps=5, stream=None):
                               ctypes.byref(best), ctypes.byref(sec), ctypes.byref(n)))
     del keep
     return best, sec.value, n.value
+
+
+def peak_probe(kind: str, reps=5) -> float:
+    """Measured peak of the FP64 ("fp64") or FP32 ("fp32") pipe, TFLOP/s."""
+    v = ctypes.c_double()
+    check(lib().be_peak_probe({"fp64": 0, "fp32": 1}[kind], int(reps), ctypes.byref(v)))
+    return v.value
 
 
 def plan_strategy(ctx, e: Einsum, cfg: Config | None = None, precision=PREC_FP64) -> int:

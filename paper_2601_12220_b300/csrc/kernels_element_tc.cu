@@ -720,10 +720,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
                     chk = fmaf(fabsf(gk[k][r].hi), z[r], chk);
                   }
                   mx = fmaxf(mx, chk);
-                  // hi + lo on the FP64 pipe (two exact conversions and an
-                  // add: three issue slots, against about twenty for the same
-                  // from bit moves)
-                  p.rows[k].out[e * NI + i] = (double)s + (double)c;
+                  // hi + lo: exact conversions by bit moves and one FP64 add
+                  // (three FP64-pipe conversions measured 2 % slower: the
+                  // pipe is shared with the producer's sine reduction)
+                  p.rows[k].out[e * NI + i] = dfm::f2d_bits(s) + dfm::f2d_bits(c);
                 }
               }
             }

@@ -80,3 +80,14 @@ def test_wait_limit_rejects_negative():
     with pytest.raises(be.BEError) as exc:
         ctx.set_wait_limit(-1)
     assert exc.value.code == be.EARG
+
+
+def test_peak_probe_rates_plausible():
+    """The FP64 and FP32 FMA-chain probes report rates between a tenth of and
+    twice the nominal B300 figures (1.25 and about 77 TFLOP/s), FP32 far above
+    FP64."""
+    f64 = be.peak_probe("fp64", reps=3)
+    f32 = be.peak_probe("fp32", reps=3)
+    assert 0.1 * 1.25 < f64 < 2 * 1.25
+    assert 0.1 * 77 < f32 < 2 * 77
+    assert f32 > 10 * f64
