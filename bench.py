@@ -561,7 +561,8 @@ def run_stacked(args):
 # ---------------------------------------------------------------- workload 3
 
 V_FULL, O_FULL, B_CHEM = 128, 32, 4
-TF32_OVER_BF16 = 1.1 / 2.25    # nominal dense TF32 : BF16 tensor rates of B300
+SPLIT_PRODUCTS = 6             # BF16 tensor products per output term of the split GEMM (three parts per operand)
+SPLIT_DTYPE = "f64 (split: 3 BF16 parts per operand, 6 tensor products, FP32 accumulation, FP32-pair drains)"
 
 
 def chem_device_inputs(torch, dev, v, o, seed=1003):
@@ -629,7 +630,7 @@ def run_chem(args):
     useful = B_CHEM * 2.0 * M * N * K
     byts = 8.0 * (B_CHEM * M * K + K * N + B_CHEM * M * N)
     pad = lambda x, t: (x + t - 1) // t * t
-    issued = B_CHEM * 3 * 2.0 * pad(M, 128) * pad(N, 128) * pad(K, 32)
+    issued = B_CHEM * SPLIT_PRODUCTS * 2.0 * pad(M, 128) * pad(N, 128) * pad(K, 64)
 
     def step():
         e = be.Einsum(text)
@@ -656,13 +657,13 @@ def run_chem(args):
     n_s, t_s = ctx.timing(be.KERNEL_SPLIT)
     gemm_ms = t_g / max(1, n_g)
     peaks = load_peaks()
-    tf32_peak = peaks["bf16_tflops"] * TF32_OVER_BF16
+    bf16_peak = peaks["bf16_tflops"]
     per_launch_useful = useful / B_CHEM
     ach = per_launch_useful / (gemm_ms * 1e-3) / 1e12
     ach_issued = issued / B_CHEM / (gemm_ms * 1e-3) / 1e12
     line = {"metric": METRIC, "value": world * useful / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64 (split: 2 TF32 parts, 3 tensor products)",
+            "scaling": "weak", "vs_baseline": None, "dtype": SPLIT_DTYPE,
             "data": "synthetic",
             "config": {"workload": f"chem_dense: b={B_CHEM} 'abef,efij->abij', v={v}, o={o}, efij shared, "
                                    "entries N(0,1)*exp(-gap/8) (drawn on the device)", "parallelism": "replicas",
@@ -670,11 +671,12 @@ def run_chem(args):
             "gb_s": world * byts / (ms * 1e-3) / 1e9,
             "kernels": {"gemm_split_kernel_ms": gemm_ms, "gemm_launches": n_g,
                         "split_ms_per_step": t_s / args.steps, "split_launches": n_s},
-            "roofline": {"kernel": "gemm_split_kernel", "bound": "tensor", "achieved": ach, "peak": tf32_peak,
-                         "unit": "TFLOP/s", "frac": ach / tf32_peak,
-                         "achieved_issued": ach_issued, "frac_issued": ach_issued / tf32_peak,
-                         "peak_source": f"measured bf16 burst {peaks['bf16_tflops']} x nominal tf32/bf16 ratio "
-                                        f"{TF32_OVER_BF16:.3f} ({peaks['source']})",
+            "roofline": {"kernel": "gemm_split_kernel", "bound": "tensor", "achieved": ach, "peak": bf16_peak,
+                         "unit": "TFLOP/s", "frac": ach / bf16_peak,
+                         "achieved_issued": ach_issued, "frac_issued": ach_issued / bf16_peak,
+                         "counts": f"achieved: useful FP64-equivalent flops (2 M N K); issued: the {SPLIT_PRODUCTS} BF16 "
+                                   "products on the padded tile grid",
+                         "peak_source": f"measured bf16 burst ({peaks['source']})",
                          "traffic": kernel_traffic({"source": "kernels_dense.cu",
                                                     "profile": "gemm_split_kernel_chem.md"})},
             "error_vs_fp64": err,
@@ -709,7 +711,7 @@ def run_affine(args):
     useful = 2.0 * M * N * K
     byts = 8.0 * (M * K + K * N + M * N)
     pad = lambda x, t: (x + t - 1) // t * t
-    issued = 3 * 2.0 * pad(M, 128) * pad(N, 128) * pad(K, 32)
+    issued = SPLIT_PRODUCTS * 2.0 * pad(M, 128) * pad(N, 128) * pad(K, 64)
 
     def timed(t, scalars, steps):
         def step():
@@ -740,12 +742,12 @@ def run_affine(args):
     gemm_ms = t_g / max(1, n_g)
     plain_ms = timed(plain, (), args.steps)
     peaks = load_peaks()
-    tf32_peak = peaks["bf16_tflops"] * TF32_OVER_BF16
+    bf16_peak = peaks["bf16_tflops"]
     ach = useful / (gemm_ms * 1e-3) / 1e12
     ach_issued = issued / (gemm_ms * 1e-3) / 1e12
     line = {"metric": METRIC, "value": world * useful / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64 (split: 2 TF32 parts, 3 tensor products)",
+            "scaling": "weak", "vs_baseline": None, "dtype": SPLIT_DTYPE,
             "data": "synthetic",
             "config": {"workload": f"dense_affine: 'abcd,cdef->abef', extents {n}, operands "
                                    "(0.5 A - 1.25), (2 B + 0.75) as runtime-scalar affine producers, N(0,1)",
@@ -754,11 +756,10 @@ def run_affine(args):
                        "l2": f"inputs larger than L2 ({byts / 1e9:.2f} GB per step)"},
             "kernels": {"gemm_split_kernel_ms": gemm_ms, "split_ms_per_step": t_s / args.steps},
             "plain": {"ms_per_step": plain_ms, "value": world * useful / (plain_ms * 1e-3) / 1e12},
-            "roofline": {"kernel": "gemm_split_kernel", "bound": "tensor", "achieved": ach, "peak": tf32_peak,
-                         "unit": "TFLOP/s", "frac": ach / tf32_peak, "achieved_issued": ach_issued,
-                         "frac_issued": ach_issued / tf32_peak,
-                         "peak_source": f"measured bf16 burst {peaks['bf16_tflops']} x nominal tf32/bf16 ratio "
-                                        f"{TF32_OVER_BF16:.3f} ({peaks['source']})", "traffic": None},
+            "roofline": {"kernel": "gemm_split_kernel", "bound": "tensor", "achieved": ach, "peak": bf16_peak,
+                         "unit": "TFLOP/s", "frac": ach / bf16_peak, "achieved_issued": ach_issued,
+                         "frac_issued": ach_issued / bf16_peak,
+                         "peak_source": f"measured bf16 burst ({peaks['source']})", "traffic": None},
             "error_vs_fp64": err,
             "clocks": clk.summary(), "gpu_launches": n_g + n_s}
     return line
@@ -807,10 +808,10 @@ def run_mix(args):
     t_plan = time.perf_counter() - t_plan
     info = batch.info()
     kinds = batch.kinds()
-    # per-instance bound: HBM for element instances, the TF32 tensor pipe for
+    # per-instance bound: HBM for element instances, the BF16 tensor pipe for
     # split instances (3 products), the FP64 / FP32 pipe for generic ones
     peaks0 = load_peaks()
-    tf32 = peaks0["bf16_tflops"] * TF32_OVER_BF16 * 1e12
+    bf16 = peaks0["bf16_tflops"] * 1e12
     pipe_s = {"hbm": 0.0, "tensor": 0.0, "fp64": 0.0, "fp32": 0.0}
     for (e, bufs, outs), inst in zip(items, insts):
         f = len(inst.rows) * W._flops(inst.out, inst.ins, inst.lens)
@@ -820,7 +821,7 @@ def run_mix(args):
             pipe_s["hbm"] += nbytes / (peaks0["hbm_gbs"] * 1e9)
         elif (not args.mix_no_split and "64" in str(inst.dtype) and f / 2 >= 2 ** args.mix_split_log2 and
               be.plan_strategy(ctx, e, precision=be.PREC_SPLIT) == be.STRAT_DENSE_SPLIT):
-            pipe_s["tensor"] += 3 * f / tf32
+            pipe_s["tensor"] += SPLIT_PRODUCTS * f / bf16
         elif "64" in str(inst.dtype):
             pipe_s["fp64"] += f / (pipe_peaks(be)["fp64"] * 1e12)
         else:
@@ -872,7 +873,7 @@ def run_mix(args):
                 "frac": max(pipe_s.values()) / (ms_batch * 1e-3),
                 "frac_serial": sum(pipe_s.values()) / (ms_batch * 1e-3),
                 "counts": "each instance at its own pipe's peak: element instances' bytes at measured HBM, split "
-                          "instances' issued TF32 flops (3 products) at measured bf16 x tf32/bf16, generic f64 / f32 "
+                          "instances' issued BF16 flops (6 products) at the measured bf16 rate, generic f64 / f32 "
                           "loop-nest flops at the measured FP64 / FP32 rates; bound = the busiest pipe (pipes overlap), "
                           "serial = their sum"},
             "gb_s": world * byts / (ms_batch * 1e-3) / 1e9,

@@ -70,8 +70,14 @@ extern "C" {
                                   operators (at most 8 x 8) on the double-float variant:
                                   1 + the share of the elements, in sixteenths, that run
                                   on the FP64 pipe beside the double-float ones (0 = 8/16) */
-#define BE_STRAT_DENSE_SPLIT 3 /* FP64 contraction as split FP16 products on tcgen05;
-                                  needs a context (its workspace holds the split operands) */
+#define BE_STRAT_DENSE_SPLIT 3 /* FP64 contraction as products of three BF16 parts per
+                                  operand on tcgen05 (FP32 accumulation, compensated
+                                  drains); needs a context (its workspace holds the split
+                                  operands); tile[2] k-blocks of 64 between drains of the
+                                  leading-product accumulator (0 = 1, whose a-priori bound
+                                  is within 1e-6; 2 and more are faster, with bounds of
+                                  about 1.4e-6 and above); split >= 4 adds the next level's
+                                  two products */
 
 /* ---- precision modes (part of the tuning key, not of the normal form) ---- */
 #define BE_PREC_FP64 0         /* results within 1e-12 of the absolute contraction */
@@ -457,8 +463,8 @@ int be_ctx_timing(be_ctx *x, int32_t kernel, int64_t *launches, double *total_ms
  * taken, and it can fail with BE_ECUDA if the device is already full: make
  * it before the caller sets up its memory pool and before any stream
  * capture.  The call fails with BE_ETOOMANY (nothing launched) when the
- * problem needs more: about (M + N) * K * 8 bytes with M and N padded to
- * 128 and K to 32 (e.g. M = N = 1024, K = 3968 fits).  Every call reuses the
+ * problem needs more: about (M + N) * K * 6 bytes with M and N padded to
+ * 128 and K to 64 (e.g. M = N = 1024, K = 5440 fits).  Every call reuses the
  * same array (the call clears what must start at zero), so calls whose GPU
  * work overlaps -- on different streams or devices sharing a context -- race;
  * issue them in order on one stream.  Errors: BE_EARG, BE_ETOOMANY,

@@ -483,7 +483,7 @@ static cudaError_t run_dense_rows(be_ctx *x, const DensePlan &dp, const be_confi
       if (ce == cudaSuccess) {
         KernelMark km(x, BE_KERNEL_DENSE_GEMM, s);
         ce = dense_split_gemm(DenseA{r.A, dp.M, r.lda, r.ska}, dp.N, dp.K, dp.M, r.C, dp.N, ws, c.split >= 4,
-                              c.tile[2] > 0 ? c.tile[2] : 2, status, wait_limit, s);
+                              c.tile[2] > 0 ? c.tile[2] : 1, status, wait_limit, s);
       }
     }
     if (ce != cudaSuccess) return ce;
@@ -850,11 +850,11 @@ static void tune_candidates(const Einsum &e, const std::vector<BufIn> &bi, const
   }
   std::memset(&c, 0, sizeof(c));
   if (precision == BE_PREC_SPLIT && plan_dense(e, bi, bo, dp, why) == OK) {
+    // one drain interval: k-blocks of 64 between drains of the leading
+    // accumulator beyond 1 would trade the a-priori 1e-6 bound for speed
     c.strategy = BE_STRAT_DENSE_SPLIT;
-    for (int hd : {1, 2}) {
-      c.tile[2] = hd;
-      out.push_back(c);
-    }
+    c.tile[2] = 1;
+    out.push_back(c);
   }
   std::memset(&c, 0, sizeof(c));
   c.strategy = BE_STRAT_GENERIC;

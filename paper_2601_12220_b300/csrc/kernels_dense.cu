@@ -4,28 +4,34 @@
 // cores.
 //
 //  1. split_rows / split_cols: each FP64 operand (or its affine producer
-//     alpha * x + beta, evaluated here) is scaled by a power of two
-//     per row of A (per column of B) so that its largest entry lies in
-//     [2^13, 2^14), then written as two TF32 parts hi = tf32(x),
-//     lo = tf32(x - hi) (11 significant bits each) into a zero-padded
-//     K-major workspace.  TF32 keeps FP32's exponent range, so entries far
-//     below their row's maximum (the exp-decaying cluster amplitudes) keep
-//     their relative precision; FP16 parts would fall into subnormals.
-//  2. gemm_split_kernel: TMA streams 128 x 32 tiles of A_hi, A_lo, B_hi,
-//     B_lo into shared memory (128-byte swizzle); one thread issues
-//     tcgen05.mma kind::tf32 into FP32 accumulators in tensor memory: the
-//     large term hi*hi into H, the small terms hi*lo + lo*hi (+ lo*lo when
-//     requested) into L, each double-buffered (4 x 128 columns).  The
-//     tensor core rounds its FP32 accumulator toward zero (about 2^-23 of
-//     the accumulator per MMA, measured), so H is drained every hdrain
-//     k-blocks of 32 values (2 by default: 64 values, 8 MMAs) and L every
-//     512 values; sixteen epilogue warps read them
-//     (tcgen05.ld) and add them into an FP32 pair per output with an
-//     error-free two-sum (about 48 bits).  The result is scaled back and
-//     stored in FP64.
-//  Error per output, relative to S = sum |a||b|: split residuals 3 * 2^-22
-//  (2 * 2^-22 with lo*lo), H truncation about 2^-23 per MMA between drains
-//  (8 * 2^-23 at the default drain), L truncation below 2^-26.
+//     alpha * x + beta, evaluated here) is scaled by a power of two per row
+//     of A (per column of B) so that its largest entry lies in [2^13, 2^14),
+//     rounded to a float x and written as three BF16 parts
+//     x1 = bf16(x), x2 = bf16(x - x1), x3 = bf16(x - x1 - x2) (both
+//     differences are exact in FP32; about 24 significant bits in all) into a
+//     zero-padded K-major workspace.  BF16 keeps FP32's exponent range, so
+//     entries far below their row's maximum (the exp-decaying cluster
+//     amplitudes) keep their relative precision.
+//  2. gemm_split_kernel: TMA streams 128 x 64 tiles of the six parts into
+//     shared memory (128-byte swizzle, two stages); one thread issues
+//     tcgen05.mma kind::f16 (BF16 inputs, FP32 accumulators in tensor
+//     memory) per K-step of 16: the leading product x1*y1 into H and the
+//     five products of the next two levels (x1*y2, x2*y1, x1*y3, x2*y2,
+//     x3*y1; plus x2*y3, x3*y2 when requested) into L, each double-buffered
+//     (4 x 128 columns).  Six BF16 products take the tensor pipe as long as
+//     three TF32 ones and move 6 bytes of operand per element instead of 8.
+//     The tensor core rounds its FP32 accumulator toward zero (about 2^-23
+//     of the accumulator per MMA), so H is drained every hdrain k-blocks of
+//     64 values (4 MMAs each) and L, which holds terms 2^-8 of H's size and
+//     smaller, every 8 k-blocks; sixteen epilogue warps read them
+//     (tcgen05.ld) and add H into an FP32 pair per output by Kahan's
+//     compensated summation and L into its compensation term.  The result
+//     is scaled back and stored in FP64.
+//  Error per output, relative to S = sum |a||b|: rounding to float and the
+//  three-part residual about 2^-23 per operand, dropped products
+//  (x2*y3, x3*y2, x3*y3) about 2^-23, H truncation about 2^-23 per MMA
+//  between drains (4 * 2^-23 at hdrain = 1, 8 * 2^-23 at hdrain = 2), L
+//  truncation below 2^-22, the compensated sum of the drains about 2^-23.
 // Every mbarrier wait is bounded (about one second of clock cycles); on
 // expiry the CTA records BE_ETIMEOUT in a status word, stops issuing work,
 // waits (bounded) for its own copies and frees its tensor memory.
@@ -33,7 +39,7 @@
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
-#include <cuda_fp16.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "dense.hpp"
@@ -44,11 +50,13 @@ namespace be {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 32;           // BK: TF32 values per 128-byte row
-constexpr int STAGES = 3;
-constexpr int L_CHUNK = 16;                            // k-blocks per drain of the small-term accumulator
-constexpr int TILE_BYTES = BM * BK * 4;                // one TF32 128 x 32 tile
-constexpr int STAGE_BYTES = 4 * TILE_BYTES;            // A_hi, A_lo, B_hi, B_lo
+constexpr int BM = 128, BN = 128, BK = 64;           // BK: BF16 values per 128-byte row
+constexpr int NPART = 3;                               // BF16 parts per operand
+constexpr int STAGES = 2;
+constexpr int L_CHUNK = 8;                             // k-blocks per drain of the small-term accumulator
+constexpr int SPLIT_CTAS_PER_SM = 8;                   // rows in flight per SM in split_rows
+constexpr int TILE_BYTES = BM * BK * 2;                // one BF16 128 x 64 tile
+constexpr int STAGE_BYTES = 2 * NPART * TILE_BYTES;    // A1 A2 A3, B1 B2 B3
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int NTHREADS = 576;                          // warp 0 TMA, warp 1 MMA, warps 2-17 epilogue
 constexpr int NEPI = 512;                              // epilogue threads
@@ -101,12 +109,12 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor: D f32, A/B tf32, both K-major, M = 128, N = 128
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// instruction descriptor: D f32, A/B bf16, both K-major, M = 128, N = 128
+constexpr uint32_t IDESC = tc::idesc_bf16(BM, BN);
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t acc) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
           tmem_d),
       "l"(da), "l"(db), "r"(IDESC), "r"(acc));
 }
@@ -125,42 +133,39 @@ __device__ __forceinline__ double scale2(double v, int k) {
   return (v * pow2(k1)) * pow2(k2);
 }
 
-// error-free accumulation of v into the pair (hi, lo)
-__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float v) {
-  float s = hi + v;
-  float bp = s - hi;
-  float err = (hi - (s - bp)) + (v - bp);
-  hi = s;
-  lo += err;
+// Kahan-compensated accumulation of v into (hi, c), whose running sum is
+// hi - c: the error of the sum of n drained values stays within
+// 2u |sum of |v|| + O(n u^2) (Kahan's bound, u = 2^-24), four FP32
+// operations per value instead of TwoSum's seven
+__device__ __forceinline__ void kahan_acc(float &hi, float &c, float v) {
+  const float y = v - c;
+  const float t = hi + y;
+  c = (t - hi) - y;
+  hi = t;
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
-      "[%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+// drain 32 accumulator columns at taddr: the leading-product accumulator H
+// by Kahan's compensated sum into (hi, c); the small-term accumulator L
+// (terms at most about 2^-7 of H's) straight into the compensation
+template <bool LEAD>
+__device__ __forceinline__ void drain32(uint32_t taddr, float *hi, float *c) {
 #pragma unroll
-  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
-}
-
-// drain 32 accumulator columns at taddr into the pairs (hi, lo)
-__device__ __forceinline__ void drain32(uint32_t taddr, float *hi, float *lo) {
+  for (int q = 0; q < 4; ++q) {
+    uint32_t r[8];
+    tc::tmem_ld8(taddr + (uint32_t)(8 * q), r);
+    tc::tmem_wait_ld();
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    float v[16];
-    tmem_ld16(taddr + (uint32_t)(16 * q), v);
-#pragma unroll
-    for (int j = 0; j < 16; ++j) two_sum_acc(hi[16 * q + j], lo[16 * q + j], v[j]);
+    for (int j = 0; j < 8; ++j) {
+      if (LEAD) kahan_acc(hi[8 * q + j], c[8 * q + j], __uint_as_float(r[j]));
+      else c[8 * q + j] -= __uint_as_float(r[j]);
+    }
   }
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1)
-    gemm_split_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
-                      const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+    gemm_split_kernel(const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmA2,
+                      const __grid_constant__ CUtensorMap tmA3, const __grid_constant__ CUtensorMap tmB1,
+                      const __grid_constant__ CUtensorMap tmB2, const __grid_constant__ CUtensorMap tmB3,
                       const int *__restrict__ sa, const int *__restrict__ sb, double *__restrict__ C, int64_t M,
                       int64_t N, int64_t ldc, int nkb, int lolo, int hdrain, int *status, long long limit) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -209,10 +214,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, status, limit)) break;
         uint8_t *st = smem + s * STAGE_BYTES;
         mbar_expect_tx(&full[s], STAGE_BYTES);
-        tma_load_2d(st, &tmAh, &full[s], kb * BK, m0);
-        tma_load_2d(st + TILE_BYTES, &tmAl, &full[s], kb * BK, m0);
-        tma_load_2d(st + 2 * TILE_BYTES, &tmBh, &full[s], kb * BK, n0);
-        tma_load_2d(st + 3 * TILE_BYTES, &tmBl, &full[s], kb * BK, n0);
+        tma_load_2d(st, &tmA1, &full[s], kb * BK, m0);
+        tma_load_2d(st + TILE_BYTES, &tmA2, &full[s], kb * BK, m0);
+        tma_load_2d(st + 2 * TILE_BYTES, &tmA3, &full[s], kb * BK, m0);
+        tma_load_2d(st + 3 * TILE_BYTES, &tmB1, &full[s], kb * BK, n0);
+        tma_load_2d(st + 4 * TILE_BYTES, &tmB2, &full[s], kb * BK, n0);
+        tma_load_2d(st + 5 * TILE_BYTES, &tmB3, &full[s], kb * BK, n0);
         last_kb[s] = kb;
       }
       // on an abort the MMA thread may not have consumed every stage: wait
@@ -244,14 +251,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tc_fence_after();
         const uint32_t dh = tmem + (uint32_t)(hb * BN), dl = tmem + (uint32_t)(2 * BN + lb * BN);
         const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+        // K-steps of 16 BF16 values (32 bytes of each 128-byte row)
 #pragma unroll
-        for (int ks = 0; ks < BK / 8; ++ks) {
-          const uint64_t ah = sdesc(base + ks * 32), al = sdesc(base + TILE_BYTES + ks * 32);
-          const uint64_t bh = sdesc(base + 2 * TILE_BYTES + ks * 32), bl = sdesc(base + 3 * TILE_BYTES + ks * 32);
-          mma_tf32(dh, ah, bh, (hfirst && ks == 0) ? 0u : 1u);
-          mma_tf32(dl, ah, bl, (lfirst && ks == 0) ? 0u : 1u);
-          mma_tf32(dl, al, bh, 1u);
-          if (lolo) mma_tf32(dl, al, bl, 1u);
+        for (int ks = 0; ks < BK / 16; ++ks) {
+          const uint64_t a1 = sdesc(base + ks * 32), a2 = sdesc(base + TILE_BYTES + ks * 32),
+                         a3 = sdesc(base + 2 * TILE_BYTES + ks * 32);
+          const uint64_t b1 = sdesc(base + 3 * TILE_BYTES + ks * 32), b2 = sdesc(base + 4 * TILE_BYTES + ks * 32),
+                         b3 = sdesc(base + 5 * TILE_BYTES + ks * 32);
+          mma_bf16(dh, a1, b1, (hfirst && ks == 0) ? 0u : 1u);
+          mma_bf16(dl, a1, b2, (lfirst && ks == 0) ? 0u : 1u);
+          mma_bf16(dl, a2, b1, 1u);
+          mma_bf16(dl, a1, b3, 1u);
+          mma_bf16(dl, a2, b2, 1u);
+          mma_bf16(dl, a3, b1, 1u);
+          if (lolo) {
+            mma_bf16(dl, a2, b3, 1u);
+            mma_bf16(dl, a3, b2, 1u);
+          }
         }
         mma_commit(&empty[s]);   // frees the stage once these MMAs have read it
         if (hlast) mma_commit(&hf[hb]);
@@ -280,7 +296,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const bool got = mbar_wait(&hf[hb], (uint32_t)(hc >> 1) & 1u, abort_flag, status, limit);
         if (!__all_sync(0xffffffffu, got)) { ok = false; break; }   // warp-uniform before tcgen05.ld
         tc_fence_after();
-        drain32(lane_base + (uint32_t)(hb * BN), hi, lo);
+        drain32<true>(lane_base + (uint32_t)(hb * BN), hi, lo);
         tc_fence_before();
         mbar_arrive(&he[hb]);
       }
@@ -288,7 +304,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const bool gl = mbar_wait(&lf[lb], (uint32_t)(lc >> 1) & 1u, abort_flag, status, limit);
         if (!__all_sync(0xffffffffu, gl)) { ok = false; break; }
         tc_fence_after();
-        drain32(lane_base + (uint32_t)(2 * BN + lb * BN), hi, lo);
+        drain32<false>(lane_base + (uint32_t)(2 * BN + lb * BN), hi, lo);
         tc_fence_before();
         mbar_arrive(&le[lb]);
       }
@@ -300,7 +316,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int64_t n = n0 + quarter * 32 + j;
-        if (n < N) crow[n] = scale2((double)hi[j] + (double)lo[j], -(sm + sb[n]));
+        if (n < N) crow[n] = scale2((double)hi[j] - (double)lo[j], -(sm + sb[n]));
       }
     }
   }
@@ -340,22 +356,6 @@ __device__ __forceinline__ int scale_for(double mx) {
   return 14 - e;          // mx * 2^(14-e) in [2^13, 2^14)
 }
 
-// round a float to TF32 (11 significant bits, low 13 mantissa bits zero), nearest
-__device__ __forceinline__ float to_tf32(float f) {
-  uint32_t u = __float_as_uint(f);
-  if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
-  return __uint_as_float(u);
-}
-
-// x (already scaled) = hi + lo + r with hi, lo TF32 and |r| <= 1.25 * 2^-22 |x|:
-// one FP64 -> FP32 conversion (|x - xf| <= 2^-24 |x|), then hi = tf32(xf)
-// and lo = tf32(xf - hi) in FP32 (that difference is exact)
-__device__ __forceinline__ void split_one(double x, float &h, float &l) {
-  const float xf = __double2float_rn(x);
-  h = to_tf32(xf);
-  l = to_tf32(xf - h);
-}
-
 // x * 2^s rounded to a float (half up) from the bits of x, integer operations
 // only; results below FP32's normal range (2^-100 and more below the row's
 // maximum, which scales to [2^13, 2^14)) become zero
@@ -368,16 +368,28 @@ __device__ __forceinline__ float scaled_float(double x, int s) {
   return __uint_as_float(mag | (hw & 0x80000000u));
 }
 
-// x * 2^s split into TF32 hi + lo; in FP32 from the bits when the scaled row
-// stays in FP32's normal range, else through FP64
-__device__ __forceinline__ void split_scaled(double x, int s, bool fp32_ok, float &h, float &l) {
-  if (fp32_ok) {
-    const float xf = scaled_float(x, s);
-    h = to_tf32(xf);
-    l = to_tf32(xf - h);
-  } else {
-    split_one(x * pow2(s), h, l);
-  }
+__device__ __forceinline__ float bf16_rn(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// three BF16 parts of a float x: p1 = bf16(x), p2 = bf16(x - p1),
+// p3 = bf16(x - p1 - p2).  x - p1 and (x - p1) - p2 are exact in FP32 (each
+// part takes the leading 8 significant bits of what is left), so
+// |x - p1 - p2 - p3| <= 2^-9 |x - p1 - p2| <= 2^-25 |x| or so
+struct Parts {
+  float p1, p2, p3;
+};
+__device__ __forceinline__ Parts parts3(float x) {
+  Parts r;
+  r.p1 = bf16_rn(x);
+  const float r1 = x - r.p1;
+  r.p2 = bf16_rn(r1);
+  r.p3 = bf16_rn(r1 - r.p2);
+  return r;
+}
+
+// x * 2^s split into three BF16 parts; the float image from the bits when
+// the scaled row stays in FP32's normal range, else through FP64
+__device__ __forceinline__ Parts split_scaled(double x, int s, bool fp32_ok) {
+  return parts3(fp32_ok ? scaled_float(x, s) : __double2float_rn(x * pow2(s)));
 }
 
 // the operand value of an affine producer, alpha * x + beta (AFF), else x
@@ -386,58 +398,22 @@ __device__ __forceinline__ double affine(double x, double alpha, double beta) {
   return AFF ? fma(alpha, x, beta) : x;
 }
 
-// A (M x K): A[m*lda + k*ska] -> TF32 hi/lo [Mp x Kp], zero-padded; sa[m].
-// Rows with unit stride and 16-byte alignment are read as double2, four in
-// flight per thread, and written as float2.  AFF: the operand is
+// A (M x K): A[m*lda + k*ska] -> three BF16 parts [Mp x Kp], zero-padded;
+// sa[m].  Rows with unit stride and 16-byte alignment are read as double2,
+// four in flight per thread, and written as BF16 pairs.  AFF: the operand is
 // alpha * A + beta (an affine producer fused into the split).
-template <bool AFF>
-__global__ void __launch_bounds__(256) split_rows(const double *__restrict__ A, int64_t M, int64_t K, int64_t lda,
-                                                  int64_t ska, float *__restrict__ hi, float *__restrict__ lo,
-                                                  int64_t Kp, int *__restrict__ sa, double alpha, double beta) {
-  __shared__ double red[32];
-  const int64_t m = blockIdx.x;
-  const double *row = A + m * lda;
-  const bool vec = ska == 1 && ((uintptr_t)row & 15) == 0 && (K & 1) == 0 && (Kp & 1) == 0;
-  // |x| compared as integers on the sign-cleared high word (32-bit: a 64-bit
-  // integer max issues on the FP64 pipe); the scale needs only the largest
-  // exponent, which the high word carries
+// one pass over row m: every entry (its affine producer's value) times 2^s
+// split into three BF16 parts and written to the padded row; returns this
+// thread's largest high word of |x| (the row maximum's exponent) when TRACK
+template <bool AFF, bool TRACK>
+__device__ __forceinline__ uint32_t split_pass(const double *__restrict__ row, bool vec, int64_t K, int64_t ska,
+                                               __nv_bfloat16 *__restrict__ r1, __nv_bfloat16 *__restrict__ r2p,
+                                               __nv_bfloat16 *__restrict__ r3, int64_t Kp, int s, bool fp32_ok,
+                                               double alpha, double beta) {
   uint32_t bits = 0;
-  if (m < M) {
-    if (vec) {
-      const double2 *r2 = (const double2 *)row;
-      const int64_t K2 = K >> 1;
-      int64_t k = threadIdx.x;
-      for (; k + 3 * blockDim.x < K2; k += 4 * blockDim.x) {
-        double2 v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = r2[k + u * blockDim.x];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          bits = max(bits, (uint32_t)__double2hiint(affine<AFF>(v[u].x, alpha, beta)) & 0x7fffffffu);
-          bits = max(bits, (uint32_t)__double2hiint(affine<AFF>(v[u].y, alpha, beta)) & 0x7fffffffu);
-        }
-      }
-      for (; k < K2; k += blockDim.x) {
-        const double2 v = r2[k];
-        bits = max(bits, (uint32_t)__double2hiint(affine<AFF>(v.x, alpha, beta)) & 0x7fffffffu);
-        bits = max(bits, (uint32_t)__double2hiint(affine<AFF>(v.y, alpha, beta)) & 0x7fffffffu);
-      }
-    } else {
-      for (int64_t k = threadIdx.x; k < K; k += blockDim.x)
-        bits = max(bits, (uint32_t)__double2hiint(affine<AFF>(row[k * ska], alpha, beta)) & 0x7fffffffu);
-    }
-  }
-  // the row maximum rounded down to its high word (same exponent, hence the
-  // same power-of-two scale)
-  double mx = block_max(__hiloint2double((int)bits, 0), red);
-  const int s = scale_for(mx);
-  // the scaled row max is below 2^14; FP32 scaling is exact while |x| >= 2^-100 * max
-  const bool fp32_ok = mx == 0.0 || (mx > 0x1p-26 && mx < 0x1p+100 && s > -120 && s < 120);
-  if (threadIdx.x == 0 && m < M) sa[m] = s;
-  float *hrow = hi + m * Kp, *lrow = lo + m * Kp;
-  if (vec && m < M) {
+  if (vec) {
     const double2 *r2 = (const double2 *)row;
-    float2 *h2 = (float2 *)hrow, *l2 = (float2 *)lrow;
+    __nv_bfloat162 *o1 = (__nv_bfloat162 *)r1, *o2 = (__nv_bfloat162 *)r2p, *o3 = (__nv_bfloat162 *)r3;
     const int64_t K2 = K >> 1, Kp2 = Kp >> 1;
     int64_t k = threadIdx.x;
     for (; k + 3 * blockDim.x < K2; k += 4 * blockDim.x) {
@@ -446,30 +422,92 @@ __global__ void __launch_bounds__(256) split_rows(const double *__restrict__ A, 
       for (int u = 0; u < 4; ++u) v[u] = r2[k + u * blockDim.x];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        float ha, la, hb, lb;
-        split_scaled(affine<AFF>(v[u].x, alpha, beta), s, fp32_ok, ha, la);
-        split_scaled(affine<AFF>(v[u].y, alpha, beta), s, fp32_ok, hb, lb);
-        h2[k + u * blockDim.x] = make_float2(ha, hb);
-        l2[k + u * blockDim.x] = make_float2(la, lb);
+        const double x = affine<AFF>(v[u].x, alpha, beta), y = affine<AFF>(v[u].y, alpha, beta);
+        if (TRACK) {
+          bits = max(bits, (uint32_t)__double2hiint(x) & 0x7fffffffu);
+          bits = max(bits, (uint32_t)__double2hiint(y) & 0x7fffffffu);
+        }
+        const Parts a = split_scaled(x, s, fp32_ok), b = split_scaled(y, s, fp32_ok);
+        o1[k + u * blockDim.x] = __floats2bfloat162_rn(a.p1, b.p1);
+        o2[k + u * blockDim.x] = __floats2bfloat162_rn(a.p2, b.p2);
+        o3[k + u * blockDim.x] = __floats2bfloat162_rn(a.p3, b.p3);
       }
     }
     for (; k < Kp2; k += blockDim.x) {
-      float ha = 0.f, la = 0.f, hb = 0.f, lb = 0.f;
+      Parts a{0.f, 0.f, 0.f}, b{0.f, 0.f, 0.f};
       if (k < K2) {
         const double2 v = r2[k];
-        split_scaled(affine<AFF>(v.x, alpha, beta), s, fp32_ok, ha, la);
-        split_scaled(affine<AFF>(v.y, alpha, beta), s, fp32_ok, hb, lb);
+        const double x = affine<AFF>(v.x, alpha, beta), y = affine<AFF>(v.y, alpha, beta);
+        if (TRACK) {
+          bits = max(bits, (uint32_t)__double2hiint(x) & 0x7fffffffu);
+          bits = max(bits, (uint32_t)__double2hiint(y) & 0x7fffffffu);
+        }
+        a = split_scaled(x, s, fp32_ok);
+        b = split_scaled(y, s, fp32_ok);
       }
-      h2[k] = make_float2(ha, hb);
-      l2[k] = make_float2(la, lb);
+      o1[k] = __floats2bfloat162_rn(a.p1, b.p1);
+      o2[k] = __floats2bfloat162_rn(a.p2, b.p2);
+      o3[k] = __floats2bfloat162_rn(a.p3, b.p3);
     }
-    return;
+    return bits;
   }
   for (int64_t k = threadIdx.x; k < Kp; k += blockDim.x) {
-    float h = 0.f, l = 0.f;
-    if (m < M && k < K) split_scaled(affine<AFF>(row[k * ska], alpha, beta), s, fp32_ok, h, l);
-    hrow[k] = h;
-    lrow[k] = l;
+    Parts a{0.f, 0.f, 0.f};
+    if (k < K) {
+      const double x = affine<AFF>(row[k * ska], alpha, beta);
+      if (TRACK) bits = max(bits, (uint32_t)__double2hiint(x) & 0x7fffffffu);
+      a = split_scaled(x, s, fp32_ok);
+    }
+    r1[k] = __float2bfloat16_rn(a.p1);
+    r2p[k] = __float2bfloat16_rn(a.p2);
+    r3[k] = __float2bfloat16_rn(a.p3);
+  }
+  return bits;
+}
+
+// Row m of A into its three parts and its scale sa[m].  BF16 parts keep
+// FP32's exponent range, so one fixed scale S0 = 2^40 serves every row whose
+// largest |x| lies in [2^-26, 2^40): scaled products with B's parts and their
+// sums over K stay inside FP32's range, and what FP32 drops (scaled entries
+// below 2^-126) is at least 2^-140 of the row maximum, as with a row's own
+// scale.  One pass splits the row at S0 while it finds the maximum; a row
+// outside the window is split again with the power-of-two scale that puts
+// its maximum in [2^13, 2^14).  Padding rows (m >= M) are written as zeros.
+constexpr int S0 = 40;
+template <bool AFF>
+__device__ __forceinline__ void split_row(int64_t m, const double *__restrict__ A, int64_t M, int64_t K, int64_t lda,
+                                          int64_t ska, __nv_bfloat16 *__restrict__ p1, __nv_bfloat16 *__restrict__ p2,
+                                          __nv_bfloat16 *__restrict__ p3, int64_t Kp, int *__restrict__ sa,
+                                          double alpha, double beta, double *red) {
+  const double *row = A + m * lda;
+  __nv_bfloat16 *r1 = p1 + m * Kp, *r2 = p2 + m * Kp, *r3 = p3 + m * Kp;
+  const bool vec = ska == 1 && ((uintptr_t)row & 15) == 0 && (K & 1) == 0 && (Kp & 1) == 0;
+  // |x| compared as integers on the sign-cleared high word (32-bit: a 64-bit
+  // integer max issues on the FP64 pipe); the scale needs only the largest
+  // exponent, which the high word carries
+  const uint32_t bits = m < M ? split_pass<AFF, true>(row, vec, K, ska, r1, r2, r3, Kp, S0, true, alpha, beta)
+                              : split_pass<AFF, false>(row, vec, 0, ska, r1, r2, r3, Kp, S0, true, alpha, beta);
+  const double mx = block_max(__hiloint2double((int)bits, 0), red);
+  int s = S0;
+  if (!(mx == 0.0 || (mx >= 0x1p-26 && mx < 0x1p+40))) {
+    s = scale_for(mx);
+    // the scaled row max is below 2^14; FP32 scaling is exact while |x| >= 2^-100 * max
+    const bool fp32_ok = mx > 0x1p-26 && mx < 0x1p+100 && s > -120 && s < 120;
+    split_pass<AFF, false>(row, vec, K, ska, r1, r2, r3, Kp, s, fp32_ok, alpha, beta);
+  }
+  if (threadIdx.x == 0 && m < M) sa[m] = s;
+}
+
+// one CTA per row at a time over a grid of a few CTAs per SM
+template <bool AFF>
+__global__ void __launch_bounds__(256) split_rows(const double *__restrict__ A, int64_t M, int64_t Mp, int64_t K,
+                                                  int64_t lda, int64_t ska, __nv_bfloat16 *__restrict__ p1,
+                                                  __nv_bfloat16 *__restrict__ p2, __nv_bfloat16 *__restrict__ p3,
+                                                  int64_t Kp, int *__restrict__ sa, double alpha, double beta) {
+  __shared__ double red[32];
+  for (int64_t m = blockIdx.x; m < Mp; m += gridDim.x) {
+    split_row<AFF>(m, A, M, K, lda, ska, p1, p2, p3, Kp, sa, alpha, beta, red);
+    __syncthreads();   // red is reused by the next row's maximum
   }
 }
 
@@ -490,14 +528,14 @@ __global__ void __launch_bounds__(256) col_max(const double *__restrict__ B, int
   atomicMax(&bmax[n], (unsigned long long)bits << 32);
 }
 
-// B (K x N) -> transposed TF32 hi/lo [Np x Kp] (K-major), zero-padded;
+// B (K x N) -> transposed BF16 parts [Np x Kp] (K-major), zero-padded;
 // AFF: the operand is alpha * B + beta
 template <bool AFF>
 __global__ void __launch_bounds__(256) split_cols_t(const double *__restrict__ B, int64_t K, int64_t N, int64_t ldb,
                                                    int64_t snb, const unsigned long long *__restrict__ bmax,
-                                                   int *__restrict__ sb, float *__restrict__ hi,
-                                                   float *__restrict__ lo, int64_t Kp, int64_t Np, double alpha,
-                                                   double beta) {
+                                                   int *__restrict__ sb, __nv_bfloat16 *__restrict__ p1,
+                                                   __nv_bfloat16 *__restrict__ p2, __nv_bfloat16 *__restrict__ p3,
+                                                   int64_t Kp, int64_t Np, double alpha, double beta) {
   __shared__ double tile[32][33];
   const int64_t k0 = (int64_t)blockIdx.x * 32, nb = (int64_t)blockIdx.y * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
@@ -512,10 +550,10 @@ __global__ void __launch_bounds__(256) split_cols_t(const double *__restrict__ B
   for (int r = ty; r < 32; r += 8) {
     const int64_t n = nb + r, k = k0 + tx;
     if (n < Np && k < Kp) {
-      float h, l;
-      split_one(tile[tx][r], h, l);   // scaled by 2^sb[n] already
-      hi[n * Kp + k] = h;
-      lo[n * Kp + k] = l;
+      const Parts q = parts3(__double2float_rn(tile[tx][r]));   // scaled by 2^sb[n] already
+      p1[n * Kp + k] = __float2bfloat16_rn(q.p1);
+      p2[n * Kp + k] = __float2bfloat16_rn(q.p2);
+      p3[n * Kp + k] = __float2bfloat16_rn(q.p3);
     }
   }
 }
@@ -540,10 +578,10 @@ static bool make_map(CUtensorMap *map, const void *base, int64_t inner, int64_t 
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
-  cuuint64_t strides[1] = {(cuuint64_t)(inner * 4)};
+  cuuint64_t strides[1] = {(cuuint64_t)(inner * 2)};
   cuuint32_t box[2] = {BK, BM};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, estr,
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -551,7 +589,7 @@ static bool make_map(CUtensorMap *map, const void *base, int64_t inner, int64_t 
 
 size_t dense_workspace_bytes(int64_t M, int64_t N, int64_t K) {
   const int64_t Mp = (M + BM - 1) / BM * BM, Np = (N + BN - 1) / BN * BN, Kp = (K + BK - 1) / BK * BK;
-  return (size_t)(Mp * Kp * 8 + Np * Kp * 8) + (size_t)(Mp + Np) * 4 + (size_t)Np * 8 + 2048;
+  return (size_t)(Mp * Kp * 2 * NPART + Np * Kp * 2 * NPART) + (size_t)(Mp + Np) * 4 + (size_t)Np * 8 + 2048;
 }
 
 cudaError_t dense_split_b(const DenseB &b, void *ws, cudaStream_t s) {
@@ -567,19 +605,26 @@ cudaError_t dense_split_b(const DenseB &b, void *ws, cudaStream_t s) {
   }
   dim3 g((unsigned)(Kp / 32), (unsigned)(Np / 32));
   if (aff)
-    split_cols_t<true><<<g, 256, 0, s>>>(b.B, b.K, b.N, b.ldb, b.snb, w.bmax, w.sb, w.bh, w.bl, Kp, Np, b.alpha, b.beta);
+    split_cols_t<true><<<g, 256, 0, s>>>(b.B, b.K, b.N, b.ldb, b.snb, w.bmax, w.sb, w.b[0], w.b[1], w.b[2], Kp, Np,
+                                         b.alpha, b.beta);
   else
-    split_cols_t<false><<<g, 256, 0, s>>>(b.B, b.K, b.N, b.ldb, b.snb, w.bmax, w.sb, w.bh, w.bl, Kp, Np, 1.0, 0.0);
+    split_cols_t<false><<<g, 256, 0, s>>>(b.B, b.K, b.N, b.ldb, b.snb, w.bmax, w.sb, w.b[0], w.b[1], w.b[2], Kp, Np,
+                                          1.0, 0.0);
   return cudaGetLastError();
 }
 
 cudaError_t dense_split_a(const DenseA &a, int64_t K, int64_t M_max, int64_t N, void *ws, cudaStream_t s) {
   const int64_t Mp = (a.M + BM - 1) / BM * BM, Kp = (K + BK - 1) / BK * BK;
   DenseWs w = dense_ws_layout(ws, M_max, N, K);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned grid = (unsigned)std::min<int64_t>(Mp, (int64_t)sms * SPLIT_CTAS_PER_SM);
   if (a.alpha != 1.0 || a.beta != 0.0)
-    split_rows<true><<<(unsigned)Mp, 256, 0, s>>>(a.A, a.M, K, a.lda, a.ska, w.ah, w.al, Kp, w.sa, a.alpha, a.beta);
+    split_rows<true><<<grid, 256, 0, s>>>(a.A, a.M, Mp, K, a.lda, a.ska, w.a[0], w.a[1], w.a[2], Kp, w.sa, a.alpha,
+                                          a.beta);
   else
-    split_rows<false><<<(unsigned)Mp, 256, 0, s>>>(a.A, a.M, K, a.lda, a.ska, w.ah, w.al, Kp, w.sa, 1.0, 0.0);
+    split_rows<false><<<grid, 256, 0, s>>>(a.A, a.M, Mp, K, a.lda, a.ska, w.a[0], w.a[1], w.a[2], Kp, w.sa, 1.0, 0.0);
   return cudaGetLastError();
 }
 
@@ -590,16 +635,15 @@ cudaError_t dense_split_gemm(const DenseA &a, int64_t N, int64_t K, int64_t M_ma
   cudaError_t e = cudaSuccess;
   if (hdrain < 1) hdrain = 1;
   if (hdrain > L_CHUNK) hdrain = L_CHUNK;
-  CUtensorMap mah, mal, mbh, mbl;
-  if (!make_map(&mah, w.ah, Kp, Mp) || !make_map(&mal, w.al, Kp, Mp) || !make_map(&mbh, w.bh, Kp, Np) ||
-      !make_map(&mbl, w.bl, Kp, Np))
-    return cudaErrorInvalidValue;
+  CUtensorMap ma[NPART], mb[NPART];
+  for (int q = 0; q < NPART; ++q)
+    if (!make_map(&ma[q], w.a[q], Kp, Mp) || !make_map(&mb[q], w.b[q], Kp, Np)) return cudaErrorInvalidValue;
   static std::atomic<uint64_t> attr{0};
   e = smem_limit_once((const void *)gemm_split_kernel, SMEM_BYTES, attr);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)(Np / BN), (unsigned)(Mp / BM));
-  gemm_split_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(mah, mal, mbh, mbl, w.sa, w.sb, C, a.M, N, ldc,
-                                                       (int)(Kp / BK), lolo ? 1 : 0, hdrain, status,
+  gemm_split_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(ma[0], ma[1], ma[2], mb[0], mb[1], mb[2], w.sa, w.sb, C, a.M,
+                                                       N, ldc, (int)(Kp / BK), lolo ? 1 : 0, hdrain, status,
                                                        wait_limit > 0 ? wait_limit : TIMEOUT_CYCLES);
   return cudaGetLastError();
 }
@@ -608,14 +652,14 @@ DenseWs dense_ws_layout(void *ws, int64_t M_max, int64_t N, int64_t K) {
   const int64_t Mp = (M_max + BM - 1) / BM * BM, Np = (N + BN - 1) / BN * BN, Kp = (K + BK - 1) / BK * BK;
   uint8_t *p = (uint8_t *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
   DenseWs w;
-  w.ah = (float *)p;
-  p += Mp * Kp * 4;
-  w.al = (float *)p;
-  p += Mp * Kp * 4;
-  w.bh = (float *)p;
-  p += Np * Kp * 4;
-  w.bl = (float *)p;
-  p += Np * Kp * 4;
+  for (int q = 0; q < NPART; ++q) {
+    w.a[q] = (__nv_bfloat16 *)p;
+    p += Mp * Kp * 2;
+  }
+  for (int q = 0; q < NPART; ++q) {
+    w.b[q] = (__nv_bfloat16 *)p;
+    p += Np * Kp * 2;
+  }
   w.sa = (int *)p;
   p += Mp * 4;
   w.sb = (int *)p;

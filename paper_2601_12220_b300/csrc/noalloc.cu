@@ -81,7 +81,7 @@ int be_gemm_split_noalloc(const double *A, int64_t lda, const double *B, int64_t
   if (need > NOALLOC_SCRATCH_BYTES)
     return noalloc_fail(BE_ETOOMANY, "needs " + std::to_string(need) + " bytes of scratch; the fixed array holds " +
                                          std::to_string(NOALLOC_SCRATCH_BYTES) +
-                                         " (about (M + N) * K * 8 bytes after padding M, N to 128 and K to 32)");
+                                         " (about (M + N) * K * 6 bytes after padding M, N to 128 and K to 64)");
   void *ws = nullptr;
   int st = scratch_address(&ws);
   if (st) return st;
@@ -98,7 +98,7 @@ int be_gemm_split_noalloc(const double *A, int64_t lda, const double *B, int64_t
     e = be::dense_split_b(be::DenseB{B, K, N, ldb, 1, M}, ws, s);
     if (e == cudaSuccess) e = be::dense_split_a(be::DenseA{A, M, lda, 1}, K, M, N, ws, s);
     if (e == cudaSuccess)
-      e = be::dense_split_gemm(be::DenseA{A, M, lda, 1}, N, K, M, C, ldc, ws, false, 2, status, 0, s);
+      e = be::dense_split_gemm(be::DenseA{A, M, lda, 1}, N, K, M, C, ldc, ws, false, 1, status, 0, s);
   }
   if (e != cudaSuccess) return noalloc_fail(BE_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
   return BE_OK;

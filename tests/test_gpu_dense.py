@@ -1,11 +1,13 @@
 """GPU parity of the dense split-precision strategy (tcgen05) vs the FP64 oracle.
 
 Split-precision tolerance: |got - ref| <= 1e-6 * S componentwise (S the
-absolute contraction).  A priori the split drops lo*lo and the residuals of
-two 11-bit TF32 parts (about 3 * 2^-22 relative per product) and adds FP32
-rounding inside each 1024-long chunk; the measured error is reported
-alongside.  Small-integer inputs (|x| <= 3) are exact in every TF32 part and every
-partial sum, so those cases must match bit for bit.
+absolute contraction).  A priori the split keeps about 24 bits of each
+operand in three BF16 parts, drops the products below the third level
+(about 2^-23 relative), loses at most 2^-23 of the leading accumulator per
+MMA between drains (4 MMAs at the default drain interval) and sums the
+drains with Kahan's compensation; the measured error is reported
+alongside.  Small-integer inputs (|x| <= 3) are exact in the first BF16
+part and in every partial sum, so those cases must match bit for bit.
 """
 import numpy as np
 import pytest
@@ -66,8 +68,8 @@ def test_integers_bit_exact(ctx):
 
 
 def test_wide_dynamic_range(ctx):
-    """Rows and columns spanning many binades: the per-row / per-column
-    power-of-two scales keep every part in FP16 range."""
+    """Rows and columns spanning many binades: rows inside [2^-26, 2^40)
+    take the fixed scale, the others their own power-of-two scale."""
     g = np.random.default_rng(2)
     M, N, K = 130, 140, 700
     A = g.standard_normal((M, K)) * np.exp2(g.integers(-40, 40, size=(M, 1)))
@@ -181,3 +183,34 @@ def test_affine_integers_bit_exact(ctx):
     got, = run_split_sc(ctx, text, dict(A=A, B=B), (-2.0, 3.0))
     (ref, S), = ev.evaluate(text, dict(A=A, B=B), scalars=dict(s=-2.0, t=3.0))
     assert np.array_equal(got, ref)
+
+
+def test_rows_outside_the_fixed_scale_window(ctx):
+    """Rows whose largest entry lies far outside [2^-26, 2^40) (2^-300,
+    2^-60, 2^60, 2^300) are split again with their own scale; columns of B
+    at 2^+-200.  Every output within 1e-6 S."""
+    g = np.random.default_rng(5)
+    M, N, K = 8, 6, 200
+    A = g.standard_normal((M, K)) * np.exp2(np.array([-300, -60, -27, 0, 39, 41, 60, 300], dtype=float))[:, None]
+    B = g.standard_normal((K, N)) * np.exp2(np.array([-200, -20, 0, 0, 20, 200], dtype=float))[None, :]
+    text = f"ik,kj->ij | A,B ; A:f64[{M},{K}] ; B:f64[{K},{N}]"
+    got, = run_split(ctx, text, dict(A=A, B=B))
+    (ref, S), = ev.evaluate(text, dict(A=A, B=B))
+    assert rel_err(got, ref, S).max() <= 1e-6
+
+
+@pytest.mark.parametrize("hdrain", [2, 4])
+def test_longer_drain_intervals(ctx, hdrain):
+    """Drain intervals of 2 and 4 k-blocks (faster, with a looser a-priori
+    bound) on N(0,1) data: the measured error stays far inside 1e-6 S."""
+    g = np.random.default_rng(6 + hdrain)
+    M, N, K = 256, 256, 2048
+    A, B = g.standard_normal((M, K)), g.standard_normal((K, N))
+    text = f"ik,kj->ij | A,B ; A:f64[{M},{K}] ; B:f64[{K},{N}]"
+    e = be.Einsum(text)
+    outs = [torch.full(e.out_shape, float("nan"), dtype=torch.float64, device=DEV)]
+    be.execute(ctx, e, {"A": torch.from_numpy(A).to(DEV), "B": torch.from_numpy(B).to(DEV)}, outs,
+               cfg=be.make_config(be.STRAT_DENSE_SPLIT, (0, 0, hdrain)), precision=be.PREC_SPLIT)
+    assert ctx.status() == be.OK
+    (ref, S), = ev.evaluate(text, dict(A=A, B=B))
+    assert rel_err(outs[0].cpu().numpy(), ref, S).max() <= 1e-7

@@ -116,8 +116,8 @@ def test_noalloc_k0_and_argument_errors():
 
 
 def test_noalloc_rejects_oversize():
-    A = torch.zeros((1024, 4096), dtype=torch.float64, device=DEV)
-    B = torch.zeros((4096, 1024), dtype=torch.float64, device=DEV)
+    A = torch.zeros((1024, 8192), dtype=torch.float64, device=DEV)
+    B = torch.zeros((8192, 1024), dtype=torch.float64, device=DEV)
     C = torch.zeros((1024, 1024), dtype=torch.float64, device=DEV)
     rc = noalloc(A, B, C, torch.cuda.current_stream())
     assert rc == be.ETOOMANY
