@@ -269,6 +269,35 @@ __device__ __forceinline__ bool produce_fast_ok(const EProd &q, double a, double
   return dfm::sin_fast_ok(a) && dfm::df_fast_ok(b);
 }
 
+// digits of the pair (u0, u1) = u[e, j], u[e, j + 1] of pair pi of a tile,
+// scaled by the element's row scale, into the six digit planes of u
+__device__ __forceinline__ void pair_digits(df u0, df u1, int pi, int JP, uint32_t jinv, const int *ku, uint8_t *A,
+                                            int aplane) {
+  const int m = (int)(((uint32_t)pi * jinv) >> 20), j = 2 * (pi - m * JP);
+  const float sc = pow2f(-ku[m]);
+  float d0[TC_P], d1[TC_P];
+  digits_df(u0.hi * sc, u0.lo * sc, d0);
+  digits_df(u1.hi * sc, u1.lo * sc, d1);
+  uint8_t *dst = A + sw32(TC_M, m, j >> 3) + (j & 7) * 2;
+#pragma unroll
+  for (int k = 0; k < TC_P; ++k) *(uint32_t *)(dst + k * aplane) = pack_bf16(d0[k], d1[k]);
+}
+
+// a producer batch with an operand outside the fast range: the operands are
+// read again and every value takes the tested producer; out of line, so
+// that the hot loop's code stays small
+static __device__ __noinline__ void pairs_slow(const EProd &q, TileRows rows, bool need_b, int p0, int pb, int stride,
+                                               int np, int JP, uint32_t jinv, int NJ, const int *ku, uint8_t *A,
+                                               int aplane, const float2 *sin_tab) {
+  for (int u = 0; u < pb; ++u) {
+    const int pi = p0 + u * stride;
+    if (pi >= np) break;
+    double v[4];
+    load_pair(rows, need_b, pi, np, JP, jinv, NJ, v);
+    pair_digits(produce(q, v[0], v[2], sin_tab), produce(q, v[1], v[3], sin_tab), pi, JP, jinv, ku, A, aplane);
+  }
+}
+
 // named barriers: 1 for the producer warps, 2 for the epilogue warps (the
 // .red forms return the AND / OR of a predicate over the participants, so
 // that a role leaves its loop together)
@@ -301,8 +330,9 @@ __device__ __forceinline__ bool brow(const TcParams &tp, int n, int &i, int &r) 
   const int cb = n >> 5, c = n & 31, h = c >> 4, cc = c & 15;
   r = cc % R;
   const int il = cc / R;
-  i = cb * 2 * H0 + h * H0 + il;
-  return il < H0 && i < tp.p.NI;
+  const int nI = min(2 * H0, tp.p.NI - cb * 2 * H0), h0 = min(H0, (nI + 1) >> 1);
+  i = cb * 2 * H0 + h * h0 + il;
+  return il < H0 && il < (h == 0 ? h0 : nI - h0);
 }
 
 // |k| of a scale outside the certified window
@@ -530,31 +560,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
 #pragma unroll
           for (int u = 0; u < PB; ++u) load_pair(rows, need_b, p0 + (PB + u) * NPROD, np, JP, jinv, NJ, an + 4 * u);
         }
-        auto batch = [&](auto fast) {
-          constexpr bool F = decltype(fast)::value;
-#pragma unroll
-          for (int u = 0; u < PB; ++u) {
-            const int pi = p0 + u * NPROD;
-            if (pi < np) {
-              const int m = (int)(((uint32_t)pi * jinv) >> 20), j = 2 * (pi - m * JP);
-              const float sc = pow2f(-ku[m]);
-              float d0[TC_P], d1[TC_P];
-              const df u0 = produce_t<F>(q, av[4 * u], av[4 * u + 2], sin_tab);
-              const df u1 = produce_t<F>(q, av[4 * u + 1], av[4 * u + 3], sin_tab);   // zero past NJ
-              digits_df(u0.hi * sc, u0.lo * sc, d0);
-              digits_df(u1.hi * sc, u1.lo * sc, d1);
-              uint8_t *dst = A + sw32(TC_M, m, j >> 3) + (j & 7) * 2;
-#pragma unroll
-              for (int k = 0; k < TC_P; ++k) *(uint32_t *)(dst + k * aplane) = pack_bf16(d0[k], d1[k]);
-            }
-          }
-        };
         bool fast = true;
 #pragma unroll
         for (int u = 0; u < PB; ++u)
           fast = fast && produce_fast_ok(q, av[4 * u], av[4 * u + 2]) && produce_fast_ok(q, av[4 * u + 1], av[4 * u + 3]);
-        if (fast) batch(std::true_type{});
-        else batch(std::false_type{});
+        if (fast) {
+#pragma unroll
+          for (int u = 0; u < PB; ++u) {
+            const int pi = p0 + u * NPROD;
+            if (pi < np)
+              pair_digits(produce_t<true>(q, av[4 * u], av[4 * u + 2], sin_tab),
+                          produce_t<true>(q, av[4 * u + 1], av[4 * u + 3], sin_tab), pi, JP, jinv, ku, A, aplane);
+          }
+        } else {
+          pairs_slow(q, rows, need_b, p0, PB, NPROD, np, JP, jinv, NJ, ku, A, aplane, sin_tab);
+        }
       }
       tc::fence_proxy_async();
       tc::mbar_arrive(&a_full[ab]);
@@ -657,8 +677,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
 #pragma unroll
             for (int r = 0; r < R; ++r) gk[k][r] = df{gk[k][r].hi * sg, gk[k][r].lo * sg};
         }
-        const int nI = min(IB, NI - cb * IB);
-        const int nIh = max(0, min(H0, nI - half * H0));      // i of this half (warp-uniform)
+        // i of this half (warp-uniform): a block's i split evenly between its
+        // halves, the first taking the odd one
+        const int nI = min(IB, NI - cb * IB), h0 = min(H0, (nI + 1) >> 1);
+        const int nIh = half == 0 ? h0 : nI - h0;
         const int nch = (nIh * R + 7) >> 3;                      // 8-column chunks holding them
         const int nb = cb * TC_NCOL + half * (TC_NCOL / 2);      // first B row of this half
         // t for this half's columns: the 7 level accumulators of a column
@@ -701,7 +723,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
 #pragma unroll
           for (int il = 0; il < H0; ++il) {
             if (il < nIh) {
-              const int i = cb * IB + half * H0 + il;
+              const int i = cb * IB + half * h0 + il;
               // check terms of the R columns of this i
               float z[R];
 #pragma unroll
