@@ -387,9 +387,11 @@ __device__ __forceinline__ Parts parts3(float x) {
 }
 
 // x * 2^s split into three BF16 parts; the float image from the bits when
-// the scaled row stays in FP32's normal range, else through FP64
-__device__ __forceinline__ Parts split_scaled(double x, int s, bool fp32_ok) {
-  return parts3(fp32_ok ? scaled_float(x, s) : __double2float_rn(x * pow2(s)));
+// the scaled row stays in FP32's normal range (F32, a template parameter so
+// that the FP64 form is not evaluated beside it), else through FP64
+template <bool F32>
+__device__ __forceinline__ Parts split_scaled(double x, int s) {
+  return parts3(F32 ? scaled_float(x, s) : __double2float_rn(x * pow2(s)));
 }
 
 // the operand value of an affine producer, alpha * x + beta (AFF), else x
@@ -405,10 +407,10 @@ __device__ __forceinline__ double affine(double x, double alpha, double beta) {
 // one pass over row m: every entry (its affine producer's value) times 2^s
 // split into three BF16 parts and written to the padded row; returns this
 // thread's largest high word of |x| (the row maximum's exponent) when TRACK
-template <bool AFF, bool TRACK>
+template <bool AFF, bool TRACK, bool F32>
 __device__ __forceinline__ uint32_t split_pass(const double *__restrict__ row, bool vec, int64_t K, int64_t ska,
                                                __nv_bfloat16 *__restrict__ r1, __nv_bfloat16 *__restrict__ r2p,
-                                               __nv_bfloat16 *__restrict__ r3, int64_t Kp, int s, bool fp32_ok,
+                                               __nv_bfloat16 *__restrict__ r3, int64_t Kp, int s,
                                                double alpha, double beta) {
   uint32_t bits = 0;
   if (vec) {
@@ -427,7 +429,7 @@ __device__ __forceinline__ uint32_t split_pass(const double *__restrict__ row, b
           bits = max(bits, (uint32_t)__double2hiint(x) & 0x7fffffffu);
           bits = max(bits, (uint32_t)__double2hiint(y) & 0x7fffffffu);
         }
-        const Parts a = split_scaled(x, s, fp32_ok), b = split_scaled(y, s, fp32_ok);
+        const Parts a = split_scaled<F32>(x, s), b = split_scaled<F32>(y, s);
         o1[k + u * blockDim.x] = __floats2bfloat162_rn(a.p1, b.p1);
         o2[k + u * blockDim.x] = __floats2bfloat162_rn(a.p2, b.p2);
         o3[k + u * blockDim.x] = __floats2bfloat162_rn(a.p3, b.p3);
@@ -442,8 +444,8 @@ __device__ __forceinline__ uint32_t split_pass(const double *__restrict__ row, b
           bits = max(bits, (uint32_t)__double2hiint(x) & 0x7fffffffu);
           bits = max(bits, (uint32_t)__double2hiint(y) & 0x7fffffffu);
         }
-        a = split_scaled(x, s, fp32_ok);
-        b = split_scaled(y, s, fp32_ok);
+        a = split_scaled<F32>(x, s);
+        b = split_scaled<F32>(y, s);
       }
       o1[k] = __floats2bfloat162_rn(a.p1, b.p1);
       o2[k] = __floats2bfloat162_rn(a.p2, b.p2);
@@ -456,7 +458,7 @@ __device__ __forceinline__ uint32_t split_pass(const double *__restrict__ row, b
     if (k < K) {
       const double x = affine<AFF>(row[k * ska], alpha, beta);
       if (TRACK) bits = max(bits, (uint32_t)__double2hiint(x) & 0x7fffffffu);
-      a = split_scaled(x, s, fp32_ok);
+      a = split_scaled<F32>(x, s);
     }
     r1[k] = __float2bfloat16_rn(a.p1);
     r2p[k] = __float2bfloat16_rn(a.p2);
@@ -485,15 +487,17 @@ __device__ __forceinline__ void split_row(int64_t m, const double *__restrict__ 
   // |x| compared as integers on the sign-cleared high word (32-bit: a 64-bit
   // integer max issues on the FP64 pipe); the scale needs only the largest
   // exponent, which the high word carries
-  const uint32_t bits = m < M ? split_pass<AFF, true>(row, vec, K, ska, r1, r2, r3, Kp, S0, true, alpha, beta)
-                              : split_pass<AFF, false>(row, vec, 0, ska, r1, r2, r3, Kp, S0, true, alpha, beta);
+  const uint32_t bits = m < M ? split_pass<AFF, true, true>(row, vec, K, ska, r1, r2, r3, Kp, S0, alpha, beta)
+                              : split_pass<AFF, false, true>(row, vec, 0, ska, r1, r2, r3, Kp, S0, alpha, beta);
   const double mx = block_max(__hiloint2double((int)bits, 0), red);
   int s = S0;
   if (!(mx == 0.0 || (mx >= 0x1p-26 && mx < 0x1p+40))) {
     s = scale_for(mx);
     // the scaled row max is below 2^14; FP32 scaling is exact while |x| >= 2^-100 * max
-    const bool fp32_ok = mx > 0x1p-26 && mx < 0x1p+100 && s > -120 && s < 120;
-    split_pass<AFF, false>(row, vec, K, ska, r1, r2, r3, Kp, s, fp32_ok, alpha, beta);
+    if (mx > 0x1p-26 && mx < 0x1p+100 && s > -120 && s < 120)
+      split_pass<AFF, false, true>(row, vec, K, ska, r1, r2, r3, Kp, s, alpha, beta);
+    else
+      split_pass<AFF, false, false>(row, vec, K, ska, r1, r2, r3, Kp, s, alpha, beta);
   }
   if (threadIdx.x == 0 && m < M) sa[m] = s;
 }
