@@ -853,6 +853,12 @@ def run_mix(args):
     generic_only = be.Batch(ctx, items, be.make_config(stage_mask=1))
     ms_generic = timed(lambda: generic_only.run(stream), max(1, args.steps // 2), 1)
     generic_only.close()
+    # the same policy with every generic instance on its loop nest (no factoring)
+    unfactored = be.Batch(ctx, items, be.make_config(tile=(0, 0, 0, args.mix_split_log2),
+                                                      split=0 if args.mix_no_split else 1, stage_mask=2))
+    ms_unfactored = timed(lambda: unfactored.run(stream), max(1, args.steps // 2), 1)
+    unfactored.close()
+    fac = batch.factored()
     peaks = load_peaks()
     kms = t_k / max(1, n_k)
     line = {"metric": METRIC, "value": world * args.mix_n / (ms_batch * 1e-3), "unit": "einsums/s",
@@ -867,6 +873,8 @@ def run_mix(args):
             "one_launch_per_einsum": {"ms_per_step": ms_single, "einsums_per_s": args.mix_n / (ms_single * 1e-3)},
             "speedup_vs_one_launch_per_einsum": ms_single / ms_batch,
             "all_generic_batch": {"ms_per_step": ms_generic, "einsums_per_s": args.mix_n / (ms_generic * 1e-3)},
+            "factored": dict(fac, unfactored_batch={"ms_per_step": ms_unfactored,
+                                                    "einsums_per_s": args.mix_n / (ms_unfactored * 1e-3)}),
             "per_pipe_bound_ms": {k: v * 1e3 for k, v in pipe_s.items()},
             "roofline_per_instance_pipe": {
                 "bound_ms": max(pipe_s.values()) * 1e3, "serial_bound_ms": sum(pipe_s.values()) * 1e3,

@@ -325,10 +325,19 @@ int be_tune(be_ctx *x, const be_einsum *e, int32_t precision, const be_buf *bufs
  *   of its rows becomes a descriptor whose outputs are cut into tiles of
  *   about 2^tile[1] operand terms (default 20) for one persistent launch
  *   (cfg->tile[0] its block size, default 256, and 256 whenever a row is
- *   evaluated as GEMM tiles; cfg->tile[2] CTAs per SM, default 4).  cfg may be NULL.  Everything is captured once in a CUDA
- *   graph with three concurrent branches: the persistent grid of generic
- *   tiles, the element launches and the split / GEMM launches (which use a
- *   split workspace owned by the batch).  The element and dense launches
+ *   evaluated as GEMM tiles; cfg->tile[2] CTAs per SM, default 4).  A
+ *   generic instance of 3 to 5 operands, all views of buffers, whose best
+ *   pairwise order (fewest multiply-adds over all orders of two-operand
+ *   contractions) cuts the multiply-adds of Eq. (1)'s loop nest at least 4
+ *   times is factored: each row runs as that sequence of two-operand
+ *   einsums over dense intermediates (the same sum with its terms grouped
+ *   differently), the steps in phases by dependency, one persistent launch
+ *   per phase, the intermediates in a workspace owned by the batch
+ *   (cfg->stage_mask bit 1 keeps every instance on its loop nest).  cfg may
+ *   be NULL.  Everything is captured once in a CUDA
+ *   graph with three concurrent branches: the persistent launches of
+ *   generic tiles, the element launches and the split / GEMM launches
+ *   (which use a split workspace owned by the batch).  The element and dense launches
  *   run once during creation.  The buffers are borrowed and must stay valid
  *   while the batch is used; their CONTENTS may change between runs.
  *   Device memory for descriptors, tiles and the workspace is allocated
@@ -336,9 +345,14 @@ int be_tune(be_ctx *x, const be_einsum *e, int32_t precision, const be_buf *bufs
  * be_batch_run -- replay the captured graph on `stream` (asynchronous).
  *   Every output has a single owner and a fixed evaluation order, so the
  *   results are bitwise those of be_execute on each instance alone with
- *   the strategy it was given (BE_STRAT_GENERIC for generic instances).
- * be_batch_info -- rows, tiles and total operand terms of the generic part.
+ *   the strategy it was given (BE_STRAT_GENERIC for generic instances),
+ *   except factored instances, whose grouping of the terms differs (within
+ *   the precision mode's tolerance) and is itself deterministic.
+ * be_batch_info -- rows, tiles and total operand terms of the generic part
+ *   (factored steps counted as rows).
  * be_batch_kinds -- number of instances given each strategy.
+ * be_batch_factored -- number of factored instances, persistent launches
+ *   (phases) per run, and bytes of the intermediates' workspace.
  */
 int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_buf *const *bufs,
                     const int32_t *n_bufs, const be_buf *const *outs, const int32_t *n_outs,
@@ -347,6 +361,7 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
 int be_batch_run(be_batch *b, void *stream);
 int be_batch_info(const be_batch *b, int64_t *rows, int64_t *tiles, double *terms);
 int be_batch_kinds(const be_batch *b, int32_t *generic, int32_t *element, int32_t *dense);
+int be_batch_factored(const be_batch *b, int32_t *instances, int32_t *phases, int64_t *workspace_bytes);
 
 /*
  * be_tune_batch -- the autotuner for a batch (spec pattern 2: tile

@@ -865,6 +865,9 @@ static void tune_candidates(const Einsum &e, const std::vector<BufIn> &bi, const
 
 }  // extern "C"
 
+// largest workspace of a batch's factored intermediates (bytes)
+static constexpr double FACTOR_WS_MAX = 4.0 * (1ull << 30);
+
 struct be_batch {
   be_ctx *x = nullptr;
   std::vector<GParams> rows;
@@ -884,6 +887,15 @@ struct be_batch {
   void *ws = nullptr;
   int *status = nullptr;
   bool own_status = false;
+  // factored instances: their pairwise steps run in dependency phases, one
+  // persistent launch per phase (tiles of phase q at phase_off[q]), with the
+  // intermediates in a workspace owned by the batch
+  int phases = 1;
+  std::vector<int64_t> phase_off, phase_n;
+  std::vector<int> phase_grid;
+  int32_t n_factored = 0;
+  void *fws = nullptr;
+  size_t fws_bytes = 0;
   ~be_batch() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -896,6 +908,7 @@ struct be_batch {
     if (d_tiles) cudaFree(d_tiles);
     if (d_counter) cudaFree(d_counter);
     if (ws) cudaFree(ws);
+    if (fws) cudaFree(fws);
     if (own_status && status) cudaFree(status);
   }
 };
@@ -958,11 +971,50 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
   // split-precision tensor-core strategy
   const bool allow_element = !(c.stage_mask & 1u);
   const double dense_min = std::ldexp(1.0, c.tile[3] > 0 ? c.tile[3] : 20);
+  // factored steps are two-operand rows, often GEMM tiles, which need the
+  // 256-thread block
+  const bool allow_factor = !(c.stage_mask & 2u) && b->block == 256;
   std::vector<int> el_inst, dn_inst;
   std::vector<be_config_t> el_cfg;
   std::vector<DensePlan> dn_plan;
   size_t ws_need = 0;
   std::string err;
+  struct FacInst {
+    int k = 0;
+    FactorOrder fo;
+    std::vector<std::vector<FOp>> ops;   // per row, the operand views
+    std::vector<void *> outs;            // per row, the output
+  };
+  std::vector<FacInst> fac_inst;
+  // a generic row (or a factored step) into the tile list of its phase:
+  // outputs per tile so that each tile costs about cost_target operand terms
+  std::vector<std::vector<PTile>> ptiles(1);
+  auto add_row = [&](const GParams &p, int phase, int k) -> int {
+    if (p.total_out == 0) return BE_OK;
+    if (p.mode == 3 && b->block != 256)
+      return fail(BE_EARG, "instance " + std::to_string(k) + ": rows evaluated as GEMM tiles need a block of 256 threads");
+    if ((int)ptiles.size() <= phase) ptiles.resize(phase + 1);
+    std::vector<PTile> &pt = ptiles[phase];
+    const int row = (int)b->rows.size();
+    b->rows.push_back(p);
+    const double per_out = (double)std::max<int64_t>(1, p.total_con) * std::max(1, p.n_ops);
+    b->terms += per_out * (double)p.total_out;
+    if (p.mode == 3) {   // units are GEMM tiles of tile x tile outputs
+      const double per_tile = per_out * p.gemm.tile * p.gemm.tile;
+      const int64_t tile = std::max<int64_t>(1, std::min<int64_t>((int64_t)(cost_target / per_tile), 65536));
+      for (int64_t s0 = 0; s0 < p.gemm.tiles; s0 += tile) pt.push_back(PTile{row, 0, s0, std::min(tile, p.gemm.tiles - s0)});
+      return BE_OK;
+    }
+    int64_t tile = (int64_t)(cost_target / per_out);
+    if (p.mode == 0) {
+      tile = std::max<int64_t>(32, std::min<int64_t>(tile, 65536));
+      tile = (tile + 31) / 32 * 32;
+    } else {
+      tile = std::max<int64_t>(1, std::min<int64_t>(tile, 65536));
+    }
+    for (int64_t s0 = 0; s0 < p.total_out; s0 += tile) pt.push_back(PTile{row, 0, s0, std::min(tile, p.total_out - s0)});
+    return BE_OK;
+  };
   for (int k = 0; k < n; ++k) {
     if (!es[k]) return fail(BE_EARG, "NULL einsum in batch");
     const Einsum &e = es[k]->e;
@@ -1000,58 +1052,116 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
       }
     }
     ++b->n_kind[0];
+    // factored evaluation: an instance whose pairwise order cuts the loop
+    // nest's multiply-adds at least 4 times runs as two-operand steps over
+    // dense intermediates (stage_mask bit 1 turns this off)
+    if (allow_factor) {
+      FactorOrder fo;
+      bool fac = factor_order(e, 4.0, fo) &&
+                 (double)fo.inter_elems * e.b * dtype_size(e.out_dtype) <= FACTOR_WS_MAX;
+      std::vector<std::vector<FOp>> ops;
+      for (int i = 0; fac && i < e.b; ++i) {
+        std::vector<FOp> r(e.n);
+        for (int j = 0; fac && j < e.n; ++j) fac = operand_fop(e, i, j, bi, r[j]);
+        ops.push_back(r);
+      }
+      if (fac) {
+        FacInst fi;
+        fi.k = k;
+        fi.fo = fo;
+        fi.ops = ops;
+        for (int i = 0; i < e.b; ++i) fi.outs.push_back(bo[i].ptr);
+        fac_inst.push_back(std::move(fi));
+        ++b->n_factored;
+        continue;
+      }
+    }
     for (int i = 0; i < e.b; ++i) {
       GParams p;
       st = plan_generic_row(e, i, bi, bo[i], sc, p, err);
       if (st) return fail(st, "instance " + std::to_string(k) + ": " + err);
-      if (p.total_out == 0) continue;
-      if (p.mode == 3 && b->block != 256)
-        return fail(BE_EARG, "instance " + std::to_string(k) + ": rows evaluated as GEMM tiles need a block of 256 threads");
-      const int row = (int)b->rows.size();
-      b->rows.push_back(p);
-      // outputs per tile so that each tile costs about cost_target operand terms
-      const double per_out = (double)std::max<int64_t>(1, p.total_con) * std::max(1, p.n_ops);
-      if (p.mode == 3) {   // units are GEMM tiles of tile x tile outputs
-        const double per_tile = per_out * p.gemm.tile * p.gemm.tile;
-        const int64_t tile = std::max<int64_t>(1, std::min<int64_t>((int64_t)(cost_target / per_tile), 65536));
-        for (int64_t s0 = 0; s0 < p.gemm.tiles; s0 += tile)
-          b->tiles.push_back(PTile{row, 0, s0, std::min(tile, p.gemm.tiles - s0)});
-        b->terms += per_out * (double)p.total_out;
-        continue;
-      }
-      int64_t tile = (int64_t)(cost_target / per_out);
-      if (p.mode == 0) {
-        tile = std::max<int64_t>(32, std::min<int64_t>(tile, 65536));
-        tile = (tile + 31) / 32 * 32;
-      } else {
-        tile = std::max<int64_t>(1, std::min<int64_t>(tile, 65536));
-      }
-      for (int64_t s0 = 0; s0 < p.total_out; s0 += tile)
-        b->tiles.push_back(PTile{row, 0, s0, std::min(tile, p.total_out - s0)});
-      b->terms += per_out * (double)p.total_out;
+      st = add_row(p, 0, k);
+      if (st) return st;
     }
   }
-  // longest tiles first (cost = outputs x terms per output); ties by position
-  std::vector<double> cost(b->tiles.size());
-  for (size_t t = 0; t < b->tiles.size(); ++t) {
-    const GParams &p = b->rows[b->tiles[t].row];
-    cost[t] = (double)b->tiles[t].count * (double)std::max<int64_t>(1, p.total_con) * std::max(1, p.n_ops) *
-              (p.mode == 3 ? (double)p.gemm.tile * p.gemm.tile : 1.0);
+  // the factored instances' steps: intermediates carved from one workspace,
+  // each step in the phase after the steps it reads
+  {
+    size_t need = 0;
+    for (auto &fi : fac_inst) {
+      const Einsum &e = es[fi.k]->e;
+      for (int i = 0; i < e.b; ++i)
+        for (size_t q = 0; q + 1 < fi.fo.steps.size(); ++q) {
+          double elems = 1.0;
+          for (int8_t c : fi.fo.letters[q]) elems *= (double)e.len[c];
+          need += ((size_t)elems * dtype_size(e.out_dtype) + 255) / 256 * 256;
+        }
+    }
+    if (need) {
+      cudaError_t ce0 = cudaMalloc(&b->fws, need);
+      if (ce0 != cudaSuccess) return fail(BE_ECUDA, std::string("batch workspace: ") + cudaGetErrorString(ce0));
+      b->fws_bytes = need;
+    }
+    size_t off = 0;
+    for (auto &fi : fac_inst) {
+      const Einsum &e = es[fi.k]->e;
+      const int n = e.n;
+      for (int i = 0; i < e.b; ++i) {
+        std::vector<FOp> slot = fi.ops[i];
+        std::vector<int> slot_phase(n, -1);
+        for (size_t q = 0; q < fi.fo.steps.size(); ++q) {
+          const bool last = q + 1 == fi.fo.steps.size();
+          const int sa = fi.fo.steps[q][0], sb = fi.fo.steps[q][1];
+          const int phase = 1 + std::max(slot_phase[sa], slot_phase[sb]);
+          FOp r;
+          r.dtype = e.out_dtype;
+          r.letters = fi.fo.letters[q];
+          void *dst = fi.outs[i];
+          if (!last) {
+            dst = (char *)b->fws + off;
+            double elems = 1.0;
+            for (int8_t c : r.letters) elems *= (double)e.len[c];
+            off += ((size_t)elems * dtype_size(e.out_dtype) + 255) / 256 * 256;
+          }
+          r.ptr = dst;
+          r.strides.assign(r.letters.size(), 1);
+          for (int d = (int)r.letters.size() - 2; d >= 0; --d) r.strides[d] = r.strides[d + 1] * e.len[r.letters[d + 1]];
+          GParams p;
+          int st = plan_factor_step(e, slot[sa], slot[sb], r.letters, dst, p, err);
+          if (st) return fail(st, "instance " + std::to_string(fi.k) + ", factored step: " + err);
+          st = add_row(p, phase, fi.k);
+          if (st) return st;
+          slot.push_back(r);
+          slot_phase.push_back(phase);
+        }
+      }
+    }
   }
-  std::vector<size_t> order(b->tiles.size());
-  for (size_t t = 0; t < order.size(); ++t) order[t] = t;
-  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t c2) { return cost[a] > cost[c2]; });
-  std::vector<PTile> sorted;
-  for (size_t t : order) sorted.push_back(b->tiles[t]);
-  b->tiles.swap(sorted);
-
+  // per phase, longest tiles first (cost = outputs x terms per output); ties
+  // by position; the phases' lists one after the other
+  b->phases = (int)ptiles.size();
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  b->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->tiles.size(), (int64_t)sms * per_sm));
+  for (auto &pt : ptiles) {
+    std::vector<double> cost(pt.size());
+    for (size_t t = 0; t < pt.size(); ++t) {
+      const GParams &p = b->rows[pt[t].row];
+      cost[t] = (double)pt[t].count * (double)std::max<int64_t>(1, p.total_con) * std::max(1, p.n_ops) *
+                (p.mode == 3 ? (double)p.gemm.tile * p.gemm.tile : 1.0);
+    }
+    std::vector<size_t> order(pt.size());
+    for (size_t t = 0; t < order.size(); ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a2, size_t c2) { return cost[a2] > cost[c2]; });
+    b->phase_off.push_back((int64_t)b->tiles.size());
+    b->phase_n.push_back((int64_t)pt.size());
+    b->phase_grid.push_back((int)std::max<int64_t>(1, std::min<int64_t>((int64_t)pt.size(), (int64_t)sms * per_sm)));
+    for (size_t t : order) b->tiles.push_back(pt[t]);
+  }
+  b->grid = *std::max_element(b->phase_grid.begin(), b->phase_grid.end());
   cudaError_t ce = cudaMalloc(&b->d_rows, sizeof(GParams) * std::max<size_t>(1, b->rows.size()));
   if (ce == cudaSuccess) ce = cudaMalloc(&b->d_tiles, sizeof(PTile) * std::max<size_t>(1, b->tiles.size()));
-  if (ce == cudaSuccess) ce = cudaMalloc(&b->d_counter, sizeof(unsigned long long));
+  if (ce == cudaSuccess) ce = cudaMalloc(&b->d_counter, sizeof(unsigned long long) * (size_t)b->phases);
   if (ce == cudaSuccess && !b->rows.empty())
     ce = cudaMemcpy(b->d_rows, b->rows.data(), sizeof(GParams) * b->rows.size(), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess && !b->tiles.empty())
@@ -1125,9 +1235,12 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
       }
       if (c1 == cudaSuccess) c1 = launch_dn(b->branch[1]);
     }
-    if (c1 == cudaSuccess) c1 = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), b->cap);
-    if (c1 == cudaSuccess)
-      c1 = launch_persistent(b->d_rows, b->d_tiles, (int64_t)b->tiles.size(), b->d_counter, b->grid, b->block, b->cap);
+    if (c1 == cudaSuccess) c1 = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long) * (size_t)b->phases, b->cap);
+    // one persistent launch per phase, in order on the capture stream (a
+    // factored step reads the intermediates of the phases before it)
+    for (int q = 0; q < b->phases && c1 == cudaSuccess; ++q)
+      c1 = launch_persistent(b->d_rows, b->d_tiles + b->phase_off[q], b->phase_n[q], b->d_counter + q, b->phase_grid[q],
+                             b->block, b->cap);
     if (side) {
       for (int q = 0; q < 2 && c1 == cudaSuccess; ++q) c1 = cudaEventRecord(b->ev[1 + q], b->branch[q]);
       for (int q = 0; q < 2 && c1 == cudaSuccess; ++q) c1 = cudaStreamWaitEvent(b->cap, b->ev[1 + q], 0);
@@ -1209,6 +1322,14 @@ int be_batch_kinds(const be_batch *b, int32_t *generic, int32_t *element, int32_
   if (generic) *generic = b->n_kind[0];
   if (element) *element = b->n_kind[1];
   if (dense) *dense = b->n_kind[2];
+  return BE_OK;
+}
+
+int be_batch_factored(const be_batch *b, int32_t *instances, int32_t *phases, int64_t *workspace_bytes) {
+  if (!b) return fail(BE_EARG, "NULL batch");
+  if (instances) *instances = b->n_factored;
+  if (phases) *phases = b->phases;
+  if (workspace_bytes) *workspace_bytes = (int64_t)b->fws_bytes;
   return BE_OK;
 }
 

@@ -780,4 +780,160 @@ int plan_dense(const Einsum &e, const std::vector<BufIn> &bufs, const std::vecto
   return OK;
 }
 
+
+// ------------------------------------------------------------ factored rows
+//
+// Eq. (1) sums the product of a row's n operands over the contracted
+// letters as one loop nest.  Summing some contracted letters inside a pair
+// of operands first (an intermediate over the letters still needed) gives
+// the same sum with the terms grouped differently -- each pairwise step is
+// itself a two-operand einsum -- and, for notations such as the triple
+// product 'ik,kl,lj->ij' or Fig. 1's 'mnj,mni,kli->ijkl', far fewer
+// multiply-adds than the full nest.  The order is chosen per notation and
+// lengths; every step runs on the generic evaluator (as GEMM tiles when
+// its form allows).
+
+namespace {
+
+double letters_volume(const Einsum &e, uint32_t mask) {
+  double v = 1.0;
+  for (int c = 0; c < 26; ++c)
+    if (mask >> c & 1u) v *= (double)e.len[c];
+  return v;
+}
+
+uint32_t mask_of(const std::vector<int8_t> &ls) {
+  uint32_t m = 0;
+  for (int8_t c : ls) m |= 1u << c;
+  return m;
+}
+
+// exhaustive search over pairwise orders: slots holds the letter masks of
+// the operands still to combine, path the steps taken so far
+void search_orders(const Einsum &e, uint32_t out_mask, std::vector<uint32_t> &slots, std::vector<int> &ids,
+                   int next_id, double cost, std::vector<std::array<int, 2>> &path, std::vector<uint32_t> &kept,
+                   double &best, std::vector<std::array<int, 2>> &best_path, std::vector<uint32_t> &best_kept) {
+  if (slots.size() == 1) {
+    if (cost < best) {
+      best = cost;
+      best_path = path;
+      best_kept = kept;
+    }
+    return;
+  }
+  for (size_t a = 0; a < slots.size(); ++a)
+    for (size_t b2 = a + 1; b2 < slots.size(); ++b2) {
+      uint32_t rest = out_mask;
+      for (size_t k = 0; k < slots.size(); ++k)
+        if (k != a && k != b2) rest |= slots[k];
+      const uint32_t both = slots[a] | slots[b2];
+      const double c = cost + letters_volume(e, both);
+      if (c >= best) continue;
+      const uint32_t keep = both & rest;
+      std::vector<uint32_t> ns;
+      std::vector<int> nid;
+      for (size_t k = 0; k < slots.size(); ++k)
+        if (k != a && k != b2) {
+          ns.push_back(slots[k]);
+          nid.push_back(ids[k]);
+        }
+      ns.push_back(keep);
+      nid.push_back(next_id);
+      path.push_back({ids[a], ids[b2]});
+      kept.push_back(keep);
+      search_orders(e, out_mask, ns, nid, next_id + 1, c, path, kept, best, best_path, best_kept);
+      path.pop_back();
+      kept.pop_back();
+    }
+}
+
+}  // namespace
+
+bool factor_order(const Einsum &e, double min_gain, FactorOrder &fo) {
+  if (e.n < 3 || e.n > 5) return false;
+  uint32_t all = mask_of(e.out);
+  std::vector<uint32_t> slots;
+  std::vector<int> ids;
+  for (int j = 0; j < e.n; ++j) {
+    slots.push_back(mask_of(e.in[j]));
+    ids.push_back(j);
+    all |= slots.back();
+  }
+  fo.direct = letters_volume(e, all) * (double)(e.n - 1);
+  double best = fo.direct / min_gain;
+  std::vector<std::array<int, 2>> path, best_path;
+  std::vector<uint32_t> kept, best_kept;
+  search_orders(e, mask_of(e.out), slots, ids, e.n, 0.0, path, kept, best, best_path, best_kept);
+  if (best_path.empty()) return false;
+  fo.factored = best;
+  fo.steps = best_path;
+  fo.letters.clear();
+  fo.inter_elems = 0;
+  for (size_t s = 0; s < best_kept.size(); ++s) {
+    std::vector<int8_t> ls;
+    if (s + 1 == best_kept.size()) {
+      ls = e.out;   // the last step writes the output, in its letter order
+    } else {
+      for (int c = 0; c < 26; ++c)
+        if (best_kept[s] >> c & 1u) ls.push_back((int8_t)c);
+      fo.inter_elems += (int64_t)letters_volume(e, best_kept[s]);
+    }
+    fo.letters.push_back(ls);
+  }
+  return true;
+}
+
+bool operand_fop(const Einsum &e, int row, int pos, const std::vector<BufIn> &bufs, FOp &f) {
+  View v;
+  if (!arg_view(e, e.rows[row][pos], pos, bufs, v)) return false;
+  // the view's coefficients by letter; a letter repeated within the operand
+  // (a diagonal) already carries the sum of its strides
+  f.ptr = v.ptr;
+  f.dtype = v.dtype;
+  f.letters.clear();
+  f.strides.clear();
+  bool seen[26] = {false};
+  for (int8_t c : e.in[pos]) {
+    if (seen[c]) continue;
+    seen[c] = true;
+    f.letters.push_back(c);
+    f.strides.push_back(v.coef[c]);
+  }
+  return true;
+}
+
+int plan_factor_step(const Einsum &e, const FOp &x, const FOp &y, const std::vector<int8_t> &out_letters, void *out,
+                     GParams &p, std::string &err) {
+  // the step as a batched einsum of one row and two identity arguments
+  Einsum s;
+  s.b = 1;
+  s.n = 2;
+  s.out = out_letters;
+  s.in = {x.letters, y.letters};
+  s.rows = {{0, 1}};
+  for (int c = 0; c < 26; ++c) s.len[c] = e.len[c];
+  for (int8_t c : x.letters) s.used[c] = true;
+  for (int8_t c : y.letters) s.used[c] = true;
+  for (int8_t c : out_letters) s.used[c] = true;
+  s.out_dtype = e.out_dtype;
+  const FOp *ops[2] = {&x, &y};
+  for (int k = 0; k < 2; ++k) {
+    Buffer bf;
+    bf.name = k ? "Y" : "X";
+    bf.dtype = ops[k]->dtype;
+    for (int8_t c : ops[k]->letters) bf.shape.push_back(e.len[c]);
+    s.buffers.push_back(bf);
+    Arg a;
+    a.name = bf.name;
+    a.dtype = bf.dtype;
+    a.shape = bf.shape;
+    a.buffer = k;
+    s.args.push_back(a);
+  }
+  std::vector<BufIn> bufs = {BufIn{const_cast<void *>(x.ptr), x.strides.data(), (int32_t)x.letters.size(), x.dtype},
+                             BufIn{const_cast<void *>(y.ptr), y.strides.data(), (int32_t)y.letters.size(), y.dtype}};
+  BufIn bo{out, nullptr, (int32_t)out_letters.size(), e.out_dtype};
+  return plan_generic_row(s, 0, bufs, bo, {}, p, err);
+}
+
 }  // namespace be

@@ -1,6 +1,7 @@
 // Planner interface: caller buffers, operand views and strategy planners.
 #pragma once
 
+#include <array>
 #include <string>
 #include <vector>
 
@@ -59,5 +60,39 @@ int plan_element(const Einsum &e, const std::vector<BufIn> &bufs, const std::vec
 // or nullptr when only the form is checked
 int plan_dense(const Einsum &e, const std::vector<BufIn> &bufs, const std::vector<BufIn> &outs, DensePlan &p,
                std::string &why, const std::vector<double> *scalars = nullptr);
+
+// ---- factored evaluation (a row as a sequence of two-operand einsums)
+
+// One operand of a pairwise step: a strided view (pointer, dtype, the index
+// letter of each dimension and its stride in elements).
+struct FOp {
+  const void *ptr = nullptr;
+  int dtype = F64;
+  std::vector<int8_t> letters;
+  std::vector<int64_t> strides;
+};
+
+// Pairwise order of a row's n operands: step s combines slots steps[s][0]
+// and steps[s][1] (slots 0..n-1 are the operands, slot n + s the result of
+// step s) into a dense row-major intermediate over letters[s]; the last
+// step's letters are the output's.  Costs count multiply-adds of one row.
+struct FactorOrder {
+  std::vector<std::array<int, 2>> steps;
+  std::vector<std::vector<int8_t>> letters;
+  double direct = 0, factored = 0;
+  int64_t inter_elems = 0;      // elements of one row's intermediates
+};
+
+// The order with the fewest multiply-adds over all pairwise orders (n <= 5);
+// false unless e has 3 to 5 operands and the order cuts the loop nest's
+// multiply-adds at least `min_gain` times.
+bool factor_order(const Einsum &e, double min_gain, FactorOrder &fo);
+// operand pos of row `row` as a view; false for a functional argument other
+// than a single buffer reference
+bool operand_fop(const Einsum &e, int row, int pos, const std::vector<BufIn> &bufs, FOp &f);
+// one pairwise step as a generic row writing `out` (dense row-major over
+// out_letters); out_dtype is the einsum's
+int plan_factor_step(const Einsum &e, const FOp &x, const FOp &y, const std::vector<int8_t> &out_letters, void *out,
+                     GParams &p, std::string &err);
 
 }  // namespace be

@@ -1,8 +1,11 @@
 """Persistent multi-instance executor (be_batch_*) on the GPU.
 
-Every output has one owner and a fixed evaluation order, so the batch must
-reproduce BE_STRAT_GENERIC on each instance alone bit for bit; a sample is
-also checked against the FP64 oracle with the tolerances of test_gpu_parity.
+Every output has one owner and a fixed evaluation order, so with factoring
+off (stage_mask bit 1) the batch must reproduce BE_STRAT_GENERIC on each
+instance alone bit for bit; a sample is also checked against the FP64
+oracle with the tolerances of test_gpu_parity.  Factored instances (the
+same sum as a sequence of two-operand einsums) are checked against the
+oracle and for bitwise-identical replays.
 """
 import math
 
@@ -18,6 +21,7 @@ from oracle import evaluate as ev  # noqa: E402
 import workloads as W  # noqa: E402
 
 DEV = "cuda:0"
+NO_FACTOR = be.make_config(stage_mask=2)       # every generic instance on its loop nest
 
 
 def make_items(n, seed, **caps):
@@ -56,7 +60,7 @@ def test_batch_bitwise_equals_generic_and_oracle():
     match be_execute's default (the same kernel) bit for bit."""
     items, meta = make_items(40, 7, lo_exp=1.0, hi_exp=5.0, max_operand=1 << 16, max_flops=1 << 22)
     ctx = be.Context(None, device=0)
-    b = be.Batch(ctx, items)
+    b = be.Batch(ctx, items, NO_FACTOR)
     kinds = b.kinds()
     n_el = sum(1 for e, _, _ in items if be.plan_strategy(ctx, e) == be.STRAT_ELEMENT)
     assert kinds["element"] == n_el and kinds["dense"] == 0 and kinds["generic"] == len(items) - n_el
@@ -84,7 +88,7 @@ def test_batch_bitwise_equals_generic_and_oracle():
 
 def test_batch_replay_sees_new_contents():
     items, meta = make_items(10, 9, lo_exp=1.0, hi_exp=4.0, max_operand=1 << 14, max_flops=1 << 20)
-    b = be.Batch(None, items, be.make_config(tile=(128, 12, 2)))
+    b = be.Batch(None, items, be.make_config(tile=(128, 12, 2), stage_mask=2))
     b.run()
     torch.cuda.synchronize()
     first = [[o.clone() for o in outs] for _, _, outs in items]
@@ -161,7 +165,7 @@ def test_gemm_tiles_same_bits_at_any_tile_side(dt):
                 "B": torch.from_numpy(g.standard_normal(sb)).to(tdt).to(DEV)}
         items.append((e, bufs, [torch.full(e.out_shape, float("nan"), dtype=tdt, device=DEV)]))
     ctx = be.Context(None, device=0)
-    be.Batch(ctx, items).run()
+    be.Batch(ctx, items, NO_FACTOR).run()
     torch.cuda.synchronize()
     for e, bufs, outs in items:
         alone = generic_alone(e, bufs)
@@ -212,7 +216,7 @@ def test_mixed_kind_batch():
         meta.append((m[1], m[2]))
         kind.append("generic")
     ctx = be.Context(None, device=0)
-    batch = be.Batch(ctx, items, be.make_config(split=1))
+    batch = be.Batch(ctx, items, be.make_config(split=1, stage_mask=2))
     k = batch.kinds()
     assert k == {"generic": kind.count("generic"), "element": 2, "dense": 2}
     batch.run()
@@ -257,3 +261,77 @@ def test_tune_batch_records_under_batch_key(tmp_path):
     # resume: a fresh context reading the same file finds the record
     ctx2 = be.Context(str(tmp_path / "db.txt"), device=0)
     assert be.Batch(ctx2, items).info() == ref.info()
+
+
+FACTOR_SPECS = [
+    # (spec without declarations, shapes per buffer, dtype, factored?)
+    ("ik,kl,lj->ij | A,B,C | A,D,C", {"A": (40, 50), "B": (50, 60), "C": (60, 30), "D": (50, 60)}, True),
+    ("mnj,mni,kli->ijkl | A,B,C", {"A": (9, 11, 7), "B": (9, 11, 6), "C": (5, 4, 6)}, True),
+    ("ij,kl,jl->ik | A,B,C", {"A": (30, 40), "B": (20, 50), "C": (40, 50)}, True),
+    ("xre,rij,xej->ei | F,D,U", {"F": (3, 3, 200), "D": (3, 20, 20), "U": (3, 200, 20)}, True),
+    ("ab,bc,cd,de->ae | P,Q,R,T", {"P": (16, 24), "Q": (24, 32), "R": (32, 20), "T": (20, 12)}, True),
+    ("iij,jk,kl->il | A,B,C", {"A": (12, 12, 30), "B": (30, 25), "C": (25, 14)}, True),
+    ("ijk,ik,ij,ij->i | A,B,C,D", {"A": (6, 7, 8), "B": (6, 8), "C": (6, 7), "D": (6, 7)}, False),
+]
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_factored_instances_match_the_oracle(dt):
+    """Instances whose best pairwise order cuts the loop nest's multiply-adds
+    at least 4 times run as two-operand steps over intermediates, in phases
+    (the 4-operand chain needs 2 or 3 launches): every output within the
+    precision's tolerance of the FP64 oracle (1e-12 S; FP32 max(gamma_K,
+    1e-6) S), replays bitwise identical, and the same batch with factoring
+    off still equals the generic strategy alone bit for bit."""
+    g = np.random.default_rng(41)
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    items, meta = [], []
+    for spec, shapes, _ in FACTOR_SPECS:
+        decl = " ; ".join(f"{k}:{dt}[{','.join(map(str, v))}]" for k, v in shapes.items())
+        text = f"{spec} ; {decl}"
+        arrs = {k: g.standard_normal(v).astype(np.float32 if dt == "f32" else np.float64) for k, v in shapes.items()}
+        e = be.Einsum(text)
+        bufs = {k: torch.from_numpy(v).to(DEV) for k, v in arrs.items()}
+        outs = [torch.full(e.out_shape, float("nan"), dtype=tdt, device=DEV) for _ in range(e.b)]
+        items.append((e, bufs, outs))
+        meta.append((text, arrs))
+    b = be.Batch(None, items)
+    f = b.factored()
+    # the divergence form is element-shaped in FP64 and takes that strategy
+    assert f["instances"] == sum(1 for s, (e, _, _) in zip(FACTOR_SPECS, items)
+                                 if s[2] and be.plan_strategy(None, e) != be.STRAT_ELEMENT)
+    assert f["phases"] >= 3 and f["workspace_bytes"] > 0
+    b.run()
+    torch.cuda.synchronize()
+    first = [[o.clone() for o in outs] for _, _, outs in items]
+    b.run()
+    torch.cuda.synchronize()
+    for (e, bufs, outs), fst, (text, arrs) in zip(items, first, meta):
+        for o, a in zip(outs, fst):
+            assert torch.equal(o, a)
+        ref = ev.evaluate(text, arrs)
+        tol = 1e-12
+        if dt == "f32":
+            # gamma_K of the whole contraction: K = contracted terms + operands
+            notation, row0 = text.split("|")[0], text.split("|")[1].split(";")[0]
+            lhs, out = notation.strip().split("->")
+            lens = {}
+            for letters, name in zip(lhs.split(","), row0.strip().split(",")):
+                lens.update(zip(letters, arrs[name.strip()].shape))
+            K = math.prod(v for c, v in lens.items() if c not in out) + len(lhs.split(","))
+            tol = max(K * 2.0 ** -24 / (1 - K * 2.0 ** -24), 1e-6)
+        for k, (r, S) in enumerate(ref):
+            got = outs[k].cpu().numpy().astype(np.float64)
+            assert np.all(np.abs(got - r) <= tol * S), text[:40]
+    off = be.Batch(None, items, NO_FACTOR)
+    assert off.factored()["instances"] == 0 and off.factored()["phases"] == 1
+    off.run()
+    torch.cuda.synchronize()
+    for e, bufs, outs in items:
+        if be.plan_strategy(None, e) == be.STRAT_ELEMENT:
+            alone = default_alone(None, e, bufs)
+        else:
+            alone = generic_alone(e, bufs)
+        torch.cuda.synchronize()
+        for o, a in zip(outs, alone):
+            assert torch.equal(o, a)
