@@ -221,6 +221,26 @@ __device__ __forceinline__ void prefetch_rows(const EView &v, int64_t e1, int te
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(b - a)) : "memory");
 }
 
+// L2 prefetch of the geometric factors g_k[e, r] of elements e1 .. e1+te1-1
+// (every row k, every r) when they span at most 64 KB (for the gradient's
+// G[e, r, x] the 128 elements' 9 values are one contiguous 9 KB range)
+__device__ __forceinline__ void prefetch_g(const EParams &p, int64_t e1, int te1) {
+  if (te1 <= 0) return;
+  uintptr_t lo = ~(uintptr_t)0, hi = 0;
+  for (int k = 0; k < p.n_rows; ++k) {
+    const EView &g = p.rows[k].g;
+    for (int r = 0; r < p.R; r += max(1, p.R - 1))
+      for (int64_t e : {e1, e1 + te1 - 1}) {
+        const uintptr_t a = (uintptr_t)(g.ptr + e * g.se + r * g.sk);
+        lo = min(lo, a);
+        hi = max(hi, a + 8);
+      }
+  }
+  const uintptr_t a = (lo + 15) & ~(uintptr_t)15, b = hi & ~(uintptr_t)15;
+  if (b <= a || b - a > 65536) return;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(b - a)) : "memory");
+}
+
 // six balanced base-512 digits of x * 2^-k (|x| < 2^k), each times 2^-9q,
 // by integer arithmetic on the bits of x: X = round(x * 2^(53 - k)) is split
 // from the bottom, d = ((X + 256) mod 512) - 256, X = (X - d) / 512.  A value
@@ -512,6 +532,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
         const int te1 = (int)(p.E - e1 < TC_M ? p.E - e1 : TC_M);
         prefetch_rows(q.a, e1, te1, NJ);
         if (q.kind != 0) prefetch_rows(q.b, e1, te1, NJ);
+        if (p.has_g) prefetch_g(p, e1, te1);
       }
       if (tid < TC_M) mxw[tid] = 0;
       prod_sync();
