@@ -867,6 +867,8 @@ static void tune_candidates(const Einsum &e, const std::vector<BufIn> &bi, const
 
 // largest workspace of a batch's factored intermediates (bytes)
 static constexpr double FACTOR_WS_MAX = 4.0 * (1ull << 30);
+// concurrent graph branches of a batch's dense instances
+static constexpr int NDN = 4;
 
 struct be_batch {
   be_ctx *x = nullptr;
@@ -875,8 +877,11 @@ struct be_batch {
   GParams *d_rows = nullptr;
   PTile *d_tiles = nullptr;
   unsigned long long *d_counter = nullptr;
-  cudaStream_t cap = nullptr, branch[2] = {nullptr, nullptr};
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  // branch 0 runs the element instances, branches 1..NDN the dense ones
+  // (round robin, each with its own split workspace)
+  cudaStream_t cap = nullptr, branch[1 + NDN] = {};
+  cudaEvent_t ev[2 + NDN] = {};
+  size_t ws_stride = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int grid = 0, block = 256;
@@ -1166,7 +1171,8 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
     ce = cudaMemcpy(b->d_rows, b->rows.data(), sizeof(GParams) * b->rows.size(), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess && !b->tiles.empty())
     ce = cudaMemcpy(b->d_tiles, b->tiles.data(), sizeof(PTile) * b->tiles.size(), cudaMemcpyHostToDevice);
-  if (ce == cudaSuccess && ws_need) ce = cudaMalloc(&b->ws, ws_need);
+  b->ws_stride = (ws_need + 255) / 256 * 256;
+  if (ce == cudaSuccess && ws_need) ce = cudaMalloc(&b->ws, b->ws_stride * (size_t)NDN);
   if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("batch setup: ") + cudaGetErrorString(ce));
   if (!el_inst.empty() || !dn_inst.empty()) {
     if (x) {
@@ -1182,8 +1188,8 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
     }
   }
   if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-  for (int q = 0; q < 2 && ce == cudaSuccess; ++q) ce = cudaStreamCreateWithFlags(&b->branch[q], cudaStreamNonBlocking);
-  for (int q = 0; q < 3 && ce == cudaSuccess; ++q) ce = cudaEventCreateWithFlags(&b->ev[q], cudaEventDisableTiming);
+  for (int q = 0; q < 1 + NDN && ce == cudaSuccess; ++q) ce = cudaStreamCreateWithFlags(&b->branch[q], cudaStreamNonBlocking);
+  for (int q = 0; q < 2 + NDN && ce == cudaSuccess; ++q) ce = cudaEventCreateWithFlags(&b->ev[q], cudaEventDisableTiming);
   if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("batch setup: ") + cudaGetErrorString(ce));
   const bool timing = x && x->timing;
   if (x) x->timing = false;   // no timing events inside the captured graph
@@ -1202,17 +1208,18 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
     }
     return BE_OK;
   };
-  auto launch_dn = [&](cudaStream_t st) -> cudaError_t {
+  auto launch_dn = [&](int br, cudaStream_t st) -> cudaError_t {
     be_config_t cd;
     std::memset(&cd, 0, sizeof(cd));
-    for (size_t q = 0; q < dn_inst.size(); ++q) {
-      cudaError_t r = run_dense_rows(nullptr, dn_plan[q], cd, b->ws, b->status, wl, st);
+    for (size_t q = br; q < dn_inst.size(); q += NDN) {
+      cudaError_t r = run_dense_rows(nullptr, dn_plan[q], cd, (char *)b->ws + b->ws_stride * br, b->status, wl, st);
       if (r != cudaSuccess) return r;
     }
     return cudaSuccess;
   };
   int est = launch_el(b->branch[0]);
-  if (!est && (ce = launch_dn(b->branch[1])) == cudaSuccess) ce = cudaDeviceSynchronize();
+  for (int q = 0; !est && q < NDN && ce == cudaSuccess; ++q) ce = launch_dn(q, b->branch[1 + q]);
+  if (!est && ce == cudaSuccess) ce = cudaDeviceSynchronize();
   if (est || ce != cudaSuccess) {
     if (x) x->timing = timing;
     return est ? est : fail(BE_ECUDA, std::string("batch first launch: ") + cudaGetErrorString(ce));
@@ -1228,12 +1235,12 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
     const bool side = !el_inst.empty() || !dn_inst.empty();
     if (side) {
       c1 = cudaEventRecord(b->ev[0], b->cap);
-      for (int q = 0; q < 2 && c1 == cudaSuccess; ++q) c1 = cudaStreamWaitEvent(b->branch[q], b->ev[0], 0);
+      for (int q = 0; q < 1 + NDN && c1 == cudaSuccess; ++q) c1 = cudaStreamWaitEvent(b->branch[q], b->ev[0], 0);
       if (c1 == cudaSuccess) {
         est = launch_el(b->branch[0]);
         if (est) c1 = cudaErrorUnknown;
       }
-      if (c1 == cudaSuccess) c1 = launch_dn(b->branch[1]);
+      for (int q = 0; q < NDN && c1 == cudaSuccess; ++q) c1 = launch_dn(q, b->branch[1 + q]);
     }
     if (c1 == cudaSuccess) c1 = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long) * (size_t)b->phases, b->cap);
     // one persistent launch per phase, in order on the capture stream (a
@@ -1242,8 +1249,8 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
       c1 = launch_persistent(b->d_rows, b->d_tiles + b->phase_off[q], b->phase_n[q], b->d_counter + q, b->phase_grid[q],
                              b->block, b->cap);
     if (side) {
-      for (int q = 0; q < 2 && c1 == cudaSuccess; ++q) c1 = cudaEventRecord(b->ev[1 + q], b->branch[q]);
-      for (int q = 0; q < 2 && c1 == cudaSuccess; ++q) c1 = cudaStreamWaitEvent(b->cap, b->ev[1 + q], 0);
+      for (int q = 0; q < 1 + NDN && c1 == cudaSuccess; ++q) c1 = cudaEventRecord(b->ev[1 + q], b->branch[q]);
+      for (int q = 0; q < 1 + NDN && c1 == cudaSuccess; ++q) c1 = cudaStreamWaitEvent(b->cap, b->ev[1 + q], 0);
     }
     ce = cudaStreamEndCapture(b->cap, &b->graph);
     if (c1 != cudaSuccess) ce = c1;
