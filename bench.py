@@ -1093,7 +1093,7 @@ def main():
     ap.add_argument("--serve-templates", type=int, default=256)
     ap.add_argument("--serve-streams", type=int, default=8)
     ap.add_argument("--mix-n", type=int, default=512)
-    ap.add_argument("--mix-split-log2", type=int, default=24,
+    ap.add_argument("--mix-split-log2", type=int, default=20,
                     help="FP64 GEMM-form mix instances of at least 2^this multiply-adds take the split path")
     ap.add_argument("--mix-no-split", action="store_true",
                     help="keep FP64 GEMM-form mix instances on the FP64 generic path")

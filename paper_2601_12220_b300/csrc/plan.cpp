@@ -729,24 +729,27 @@ int plan_dense(const Einsum &e, const std::vector<BufIn> &bufs, const std::vecto
     }
   }
   for (int8_t c : e.out) is_out[c] = true;
-  // output = M letters (from operand 0) then N letters (from operand 1)
-  std::vector<int8_t> Ml, Nl, Kl;
-  for (int8_t c : e.out) {
+  // output = M letters (from the A operand) then N letters (from the B
+  // operand); A is operand 0 when the output starts with operand 0's free
+  // letters, else operand 1 (C = A B either way, with the roles swapped)
+  for (int8_t c : e.out)
     if (in0[c] && in1[c]) { why = "batch index shared by both operands and the output"; return EUNSUPPORTED; }
-    (in0[c] ? Ml : Nl).push_back(c);
-  }
+  const int opA = (!e.out.empty() && !in0[e.out[0]]) ? 1 : 0, opB = 1 - opA;
+  const bool *inA = opA ? in1 : in0, *inB = opA ? in0 : in1;
+  std::vector<int8_t> Ml, Nl, Kl;
+  for (int8_t c : e.out) (inA[c] ? Ml : Nl).push_back(c);
   for (size_t k = 0; k < e.out.size(); ++k)
     if (k < Ml.size() ? e.out[k] != Ml[k] : e.out[k] != Nl[k - Ml.size()]) {
-      why = "output letters are not (free letters of operand 1, free letters of operand 2)";
+      why = "output letters are not (free letters of one operand, free letters of the other)";
       return EUNSUPPORTED;
     }
-  for (int8_t c : e.in[0])
+  for (int8_t c : e.in[opA])
     if (!is_out[c]) {
-      if (!in1[c]) { why = "index summed inside one operand"; return EUNSUPPORTED; }
+      if (!inB[c]) { why = "index summed inside one operand"; return EUNSUPPORTED; }
       Kl.push_back(c);
     }
-  for (int8_t c : e.in[1])
-    if (!is_out[c] && !in0[c]) { why = "index summed inside one operand"; return EUNSUPPORTED; }
+  for (int8_t c : e.in[opB])
+    if (!is_out[c] && !inA[c]) { why = "index summed inside one operand"; return EUNSUPPORTED; }
   p.M = 1;
   for (auto c : Ml) p.M *= e.len[c];
   p.N = 1;
@@ -757,13 +760,13 @@ int plan_dense(const Einsum &e, const std::vector<BufIn> &bufs, const std::vecto
   for (int i = 0; i < e.b; ++i) {
     View va, vb;
     DenseRow r;
-    if (!dense_operand(e, e.rows[i][0], 0, bufs, scalars, va, r.alA, r.beA) ||
-        !dense_operand(e, e.rows[i][1], 1, bufs, scalars, vb, r.alB, r.beB)) {
+    if (!dense_operand(e, e.rows[i][opA], opA, bufs, scalars, va, r.alA, r.beA) ||
+        !dense_operand(e, e.rows[i][opB], opB, bufs, scalars, vb, r.alB, r.beB)) {
       why = "dense operands must be views or affine producers of one view";
       return EUNSUPPORTED;
     }
-    r.argA = e.rows[i][0];
-    r.argB = e.rows[i][1];
+    r.argA = e.rows[i][opA];
+    r.argB = e.rows[i][opB];
     r.A = (const double *)va.ptr;
     r.B = (const double *)vb.ptr;
     r.lda = flat_stride(e, va, Ml);

@@ -91,10 +91,22 @@ def test_chem_reduced(ctx):
         assert rel_err(got[k], ref[k][0], ref[k][1]).max() <= 1e-6
 
 
-def test_transposed_output_rejected_then_generic(ctx):
-    """'kj,ik->ij' puts the free letters of the second operand first: not a
-    plain GEMM layout; AUTO falls back to the generic kernel."""
-    e = be.Einsum("kj,ik->ij | B,A ; A:f64[30,20] ; B:f64[20,40]")
+def test_swapped_operand_roles(ctx):
+    """'kj,ik->ij' puts the free letters of the second operand first: the
+    plan takes the second operand as A and the first as B (C = A B with the
+    roles swapped); within 1e-6 S of the oracle."""
+    g = np.random.default_rng(9)
+    A, B = g.standard_normal((30, 20)), g.standard_normal((20, 40))
+    text = "kj,ik->ij | B,A ; A:f64[30,20] ; B:f64[20,40]"
+    got, = run_split(ctx, text, dict(A=A, B=B))
+    (ref, S), = ev.evaluate(text, dict(A=A, B=B))
+    assert rel_err(got, ref, S).max() <= 1e-6
+
+
+def test_interleaved_output_rejected_then_generic(ctx):
+    """'abk,kc->acb' interleaves the two operands' free letters in the output:
+    not a plain GEMM layout; AUTO falls back to the generic kernel."""
+    e = be.Einsum("abk,kc->acb | A,B ; A:f64[6,5,20] ; B:f64[20,7]")
     assert be.plan_strategy(ctx, e, precision=be.PREC_SPLIT) == be.STRAT_GENERIC
     with pytest.raises(be.BEError) as ex:
         be.plan_strategy(ctx, e, be.make_config(be.STRAT_DENSE_SPLIT), precision=be.PREC_SPLIT)
