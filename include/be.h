@@ -331,13 +331,14 @@ int be_tune(be_ctx *x, const be_einsum *e, int32_t precision, const be_buf *bufs
  *   contractions) cuts the multiply-adds of Eq. (1)'s loop nest at least 4
  *   times is factored: each row runs as that sequence of two-operand
  *   einsums over dense intermediates (the same sum with its terms grouped
- *   differently), the steps in phases by dependency, one persistent launch
- *   per phase, the intermediates in a workspace owned by the batch
+ *   differently); a step's tiles follow the tiles of the steps it reads in
+ *   the one persistent launch and wait (bounded) until those have finished,
+ *   the intermediates in a workspace owned by the batch
  *   (cfg->stage_mask bit 1 keeps every instance on its loop nest).  cfg may
  *   be NULL.  Everything is captured once in a CUDA
- *   graph with three concurrent branches: the persistent launches of
- *   generic tiles, the element launches and the split / GEMM launches
- *   (which use a split workspace owned by the batch).  The element and dense launches
+ *   graph with concurrent branches: the persistent launch of generic
+ *   tiles, the element launches and the split / GEMM launches (four
+ *   branches, each with a split workspace owned by the batch).  The element and dense launches
  *   run once during creation.  The buffers are borrowed and must stay valid
  *   while the batch is used; their CONTENTS may change between runs.
  *   Device memory for descriptors, tiles and the workspace is allocated
@@ -351,8 +352,9 @@ int be_tune(be_ctx *x, const be_einsum *e, int32_t precision, const be_buf *bufs
  * be_batch_info -- rows, tiles and total operand terms of the generic part
  *   (factored steps counted as rows).
  * be_batch_kinds -- number of instances given each strategy.
- * be_batch_factored -- number of factored instances, persistent launches
- *   (phases) per run, and bytes of the intermediates' workspace.
+ * be_batch_factored -- number of factored instances, the longest chain of
+ *   dependent steps (phases; 1 without factored instances), and bytes of
+ *   the intermediates' workspace.
  */
 int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_buf *const *bufs,
                     const int32_t *n_bufs, const be_buf *const *outs, const int32_t *n_outs,

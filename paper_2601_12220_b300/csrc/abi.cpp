@@ -892,12 +892,11 @@ struct be_batch {
   void *ws = nullptr;
   int *status = nullptr;
   bool own_status = false;
-  // factored instances: their pairwise steps run in dependency phases, one
-  // persistent launch per phase (tiles of phase q at phase_off[q]), with the
-  // intermediates in a workspace owned by the batch
+  // factored instances: their pairwise steps, ordered by dependency depth
+  // (phases) in the one tile list, with the intermediates in a workspace
+  // owned by the batch
   int phases = 1;
-  std::vector<int64_t> phase_off, phase_n;
-  std::vector<int> phase_grid;
+  unsigned int *d_done = nullptr;   // finished tiles per row (factored batches)
   int32_t n_factored = 0;
   void *fws = nullptr;
   size_t fws_bytes = 0;
@@ -912,6 +911,7 @@ struct be_batch {
     if (d_rows) cudaFree(d_rows);
     if (d_tiles) cudaFree(d_tiles);
     if (d_counter) cudaFree(d_counter);
+    if (d_done) cudaFree(d_done);
     if (ws) cudaFree(ws);
     if (fws) cudaFree(fws);
     if (own_status && status) cudaFree(status);
@@ -991,33 +991,55 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
     std::vector<void *> outs;            // per row, the output
   };
   std::vector<FacInst> fac_inst;
-  // a generic row (or a factored step) into the tile list of its phase:
-  // outputs per tile so that each tile costs about cost_target operand terms
-  std::vector<std::vector<PTile>> ptiles(1);
-  auto add_row = [&](const GParams &p, int phase, int k) -> int {
+  // a generic row (or a factored step) into the tile list of its group
+  // (group 0: the factored steps without dependencies, 1: the unfactored
+  // rows, q + 1: the factored steps of dependency depth q >= 1); outputs
+  // per tile so that each tile costs about cost_target operand terms.  deps
+  // are rows whose tiles must all finish first (-1: none); *row_out gets
+  // the new row, or -1 for a row without outputs
+  std::vector<std::vector<PTile>> ptiles(2);
+  std::vector<int> row_tiles;
+  auto add_row = [&](const GParams &p, int group, int k, const int deps[2], int *row_out) -> int {
+    *row_out = -1;
     if (p.total_out == 0) return BE_OK;
     if (p.mode == 3 && b->block != 256)
       return fail(BE_EARG, "instance " + std::to_string(k) + ": rows evaluated as GEMM tiles need a block of 256 threads");
-    if ((int)ptiles.size() <= phase) ptiles.resize(phase + 1);
-    std::vector<PTile> &pt = ptiles[phase];
+    if ((int)ptiles.size() <= group) ptiles.resize(group + 1);
+    std::vector<PTile> &pt = ptiles[group];
     const int row = (int)b->rows.size();
     b->rows.push_back(p);
+    row_tiles.push_back(0);
+    *row_out = row;
+    PTile base{row, 0, 0, 0, {-1, -1}, {0, 0}};
+    for (int q = 0; q < 2; ++q)
+      if (deps[q] >= 0) {
+        base.dep[q] = deps[q];
+        base.need[q] = row_tiles[deps[q]];
+      }
     const double per_out = (double)std::max<int64_t>(1, p.total_con) * std::max(1, p.n_ops);
     b->terms += per_out * (double)p.total_out;
+    int64_t tile, units;
     if (p.mode == 3) {   // units are GEMM tiles of tile x tile outputs
       const double per_tile = per_out * p.gemm.tile * p.gemm.tile;
-      const int64_t tile = std::max<int64_t>(1, std::min<int64_t>((int64_t)(cost_target / per_tile), 65536));
-      for (int64_t s0 = 0; s0 < p.gemm.tiles; s0 += tile) pt.push_back(PTile{row, 0, s0, std::min(tile, p.gemm.tiles - s0)});
-      return BE_OK;
-    }
-    int64_t tile = (int64_t)(cost_target / per_out);
-    if (p.mode == 0) {
-      tile = std::max<int64_t>(32, std::min<int64_t>(tile, 65536));
-      tile = (tile + 31) / 32 * 32;
+      tile = std::max<int64_t>(1, std::min<int64_t>((int64_t)(cost_target / per_tile), 65536));
+      units = p.gemm.tiles;
     } else {
-      tile = std::max<int64_t>(1, std::min<int64_t>(tile, 65536));
+      tile = (int64_t)(cost_target / per_out);
+      if (p.mode == 0) {
+        tile = std::max<int64_t>(32, std::min<int64_t>(tile, 65536));
+        tile = (tile + 31) / 32 * 32;
+      } else {
+        tile = std::max<int64_t>(1, std::min<int64_t>(tile, 65536));
+      }
+      units = p.total_out;
     }
-    for (int64_t s0 = 0; s0 < p.total_out; s0 += tile) pt.push_back(PTile{row, 0, s0, std::min(tile, p.total_out - s0)});
+    for (int64_t s0 = 0; s0 < units; s0 += tile) {
+      PTile t = base;
+      t.start = s0;
+      t.count = std::min(tile, units - s0);
+      pt.push_back(t);
+      ++row_tiles[row];
+    }
     return BE_OK;
   };
   for (int k = 0; k < n; ++k) {
@@ -1085,7 +1107,9 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
       GParams p;
       st = plan_generic_row(e, i, bi, bo[i], sc, p, err);
       if (st) return fail(st, "instance " + std::to_string(k) + ": " + err);
-      st = add_row(p, 0, k);
+      const int none[2] = {-1, -1};
+      int row;
+      st = add_row(p, 1, k, none, &row);
       if (st) return st;
     }
   }
@@ -1113,7 +1137,7 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
       const int n = e.n;
       for (int i = 0; i < e.b; ++i) {
         std::vector<FOp> slot = fi.ops[i];
-        std::vector<int> slot_phase(n, -1);
+        std::vector<int> slot_phase(n, -1), slot_row(n, -1);
         for (size_t q = 0; q < fi.fo.steps.size(); ++q) {
           const bool last = q + 1 == fi.fo.steps.size();
           const int sa = fi.fo.steps[q][0], sb = fi.fo.steps[q][1];
@@ -1134,17 +1158,21 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
           GParams p;
           int st = plan_factor_step(e, slot[sa], slot[sb], r.letters, dst, p, err);
           if (st) return fail(st, "instance " + std::to_string(fi.k) + ", factored step: " + err);
-          st = add_row(p, phase, fi.k);
+          const int deps[2] = {slot_row[sa], slot_row[sb]};
+          int row;
+          st = add_row(p, phase == 0 ? 0 : phase + 1, fi.k, deps, &row);
           if (st) return st;
+          b->phases = std::max(b->phases, phase + 1);
           slot.push_back(r);
           slot_phase.push_back(phase);
+          slot_row.push_back(row);
         }
       }
     }
   }
-  // per phase, longest tiles first (cost = outputs x terms per output); ties
-  // by position; the phases' lists one after the other
-  b->phases = (int)ptiles.size();
+  // within each group, longest tiles first (cost = outputs x terms per
+  // output; ties by position); the groups one after the other, so that
+  // every tile comes after the tiles it depends on
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1158,15 +1186,13 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
     std::vector<size_t> order(pt.size());
     for (size_t t = 0; t < order.size(); ++t) order[t] = t;
     std::stable_sort(order.begin(), order.end(), [&](size_t a2, size_t c2) { return cost[a2] > cost[c2]; });
-    b->phase_off.push_back((int64_t)b->tiles.size());
-    b->phase_n.push_back((int64_t)pt.size());
-    b->phase_grid.push_back((int)std::max<int64_t>(1, std::min<int64_t>((int64_t)pt.size(), (int64_t)sms * per_sm)));
     for (size_t t : order) b->tiles.push_back(pt[t]);
   }
-  b->grid = *std::max_element(b->phase_grid.begin(), b->phase_grid.end());
+  b->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->tiles.size(), (int64_t)sms * per_sm));
   cudaError_t ce = cudaMalloc(&b->d_rows, sizeof(GParams) * std::max<size_t>(1, b->rows.size()));
   if (ce == cudaSuccess) ce = cudaMalloc(&b->d_tiles, sizeof(PTile) * std::max<size_t>(1, b->tiles.size()));
-  if (ce == cudaSuccess) ce = cudaMalloc(&b->d_counter, sizeof(unsigned long long) * (size_t)b->phases);
+  if (ce == cudaSuccess) ce = cudaMalloc(&b->d_counter, sizeof(unsigned long long));
+  if (ce == cudaSuccess && b->n_factored) ce = cudaMalloc(&b->d_done, sizeof(unsigned int) * std::max<size_t>(1, b->rows.size()));
   if (ce == cudaSuccess && !b->rows.empty())
     ce = cudaMemcpy(b->d_rows, b->rows.data(), sizeof(GParams) * b->rows.size(), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess && !b->tiles.empty())
@@ -1174,7 +1200,7 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
   b->ws_stride = (ws_need + 255) / 256 * 256;
   if (ce == cudaSuccess && ws_need) ce = cudaMalloc(&b->ws, b->ws_stride * (size_t)NDN);
   if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("batch setup: ") + cudaGetErrorString(ce));
-  if (!el_inst.empty() || !dn_inst.empty()) {
+  if (!el_inst.empty() || !dn_inst.empty() || b->n_factored) {
     if (x) {
       std::lock_guard<std::mutex> g(x->mu);
       int st = ensure_status(x);
@@ -1242,12 +1268,13 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
       }
       for (int q = 0; q < NDN && c1 == cudaSuccess; ++q) c1 = launch_dn(q, b->branch[1 + q]);
     }
-    if (c1 == cudaSuccess) c1 = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long) * (size_t)b->phases, b->cap);
-    // one persistent launch per phase, in order on the capture stream (a
-    // factored step reads the intermediates of the phases before it)
-    for (int q = 0; q < b->phases && c1 == cudaSuccess; ++q)
-      c1 = launch_persistent(b->d_rows, b->d_tiles + b->phase_off[q], b->phase_n[q], b->d_counter + q, b->phase_grid[q],
-                             b->block, b->cap);
+    if (c1 == cudaSuccess) c1 = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), b->cap);
+    if (c1 == cudaSuccess && b->d_done)
+      c1 = cudaMemsetAsync(b->d_done, 0, sizeof(unsigned int) * b->rows.size(), b->cap);
+    // one persistent launch; factored steps wait in it for the steps they read
+    if (c1 == cudaSuccess)
+      c1 = launch_persistent(b->d_rows, b->d_tiles, (int64_t)b->tiles.size(), b->d_counter, b->d_done,
+                             b->d_done ? b->status : nullptr, b->grid, b->block, b->cap);
     if (side) {
       for (int q = 0; q < 1 + NDN && c1 == cudaSuccess; ++q) c1 = cudaEventRecord(b->ev[1 + q], b->branch[q]);
       for (int q = 0; q < 1 + NDN && c1 == cudaSuccess; ++q) c1 = cudaStreamWaitEvent(b->cap, b->ev[1 + q], 0);

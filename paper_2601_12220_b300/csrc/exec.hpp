@@ -91,13 +91,20 @@ cudaError_t launch_generic(const GParams &p, cudaStream_t s);
 // ---------------------------------------------------------------- persistent
 
 // one unit of work of the persistent executor: outputs [start, start+count) of row
+// a tile of outputs of one row; dep[q] >= 0 names a row whose every tile
+// (need[q] of them) must be finished before this tile starts (a factored
+// step reading an intermediate)
 struct PTile {
   int32_t row, pad;
   int64_t start, count;
+  int32_t dep[2], need[2];
 };
 
+// done[row] counts the finished tiles of each row (zeroed before a launch
+// whose tiles have dependencies; may be null when none has); status
+// receives BE_ETIMEOUT if a dependency wait gives up
 cudaError_t launch_persistent(const GParams *rows, const PTile *tiles, int64_t n_tiles, unsigned long long *counter,
-                              int grid, int block, cudaStream_t s);
+                              unsigned int *done, int *status, int grid, int block, cudaStream_t s);
 
 // ---------------------------------------------------------------- element
 

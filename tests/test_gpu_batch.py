@@ -279,7 +279,8 @@ FACTOR_SPECS = [
 def test_factored_instances_match_the_oracle(dt):
     """Instances whose best pairwise order cuts the loop nest's multiply-adds
     at least 4 times run as two-operand steps over intermediates, in phases
-    (the 4-operand chain needs 2 or 3 launches): every output within the
+    (the 4-operand chain is 3 steps deep), waiting in one launch for the
+    steps they read: every output within the
     precision's tolerance of the FP64 oracle (1e-12 S; FP32 max(gamma_K,
     1e-6) S), replays bitwise identical, and the same batch with factoring
     off still equals the generic strategy alone bit for bit."""
