@@ -440,8 +440,9 @@ int be_status(be_ctx *x, int32_t *device_status);
 /*
  * be_ctx_set_wait_limit -- limit, in SM clock cycles, of every pipeline
  * wait of the tensor-core kernels (the element strategy's digit-split GEMM
- * and the dense split GEMM) launched through x; 0 restores the default of
- * about one second.  A wait that runs out stops its kernel early (outputs
+ * and the dense split GEMM) launched through x, and of the dependency waits
+ * of factored steps in batches created with x (the limit in force when the
+ * batch is created); 0 restores the default of about one second.  A wait that runs out stops its kernel early (outputs
  * not valid), frees the kernel's tensor memory after its issued work has
  * completed, and leaves BE_ETIMEOUT for be_status.  A limit of a few
  * thousand cycles makes the waits run out on purpose (failure-path tests);

@@ -1274,7 +1274,7 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
     // one persistent launch; factored steps wait in it for the steps they read
     if (c1 == cudaSuccess)
       c1 = launch_persistent(b->d_rows, b->d_tiles, (int64_t)b->tiles.size(), b->d_counter, b->d_done,
-                             b->d_done ? b->status : nullptr, b->grid, b->block, b->cap);
+                             b->d_done ? b->status : nullptr, wl, b->grid, b->block, b->cap);
     if (side) {
       for (int q = 0; q < 1 + NDN && c1 == cudaSuccess; ++q) c1 = cudaEventRecord(b->ev[1 + q], b->branch[q]);
       for (int q = 0; q < 1 + NDN && c1 == cudaSuccess; ++q) c1 = cudaStreamWaitEvent(b->cap, b->ev[1 + q], 0);

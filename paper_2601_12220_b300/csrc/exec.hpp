@@ -102,9 +102,11 @@ struct PTile {
 
 // done[row] counts the finished tiles of each row (zeroed before a launch
 // whose tiles have dependencies; may be null when none has); status
-// receives BE_ETIMEOUT if a dependency wait gives up
+// receives BE_ETIMEOUT if a dependency wait gives up after wait_limit SM
+// cycles (0: about one second)
 cudaError_t launch_persistent(const GParams *rows, const PTile *tiles, int64_t n_tiles, unsigned long long *counter,
-                              unsigned int *done, int *status, int grid, int block, cudaStream_t s);
+                              unsigned int *done, int *status, long long wait_limit, int grid, int block,
+                              cudaStream_t s);
 
 // ---------------------------------------------------------------- element
 

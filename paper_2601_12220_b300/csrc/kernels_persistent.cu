@@ -16,8 +16,9 @@
 // tile depends on comes before it, and a tile is only pulled by a running
 // CTA, so every awaited tile is held by a running CTA whose own waits point
 // further back: the waits cannot form a cycle.  Each wait is bounded
-// (about one second); on expiry BE_ETIMEOUT goes to the status word and the
-// tile is skipped.
+// (about one second of SM cycles, or the caller's limit); on expiry
+// BE_ETIMEOUT goes to the status word, the tile is skipped and still
+// counted, so that no later wait depends on it.
 #include "generic_eval.cuh"
 
 namespace be {
@@ -33,7 +34,7 @@ __device__ __forceinline__ unsigned int load_acquire(const unsigned int *p) {
 __global__ void __launch_bounds__(256, 4) persistent_kernel(const GParams *__restrict__ rows,
                                                          const PTile *__restrict__ tiles, int64_t n_tiles,
                                                          unsigned long long *__restrict__ counter,
-                                                         unsigned int *done, int *status) {
+                                                         unsigned int *done, int *status, long long limit) {
   __shared__ GParams sp;
   __shared__ double red[256];
   __shared__ __align__(16) unsigned char gsm[gen::GEMM_SMEM];
@@ -53,7 +54,7 @@ __global__ void __launch_bounds__(256, 4) persistent_kernel(const GParams *__res
         if (tl.dep[q] < 0 || !done) continue;
         const long long t0 = clock64();
         while (load_acquire(done + tl.dep[q]) < (unsigned int)tl.need[q]) {
-          if (clock64() - t0 > 2000000000LL) {
+          if (clock64() - t0 > limit) {
             if (status) atomicExch(status, 9);   // BE_ETIMEOUT
             skip = 1;
             break;
@@ -83,9 +84,11 @@ static_assert(sizeof(GParams) % sizeof(int4) == 0, "descriptor copied as int4 wo
 }  // namespace
 
 cudaError_t launch_persistent(const GParams *rows, const PTile *tiles, int64_t n_tiles, unsigned long long *counter,
-                              unsigned int *done, int *status, int grid, int block, cudaStream_t s) {
+                              unsigned int *done, int *status, long long wait_limit, int grid, int block,
+                              cudaStream_t s) {
   if (n_tiles == 0) return cudaSuccess;
-  persistent_kernel<<<grid, block, 0, s>>>(rows, tiles, n_tiles, counter, done, status);
+  persistent_kernel<<<grid, block, 0, s>>>(rows, tiles, n_tiles, counter, done, status,
+                                           wait_limit > 0 ? wait_limit : 2000000000LL);
   return cudaGetLastError();
 }
 

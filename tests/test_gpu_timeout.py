@@ -1,4 +1,5 @@
-"""Failure detection on the tensor-core kernels, tested without a GPU fault.
+"""Failure detection on the tensor-core kernels and on the dependency waits
+of factored batch steps, tested without a GPU fault.
 
 A context's wait limit (be_ctx_set_wait_limit) of a hundred SM cycles makes
 the pipeline waits of the element strategy's digit-split GEMM and of the
@@ -91,3 +92,39 @@ def test_peak_probe_rates_plausible():
     assert 0.1 * 1.25 < f64 < 2 * 1.25
     assert 0.1 * 77 < f32 < 2 * 77
     assert f32 > 10 * f64
+
+
+def _chain_batch(ctx, seed):
+    """A batch with one factored instance ('ab,bc,cd,de->ae', three steps
+    deep): its later steps wait for the earlier ones inside the launch."""
+    g = np.random.default_rng(seed)
+    shapes = {"P": (32, 48), "Q": (48, 40), "R": (40, 36), "T": (36, 24)}   # the oracle's nest stays small
+    arrs = {k: g.standard_normal(v) for k, v in shapes.items()}
+    text = "ab,bc,cd,de->ae | P,Q,R,T ; " + " ; ".join(f"{k}:f64[{v[0]},{v[1]}]" for k, v in shapes.items())
+    e = be.Einsum(text)
+    out = [torch.full(e.out_shape, float("nan"), dtype=torch.float64, device=DEV)]
+    b = be.Batch(ctx, [(e, {k: torch.from_numpy(v).to(DEV) for k, v in arrs.items()}, out)])
+    assert b.factored()["instances"] == 1 and b.factored()["phases"] == 3
+    return b, text, arrs, out
+
+
+def test_factored_step_wait_runs_out_then_recovers():
+    """A wait limit of a hundred SM cycles, in force when a factored batch is
+    created, makes its dependency waits run out while the earlier steps are
+    still running: BE_ETIMEOUT in the context's status word, the waiting
+    tiles skipped (and still counted, so that nothing waits for them).  A
+    batch created afterwards with the default limit is correct."""
+    ctx = be.Context(None, device=0)
+    ctx.set_wait_limit(100)
+    b, _, _, _ = _chain_batch(ctx, 3)
+    b.run()
+    torch.cuda.synchronize()
+    assert ctx.status() == be.ETIMEOUT
+    assert ctx.status() == be.OK
+    ctx.set_wait_limit(0)
+    b, text, arrs, out = _chain_batch(ctx, 4)
+    b.run()
+    torch.cuda.synchronize()
+    assert ctx.status() == be.OK
+    (r, S), = ev.evaluate(text, arrs)
+    assert np.all(np.abs(out[0].cpu().numpy() - r) <= 1e-12 * S)
