@@ -741,6 +741,18 @@ def run_affine(args):
     n_g, t_g = ctx.timing(be.KERNEL_DENSE_GEMM)
     n_s, t_s = ctx.timing(be.KERNEL_SPLIT)
     gemm_ms = t_g / max(1, n_g)
+    # componentwise error of sampled outputs of the affine contraction (its
+    # result is in `out` after the timed steps; the plain run follows)
+    rs = np.random.default_rng(11)
+    mi, ni = rs.integers(0, M, 256), rs.integers(0, N, 256)
+    Pm = sc[0] * A.reshape(M, K)[mi] + sc[1]
+    Qn = sc[2] * B.reshape(K, N)[:, ni] + sc[3]
+    got = out[0].reshape(M, N)[torch.as_tensor(mi, device=dev), torch.as_tensor(ni, device=dev)].cpu().numpy()
+    ref = np.einsum("nk,kn->n", Pm, Qn)
+    S = np.einsum("nk,kn->n", np.abs(Pm), np.abs(Qn))
+    rel = np.abs(got - ref) / S
+    err = {"max_over_S": float(rel.max()), "median_over_S": float(np.median(rel)), "samples": int(rel.size),
+           "tolerance": 1e-6, "reference": "FP64 dot products of the sampled rows and columns (numpy)"}
     plain_ms = timed(plain, (), args.steps)
     peaks = load_peaks()
     bf16_peak = peaks["bf16_tflops"]
