@@ -548,7 +548,7 @@ __global__ void __launch_bounds__(256) split_cols_t(const double *__restrict__ B
   if (blockIdx.x == 0 && ty == 0 && nn < N) sb[nn] = scl;
   for (int r = ty; r < 32; r += 8) {
     const int64_t k = k0 + r;
-    tile[r][tx] = (k < K && nn < N) ? ldexp(affine<AFF>(B[k * ldb + nn * snb], alpha, beta), scl) : 0.0;
+    tile[r][tx] = (k < K && nn < N) ? scale2(affine<AFF>(B[k * ldb + nn * snb], alpha, beta), scl) : 0.0;
   }
   __syncthreads();
   for (int r = ty; r < 32; r += 8) {
