@@ -845,7 +845,7 @@ def run_mix(args):
     stream = torch.cuda.current_stream(dev)
     # strategy policy: element-shaped FP64 instances on the element strategy;
     # FP64 GEMM-form instances of >= 2^mix_split_log2 multiply-adds on the
-    # split-precision tensor cores (judged at 1e-6 S) unless --mix-no-split
+    # split-precision tensor cores (held to 1e-6 S) unless --mix-no-split
     policy = be.make_config(tile=(0, 0, 0, args.mix_split_log2), split=0 if args.mix_no_split else 1)
     t_plan = time.perf_counter()
     batch = be.Batch(ctx, items, policy)

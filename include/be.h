@@ -366,9 +366,9 @@ int be_batch_kinds(const be_batch *b, int32_t *generic, int32_t *element, int32_
 int be_batch_factored(const be_batch *b, int32_t *instances, int32_t *phases, int64_t *workspace_bytes);
 
 /*
- * be_tune_batch -- the autotuner for a batch (spec pattern 2: tile
- * shapes and schedules chosen by the engine's own tuner, results kept in
- * the normal-form-keyed database).  Creates the batch of be_batch_create
+ * be_tune_batch -- the autotuner for a batch (tile shapes and schedules
+ * chosen by the engine's own tuner, results kept in the database beside
+ * the normal-form keys, Sec. "Integration..." performance facts).  Creates the batch of be_batch_create
  * under each candidate launch shape of its persistent part -- block size
  * 128 (skipped when a row is evaluated as GEMM tiles) or 256, 2, 3 or 4 CTAs
  * per SM, tiles of 2^18, 2^20 or 2^22 operand terms -- with base's strategy policy (split, tile[3], stage_mask; base
