@@ -780,7 +780,7 @@ def run_affine(args):
 
 # ---------------------------------------------------------------- workload 4
 
-def factored_macs(out, ins, lens, min_gain=4.0):
+def factored_macs(out, ins, lens, min_gain=1.5):
     """Multiply-adds of one row under the pairwise order the batched executor
     picks (fewest multiply-adds over all orders of two-operand contractions)
     when it cuts the loop nest's (volume x (operands - 1)) at least min_gain

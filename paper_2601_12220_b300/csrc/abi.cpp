@@ -1080,11 +1080,11 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
     }
     ++b->n_kind[0];
     // factored evaluation: an instance whose pairwise order cuts the loop
-    // nest's multiply-adds at least 4 times runs as two-operand steps over
+    // nest's multiply-adds at least 1.5 times runs as two-operand steps over
     // dense intermediates (stage_mask bit 1 turns this off)
     if (allow_factor) {
       FactorOrder fo;
-      bool fac = factor_order(e, 4.0, fo) &&
+      bool fac = factor_order(e, 1.5, fo) &&
                  (double)fo.inter_elems * e.b * dtype_size(e.out_dtype) <= FACTOR_WS_MAX;
       std::vector<std::vector<FOp>> ops;
       for (int i = 0; fac && i < e.b; ++i) {

@@ -271,14 +271,15 @@ FACTOR_SPECS = [
     ("xre,rij,xej->ei | F,D,U", {"F": (3, 3, 200), "D": (3, 20, 20), "U": (3, 200, 20)}, True),
     ("ab,bc,cd,de->ae | P,Q,R,T", {"P": (16, 24), "Q": (24, 32), "R": (32, 20), "T": (20, 12)}, True),
     ("iij,jk,kl->il | A,B,C", {"A": (12, 12, 30), "B": (30, 25), "C": (25, 14)}, True),
-    ("ijk,ik,ij,ij->i | A,B,C,D", {"A": (6, 7, 8), "B": (6, 8), "C": (6, 7), "D": (6, 7)}, False),
+    ("ijk,ik,ij,ij->i | A,B,C,D", {"A": (6, 7, 8), "B": (6, 8), "C": (6, 7), "D": (6, 7)}, True),
+    ("ij,j->i | A,x", {"A": (30, 40), "x": (40,)}, False),
 ]
 
 
 @pytest.mark.parametrize("dt", ["f64", "f32"])
 def test_factored_instances_match_the_oracle(dt):
     """Instances whose best pairwise order cuts the loop nest's multiply-adds
-    at least 4 times run as two-operand steps over intermediates, in phases
+    at least 1.5 times run as two-operand steps over intermediates, in phases
     (the 4-operand chain is 3 steps deep), waiting in one launch for the
     steps they read: every output within the
     precision's tolerance of the FP64 oracle (1e-12 S; FP32 max(gamma_K,
