@@ -781,13 +781,14 @@ def run_affine(args):
 # ---------------------------------------------------------------- workload 4
 
 def factored_macs(out, ins, lens, min_gain=1.5):
-    """Multiply-adds of one row under the pairwise order the batched executor
-    picks (fewest multiply-adds over all orders of two-operand contractions)
-    when it cuts the loop nest's (volume x (operands - 1)) at least min_gain
-    times and the notation has 3 to 5 operands; None otherwise (the row then
-    runs its loop nest)."""
+    """Multiply-adds of one row under the order of steps the batched executor
+    picks (fewest multiply-adds over all orders of two-operand contractions
+    and of one-operand sums of an operand's own letters) when it cuts the
+    loop nest's (volume x (operands - 1)) at least min_gain times and the
+    notation has 2 to 5 operands; None otherwise (the row then runs its loop
+    nest)."""
     import itertools
-    if not 3 <= len(ins) <= 5:
+    if not 2 <= len(ins) <= 5:
         return None
     vol = lambda letters: math.prod(lens[c] for c in letters)
     all_l = set(out).union(*[set(x) for x in ins])
@@ -800,6 +801,12 @@ def factored_macs(out, ins, lens, min_gain=1.5):
             if cost < best[0]:
                 best[0], found[0] = cost, True
             return
+        for a in range(len(slots)):
+            rest = set(out).union(*[slots[k] for k in range(len(slots)) if k != a])
+            keep = slots[a] & rest
+            c = cost + vol(slots[a])
+            if keep != slots[a] and c < best[0]:
+                rec(slots[:a] + [keep] + slots[a + 1:], c)
         for a, b in itertools.combinations(range(len(slots)), 2):
             rest = set(out).union(*[slots[k] for k in range(len(slots)) if k not in (a, b)])
             both = slots[a] | slots[b]

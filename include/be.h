@@ -326,9 +326,9 @@ int be_tune(be_ctx *x, const be_einsum *e, int32_t precision, const be_buf *bufs
  *   about 2^tile[1] operand terms (default 20) for one persistent launch
  *   (cfg->tile[0] its block size, default 256, and 256 whenever a row is
  *   evaluated as GEMM tiles; cfg->tile[2] CTAs per SM, default 4).  A
- *   generic instance of 3 to 5 operands, all views of buffers, whose best
- *   pairwise order (fewest multiply-adds over all orders of two-operand
- *   contractions) cuts the multiply-adds of Eq. (1)'s loop nest at least
+ *   generic instance of 2 to 5 operands, all views of buffers, whose best
+ *   order of steps (fewest multiply-adds over all orders of two-operand
+ *   contractions and of one-operand sums of an operand's own letters) cuts the multiply-adds of Eq. (1)'s loop nest at least
  *   1.5 times is factored: each row runs as that sequence of two-operand
  *   einsums over dense intermediates (the same sum with its terms grouped
  *   differently); a step's tiles follow the tiles of the steps it reads in

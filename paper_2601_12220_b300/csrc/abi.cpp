@@ -1079,8 +1079,8 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
       }
     }
     ++b->n_kind[0];
-    // factored evaluation: an instance whose pairwise order cuts the loop
-    // nest's multiply-adds at least 1.5 times runs as two-operand steps over
+    // factored evaluation: an instance whose order of steps cuts the loop
+    // nest's multiply-adds at least 1.5 times runs as one- and two-operand steps over
     // dense intermediates (stage_mask bit 1 turns this off)
     if (allow_factor) {
       FactorOrder fo;
@@ -1140,8 +1140,8 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
         std::vector<int> slot_phase(n, -1), slot_row(n, -1);
         for (size_t q = 0; q < fi.fo.steps.size(); ++q) {
           const bool last = q + 1 == fi.fo.steps.size();
-          const int sa = fi.fo.steps[q][0], sb = fi.fo.steps[q][1];
-          const int phase = 1 + std::max(slot_phase[sa], slot_phase[sb]);
+          const int sa = fi.fo.steps[q][0], sb = fi.fo.steps[q][1];   // sb < 0: a unary step
+          const int phase = 1 + std::max(slot_phase[sa], sb >= 0 ? slot_phase[sb] : -1);
           FOp r;
           r.dtype = e.out_dtype;
           r.letters = fi.fo.letters[q];
@@ -1156,9 +1156,9 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
           r.strides.assign(r.letters.size(), 1);
           for (int d = (int)r.letters.size() - 2; d >= 0; --d) r.strides[d] = r.strides[d + 1] * e.len[r.letters[d + 1]];
           GParams p;
-          int st = plan_factor_step(e, slot[sa], slot[sb], r.letters, dst, p, err);
+          int st = plan_factor_step(e, slot[sa], sb >= 0 ? &slot[sb] : nullptr, r.letters, dst, p, err);
           if (st) return fail(st, "instance " + std::to_string(fi.k) + ", factored step: " + err);
-          const int deps[2] = {slot_row[sa], slot_row[sb]};
+          const int deps[2] = {slot_row[sa], sb >= 0 ? slot_row[sb] : -1};
           int row;
           st = add_row(p, phase == 0 ? 0 : phase + 1, fi.k, deps, &row);
           if (st) return st;

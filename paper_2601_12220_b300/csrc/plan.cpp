@@ -824,6 +824,26 @@ void search_orders(const Einsum &e, uint32_t out_mask, std::vector<uint32_t> &sl
     }
     return;
   }
+  // a unary step: an operand with letters that no other operand and not the
+  // output uses sums them first (e.g. both sides of 'ij,ik->i')
+  for (size_t a = 0; a < slots.size(); ++a) {
+    uint32_t rest = out_mask;
+    for (size_t k = 0; k < slots.size(); ++k)
+      if (k != a) rest |= slots[k];
+    const uint32_t keep = slots[a] & rest;
+    if (keep == slots[a]) continue;
+    const double c = cost + letters_volume(e, slots[a]);
+    if (c >= best) continue;
+    std::vector<uint32_t> ns = slots;
+    std::vector<int> nid = ids;
+    ns[a] = keep;
+    nid[a] = next_id;
+    path.push_back({ids[a], -1});
+    kept.push_back(keep);
+    search_orders(e, out_mask, ns, nid, next_id + 1, c, path, kept, best, best_path, best_kept);
+    path.pop_back();
+    kept.pop_back();
+  }
   for (size_t a = 0; a < slots.size(); ++a)
     for (size_t b2 = a + 1; b2 < slots.size(); ++b2) {
       uint32_t rest = out_mask;
@@ -853,7 +873,7 @@ void search_orders(const Einsum &e, uint32_t out_mask, std::vector<uint32_t> &sl
 }  // namespace
 
 bool factor_order(const Einsum &e, double min_gain, FactorOrder &fo) {
-  if (e.n < 3 || e.n > 5) return false;
+  if (e.n < 2 || e.n > 5) return false;
   uint32_t all = mask_of(e.out);
   std::vector<uint32_t> slots;
   std::vector<int> ids;
@@ -905,22 +925,29 @@ bool operand_fop(const Einsum &e, int row, int pos, const std::vector<BufIn> &bu
   return true;
 }
 
-int plan_factor_step(const Einsum &e, const FOp &x, const FOp &y, const std::vector<int8_t> &out_letters, void *out,
+int plan_factor_step(const Einsum &e, const FOp &x, const FOp *y, const std::vector<int8_t> &out_letters, void *out,
                      GParams &p, std::string &err) {
-  // the step as a batched einsum of one row and two identity arguments
+  // the step as a batched einsum of one row and one or two identity
+  // arguments (one: a unary step summing the operand's own letters)
+  const int n = y ? 2 : 1;
   Einsum s;
   s.b = 1;
-  s.n = 2;
+  s.n = n;
   s.out = out_letters;
-  s.in = {x.letters, y.letters};
-  s.rows = {{0, 1}};
+  s.in = {x.letters};
+  s.rows = {{0}};
+  if (y) {
+    s.in.push_back(y->letters);
+    s.rows[0].push_back(1);
+  }
   for (int c = 0; c < 26; ++c) s.len[c] = e.len[c];
-  for (int8_t c : x.letters) s.used[c] = true;
-  for (int8_t c : y.letters) s.used[c] = true;
+  for (int j = 0; j < n; ++j)
+    for (int8_t c : s.in[j]) s.used[c] = true;
   for (int8_t c : out_letters) s.used[c] = true;
   s.out_dtype = e.out_dtype;
-  const FOp *ops[2] = {&x, &y};
-  for (int k = 0; k < 2; ++k) {
+  const FOp *ops[2] = {&x, y};
+  std::vector<BufIn> bufs;
+  for (int k = 0; k < n; ++k) {
     Buffer bf;
     bf.name = k ? "Y" : "X";
     bf.dtype = ops[k]->dtype;
@@ -932,9 +959,9 @@ int plan_factor_step(const Einsum &e, const FOp &x, const FOp &y, const std::vec
     a.shape = bf.shape;
     a.buffer = k;
     s.args.push_back(a);
+    bufs.push_back(BufIn{const_cast<void *>(ops[k]->ptr), ops[k]->strides.data(), (int32_t)ops[k]->letters.size(),
+                         ops[k]->dtype});
   }
-  std::vector<BufIn> bufs = {BufIn{const_cast<void *>(x.ptr), x.strides.data(), (int32_t)x.letters.size(), x.dtype},
-                             BufIn{const_cast<void *>(y.ptr), y.strides.data(), (int32_t)y.letters.size(), y.dtype}};
   BufIn bo{out, nullptr, (int32_t)out_letters.size(), e.out_dtype};
   return plan_generic_row(s, 0, bufs, bo, {}, p, err);
 }

@@ -74,8 +74,10 @@ struct FOp {
 
 // Pairwise order of a row's n operands: step s combines slots steps[s][0]
 // and steps[s][1] (slots 0..n-1 are the operands, slot n + s the result of
-// step s) into a dense row-major intermediate over letters[s]; the last
-// step's letters are the output's.  Costs count multiply-adds of one row.
+// step s), or, when steps[s][1] < 0, sums the letters that only slot
+// steps[s][0] uses, into a dense row-major intermediate over letters[s];
+// the last step's letters are the output's.  Costs count multiply-adds of
+// one row.
 struct FactorOrder {
   std::vector<std::array<int, 2>> steps;
   std::vector<std::vector<int8_t>> letters;
@@ -83,16 +85,17 @@ struct FactorOrder {
   int64_t inter_elems = 0;      // elements of one row's intermediates
 };
 
-// The order with the fewest multiply-adds over all pairwise orders (n <= 5);
-// false unless e has 3 to 5 operands and the order cuts the loop nest's
-// multiply-adds at least `min_gain` times.
+// The order with the fewest multiply-adds over all orders of pairwise and
+// unary steps (n <= 5); false unless e has 2 to 5 operands and the order
+// cuts the loop nest's multiply-adds at least `min_gain` times.
 bool factor_order(const Einsum &e, double min_gain, FactorOrder &fo);
 // operand pos of row `row` as a view; false for a functional argument other
 // than a single buffer reference
 bool operand_fop(const Einsum &e, int row, int pos, const std::vector<BufIn> &bufs, FOp &f);
-// one pairwise step as a generic row writing `out` (dense row-major over
-// out_letters); out_dtype is the einsum's
-int plan_factor_step(const Einsum &e, const FOp &x, const FOp &y, const std::vector<int8_t> &out_letters, void *out,
+// one step as a generic row writing `out` (dense row-major over
+// out_letters): x with y, or x alone when y is null; out_dtype is the
+// einsum's
+int plan_factor_step(const Einsum &e, const FOp &x, const FOp *y, const std::vector<int8_t> &out_letters, void *out,
                      GParams &p, std::string &err);
 
 }  // namespace be

@@ -273,6 +273,8 @@ FACTOR_SPECS = [
     ("iij,jk,kl->il | A,B,C", {"A": (12, 12, 30), "B": (30, 25), "C": (25, 14)}, True),
     ("ijk,ik,ij,ij->i | A,B,C,D", {"A": (6, 7, 8), "B": (6, 8), "C": (6, 7), "D": (6, 7)}, True),
     ("ij,j->i | A,x", {"A": (30, 40), "x": (40,)}, False),
+    ("ij,ik->i | A,B | C,B", {"A": (20, 30), "B": (20, 25), "C": (20, 30)}, True),
+    ("ijl,jk,kl->il | A,B,C", {"A": (10, 12, 9), "B": (12, 14), "C": (14, 9)}, True),
 ]
 
 
