@@ -360,6 +360,20 @@ __device__ __forceinline__ T out_block(const GParams &p, int64_t o, double *red)
 // outputs (R = TM / 16), every output summing its terms in increasing k (so
 // the result does not depend on which kernel runs the tile).  Must be called
 // by the whole CTA.
+// one mixed-radix digit of x (v = x mod len, x = x / len), in 32-bit
+// arithmetic when both fit; the outermost digit needs no division (x is
+// below its length)
+__device__ __forceinline__ void digit_step(int64_t &x, int64_t len, int64_t &v) {
+  if ((uint64_t)x < 0x80000000ull && (uint64_t)len < 0x80000000ull) {
+    const uint32_t xu = (uint32_t)x, lu = (uint32_t)len, q = xu / lu;
+    v = (int64_t)(xu - q * lu);
+    x = (int64_t)q;
+  } else {
+    v = x % len;
+    x /= len;
+  }
+}
+
 constexpr int GEMM_SMEM = 2 * GT_K * (GT_MAX + 2) * 8 + (6 * GT_MAX + 2 * GT_K) * 8;
 
 template <typename T, int TM>
@@ -404,8 +418,8 @@ __device__ void gemm_tile(const GParams &p, int64_t tile, unsigned char *sm) {
     if (tid < vm)
       for (int d = g.nm - 1; d >= 0; --d) {
         const int L = g.m[d];
-        const int64_t v = x % p.len[L];
-        x /= p.len[L];
+        int64_t v = x;
+        if (d > 0) digit_step(x, p.len[L], v);
         oa += ca[L] * v;
         oc += g.out_coef[L] * v;
         oh += ch[L] * v;
@@ -419,8 +433,8 @@ __device__ void gemm_tile(const GParams &p, int64_t tile, unsigned char *sm) {
     if (t < vn)
       for (int d = g.nn - 1; d >= 0; --d) {
         const int L = g.n[d];
-        const int64_t v = x % p.len[L];
-        x /= p.len[L];
+        int64_t v = x;
+        if (d > 0) digit_step(x, p.len[L], v);
         ob += cb[L] * v;
         oc += g.out_coef[L] * v;
         oh += ch[L] * v;
@@ -447,8 +461,8 @@ __device__ void gemm_tile(const GParams &p, int64_t tile, unsigned char *sm) {
       if (t < vk)
         for (int d = g.nk - 1; d >= 0; --d) {
           const int L = g.k[d];
-          const int64_t v = x % p.len[L];
-          x /= p.len[L];
+          int64_t v = x;
+          if (d > 0) digit_step(x, p.len[L], v);
           oa += ca[L] * v;
           ob += cb[L] * v;
         }
