@@ -158,6 +158,14 @@ struct EParams {
   EProd groups[EM_MAXROWS];
 };
 
+// whether a producer group evaluates sin(a) * b (the kernels fill their
+// sine tables only then)
+__host__ __device__ inline bool uses_sin(const EParams &p) {
+  for (int g = 0; g < p.n_groups; ++g)
+    if (p.groups[g].kind == 1) return true;
+  return false;
+}
+
 // shared-memory doubles (or float pairs) of the FP64 and double-float
 // element kernels: the operator, one producer group's operand tile (groups
 // are staged one after another) and every row's geometric factors

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(512, 2) element_df_kernel(const __grid_constan
   const int n_f2 = (int)element_smem_words(p);
   float2 *sin_tab = smf + n_f2;                       // full-circle sine table
   const int tid = threadIdx.x, nt = blockDim.x;
-  dfm::sin2_table_fill(sin_tab);
+  if (uses_sin(p)) dfm::sin2_table_fill(sin_tab);
 
   for (int idx = tid; idx < R * NI * NJ; idx += nt) {
     const int r = idx / (NI * NJ), rem = idx % (NI * NJ);
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(256, (NB == 4 && RM == 1) ? 4 : 2)
   __shared__ double Dd[RM * NB * NB];   // the same in FP64
   __shared__ float2 sin_tab[dfm::SIN2_N];
   const int R = p.R, NI = p.NI, NJ = p.NJ;
-  dfm::sin2_table_fill(sin_tab);
+  if (uses_sin(p)) dfm::sin2_table_fill(sin_tab);
   for (int idx = threadIdx.x; idx < RM * NB * NB; idx += blockDim.x) {
     const int r = idx / (NB * NB), i = (idx / NB) % NB, j = idx % NB;
     const double v = (r < R && i < NI && j < NJ) ? p.D[d_offset(p, r, i, j)] : 0.0;

@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
     const int n16 = (int)(SL.a + 2 * TC_P * aplane) / 16;
     for (int k = tid; k < n16; k += TC_THREADS) z[k] = make_uint4(0u, 0u, 0u, 0u);
   }
-  dfm::sin_half_table_fill(sin_tab, tid, TC_THREADS);
+  if (uses_sin(p)) dfm::sin_half_table_fill(sin_tab, tid, TC_THREADS);
   // per row n of D: scale exponent, 2^k, and the check term
   //   zc = F 2^k (2^-46 (sum_j |D_nj| 2^-k + K) + 2^-42) (1 + 2^-20)
   // (0 for a row of zeros, which is exact; infinite for a row whose scale
