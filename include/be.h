@@ -320,7 +320,7 @@ int be_tune(be_ctx *x, const be_einsum *e, int32_t precision, const be_buf *bufs
  *   per-element operands) take the element strategy with their database
  *   configuration (cfg->stage_mask bit 0 keeps them generic); with
  *   cfg->split >= 1, FP64 instances of GEMM form with at least
- *   2^cfg->tile[3] multiply-adds (default 2^20) take the split-precision
+ *   2^cfg->tile[3] multiply-adds (default 2^23) take the split-precision
  *   tensor-core strategy (1e-6 * S); every other instance is generic: each
  *   of its rows becomes a descriptor whose outputs are cut into tiles of
  *   about 2^tile[1] operand terms (default 20) for one persistent launch

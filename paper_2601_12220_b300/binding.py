@@ -162,6 +162,33 @@ def _string(fn, *args):
 
 # ---------------------------------------------------------------- IR
 
+# parse text -> the metadata of its handle (counts, output shape, buffer
+# declarations), a function of the text alone: a text parsed again (a
+# repeated request) still runs be_parse but skips the queries
+_META: dict = {}
+_META_MAX = 4096
+
+
+def _describe(h):
+    v = [ctypes.c_int32() for _ in range(7)]
+    check(lib().be_einsum_info(h, *[ctypes.byref(x) for x in v]))
+    info = tuple(x.value for x in v)
+    out_ndim = info[5]
+    shp = (ctypes.c_int64 * max(1, out_ndim))()
+    check(lib().be_einsum_out_shape(h, shp))
+    buffers = []
+    for k in range(info[2]):
+        dt, nd = ctypes.c_int32(), ctypes.c_int32()
+        s = (ctypes.c_int64 * 26)()
+        need = ctypes.c_size_t(0)
+        lib().be_einsum_buffer(h, k, None, 0, ctypes.byref(need), None, None, None)
+        nm = ctypes.create_string_buffer(need.value)
+        check(lib().be_einsum_buffer(h, k, nm, need.value, ctypes.byref(need), ctypes.byref(dt),
+                                     ctypes.byref(nd), s))
+        buffers.append((nm.value.decode(), dt.value, tuple(s[d] for d in range(nd.value))))
+    return info, tuple(shp[k] for k in range(out_ndim)), tuple(buffers)
+
+
 class Einsum:
     """be_parse handle (or, through raise_kernel, a be_raise handle)."""
 
@@ -169,27 +196,19 @@ class Einsum:
         if _handle is None:
             h = ctypes.c_void_p()
             check(lib().be_parse(text.encode(), ctypes.byref(h)))
+            meta = _META.get(text)
+            if meta is None:
+                meta = _describe(h)
+                if len(_META) >= _META_MAX:
+                    _META.clear()
+                _META[text] = meta
         else:
             h = _handle
+            meta = _describe(h)
         self._h = h
         self.text = text
-        v = [ctypes.c_int32() for _ in range(7)]
-        check(lib().be_einsum_info(h, *[ctypes.byref(x) for x in v]))
-        self.b, self.n, self.n_buffers, self.n_args, self.n_scalars, self.out_ndim, self.out_dtype = \
-            [x.value for x in v]
-        shp = (ctypes.c_int64 * max(1, self.out_ndim))()
-        check(lib().be_einsum_out_shape(h, shp))
-        self.out_shape = tuple(shp[k] for k in range(self.out_ndim))
-        self.buffers = []
-        for k in range(self.n_buffers):
-            dt, nd = ctypes.c_int32(), ctypes.c_int32()
-            s = (ctypes.c_int64 * 26)()
-            need = ctypes.c_size_t(0)
-            lib().be_einsum_buffer(h, k, None, 0, ctypes.byref(need), None, None, None)
-            nm = ctypes.create_string_buffer(need.value)
-            check(lib().be_einsum_buffer(h, k, nm, need.value, ctypes.byref(need), ctypes.byref(dt),
-                                         ctypes.byref(nd), s))
-            self.buffers.append((nm.value.decode(), dt.value, tuple(s[d] for d in range(nd.value))))
+        info, self.out_shape, self.buffers = meta
+        self.b, self.n, self.n_buffers, self.n_args, self.n_scalars, self.out_ndim, self.out_dtype = info
 
     @property
     def handle(self):
@@ -264,16 +283,30 @@ class Canon:
         h = ctypes.c_void_p()
         check(lib().be_canonicalize(e.handle, ctypes.byref(h)))
         self._h = h
-        self.key = _string(lib().be_canon_key, h)
-        n = ctypes.c_size_t()
-        lib().be_canon_tokens(h, None, 0, ctypes.byref(n))
-        t = (ctypes.c_int64 * max(1, n.value))()
-        check(lib().be_canon_tokens(h, t, n.value, ctypes.byref(n)))
-        self.tokens = list(t[:n.value])
+        self._key = None
+        self._tokens = None
 
     @property
     def handle(self):
         return self._h
+
+    @property
+    def key(self) -> str:
+        """The normal form's printed key (read from the handle on first use)."""
+        if self._key is None:
+            self._key = _string(lib().be_canon_key, self._h)
+        return self._key
+
+    @property
+    def tokens(self) -> list:
+        """The normal form's token vector (read from the handle on first use)."""
+        if self._tokens is None:
+            n = ctypes.c_size_t()
+            lib().be_canon_tokens(self._h, None, 0, ctypes.byref(n))
+            t = (ctypes.c_int64 * max(1, n.value))()
+            check(lib().be_canon_tokens(self._h, t, n.value, ctypes.byref(n)))
+            self._tokens = list(t[:n.value])
+        return self._tokens
 
     def sigma(self, kind: int, k: int) -> str:
         return _string(lib().be_canon_sigma, self._h, kind, k)

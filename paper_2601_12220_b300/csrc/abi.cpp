@@ -972,10 +972,11 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
   const double cost_target = std::ldexp(1.0, cost_log2);
   // strategy policy: element-shaped FP64 instances take the element strategy
   // unless stage_mask bit 0 is set; with split >= 1, FP64 instances of GEMM
-  // form with at least 2^tile[3] (default 2^20) multiply-adds take the
-  // split-precision tensor-core strategy
+  // form with at least 2^tile[3] (default 2^23, the best of 2^16 .. 2^25 on
+  // the uneven mix: smaller GEMMs spend more in the split kernels than they
+  // save) multiply-adds take the split-precision tensor-core strategy
   const bool allow_element = !(c.stage_mask & 1u);
-  const double dense_min = std::ldexp(1.0, c.tile[3] > 0 ? c.tile[3] : 20);
+  const double dense_min = std::ldexp(1.0, c.tile[3] > 0 ? c.tile[3] : 23);
   // factored steps are two-operand rows, often GEMM tiles, which need the
   // 256-thread block
   const bool allow_factor = !(c.stage_mask & 2u) && b->block == 256;
