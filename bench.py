@@ -383,6 +383,32 @@ def run_ours(args):
 
 # ---------------------------------------------------------------- FEM action
 
+def back_to_back_ms(torch, be, ctx, text, bufs, outs, stream, steps, cfg=None, precision=None):
+    """Device time per launch of one parsed einsum's execute, back to back:
+    the executes are queued behind a bounded spin kernel while the host
+    submits them, and one event pair brackets all of them (on an idle GPU a
+    per-launch event pair would also count the host's submission).  Returns
+    (ms per launch, host seconds per execute)."""
+    e = be.Einsum(text)
+    kw = {} if precision is None else {"precision": precision}
+    hit = ctx.lookup(e.canonicalize(), **kw)
+    cfg = cfg or (hit[0] if hit else None)
+    h0 = time.perf_counter()
+    for _ in range(10):
+        be.execute(ctx, e, bufs, outs, cfg=cfg, stream=stream, **kw)
+    host_s = (time.perf_counter() - h0) / 10
+    torch.cuda.synchronize()
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # spin for 4x the host's submission time of all the launches (at least 20 ms)
+    torch.cuda._sleep(int(2.0e9 * max(20e-3, 4.0 * host_s * steps)))
+    k0.record(stream)
+    for _ in range(steps):
+        be.execute(ctx, e, bufs, outs, cfg=cfg, stream=stream, **kw)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    return k0.elapsed_time(k1) / steps, host_s
+
+
 def run_fem(args):
     """FEM action 'ij,ej->ei', b = 4 rows sharing D (4 x 4), E = 4096: time per
     batched einsum through be_execute and as a CUDA-graph replay of a batch,
@@ -426,28 +452,9 @@ def run_fem(args):
     steps = max(args.steps, 100)
     with Clocks(local) as clk:
         ms = timed(step, steps)
-    # kernel time per launch, back to back: the executes of one parsed
-    # einsum (the step's host work left out) are queued behind a bounded
-    # spin kernel while the host submits them, and one event pair brackets
-    # all of them (on an idle GPU each kernel would start only when the host
-    # had submitted it)
-    e_pre = be.Einsum(text)
-    hit = ctx.lookup(e_pre.canonicalize())
-    cfg_pre = hit[0] if hit else None
-    h0 = time.perf_counter()
-    for _ in range(10):
-        be.execute(ctx, e_pre, bufs, outs, cfg=cfg_pre, stream=stream)
-    host_s = (time.perf_counter() - h0) / 10           # host time per execute
-    torch.cuda.synchronize()
-    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    # spin for 4x the host's submission time of all the steps (at least 20 ms)
-    torch.cuda._sleep(int(2.0e9 * max(20e-3, 4.0 * host_s * steps)))
-    k0.record(stream)
-    for _ in range(steps):
-        be.execute(ctx, e_pre, bufs, outs, cfg=cfg_pre, stream=stream)
-    k1.record(stream)
-    torch.cuda.synchronize()
-    n_k, t_k = steps, k0.elapsed_time(k1)
+    # kernel time per launch, back to back (the step's host work left out)
+    kms_b2b, host_s = back_to_back_ms(torch, be, ctx, text, bufs, outs, stream, steps)
+    n_k, t_k = steps, kms_b2b * steps
     batch = be.Batch(ctx, [(be.Einsum(text), bufs, outs)])
     ms_graph = timed(lambda: batch.run(stream), steps)
     # canonicalization of 200 relabeled copies
@@ -529,12 +536,23 @@ def run_stacked(args):
     # contraction (N x K) and the production of v (K x X), per row
     df_flops = 15.0 * rows * E * (N * K + K * X)
     strat = be.plan_strategy(ctx, be.Einsum(text))
+    # the element variant: double-float by default for the stacked form;
+    # --element-variant 3 runs the tensor-core kernel (contractions of up to
+    # 64 values: every face mass, the divergence up to P3)
+    variant = args.element_variant or 2
+    forced = be.make_config(be.STRAT_ELEMENT, (0, 0, args.element_variant)) if args.element_variant else None
+    # bf16 MMA flops the tensor-core kernel issues per element and row: per
+    # K-slice of 16 and column block of 32, u's six digits against D's
+    # planes p <= 6 - q (26 planes of 32 columns)
+    ncb = (N + 31) // 32
+    tc_mma_flops = 2.0 * 16 * ((K + 15) // 16) * ncb * 32 * 26 * E * rows
 
     def step(cfg=None):
         e = be.Einsum(text)
         c = e.canonicalize()
         hit = ctx.lookup(c, be.PREC_FP64)
-        be.execute(ctx, e, bufs, outs, cfg=cfg or (hit[0] if hit else None), precision=be.PREC_FP64, stream=stream)
+        be.execute(ctx, e, bufs, outs, cfg=cfg or forced or (hit[0] if hit else None), precision=be.PREC_FP64,
+                   stream=stream)
 
     def timed(cfg, steps):
         for _ in range(args.warmup):
@@ -548,31 +566,45 @@ def run_stacked(args):
         torch.cuda.synchronize()
         return t0.elapsed_time(t1) / steps
 
-    ctx.set_timing(True)
     with Clocks(local) as clk:
         ms = timed(None, args.steps)
-    ctx.set_timing(False)
-    n_launch, k_total = ctx.timing(be.KERNEL_ELEMENT)
-    kms = k_total / max(1, n_launch)
+    n_launch = args.steps                     # one element-kernel launch per step
+    # kernel time per launch, back to back (the step's host work left out)
+    kms, _ = back_to_back_ms(torch, be, ctx, text, bufs, outs, stream, max(20, args.steps), cfg=forced,
+                             precision=be.PREC_FP64)
     gen_ms = timed(be.make_config(be.STRAT_GENERIC), max(3, args.steps // 4))
     peaks = load_peaks()
     ach_tf = df_flops / (kms * 1e-3) / 1e12
     ach_gb = byts / (kms * 1e-3) / 1e9
+    if variant == 3:
+        ach_mma = tc_mma_flops / (kms * 1e-3) / 1e12
+        roof = {"kernel": "element_tc_kernel (stacked form)", "bound": "hbm", "achieved": ach_gb,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach_gb / peaks["hbm_gbs"],
+                "peak_source": peaks["source"], "traffic": None, "algorithmic_bytes": byts,
+                "timing": "CUDA events around back-to-back launches queued behind a spin kernel",
+                "tensor": {"achieved": ach_mma, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                           "frac": ach_mma / peaks["bf16_tflops"],
+                           "counts": "bf16 digit-product MMA flops issued (26 planes of 32 columns per K-slice and "
+                                     "column block)"}}
+    else:
+        roof = {"kernel": "element_df_kernel" if variant == 2 else "element_kernel", "bound": "alu",
+                "achieved": ach_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach_tf / FP32_PEAK_TFLOPS,
+                "timing": "CUDA events around back-to-back launches queued behind a spin kernel",
+                "counts": "FP32 flops of the compensated terms (15 per term, contraction and production)",
+                "peak_source": "FP32 pipe from unit counts and clock: 148 SMs x 128 lanes x 2 x 2.032 GHz",
+                "traffic": None, "algorithmic_bytes": byts,
+                "hbm": {"achieved": ach_gb, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": ach_gb / peaks["hbm_gbs"], "peak_source": peaks["source"]}}
     line = {"metric": METRIC, "value": world * byts / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc, "E": E, "order": order, "b": rows, "K": K,
                        "parallelism": f"replicas x{world}", "l2": f"{byts / 1e6:.0f} MB per step, no flush",
                        "strategy": {1: "generic", 2: "element"}.get(strat, str(strat)),
-                       "element_variant": "double-float (stacked form)"},
+                       "element_variant": {1: "fp64 pipe", 2: "double-float", 3: "tensor cores"}[variant]
+                                          + " (stacked form)"},
             "kernel_ms": kms,
-            "roofline": {"kernel": "element_df_kernel", "bound": "alu", "achieved": ach_tf,
-                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach_tf / FP32_PEAK_TFLOPS,
-                         "counts": "FP32 flops of the compensated terms (15 per term, contraction and production)",
-                         "peak_source": "FP32 pipe from unit counts and clock: 148 SMs x 128 lanes x 2 x 2.032 GHz",
-                         "traffic": None, "algorithmic_bytes": byts,
-                         "hbm": {"achieved": ach_gb, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                                 "frac": ach_gb / peaks["hbm_gbs"], "peak_source": peaks["source"]}},
+            "roofline": roof,
             "generic": {"ms_per_step": gen_ms, "value": world * byts / (gen_ms * 1e-3) / 1e9,
                         "speedup_of_element": gen_ms / ms},
             "clocks": clk.summary(), "gpu_launches": n_launch}
@@ -1115,7 +1147,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=32768)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--element-variant", type=int, default=0,
-                    help="0 default (double-float on the FP32 pipe), 1 FP64 pipe")
+                    help="element kernel: 0 the default (tensor cores where the shape allows, else "
+                         "double-float), 1 FP64 pipe, 2 double-float, 3 tensor cores")
     ap.add_argument("--workload", default="dg_gradient",
                     choices=["dg_gradient", "chem_dense", "uneven_mix", "serving", "dg_divergence", "face_mass",
                              "dense_affine", "fem_action"])

@@ -65,8 +65,10 @@ extern "C" {
 #define BE_STRAT_ELEMENT 2     /* shared small operators x streamed per-element operands;
                                   tile[0] elements per tile, tile[1] threads per CTA,
                                   tile[2] variant (1 FP64 pipe, 2 double-float on the FP32
-                                  pipe, 3 tensor-core digit split; 0 = tensor cores where
-                                  the shape allows, else double-float), tile[3] for small
+                                  pipe, 3 tensor-core digit split, also for the stacked
+                                  divergence / face-mass form up to 64 contracted values;
+                                  0 = tensor cores where the shape allows and the form is
+                                  not stacked, else double-float), tile[3] for small
                                   operators (at most 8 x 8) on the double-float variant:
                                   1 + the share of the elements, in sixteenths, that run
                                   on the FP64 pipe beside the double-float ones (0 = 8/16) */

@@ -529,10 +529,14 @@ static int do_execute(be_ctx *x, const be_einsum *hc, const be_config *cfg, int3
   }
   if (strategy == BE_STRAT_ELEMENT) {
     // tile[2]: 1 = FP64 pipe, 2 = double-float on the FP32 pipe, 3 = tensor
-    // cores; unset = tensor cores where the shape allows, else double-float
+    // cores; unset = tensor cores where the shape allows, else double-float.
+    // The stacked form (divergence, face mass) defaults to double-float: its
+    // tensor-core form measured slower at every order but face mass P4 (a
+    // few thousand instructions per element leave the tile hand-offs
+    // exposed); the autotuner times both.
     std::string why_tc;
     const bool tc_ok = element_tc_supported(ep, why_tc);
-    const int variant = c.tile[2] > 0 ? c.tile[2] : (tc_ok ? 3 : 2);
+    const int variant = c.tile[2] > 0 ? c.tile[2] : (tc_ok && ep.NJ0 == 0 ? 3 : 2);
     if (variant == 3) {
       if (!tc_ok) return fail(BE_EUNSUPPORTED, "tensor-core element variant: " + why_tc);
       int *status = nullptr;

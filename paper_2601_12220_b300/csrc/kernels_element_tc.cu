@@ -104,7 +104,12 @@ struct TcParams {
   int *status;
   long long wait_limit;                         // SM cycles before a wait gives up
   int ncb, IB, KS, NG, NB;                      // column blocks, i per block, K-slices of 16, j groups of 8, B rows
+  int G;                                        // producer groups; tiles run over G x element tiles
+  int nbuf;                                     // buffers of u's digit planes: 2, or 1 where two do not fit
+  int npl;                                      // planes per operand: the six digits (+ |v|, |D| in the stacked form)
   double fcheck;                                // F of the per-output check (margins included)
+  int8_t gstart[EM_MAXROWS + 1];                // rows of group g: grow[gstart[g] .. gstart[g + 1])
+  int8_t grow[EM_MAXROWS];
 };
 
 // byte offsets of the shared-memory regions (from a 256-byte aligned base)
@@ -114,8 +119,8 @@ struct TcSmem {
 __host__ __device__ inline TcSmem tc_smem(const TcParams &tp) {
   TcSmem s;
   uint32_t o = 0;
-  s.b = o;    o += (uint32_t)(tp.ncb * tp.KS * TC_P * TC_BPLANE);
-  s.a = o;    o += (uint32_t)(2 * TC_P * tp.KS * TC_M * 32);
+  s.b = o;    o += (uint32_t)(tp.ncb * tp.KS * tp.npl * TC_BPLANE);
+  s.a = o;    o += (uint32_t)(tp.nbuf * tp.npl * tp.KS * TC_M * 32);
   s.sin = o;  o += (uint32_t)(sizeof(float2) * dfm::SINH_N);
   s.kD = o;   o += 4u * tp.NB;
   s.kDs = o;  o += 4u * tp.NB;
@@ -318,6 +323,144 @@ static __device__ __noinline__ void pairs_slow(const EProd &q, TileRows rows, bo
   }
 }
 
+// Stacked producer (divergence / face-mass form): v[e, k] = sum_x
+// A_x[e, s, j] B_x[e, s, j] at the flat index k = s NJ0 + j; s = k / NJ0 as
+// (k * sinv) >> 20 with sinv = ceil(2^20 / NJ0), exact for k, NJ0 <= 64.
+__device__ __forceinline__ int64_t stk_off(const ESView &v, int64_t e, int s, int j) {
+  return e * v.se + (int64_t)s * v.ss + (int64_t)j * v.sj;
+}
+// exponent bound at (e, k): the largest ex(A_x) + ex(B_x) over the x whose
+// product is nonzero, ex the biased exponent field (at least 1), so that
+// |A_x B_x| < 2^(ex(A_x) + ex(B_x) - 2044); 0 when every product is zero
+template <int X>
+__device__ __forceinline__ int stk_bound(const EProd &q, int64_t e, int k, int NJ, int NJ0, uint32_t sinv) {
+  const int s = (int)(((uint32_t)k * sinv) >> 20), j = k - s * NJ0;
+  int h = 0;
+#pragma unroll
+  for (int x = 0; x < X; ++x) {
+    const long long a = k < NJ ? __double_as_longlong(q.A[x].ptr[stk_off(q.A[x], e, s, j)]) & 0x7FFFFFFFFFFFFFFFll : 0;
+    const long long b = k < NJ ? __double_as_longlong(q.B[x].ptr[stk_off(q.B[x], e, s, j)]) & 0x7FFFFFFFFFFFFFFFll : 0;
+    if (a != 0 && b != 0) h = max(h, max(1, (int)(a >> 52)) + max(1, (int)(b >> 52)));
+  }
+  return h;
+}
+// the same sum for operands outside the fast conversion range (the tested
+// conversion); out of line
+static __device__ __noinline__ df stk_slow(const EProd &q, int64_t e, int s, int j) {
+  float sh = 0.f, sl = 0.f;
+  for (int x = 0; x < q.X; ++x)
+    dfm::dot_acc(sh, sl, dfm::df_from_double(q.A[x].ptr[stk_off(q.A[x], e, s, j)]),
+                 dfm::df_from_double(q.B[x].ptr[stk_off(q.B[x], e, s, j)]));
+  return dfm::two_sum(sh, sl);
+}
+// operands of v[e, k] (zeros past the row's end) and v in double-float
+// (products and their sum through TwoSum, as the double-float element
+// kernel forms it); the loads of a batch are issued before any of its
+// arithmetic
+template <int X>
+__device__ __forceinline__ void stk_load(const EProd &q, int64_t e, int k, int NJ0, int NJ, uint32_t sinv, double *a,
+                                         double *b) {
+  const int s = (int)(((uint32_t)k * sinv) >> 20), j = k - s * NJ0;
+#pragma unroll
+  for (int x = 0; x < X; ++x) {
+    a[x] = k < NJ ? q.A[x].ptr[stk_off(q.A[x], e, s, j)] : 0.0;
+    b[x] = k < NJ ? q.B[x].ptr[stk_off(q.B[x], e, s, j)] : 0.0;
+  }
+}
+template <int X>
+__device__ __forceinline__ df stk_eval(const EProd &q, int64_t e, int k, int NJ0, uint32_t sinv, const double *a,
+                                       const double *b) {
+  bool ok = true;
+#pragma unroll
+  for (int x = 0; x < X; ++x) ok = ok && dfm::df_fast_ok(a[x]) && dfm::df_fast_ok(b[x]);
+  if (!ok) {
+    const int s = (int)(((uint32_t)k * sinv) >> 20);
+    return stk_slow(q, e, s, k - s * NJ0);
+  }
+  float sh = 0.f, sl = 0.f;
+#pragma unroll
+  for (int x = 0; x < X; ++x) dfm::dot_acc(sh, sl, dfm::df_from_double_fast(a[x]), dfm::df_from_double_fast(b[x]));
+  return dfm::two_sum(sh, sl);
+}
+
+// L2 prefetch of the stacked operands of elements e1 .. e1+te1-1: per view
+// and value of s, the span between the corners (e1 or the last element, j
+// = 0 or NJ0 - 1) when it is at most 64 KB; lane l of the calling warp
+// takes (x, operand, s) = l
+__device__ __forceinline__ void stk_prefetch(const EProd &q, int64_t e1, int te1, int S, int NJ0, int lane) {
+  if (te1 <= 0 || lane >= q.X * 2 * S) return;
+  const int x = lane / (2 * S), w = (lane / S) & 1, sv = lane % S;
+  const ESView &v = w ? q.B[x] : q.A[x];
+  if (v.ss == 0 && sv > 0) return;                      // the same span for every s
+  uintptr_t lo = ~(uintptr_t)0, hi = 0;
+  for (int64_t e : {e1, e1 + te1 - 1})
+    for (int j : {0, NJ0 - 1}) {
+      const uintptr_t a = (uintptr_t)(v.ptr + stk_off(v, e, sv, j));
+      lo = min(lo, a);
+      hi = max(hi, a + 8);
+    }
+  const uintptr_t a = (lo + 15) & ~(uintptr_t)15, b = hi & ~(uintptr_t)15;
+  if (b <= a || b - a > 65536) return;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(b - a)) : "memory");
+}
+
+// pass 1 of the stacked producer: the exponent bound of sum_x |A_x B_x| per
+// element into mxw, over the flat items (element, k) of the tile, IB items
+// per thread with their loads issued together (item / K as a multiply by
+// kinv = ceil(2^20 / K), exact below 2^13 items), the maxima by shared-memory
+// atomics
+template <int X>
+__device__ __forceinline__ void stk_rows_bound(const EProd &q, int64_t e0, int te, int NJ, int NJ0, uint32_t sinv,
+                                               int tid, int *mxw) {
+  constexpr int IB = X == 1 ? 16 : 8;
+  const int n = te * NJ;
+  const uint32_t kinv = ((1u << 20) + (uint32_t)NJ - 1u) / (uint32_t)NJ;
+  for (int i0 = tid; i0 < n; i0 += IB * NPROD) {
+    int h[IB], row[IB];
+#pragma unroll
+    for (int u = 0; u < IB; ++u) {
+      const int it = i0 + u * NPROD;
+      row[u] = it < n ? (int)(((uint32_t)it * kinv) >> 20) : 0;
+      h[u] = stk_bound<X>(q, e0 + row[u], it < n ? it - row[u] * NJ : NJ, NJ, NJ0, sinv);
+    }
+#pragma unroll
+    for (int u = 0; u < IB; ++u)
+      if (h[u] > 0) atomicMax(&mxw[row[u]], h[u]);
+  }
+}
+
+// pass 2: v over pairs (k, k + 1), PB pairs per thread with their loads
+// issued first, written as u's six digit planes and the plane of
+// bf16(|v| 2^-k_e)
+template <int X>
+__device__ __forceinline__ void stk_pairs(const EProd &q, int64_t e0, int np, int JP, uint32_t jinv, int NJ, int NJ0,
+                                          uint32_t sinv, const int *ku, uint8_t *A, int aplane, int tid) {
+  constexpr int PB = X == 1 ? 4 : 2;
+  for (int p0 = tid; p0 < np; p0 += PB * NPROD) {
+    double a[PB][2][X], b[PB][2][X];
+    int mm[PB], kk[PB];
+#pragma unroll
+    for (int u = 0; u < PB; ++u) {
+      const int pi = p0 + u * NPROD;
+      mm[u] = pi < np ? (int)(((uint32_t)pi * jinv) >> 20) : 0;
+      kk[u] = pi < np ? 2 * (pi - mm[u] * JP) : NJ;
+      stk_load<X>(q, e0 + mm[u], kk[u], NJ0, NJ, sinv, a[u][0], b[u][0]);
+      stk_load<X>(q, e0 + mm[u], kk[u] + 1, NJ0, NJ, sinv, a[u][1], b[u][1]);
+    }
+#pragma unroll
+    for (int u = 0; u < PB; ++u) {
+      const int pi = p0 + u * NPROD;
+      if (pi >= np) continue;
+      const df v0 = stk_eval<X>(q, e0 + mm[u], kk[u], NJ0, sinv, a[u][0], b[u][0]);
+      const df v1 = stk_eval<X>(q, e0 + mm[u], kk[u] + 1, NJ0, sinv, a[u][1], b[u][1]);
+      pair_digits(v0, v1, pi, JP, jinv, ku, A, aplane);
+      const float sc = pow2f(-ku[mm[u]]);
+      *(uint32_t *)(A + TC_P * aplane + sw32(TC_M, mm[u], kk[u] >> 3) + (kk[u] & 7) * 2) =
+          pack_bf16(fabsf(v0.hi * sc), fabsf(v1.hi * sc));
+    }
+  }
+}
+
 // named barriers: 1 for the producer warps, 2 for the epilogue warps (the
 // .red forms return the AND / OR of a predicate over the participants, so
 // that a role leaves its loop together)
@@ -395,12 +538,50 @@ static __device__ __noinline__ void fallback_element(const EParams &p, int64_t e
   epi_sync();
 }
 
-// ROWS: the number of einsums when specialized, 0 for any count up to 4
-template <int R, int ROWS>
+// the same for the stacked form (group grp, element e): v_k = sum_x A_x B_x
+// in FP64 (k < K), t_i = sum_k D[i, k] v_k, written to every row of the
+// group
+static __device__ __noinline__ void fallback_stacked(const TcParams &tp, int grp, int64_t e, int et, double *fu,
+                                                     double *ft) {
+  const EParams &p = tp.p;
+  const EProd &q = p.groups[grp];
+  for (int k = et; k < p.NJ; k += NEPI) {
+    const int s = k / p.NJ0, j = k - s * p.NJ0;
+    double v = 0.0;
+    for (int x = 0; x < q.X; ++x) v = fma(q.A[x].ptr[stk_off(q.A[x], e, s, j)], q.B[x].ptr[stk_off(q.B[x], e, s, j)], v);
+    fu[k] = v;
+  }
+  epi_sync();
+  for (int i = et; i < p.NI; i += NEPI) {
+    double v = 0.0;
+    for (int k = 0; k < p.NJ; ++k) v = fma(p.D[d_offset(p, 0, i, k)], fu[k], v);
+    ft[i] = v;
+  }
+  epi_sync();
+  const int r0 = tp.gstart[grp], nr = tp.gstart[grp + 1] - r0;
+  for (int o = et; o < nr * p.NI; o += NEPI) {
+    const int kk = o / p.NI, i = o - kk * p.NI;
+    p.rows[tp.grow[r0 + kk]].out[e * p.NI + i] = ft[i];
+  }
+  epi_sync();
+}
+
+// ROWS: the number of einsums when specialized, 0 for any count up to 4;
+// STK: the stacked form (R = 1, no g; tiles over producer groups x element
+// tiles, each group's value written to each of its rows); NBUF: buffers of
+// u's digit planes (1 where two do not fit in shared memory: the producer
+// then waits for the MMAs of the tile before)
+template <int R, int ROWS, bool STK, int NBUF>
 __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_constant__ TcParams tp) {
   constexpr int H0 = 16 / R;                    // i per 16-column half of a block
   constexpr int KR = ROWS ? ROWS : TC_MAXROWS;  // einsums held per thread
   constexpr int IB = 2 * H0;                    // i per column block
+  // planes per operand and tensor-memory columns per slot: the stacked form
+  // adds a plane of bf16(|v|) and one of bf16(|D|), whose product sums into
+  // an eighth accumulator sum_k |D_ik| |v_k| (a lower bound of S for the
+  // per-output check, where one |t| alone would be a weak one)
+  constexpr int NPL = STK ? TC_P + 1 : TC_P;
+  constexpr int SLOT = STK ? TC_SLOT + TC_NCOL : TC_SLOT;
   const EParams &p = tp.p;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 255) & ~(uintptr_t)255);
@@ -448,7 +629,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
   // zero both operand regions (K padding and padding rows stay zero)
   {
     uint4 *z = (uint4 *)smem;
-    const int n16 = (int)(SL.a + 2 * TC_P * aplane) / 16;
+    const int n16 = (int)(SL.a + NBUF * NPL * aplane) / 16;
     for (int k = tid; k < n16; k += TC_THREADS) z[k] = make_uint4(0u, 0u, 0u, 0u);
   }
   if (uses_sin(p)) dfm::sin_half_table_fill(sin_tab, tid, TC_THREADS);
@@ -461,9 +642,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
     int hw = 0;
     double sabs = 0.0;
     if (brow<R>(tp, n, i, r)) {
-      const double *d = p.D + r * p.sr + i * p.si;
       for (int j = 0; j < NJ; ++j) {
-        const double x = d[j * p.sj];
+        const double x = p.D[d_offset(p, r, i, j)];
         hw = max(hw, __double2hiint(x) & 0x7FFFFFFF);
         sabs += fabs(x);
       }
@@ -489,21 +669,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
     int i, r;
     if (!brow<R>(tp, n, i, r)) continue;
     const int kn = kD[n];
-    const double *d = p.D + r * p.sr + i * p.si;
-    uint32_t w[TC_P][4];
+    uint32_t w[NPL][4];
 #pragma unroll
     for (int jp = 0; jp < 4; ++jp) {
       float d0[TC_P], d1[TC_P];
       const int j = g * 8 + 2 * jp;
-      digits_bits(j < NJ ? d[j * p.sj] : 0.0, kn, d0);
-      digits_bits(j + 1 < NJ ? d[(j + 1) * p.sj] : 0.0, kn, d1);
+      const double x0 = j < NJ ? p.D[d_offset(p, r, i, j)] : 0.0, x1 = j + 1 < NJ ? p.D[d_offset(p, r, i, j + 1)] : 0.0;
+      digits_bits(x0, kn, d0);
+      digits_bits(x1, kn, d1);
 #pragma unroll
       for (int q = 0; q < TC_P; ++q) w[q][jp] = pack_bf16(d0[q], d1[q]);
+      if constexpr (STK)   // |D| 2^(8 - k_n), in the units of the digits' products
+        w[TC_P][jp] = pack_bf16((float)(fabs(x0) * ldexp(1.0, 8 - kn)), (float)(fabs(x1) * ldexp(1.0, 8 - kn)));
     }
     const int cb = n >> 5, nl = n & 31, ks = g >> 1;
-    const uint32_t base = (uint32_t)((cb * tp.KS + ks) * TC_P) * TC_BPLANE + sw32_row(nl, g & 1);
+    const uint32_t base = (uint32_t)((cb * tp.KS + ks) * NPL) * TC_BPLANE + sw32_row(nl, g & 1);
 #pragma unroll
-    for (int q = 0; q < TC_P; ++q)
+    for (int q = 0; q < NPL; ++q)
       *(uint4 *)(Bp + base + q * TC_BPLANE) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
   }
   tc::fence_proxy_async();
@@ -512,10 +694,59 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
   tc::fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  const int64_t n_tiles = (p.E + TC_M - 1) / TC_M;
+  // tiles: element tiles, times the producer groups in the stacked form
+  // (tile -> group tile % G, element tile tile / G)
+  const int64_t n_tiles = (p.E + TC_M - 1) / TC_M * (STK ? tp.G : 1);
   int *status = tp.status;
 
-  if (warp < MMA_WARP) {
+  if (STK && warp < MMA_WARP) {
+    // ------------------------------------------------------------ producer (stacked form)
+    // Pass 1: per element the exponent bound of sum_x |A_x B_x| over k
+    // (flat items (element, k) over all producer threads), which gives the
+    // row scale 2^k_e (k_e = bound - 2044 + ceil(log2 X)); the a_empty wait
+    // (a barrier of the producer warps) orders its atomics before the scales
+    // are read.  Pass 2: v over pairs (k, k + 1) in double-float and its
+    // digits.  Warp 0 prefetches the next tile's operands into L2.
+    const int NJ0 = p.NJ0;
+    const uint32_t sinv = ((1u << 20) + (uint32_t)NJ0 - 1u) / (uint32_t)NJ0;
+    int t = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++t) {
+      const int grp = (int)(tile % tp.G);
+      const int64_t e0 = tile / tp.G * TC_M;
+      const int te = (int)(p.E - e0 < TC_M ? p.E - e0 : TC_M);
+      const EProd &q = p.groups[grp];
+      const int xlog2 = q.X <= 1 ? 0 : (q.X <= 2 ? 1 : 2);
+      if (warp == 0 && tile + gridDim.x < n_tiles) {       // the next tile's operands into L2
+        const int64_t t1 = tile + gridDim.x, e1 = t1 / tp.G * TC_M;
+        stk_prefetch(p.groups[(int)(t1 % tp.G)], e1, (int)(p.E - e1 < TC_M ? p.E - e1 : TC_M), NJ / NJ0, NJ0, lane);
+      }
+      if (tid < TC_M) mxw[tid] = 0;
+      prod_sync();
+      switch (q.X) {
+        case 1: stk_rows_bound<1>(q, e0, te, NJ, NJ0, sinv, tid, mxw); break;
+        case 2: stk_rows_bound<2>(q, e0, te, NJ, NJ0, sinv, tid, mxw); break;
+        case 3: stk_rows_bound<3>(q, e0, te, NJ, NJ0, sinv, tid, mxw); break;
+        default: stk_rows_bound<4>(q, e0, te, NJ, NJ0, sinv, tid, mxw); break;
+      }
+      const int ab = NBUF == 2 ? (t & 1) : 0;
+      const uint32_t use = NBUF == 2 ? (uint32_t)(t >> 1) : (uint32_t)t;
+      if (!prod_all(tc::mbar_wait(&a_empty[ab], (use & 1u) ^ 1u, abort_flag, status, limit))) break;
+      int *ku = kU + (t & (TC_KU - 1)) * TC_M;
+      if (tid < TC_M) ku[tid] = mxw[tid] == 0 ? KU_ZERO : min(100, max(-100, mxw[tid] - 2044 + xlog2));
+      prod_sync();
+      uint8_t *A = Ap + ab * NPL * aplane;
+      const int JP = (NJ + 1) >> 1, np = te * JP;
+      const uint32_t jinv = ((1u << 20) + (uint32_t)JP - 1u) / (uint32_t)JP;
+      switch (q.X) {
+        case 1: stk_pairs<1>(q, e0, np, JP, jinv, NJ, NJ0, sinv, ku, A, aplane, tid); break;
+        case 2: stk_pairs<2>(q, e0, np, JP, jinv, NJ, NJ0, sinv, ku, A, aplane, tid); break;
+        case 3: stk_pairs<3>(q, e0, np, JP, jinv, NJ, NJ0, sinv, ku, A, aplane, tid); break;
+        default: stk_pairs<4>(q, e0, np, JP, jinv, NJ, NJ0, sinv, ku, A, aplane, tid); break;
+      }
+      tc::fence_proxy_async();
+      tc::mbar_arrive(&a_full[ab]);
+    }
+  } else if (warp < MMA_WARP) {
     // ------------------------------------------------------------ producer
     // Two buffers of digit planes: tile t+1 is produced while the MMAs of
     // tile t run.  Pass 1 takes the largest |u| bound per element (the row
@@ -554,8 +785,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
           if (lane == 0 && r0 + NPW * u < te) mxw[r0 + NPW * u] = h;
         }
       }
-      const int ab = t & 1;
-      const uint32_t use = (uint32_t)(t >> 1);
+      const int ab = NBUF == 2 ? (t & 1) : 0;
+      const uint32_t use = NBUF == 2 ? (uint32_t)(t >> 1) : (uint32_t)t;
       if (!prod_all(tc::mbar_wait(&a_empty[ab], (use & 1u) ^ 1u, abort_flag, status, limit))) break;
       int *ku = kU + (t & (TC_KU - 1)) * TC_M;
       if (tid < TC_M) ku[tid] = mxw[tid] == 0 ? KU_ZERO : row_exp_hw(mxw[tid]);
@@ -609,20 +840,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
       int64_t cnt = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++t) {
-        const int ab = t & 1;
-        if (!tc::mbar_wait(&a_full[ab], (uint32_t)(t >> 1) & 1u, abort_flag, status, limit)) break;
-        const uint64_t adesc = adesc0 + (uint64_t)((ab * TC_P * aplane) >> 4);
+        const int ab = NBUF == 2 ? (t & 1) : 0;
+        const uint32_t use_a = NBUF == 2 ? (uint32_t)(t >> 1) : (uint32_t)t;
+        if (!tc::mbar_wait(&a_full[ab], use_a & 1u, abort_flag, status, limit)) break;
+        const uint64_t adesc = adesc0 + (uint64_t)((ab * NPL * aplane) >> 4);
         tc::fence_after();
         for (int cb = 0; cb < tp.ncb; ++cb, ++cnt) {
           const int slot = (int)(cnt & 1);
           const uint32_t use = (uint32_t)(cnt >> 1);
           if (!tc::mbar_wait(&s_empty[slot], (use & 1u) ^ 1u, abort_flag, status, limit)) { ok = false; break; }
           tc::fence_after();
-          const uint32_t dslot = tmem + (uint32_t)(slot * TC_SLOT);
+          const uint32_t dslot = tmem + (uint32_t)(slot * SLOT);
           // descriptors differ only in the start-address field (bits 0-13,
           // address >> 4), which stays below 2^14 for every operand here
           for (int ks = 0; ks < tp.KS; ++ks) {
-            const uint64_t bks = bdesc0 + (uint64_t)(((cb * tp.KS + ks) * TC_P * TC_BPLANE) >> 4);
+            const uint64_t bks = bdesc0 + (uint64_t)(((cb * tp.KS + ks) * NPL * TC_BPLANE) >> 4);
             const uint64_t aks = adesc + (uint64_t)((ks * TC_M * 32) >> 4);
             // u's digit q times D's planes p = 0 .. min(5, 6 - q) into the
             // accumulators of levels q .. q + p (32 columns apart); the first
@@ -641,6 +873,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
                 tc::mma_bf16(dslot + (uint32_t)(qd * TC_NCOL), aq, bks, tc::idesc_bf16(TC_M, np_ * TC_NCOL), 1u);
               }
             }
+            // stacked form: bf16(|v|) x bf16(|D|) into the eighth accumulator
+            if constexpr (STK)
+              tc::mma_bf16(dslot + (uint32_t)(TC_LEV * TC_NCOL), aks + (uint64_t)((TC_P * aplane) >> 4),
+                           bks + (uint64_t)((TC_P * TC_BPLANE) >> 4), tc::idesc_bf16(TC_M, TC_NCOL), ks > 0 ? 1u : 0u);
           }
           tc::mma_commit(&s_full[slot]);
         }
@@ -662,7 +898,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
     int t = 0;
     int64_t cnt = 0;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++t) {
-      const int64_t e = tile * TC_M + m;
+      const int grp = STK ? (int)(tile % tp.G) : 0;
+      const int64_t e0 = (STK ? tile / tp.G : tile) * TC_M;
+      const int64_t e = e0 + m;
       const bool valid = e < p.E;
       // g_k[e, r] of this thread's element as double-float (scaled by
       // 2^(k_e - 8) once the tile's exponents are known); g outside the
@@ -708,14 +946,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
         // added in double-float (levels 0-1 and 2-3 by TwoSum, the pairs
         // combined, levels 4-6 into the low part), times 2^k_n
         float th[16], tl[16];
+        float sl[STK ? 16 : 1];                              // stacked form: sum_k |D_ik| |v_k|, same units as th
 #pragma unroll
         for (int ch = 0; ch < 2; ++ch) {
           if (ch < nch) {
-            uint32_t v[TC_LEV][8];
+            uint32_t v[TC_LEV][8], vs[8];
             __syncwarp();   // tcgen05.ld is .sync.aligned: reconverge after lane-dependent work
 #pragma unroll
             for (int L = 0; L < TC_LEV; ++L)
-              tc::tmem_ld8(lane_base + (uint32_t)(slot * TC_SLOT + L * TC_NCOL + ch * 8), v[L]);
+              tc::tmem_ld8(lane_base + (uint32_t)(slot * SLOT + L * TC_NCOL + ch * 8), v[L]);
+            if constexpr (STK) tc::tmem_ld8(lane_base + (uint32_t)(slot * SLOT + TC_LEV * TC_NCOL + ch * 8), vs);
             tc::tmem_wait_ld();
             if (ch == nch - 1) {                               // this slot is drained
               tc::fence_before();
@@ -733,6 +973,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
               const float sc = kDs[nb + ch * 8 + c];
               th[ch * 8 + c] = x.hi * sc;
               tl[ch * 8 + c] = x.lo * sc;
+              if constexpr (STK) sl[ch * 8 + c] = __uint_as_float(vs[c]) * sc;
             }
           }
         }
@@ -748,7 +989,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
               // check terms of the R columns of this i
               float z[R];
 #pragma unroll
-              for (int r = 0; r < R; ++r) z[r] = zero_el ? 0.0f : zc[nb + il * R + r] - fabsf(th[il * R + r]);
+              for (int r = 0; r < R; ++r) {
+                // S >= |t|, and in the stacked form S >= sum_k |D_ik| |v_k|,
+                // whose bf16 products summed in FP32 are within 2^-7 of it
+                float lb = fabsf(th[il * R + r]);
+                if constexpr (STK) lb = fmaxf(lb, sl[il * R + r] * (1.0f - 0x1p-6f));
+                z[r] = zero_el ? 0.0f : zc[nb + il * R + r] - lb;
+              }
 #pragma unroll
               for (int k = 0; k < KR; ++k) {
                 if (ROWS || k < n_rows) {
@@ -766,7 +1013,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
                   // hi + lo: exact conversions by bit moves and one FP64 add
                   // (three FP64-pipe conversions measured 2 % slower: the
                   // pipe is shared with the producer's sine reduction)
-                  p.rows[k].out[e * NI + i] = dfm::f2d_bits(s) + dfm::f2d_bits(c);
+                  const double o = dfm::f2d_bits(s) + dfm::f2d_bits(c);
+                  if constexpr (STK) {
+                    for (int kk = tp.gstart[grp]; kk < tp.gstart[grp + 1]; ++kk) p.rows[tp.grow[kk]].out[e * NI + i] = o;
+                  } else {
+                    p.rows[k].out[e * NI + i] = o;
+                  }
                 }
               }
             }
@@ -787,7 +1039,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
           while (fm[w]) {
             const int b = __ffs(fm[w]) - 1;
             fm[w] &= fm[w] - 1u;
-            fallback_element(p, tile * TC_M + w * 32 + b, et, fu, ft);
+            if constexpr (STK) fallback_stacked(tp, grp, e0 + w * 32 + b, et, fu, ft);
+            else fallback_element(p, e0 + w * 32 + b, et, fu, ft);
           }
         }
         // cleared before this thread reaches the next tile-end barrier; the
@@ -810,14 +1063,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) element_tc_kernel(const __grid_
 }
 
 bool build_params(const EParams &p, TcParams &tp, std::string &why) {
-  if (p.n_groups != 1) { why = "more than one fused operand"; return false; }
-  if (p.NJ0 > 0 || p.groups[0].kind == 3) { why = "stacked producer (divergence / face-mass form)"; return false; }
-  if (p.R < 1 || p.R > 4) { why = "R outside 1..4"; return false; }
-  if (p.NJ < 1 || p.NJ > 64) { why = "contracted extent outside 1..64"; return false; }
-  if (p.NI < 1) { why = "empty output extent"; return false; }
-  if (p.n_rows < 1 || p.n_rows > TC_MAXROWS) { why = "more than 4 einsums"; return false; }
-  if (!p.has_g && p.R != 1) { why = "no geometric factor with R > 1"; return false; }
-  {
+  const bool stk = p.NJ0 > 0;
+  if (stk) {
+    // the stacked form: one group per distinct pair of per-element operands
+    if (p.n_groups < 1 || p.n_groups > EM_MAXROWS) { why = "producer groups outside 1..16"; return false; }
+    for (int g = 0; g < p.n_groups; ++g)
+      if (p.groups[g].kind != 3 || p.groups[g].X < 1 || p.groups[g].X > EM_MAXX) { why = "stacked producer"; return false; }
+    if (p.R != 1 || p.has_g) { why = "stacked form with R > 1 or a geometric factor"; return false; }
+    if (p.n_rows < 1 || p.n_rows > EM_MAXROWS) { why = "rows outside 1..16"; return false; }
+  } else {
+    if (p.n_groups != 1) { why = "more than one fused operand"; return false; }
+    if (p.groups[0].kind == 3) { why = "stacked producer without the stacked layout"; return false; }
+    if (p.R < 1 || p.R > 4) { why = "R outside 1..4"; return false; }
+    if (p.n_rows < 1 || p.n_rows > TC_MAXROWS) { why = "more than 4 einsums"; return false; }
+    if (!p.has_g && p.R != 1) { why = "no geometric factor with R > 1"; return false; }
     const EProd &q = p.groups[0];
     const int64_t lim = (int64_t)1 << 23;   // in-tile offsets m * se + j * sk stay 32-bit
     if (std::abs(q.a.se) >= lim || std::abs(q.a.sk) >= lim || std::abs(q.b.se) >= lim || std::abs(q.b.sk) >= lim) {
@@ -825,7 +1084,20 @@ bool build_params(const EParams &p, TcParams &tp, std::string &why) {
       return false;
     }
   }
+  if (p.NJ < 1 || p.NJ > 64) { why = "contracted extent outside 1..64"; return false; }
+  if (p.NI < 1) { why = "empty output extent"; return false; }
   tp.p = p;
+  tp.G = stk ? p.n_groups : 1;
+  {
+    int c = 0;
+    for (int g = 0; g < tp.G; ++g) {
+      tp.gstart[g] = (int8_t)c;
+      for (int k = 0; k < p.n_rows; ++k)
+        if (p.rows[k].group == g) tp.grow[c++] = (int8_t)k;
+    }
+    tp.gstart[tp.G] = (int8_t)c;
+    if (c != p.n_rows) { why = "row groups"; return false; }
+  }
   const int h0 = 16 / p.R;
   tp.IB = 2 * h0;
   tp.ncb = (p.NI + tp.IB - 1) / tp.IB;
@@ -840,23 +1112,29 @@ bool build_params(const EParams &p, TcParams &tp, std::string &why) {
   tp.fcheck = (1.0 + 1e-9) / (1e-12 - std::ldexp(1.0, -43)) * (1.0 + std::ldexp(1.0, -19));
   tp.wait_limit = tc::TIMEOUT_CYCLES;
   tp.status = nullptr;
+  // two buffers of u's digit planes where they fit, else one (the stacked
+  // form at K > 48: four K-slices of six planes take 96 KB per buffer)
+  tp.npl = stk ? TC_P + 1 : TC_P;
+  tp.nbuf = 2;
+  if (stk && 256 + (size_t)tc_smem(tp).total > TC_SMEM_LIMIT) tp.nbuf = 1;
   return true;
 }
 
 size_t smem_bytes(const TcParams &tp) { return 256 + (size_t)tc_smem(tp).total; }
 
-template <int R, int ROWS>
+template <int R, int ROWS, bool STK, int NBUF>
 cudaError_t launch_rr(const TcParams &tp, int grid, size_t smem, cudaStream_t s) {
   static std::atomic<uint64_t> attr{0};
-  const cudaError_t st = smem_limit_once((const void *)element_tc_kernel<R, ROWS>, (int)TC_SMEM_LIMIT, attr);
+  const cudaError_t st =
+      smem_limit_once((const void *)element_tc_kernel<R, ROWS, STK, NBUF>, (int)TC_SMEM_LIMIT, attr);
   if (st != cudaSuccess) return st;
-  return be_launch(element_tc_kernel<R, ROWS>, dim3(grid), dim3(TC_THREADS), smem, s, tp);
+  return be_launch(element_tc_kernel<R, ROWS, STK, NBUF>, dim3(grid), dim3(TC_THREADS), smem, s, tp);
 }
 // one einsum per term direction (R einsums, as in a gradient) is
 // specialized; other counts take the generic row loop
 template <int R>
 cudaError_t launch_r(const TcParams &tp, int grid, size_t smem, cudaStream_t s) {
-  return tp.p.n_rows == R ? launch_rr<R, R>(tp, grid, smem, s) : launch_rr<R, 0>(tp, grid, smem, s);
+  return tp.p.n_rows == R ? launch_rr<R, R, false, 2>(tp, grid, smem, s) : launch_rr<R, 0, false, 2>(tp, grid, smem, s);
 }
 
 }  // namespace
@@ -880,8 +1158,10 @@ cudaError_t launch_element_tc(const EParams &p, int *status, long long wait_limi
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t tiles = (p.E + TC_M - 1) / TC_M;
+  const int64_t tiles = (p.E + TC_M - 1) / TC_M * tp.G;
   const int grid = (int)std::min<int64_t>(tiles, sms);
+  if (p.NJ0 > 0)
+    return tp.nbuf == 1 ? launch_rr<1, 1, true, 1>(tp, grid, smem, s) : launch_rr<1, 1, true, 2>(tp, grid, smem, s);
   switch (p.R) {
     case 1: return launch_r<1>(tp, grid, smem, s);
     case 2: return launch_r<2>(tp, grid, smem, s);

@@ -1,6 +1,7 @@
 """Stacked form of the element strategy (DG local divergence and face mass)
 against the FP64 oracle: |got - ref| <= 1e-12 * S componentwise for the
-FP64-pipe and double-float variants, bit for bit on integer inputs.
+FP64-pipe, double-float and tensor-core variants (the last for contracted
+extents up to 64), bit for bit on integer inputs.
 
 The divergence 'xre,rij,xej->ei' reads the field through a select producer
 F(x,e,j) := x==0 ? u : (x==1 ? v : w); the face mass 'fe,ifj,fej->ei' has
@@ -46,16 +47,24 @@ def check(text, arrs, cfg=None, tol=1e-12):
 
 
 @pytest.mark.parametrize("order", [1, 2, 3, 4])
-@pytest.mark.parametrize("cfg", [None, DF, FP64], ids=["default", "df", "fp64"])
+@pytest.mark.parametrize("cfg", [None, DF, FP64, TC], ids=["default", "df", "fp64", "tc"])
 def test_divergence_orders(order, cfg):
     E = 777
     D, data = W.dg_divergence(E=E, order=order, rows=1)
-    check(W.dg_divergence_spec(E=E, order=order, rows=1), W.dg_divergence_arrays(D, data), cfg)
+    text, arrs = W.dg_divergence_spec(E=E, order=order, rows=1), W.dg_divergence_arrays(D, data)
+    if cfg is TC and order == 4:                 # K = 3 x 35 = 105 > 64
+        with pytest.raises(be.BEError) as exc:
+            run(text, arrs, TC)
+        assert exc.value.code == be.EUNSUPPORTED
+        return
+    check(text, arrs, cfg)
 
 
 @pytest.mark.parametrize("order", [1, 2, 3, 4])
-@pytest.mark.parametrize("cfg", [None, DF, FP64], ids=["default", "df", "fp64"])
+@pytest.mark.parametrize("cfg", [None, DF, FP64, TC], ids=["default", "df", "fp64", "tc"])
 def test_face_mass_orders(order, cfg):
+    """K = 4 NF = 12, 24, 40, 60: every order fits the tensor-core variant
+    (P4 with one buffer of u's digit planes)."""
     E = 777
     M, data = W.face_mass(E=E, order=order, rows=1)
     check(W.face_mass_spec(E=E, order=order, rows=1), W.face_mass_arrays(M, data), cfg)
@@ -78,7 +87,7 @@ def test_ragged_elements(E):
     check(W.dg_divergence_spec(E=E, order=2, rows=1), W.dg_divergence_arrays(D, data))
 
 
-@pytest.mark.parametrize("cfg", [DF, FP64], ids=["df", "fp64"])
+@pytest.mark.parametrize("cfg", [DF, FP64, TC], ids=["df", "fp64", "tc"])
 def test_integers_bit_exact(cfg):
     E = 500
     D, data = W.dg_divergence(E=E, order=3, rows=2, ints=True)
@@ -106,9 +115,55 @@ def test_plain_field_buffer():
     check(text, dict(J=J, D=D, F=F))
 
 
-def test_tensor_core_variant_refuses_stacked_form():
+@pytest.mark.parametrize("rows", [1, 3, 8])
+def test_tensor_core_groups_and_shared_rows(rows):
+    """Tensor-core variant with several producer groups (each row its own
+    fields: the tiles run over groups x element tiles) and with rows that
+    repeat a group (the same fields: one value written to both rows)."""
+    E = 1000
+    M, fd = W.face_mass(E=E, order=4, rows=rows)
+    check(W.face_mass_spec(E=E, order=4, rows=rows), W.face_mass_arrays(M, fd), TC)
+    D, data = W.dg_divergence(E=E, order=3, rows=rows)
+    text = W.dg_divergence_spec(E=E, order=3, rows=rows)
+    arrs = W.dg_divergence_arrays(D, data)
+    check(text, arrs, TC)
+    # the first row twice: one group, two rows
+    rows_part, decls = text.split(" ; ", 1)
+    head, rows_text = rows_part.split(" | ", 1)
+    first = rows_text.split(" | ")[0]
+    check(f"{head} | {first} | {rows_text} ; {decls}", arrs, TC)
+
+
+def test_tensor_core_wide_range_and_zero_elements():
+    """Fields spanning many decades (most elements cannot be certified and
+    are recomputed in FP64 at the end of their tile), elements whose fields
+    are all zero (exact zeros) and metric terms of 2^+-40: every output
+    within 1e-12 * S."""
+    E = 640
+    g = np.random.default_rng(5)
+    D, data = W.dg_divergence(E=E, order=3, rows=1)
+    arrs = W.dg_divergence_arrays(D, data)
+    arrs = {k: v.copy() for k, v in arrs.items()}
+    fields = [k for k, v in arrs.items() if v.ndim == 2 and v.shape[0] == E]
+    for k in fields:
+        arrs[k][::3] *= np.exp2(g.integers(-40, 41, size=arrs[k][::3].shape))
+        arrs[k][5::11] = 0.0
+    text = W.dg_divergence_spec(E=E, order=3, rows=1)
+    got = check(text, arrs, TC)
+    M, fd = W.face_mass(E=E, order=2, rows=1)
+    marr = {k: v.copy() for k, v in W.face_mass_arrays(M, fd).items()}
+    marr["U0"] *= np.exp2(g.integers(-40, 41, size=marr["U0"].shape))   # U[f, e, j]
+    marr["U0"][:, 7::13] = 0.0
+    check(W.face_mass_spec(E=E, order=2, rows=1), marr, TC)
+    assert np.all(np.isfinite(got[0]))
+
+
+def test_tensor_core_variant_refuses_long_contractions():
+    """The divergence at P4 contracts K = 105 > 64 values: the tensor-core
+    variant refuses it (the default for the stacked form is the double-float
+    kernel)."""
     E = 64
-    D, data = W.dg_divergence(E=E, order=2, rows=1)
+    D, data = W.dg_divergence(E=E, order=4, rows=1)
     with pytest.raises(be.BEError) as exc:
-        run(W.dg_divergence_spec(E=E, order=2, rows=1), W.dg_divergence_arrays(D, data), TC)
+        run(W.dg_divergence_spec(E=E, order=4, rows=1), W.dg_divergence_arrays(D, data), TC)
     assert exc.value.code == be.EUNSUPPORTED
