@@ -63,6 +63,13 @@
 // on expiry the CTA records BE_ETIMEOUT, every role leaves its loop
 // collectively, and the tensor memory is freed only after all issued MMAs
 // have completed.
+//
+// The stacked form (the divergence and the face mass: R[e,i] = sum_k
+// D[i,k] v[e,k], v = sum_x A_x B_x over the flat k = (s, j), K <= 64) is a
+// second instantiation: the producer forms v in double-float with a scale
+// from an exponent bound, tiles run over producer groups x element tiles,
+// and an eighth accumulator per slot sums bf16(|D|) x bf16(|v|), a lower
+// bound of S for the per-output check (with R = 1, |t| alone is a weak one).
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -86,8 +93,7 @@ constexpr int TC_M = 128;                       // elements per tile
 constexpr int TC_P = 6;                         // digits per operand
 constexpr int TC_LEV = 7;                       // levels 0..6, one accumulator each
 constexpr int TC_NCOL = 32;                     // columns of a block (and of an accumulator)
-constexpr int TC_SLOT = TC_LEV * TC_NCOL;       // 224 columns per slot
-constexpr int TC_NSLOT = 2;                     // 448 of the 512 tensor-memory columns
+constexpr int TC_SLOT = TC_LEV * TC_NCOL;       // 224 columns per slot, two slots (448 of the 512 tensor-memory columns; 512 in the stacked form)
 constexpr int TC_KU = 4;                        // buffers of per-element row scales
 constexpr int NPROD = 224, NEPI = 256;
 constexpr int MMA_WARP = NPROD / 32;            // 7
