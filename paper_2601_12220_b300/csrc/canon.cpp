@@ -122,8 +122,12 @@ struct RowSearch {
   bool have = false;
   std::vector<int> best_rows, best_argid;
   long leaves = 0;
+  std::vector<int64_t> segs;             // [depth][row][position] segment scratch
+  std::vector<int> fresh_args;           // a segment's arguments in order of first appearance
   RowSearch(const Einsum &e_, const std::vector<int> &perm_, const Tok *prev_table, const Tok *prev_dt)
       : e(e_), perm(perm_) {
+    segs.assign((size_t)e.b * e.b * e.n, 0);
+    fresh_args.assign((size_t)e.n, 0);
     seq.resize(e.b);
     owner.assign(e.args.size(), -2);
     for (int i = 0; i < e.b; ++i)
@@ -160,32 +164,37 @@ struct RowSearch {
       }
       return;
     }
-    Tok minseg;
-    bool first = true;
-    std::vector<Tok> segs(e.b);
+    // the segment of every unused row (n ids each) in this depth's scratch
+    // row of segs (allocated once per search), and the smallest of them
+    const int n = e.n;
+    const size_t depth = rows.size();
+    int64_t *seg = segs.data() + depth * (size_t)e.b * n;
+    int *fresh = fresh_args.data();
+    int minrow = -1;
     for (int i = 0; i < e.b; ++i) {
       if (used[i]) continue;
-      Tok s;
-      int nid = next_id;
-      std::vector<std::pair<int, int>> fresh;
-      for (int a : seq[i]) {
+      int64_t *s = seg + (size_t)i * n;
+      int nid = next_id, nf = 0;
+      for (int p = 0; p < n; ++p) {
+        const int a = seq[i][p];
         int id = argid[a];
         if (id < 0) {
-          for (auto &f : fresh)
-            if (f.first == a) id = f.second;
+          for (int f = 0; f < nf; ++f)
+            if (fresh[f] == a) id = next_id + f;
           if (id < 0) {
             id = nid++;
-            fresh.push_back({a, id});
+            fresh[nf++] = a;
           }
         }
-        s.push_back(id);
+        s[p] = id;
       }
-      segs[i] = s;
-      if (first || s < minseg) { minseg = s; first = false; }
+      if (minrow < 0 || std::lexicographical_compare(s, s + n, seg + (size_t)minrow * n, seg + (size_t)minrow * n + n))
+        minrow = i;
     }
+    const int64_t *minseg = seg + (size_t)minrow * n;
     if (have && prefix_cmp(prefix, best_table) == 0) {
       size_t L = prefix.size();
-      for (size_t k = 0; k < minseg.size(); ++k) {
+      for (int k = 0; k < n; ++k) {
         int64_t want = best_table[L + k];
         if (minseg[k] < want) break;
         if (minseg[k] > want) return;
@@ -193,7 +202,7 @@ struct RowSearch {
     }
     std::vector<int> chosen;
     for (int i = 0; i < e.b; ++i) {
-      if (used[i] || segs[i] != minseg) continue;
+      if (used[i] || !std::equal(minseg, minseg + n, seg + (size_t)i * n)) continue;
       bool dup = false;
       for (int r : chosen)
         if (interchangeable(r, i, argid)) { dup = true; break; }
@@ -210,7 +219,7 @@ struct RowSearch {
       used[i] = 1;
       rows.push_back(i);
       size_t L = prefix.size();
-      prefix.insert(prefix.end(), minseg.begin(), minseg.end());
+      prefix.insert(prefix.end(), minseg, minseg + n);
       dfs(rows, used, argid, nid, prefix);
       prefix.resize(L);
       rows.pop_back();

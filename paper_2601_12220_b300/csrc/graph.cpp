@@ -17,7 +17,6 @@
 #include <algorithm>
 #include <map>
 #include <set>
-#include <unordered_set>
 
 #include "canon.hpp"
 
@@ -25,22 +24,32 @@ namespace be {
 
 namespace {
 
+// successor and predecessor lists, sorted and without repeated edges; an
+// edge test is a binary search in the source's successors
 struct Adj {
   std::vector<std::vector<int>> succ, pred;
-  std::unordered_set<int64_t> has;
   int n;
   explicit Adj(const Graph &g) : succ(g.n), pred(g.n), n(g.n) {
+    std::vector<int> dout(g.n, 0), din(g.n, 0);
     for (auto &e : g.edges) {
-      int64_t k = (int64_t)e.first * g.n + e.second;
-      if (has.insert(k).second) {
-        succ[e.first].push_back(e.second);
-        pred[e.second].push_back(e.first);
-      }
+      ++dout[e.first];
+      ++din[e.second];
     }
-    for (auto &v : succ) std::sort(v.begin(), v.end());
-    for (auto &v : pred) std::sort(v.begin(), v.end());
+    for (int v = 0; v < g.n; ++v) {
+      succ[v].reserve(dout[v]);
+      pred[v].reserve(din[v]);
+    }
+    for (auto &e : g.edges) {
+      succ[e.first].push_back(e.second);
+      pred[e.second].push_back(e.first);
+    }
+    for (auto *lists : {&succ, &pred})
+      for (auto &v : *lists) {
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+      }
   }
-  bool edge(int a, int b) const { return has.count((int64_t)a * n + b) > 0; }
+  bool edge(int a, int b) const { return std::binary_search(succ[a].begin(), succ[a].end(), b); }
 };
 
 int count_color(const std::vector<int> &v, const std::vector<int> &color, int c) {
@@ -154,6 +163,8 @@ Graph to_induced_graph(const Einsum &e) {
   g.acc_out_node.resize(n_acc_out);
   for (int d = 0; d < n_acc_out; ++d) g.acc_out_node[d] = o_accout + d;
 
+  // every node has few edges; a generous reservation avoids regrowing the list
+  g.edges.reserve((size_t)g.n * 6 + 64);
   auto E = [&](int a, int b) { g.edges.push_back({a, b}); };
   int acc = o_accin;
   g.acc_in_node.assign(e.b, std::vector<std::vector<int>>(e.n));
