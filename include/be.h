@@ -336,7 +336,14 @@ int be_tune(be_ctx *x, const be_einsum *e, int32_t precision, const be_buf *bufs
  *   differently); a step's tiles follow the tiles of the steps it reads in
  *   the one persistent launch and wait (bounded) until those have finished,
  *   the intermediates in a workspace owned by the batch
- *   (cfg->stage_mask bit 1 keeps every instance on its loop nest).  cfg may
+ *   (cfg->stage_mask bit 1 keeps every instance on its loop nest).  With
+ *   cfg->split >= 2 a factored FP64 instance of two steps whose last step
+ *   is a GEMM of at least 2^tile[3] multiply-adds (the output's letters
+ *   those of the first step's result and then those of one operand, or the
+ *   reverse), carrying at least half of its multiply-adds, runs on a dense
+ *   branch instead: per row the first step (and, when the operand's own
+ *   layout does not flatten to the GEMM, a permuted copy of it) as generic
+ *   launches, then the split-precision GEMM (1e-6 * S).  cfg may
  *   be NULL.  Everything is captured once in a CUDA
  *   graph with concurrent branches: the persistent launch of generic
  *   tiles, the element launches and the split / GEMM launches (four
@@ -353,10 +360,15 @@ int be_tune(be_ctx *x, const be_einsum *e, int32_t precision, const be_buf *bufs
  *   the precision mode's tolerance) and is itself deterministic.
  * be_batch_info -- rows, tiles and total operand terms of the generic part
  *   (factored steps counted as rows).
- * be_batch_kinds -- number of instances given each strategy.
- * be_batch_factored -- number of factored instances, the longest chain of
- *   dependent steps (phases; 1 without factored instances), and bytes of
- *   the intermediates' workspace.
+ * be_batch_kinds -- number of instances given each strategy (the
+ *   dense-routed factored instances count as dense).
+ * be_batch_instance_kind -- the evaluation of instance k: 0 generic loop
+ *   nest, 1 element, 2 dense (split precision), 3 factored steps in the
+ *   persistent launch, 4 factored steps on a dense branch (split precision);
+ *   BE_EARG for k outside 0 .. n - 1.
+ * be_batch_factored -- number of factored instances in the persistent
+ *   launch, the longest chain of dependent steps (phases; 1 without
+ *   factored instances), and bytes of the intermediates' workspace.
  */
 int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_buf *const *bufs,
                     const int32_t *n_bufs, const be_buf *const *outs, const int32_t *n_outs,
@@ -365,6 +377,7 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
 int be_batch_run(be_batch *b, void *stream);
 int be_batch_info(const be_batch *b, int64_t *rows, int64_t *tiles, double *terms);
 int be_batch_kinds(const be_batch *b, int32_t *generic, int32_t *element, int32_t *dense);
+int be_batch_instance_kind(const be_batch *b, int32_t k, int32_t *kind);
 int be_batch_factored(const be_batch *b, int32_t *instances, int32_t *phases, int64_t *workspace_bytes);
 
 /*

@@ -33,7 +33,7 @@ EXPORTS = [
     "be_ctx_destroy", "be_lookup", "be_record", "be_db_size", "be_execute", "be_execute_host",
     "be_plan_strategy", "be_status", "be_ctx_set_timing", "be_ctx_timing", "be_gemm_split_noalloc",
     "be_gemm_split_noalloc_status", "be_ctx_set_wait_limit", "be_peak_probe",
-    "be_batch_create", "be_batch_run", "be_batch_info", "be_batch_kinds", "be_batch_factored", "be_batch_destroy", "be_tune", "be_tune_batch",
+    "be_batch_create", "be_batch_run", "be_batch_info", "be_batch_kinds", "be_batch_instance_kind", "be_batch_factored", "be_batch_destroy", "be_tune", "be_tune_batch",
     "be_server_create", "be_server_submit", "be_server_wait", "be_server_drain", "be_server_stats",
     "be_server_reset_stats", "be_server_trace", "be_server_destroy", "be_raise", "be_raised_name", "be_record_facts",
     "be_load_transforms",
@@ -121,6 +121,7 @@ def lib():
             "be_batch_run": (ctypes.c_int, [vp, vp]),
             "be_batch_info": (ctypes.c_int, [vp, P(i64), P(i64), P(ctypes.c_double)]),
             "be_batch_kinds": (ctypes.c_int, [vp, P(i32), P(i32), P(i32)]),
+            "be_batch_instance_kind": (ctypes.c_int, [vp, i32, P(i32)]),
             "be_batch_factored": (ctypes.c_int, [vp, P(i32), P(i32), P(i64)]),
             "be_tune_batch": (ctypes.c_int, [vp, i32, P(vp), P(P(Buf)), P(i32), P(P(Buf)), P(i32),
                                              P(P(ctypes.c_double)), P(i32), P(Config), i32, vp, P(Config),
@@ -639,6 +640,15 @@ class Batch:
         g, m, d = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         check(lib().be_batch_kinds(self._h, ctypes.byref(g), ctypes.byref(m), ctypes.byref(d)))
         return {"generic": g.value, "element": m.value, "dense": d.value}
+
+    INSTANCE_KINDS = ("loop nest", "element", "dense", "factored", "dense factored")
+
+    def instance_kind(self, k: int) -> str:
+        """How instance k is evaluated: one of INSTANCE_KINDS ("dense" and
+        "dense factored" run in split precision)."""
+        v = ctypes.c_int32()
+        check(lib().be_batch_instance_kind(self._h, k, ctypes.byref(v)))
+        return self.INSTANCE_KINDS[v.value]
 
     def factored(self):
         """Factored instances, persistent launches (phases) per run and bytes of

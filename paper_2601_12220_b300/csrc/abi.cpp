@@ -904,6 +904,9 @@ struct be_batch {
   int32_t n_factored = 0;
   void *fws = nullptr;
   size_t fws_bytes = 0;
+  // per instance: 0 loop nest, 1 element, 2 dense, 3 factored steps in the
+  // persistent launch, 4 factored steps on a dense branch (be_batch_instance_kind)
+  std::vector<int8_t> inst_kind;
   ~be_batch() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -994,8 +997,100 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
     FactorOrder fo;
     std::vector<std::vector<FOp>> ops;   // per row, the operand views
     std::vector<void *> outs;            // per row, the output
+    // the split-precision route: two steps, the last a GEMM of the first
+    // step's result (laid out as inter_letters) and user operand `user`
+    // (permuted first into a dense user_letters layout when copy_user)
+    bool dense = false, copy_user = false;
+    int user = -1;
+    std::vector<int8_t> inter_letters, user_letters;
   };
   std::vector<FacInst> fac_inst;
+  // steps of the factored instances on the dense branches: a generic launch
+  // (the first step, a permuted copy) or a split-precision GEMM
+  struct DnStep {
+    bool gemm = false;
+    GParams gp;
+    DensePlan dp;
+  };
+  std::vector<std::vector<DnStep>> dnf_steps;   // per dense-routed instance
+  // the dense route of a factored FP64 instance (split >= 2; off at 1: on
+  // the uneven mix it cost 6 %, since the persistent grid holds every SM
+  // until its queue drains and the route's chain of small launches per
+  // instance then runs in the tail): the order has
+  // two steps, the last contracting the first step's result I with one
+  // operand U into the output as a GEMM of at least dense_min multiply-adds
+  // that carries at least half of the instance's multiply-adds; the output's
+  // letters are those of one operand followed by those of the other (no
+  // letter kept by both).  I is laid out (its output letters, K) and U, when
+  // its own layout does not flatten that way, is first copied so
+  auto dense_route = [&](const Einsum &e, FacInst &fi) {
+    if (c.split < 2 || e.out_dtype != F64 || fi.fo.steps.size() != 2) return;
+    for (auto &a : e.args)
+      if (a.dtype != F64) return;
+    const int n = e.n, sa = fi.fo.steps[1][0], sb = fi.fo.steps[1][1];
+    if (sb < 0 || (sa == n) == (sb == n) || std::max(sa, sb) != n) return;
+    const int user = sa == n ? sb : sa;
+    const FOp &U0 = fi.ops[0][user];
+    bool inU[26] = {false}, inI[26] = {false}, isOut[26] = {false};
+    for (int8_t ch : U0.letters) inU[ch] = true;
+    for (int8_t ch : fi.fo.letters[0]) inI[ch] = true;
+    for (int8_t ch : e.out) isOut[ch] = true;
+    if (e.out.empty()) return;
+    const bool A_is_I = inI[e.out[0]];
+    const bool *inA = A_is_I ? inI : inU, *inB = A_is_I ? inU : inI;
+    size_t nm = 0;
+    while (nm < e.out.size() && inA[e.out[nm]]) ++nm;
+    for (size_t k2 = 0; k2 < e.out.size(); ++k2) {
+      const int8_t ch = e.out[k2];
+      if (inA[ch] && inB[ch]) return;                               // a letter kept by both
+      if (k2 < nm ? !inA[ch] : !inB[ch]) return;
+    }
+    std::vector<std::pair<int64_t, int8_t>> kk;                      // K letters by U's stride
+    double M = 1, N = 1, K = 1;
+    for (size_t k2 = 0; k2 < U0.letters.size(); ++k2) {
+      const int8_t ch = U0.letters[k2];
+      if (isOut[ch]) continue;
+      if (!inI[ch]) return;                                          // summed inside U alone
+      kk.push_back({-std::llabs(U0.strides[k2]), ch});
+      K *= (double)e.len[ch];
+    }
+    for (int8_t ch : fi.fo.letters[0])
+      if (!isOut[ch] && !inU[ch]) return;                            // summed inside I alone
+    if (kk.empty()) return;
+    for (size_t k2 = 0; k2 < e.out.size(); ++k2) (k2 < nm ? M : N) *= (double)e.len[e.out[k2]];
+    if (M * N * K * e.b < dense_min || M * N * K < 0.5 * fi.fo.factored) return;
+    std::stable_sort(kk.begin(), kk.end());
+    std::vector<int8_t> kl;
+    for (auto &pr : kk) kl.push_back(pr.second);
+    fi.user_letters.clear();
+    fi.inter_letters.clear();
+    for (int8_t ch : e.out) {
+      if (inU[ch]) fi.user_letters.push_back(ch);
+      if (inI[ch]) fi.inter_letters.push_back(ch);
+    }
+    fi.user_letters.insert(fi.user_letters.end(), kl.begin(), kl.end());
+    fi.inter_letters.insert(fi.inter_letters.end(), kl.begin(), kl.end());
+    // U in place when its output letters (in the output's order) and K each
+    // flatten to one stride in every row
+    auto flat = [&](const FOp &f, const std::vector<int8_t> &ls) {
+      int64_t expect = 0;
+      for (int k2 = (int)ls.size() - 1; k2 >= 0; --k2) {
+        int64_t st = -1;
+        for (size_t d = 0; d < f.letters.size(); ++d)
+          if (f.letters[d] == ls[k2]) st = f.strides[d];
+        if (k2 == (int)ls.size() - 1) expect = st;
+        if (st != expect || st <= 0) return false;
+        expect *= e.len[ls[k2]];
+      }
+      return true;
+    };
+    std::vector<int8_t> uo(fi.user_letters.begin(), fi.user_letters.end() - (long)kl.size());
+    fi.copy_user = false;
+    for (int i = 0; i < e.b; ++i)
+      if (!flat(fi.ops[i][user], uo) || !flat(fi.ops[i][user], kl)) fi.copy_user = true;
+    fi.user = user;
+    fi.dense = true;
+  };
   // a generic row (or a factored step) into the tile list of its group
   // (group 0: the factored steps without dependencies, 1: the unfactored
   // rows, q + 1: the factored steps of dependency depth q >= 1); outputs
@@ -1047,6 +1142,7 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
     }
     return BE_OK;
   };
+  b->inst_kind.assign(n, 0);
   for (int k = 0; k < n; ++k) {
     if (!es[k]) return fail(BE_EARG, "NULL einsum in batch");
     const Einsum &e = es[k]->e;
@@ -1072,6 +1168,7 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
         el_inst.push_back(k);
         el_cfg.push_back(ci);
         ++b->n_kind[1];
+        b->inst_kind[k] = 1;
         continue;
       }
       if (c.split >= 1 && plan_dense(e, bi, bo, dp, why, &sc) == OK &&
@@ -1080,10 +1177,10 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
         dn_inst.push_back(k);
         dn_plan.push_back(dp);
         ++b->n_kind[2];
+        b->inst_kind[k] = 2;
         continue;
       }
     }
-    ++b->n_kind[0];
     // factored evaluation: an instance whose order of steps cuts the loop
     // nest's multiply-adds at least 1.5 times runs as one- and two-operand steps over
     // dense intermediates (stage_mask bit 1 turns this off)
@@ -1103,11 +1200,20 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
         fi.fo = fo;
         fi.ops = ops;
         for (int i = 0; i < e.b; ++i) fi.outs.push_back(bo[i].ptr);
+        dense_route(e, fi);
+        if (fi.dense) {
+          ++b->n_kind[2];
+          b->inst_kind[k] = 4;
+        } else {
+          ++b->n_kind[0];
+          ++b->n_factored;
+          b->inst_kind[k] = 3;
+        }
         fac_inst.push_back(std::move(fi));
-        ++b->n_factored;
         continue;
       }
     }
+    ++b->n_kind[0];
     for (int i = 0; i < e.b; ++i) {
       GParams p;
       st = plan_generic_row(e, i, bi, bo[i], sc, p, err);
@@ -1124,12 +1230,18 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
     size_t need = 0;
     for (auto &fi : fac_inst) {
       const Einsum &e = es[fi.k]->e;
-      for (int i = 0; i < e.b; ++i)
+      for (int i = 0; i < e.b; ++i) {
         for (size_t q = 0; q + 1 < fi.fo.steps.size(); ++q) {
           double elems = 1.0;
           for (int8_t c : fi.fo.letters[q]) elems *= (double)e.len[c];
           need += ((size_t)elems * dtype_size(e.out_dtype) + 255) / 256 * 256;
         }
+        if (fi.dense && fi.copy_user) {
+          double elems = 1.0;
+          for (int8_t c : fi.user_letters) elems *= (double)e.len[c];
+          need += ((size_t)elems * dtype_size(e.out_dtype) + 255) / 256 * 256;
+        }
+      }
     }
     if (need) {
       cudaError_t ce0 = cudaMalloc(&b->fws, need);
@@ -1140,6 +1252,55 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
     for (auto &fi : fac_inst) {
       const Einsum &e = es[fi.k]->e;
       const int n = e.n;
+      if (fi.dense) {
+        // the dense route: per row the permuted copy of U (if any), the
+        // first step into I (generic launches) and the GEMM, in that order
+        // on one dense branch
+        auto dense_fop = [&](const std::vector<int8_t> &ls) {
+          FOp r;
+          r.dtype = e.out_dtype;
+          r.letters = ls;
+          r.ptr = (char *)b->fws + off;
+          double elems = 1.0;
+          for (int8_t ch : ls) elems *= (double)e.len[ch];
+          off += ((size_t)elems * dtype_size(e.out_dtype) + 255) / 256 * 256;
+          r.strides.assign(ls.size(), 1);
+          for (int d = (int)ls.size() - 2; d >= 0; --d) r.strides[d] = r.strides[d + 1] * e.len[ls[d + 1]];
+          return r;
+        };
+        std::vector<DnStep> steps;
+        for (int i = 0; i < e.b; ++i) {
+          FOp U = fi.ops[i][fi.user];
+          int st;
+          if (fi.copy_user) {
+            const FOp Uc = dense_fop(fi.user_letters);
+            DnStep d;
+            st = plan_factor_step(e, U, nullptr, Uc.letters, const_cast<void *>(Uc.ptr), d.gp, err);
+            if (st) return fail(st, "instance " + std::to_string(fi.k) + ", operand copy: " + err);
+            steps.push_back(d);
+            U = Uc;
+          }
+          const FOp I = dense_fop(fi.inter_letters);
+          const int s0a = fi.fo.steps[0][0], s0b = fi.fo.steps[0][1];
+          DnStep d0;
+          st = plan_factor_step(e, fi.ops[i][s0a], s0b >= 0 ? &fi.ops[i][s0b] : nullptr, I.letters,
+                                const_cast<void *>(I.ptr), d0.gp, err);
+          if (st) return fail(st, "instance " + std::to_string(fi.k) + ", factored step: " + err);
+          steps.push_back(d0);
+          DnStep d1;
+          std::string why;
+          if (plan_factor_step_dense(e, I, U, e.out, fi.outs[i], d1.dp, why) == OK) {
+            d1.gemm = true;
+            ws_need = std::max(ws_need, dense_workspace_bytes(d1.dp.M, d1.dp.N, d1.dp.K));
+          } else {   // the layouts were chosen for the GEMM; a generic step keeps the result correct
+            st = plan_factor_step(e, I, &U, e.out, fi.outs[i], d1.gp, err);
+            if (st) return fail(st, "instance " + std::to_string(fi.k) + ", factored step: " + err);
+          }
+          steps.push_back(d1);
+        }
+        dnf_steps.push_back(std::move(steps));
+        continue;
+      }
       for (int i = 0; i < e.b; ++i) {
         std::vector<FOp> slot = fi.ops[i];
         std::vector<int> slot_phase(n, -1), slot_row(n, -1);
@@ -1205,7 +1366,7 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
   b->ws_stride = (ws_need + 255) / 256 * 256;
   if (ce == cudaSuccess && ws_need) ce = cudaMalloc(&b->ws, b->ws_stride * (size_t)NDN);
   if (ce != cudaSuccess) return fail(BE_ECUDA, std::string("batch setup: ") + cudaGetErrorString(ce));
-  if (!el_inst.empty() || !dn_inst.empty() || b->n_factored) {
+  if (!el_inst.empty() || !dn_inst.empty() || !dnf_steps.empty() || b->n_factored) {
     if (x) {
       std::lock_guard<std::mutex> g(x->mu);
       int st = ensure_status(x);
@@ -1246,6 +1407,15 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
       cudaError_t r = run_dense_rows(nullptr, dn_plan[q], cd, (char *)b->ws + b->ws_stride * br, b->status, wl, st);
       if (r != cudaSuccess) return r;
     }
+    // the dense-routed factored instances continue the round robin
+    for (size_t q = 0; q < dnf_steps.size(); ++q) {
+      if ((dn_inst.size() + q) % NDN != (size_t)br) continue;
+      for (const DnStep &d : dnf_steps[q]) {
+        cudaError_t r = d.gemm ? run_dense_rows(nullptr, d.dp, cd, (char *)b->ws + b->ws_stride * br, b->status, wl, st)
+                               : launch_generic(d.gp, st);
+        if (r != cudaSuccess) return r;
+      }
+    }
     return cudaSuccess;
   };
   int est = launch_el(b->branch[0]);
@@ -1263,7 +1433,7 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
     // parts are concurrent in the graph (the side kernels take SMs as the
     // persistent grid's CTAs leave) and join after it
     cudaError_t c1 = cudaSuccess;
-    const bool side = !el_inst.empty() || !dn_inst.empty();
+    const bool side = !el_inst.empty() || !dn_inst.empty() || !dnf_steps.empty();
     if (side) {
       c1 = cudaEventRecord(b->ev[0], b->cap);
       for (int q = 0; q < 1 + NDN && c1 == cudaSuccess; ++q) c1 = cudaStreamWaitEvent(b->branch[q], b->ev[0], 0);
@@ -1361,6 +1531,13 @@ int be_batch_kinds(const be_batch *b, int32_t *generic, int32_t *element, int32_
   if (generic) *generic = b->n_kind[0];
   if (element) *element = b->n_kind[1];
   if (dense) *dense = b->n_kind[2];
+  return BE_OK;
+}
+
+int be_batch_instance_kind(const be_batch *b, int32_t k, int32_t *kind) {
+  if (!b || !kind) return fail(BE_EARG, "NULL argument");
+  if (k < 0 || k >= (int32_t)b->inst_kind.size()) return fail(BE_EARG, "instance index out of range");
+  *kind = b->inst_kind[k];
   return BE_OK;
 }
 

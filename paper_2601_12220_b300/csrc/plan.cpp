@@ -925,12 +925,14 @@ bool operand_fop(const Einsum &e, int row, int pos, const std::vector<BufIn> &bu
   return true;
 }
 
-int plan_factor_step(const Einsum &e, const FOp &x, const FOp *y, const std::vector<int8_t> &out_letters, void *out,
-                     GParams &p, std::string &err) {
+// a pairwise (or unary) step as a batched einsum of one row and one or two
+// identity arguments X, Y over the operands' views, with a dense row-major
+// output over out_letters
+static void step_einsum(const Einsum &e, const FOp &x, const FOp *y, const std::vector<int8_t> &out_letters,
+                        void *out, Einsum &s, std::vector<BufIn> &bufs, BufIn &bo) {
   // the step as a batched einsum of one row and one or two identity
   // arguments (one: a unary step summing the operand's own letters)
   const int n = y ? 2 : 1;
-  Einsum s;
   s.b = 1;
   s.n = n;
   s.out = out_letters;
@@ -946,7 +948,6 @@ int plan_factor_step(const Einsum &e, const FOp &x, const FOp *y, const std::vec
   for (int8_t c : out_letters) s.used[c] = true;
   s.out_dtype = e.out_dtype;
   const FOp *ops[2] = {&x, y};
-  std::vector<BufIn> bufs;
   for (int k = 0; k < n; ++k) {
     Buffer bf;
     bf.name = k ? "Y" : "X";
@@ -962,8 +963,25 @@ int plan_factor_step(const Einsum &e, const FOp &x, const FOp *y, const std::vec
     bufs.push_back(BufIn{const_cast<void *>(ops[k]->ptr), ops[k]->strides.data(), (int32_t)ops[k]->letters.size(),
                          ops[k]->dtype});
   }
-  BufIn bo{out, nullptr, (int32_t)out_letters.size(), e.out_dtype};
+  bo = BufIn{out, nullptr, (int32_t)out_letters.size(), e.out_dtype};
+}
+
+int plan_factor_step(const Einsum &e, const FOp &x, const FOp *y, const std::vector<int8_t> &out_letters, void *out,
+                     GParams &p, std::string &err) {
+  Einsum s;
+  std::vector<BufIn> bufs;
+  BufIn bo;
+  step_einsum(e, x, y, out_letters, out, s, bufs, bo);
   return plan_generic_row(s, 0, bufs, bo, {}, p, err);
+}
+
+int plan_factor_step_dense(const Einsum &e, const FOp &x, const FOp &y, const std::vector<int8_t> &out_letters,
+                           void *out, DensePlan &dp, std::string &why) {
+  Einsum s;
+  std::vector<BufIn> bufs;
+  BufIn bo;
+  step_einsum(e, x, &y, out_letters, out, s, bufs, bo);
+  return plan_dense(s, bufs, {bo}, dp, why, nullptr);
 }
 
 }  // namespace be

@@ -97,5 +97,11 @@ bool operand_fop(const Einsum &e, int row, int pos, const std::vector<BufIn> &bu
 // einsum's
 int plan_factor_step(const Einsum &e, const FOp &x, const FOp *y, const std::vector<int8_t> &out_letters, void *out,
                      GParams &p, std::string &err);
+// The same pairwise step planned for the split-precision tensor cores (a
+// GEMM C = A B after flattening: the output's letters from one operand,
+// then from the other, the contracted letters flattenable in both views);
+// EUNSUPPORTED with the reason otherwise.
+int plan_factor_step_dense(const Einsum &e, const FOp &x, const FOp &y, const std::vector<int8_t> &out_letters,
+                           void *out, DensePlan &dp, std::string &why);
 
 }  // namespace be

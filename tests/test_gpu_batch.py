@@ -339,3 +339,67 @@ def test_factored_instances_match_the_oracle(dt):
         torch.cuda.synchronize()
         for o, a in zip(outs, alone):
             assert torch.equal(o, a)
+
+
+DENSE_FACTOR_SPECS = [
+    # (spec without declarations, shapes per buffer); sizes make the first
+    # pairwise order unique and its GEMM step at least 2^23 multiply-adds
+    # face mass with 128 output dofs (beyond the element strategy's
+    # operators): the operator's contracted letters (f, j) are contiguous
+    ("fe,ifj,fej->ei | J,M,U | K,M,V", {"J": (4, 1024), "M": (128, 4, 32), "U": (4, 1024, 32),
+                                         "K": (4, 1024), "V": (4, 1024, 32)}),
+    # DG gradient with 96 output dofs: D[r, i, j] puts i between the
+    # contracted r and j, so D is first copied into an (i, r, j) layout
+    ("rij,er,ej->ei | D,G,U", {"D": (3, 96, 48), "G": (2048, 3), "U": (2048, 48)}),
+    # triple product: the first step's result is the GEMM's A operand
+    ("ik,kl,lj->ij | A,B,C", {"A": (128, 64), "B": (64, 64), "C": (64, 1024)}),
+]
+
+
+def test_dense_routed_factored_instances():
+    """With split >= 2, factored FP64 instances of two steps whose last step
+    is a GEMM of at least 2^23 multiply-adds run on a dense branch: the first
+    step (and a permuted copy of the operator where its layout does not
+    flatten) as generic launches, the GEMM in split precision.  Every output
+    within 1e-6 S of the FP64 oracle, replays bitwise identical; with split
+    off the same instances are factored in the persistent launch and meet
+    1e-12 S."""
+    g = np.random.default_rng(43)
+    items, meta = [], []
+    for spec, shapes in DENSE_FACTOR_SPECS:
+        decl = " ; ".join(f"{k}:f64[{','.join(map(str, v))}]" for k, v in shapes.items())
+        text = f"{spec} ; {decl}"
+        arrs = {k: g.standard_normal(v) for k, v in shapes.items()}
+        e = be.Einsum(text)
+        bufs = {k: torch.from_numpy(v).to(DEV) for k, v in arrs.items()}
+        outs = [torch.full(e.out_shape, float("nan"), dtype=torch.float64, device=DEV) for _ in range(e.b)]
+        items.append((e, bufs, outs))
+        meta.append((text, arrs))
+    refs = [ev.evaluate(text, arrs) for text, arrs in meta]
+    ctx = be.Context(None, device=0)
+    b = be.Batch(ctx, items, be.make_config(split=2))
+    assert [b.instance_kind(k) for k in range(len(items))] == ["dense factored"] * len(items)
+    one = be.Batch(ctx, items, be.make_config(split=1))       # the route is off at split = 1
+    assert [one.instance_kind(k) for k in range(len(items))] == ["factored"] * len(items)
+    one.close()
+    assert b.kinds()["dense"] == len(items) and b.factored()["instances"] == 0
+    b.run()
+    torch.cuda.synchronize()
+    first = [[o.clone() for o in outs] for _, _, outs in items]
+    b.run()
+    torch.cuda.synchronize()
+    assert ctx.status() == be.OK
+    for (e, _, outs), fst, ref, (text, _) in zip(items, first, refs, meta):
+        for k, (r, S) in enumerate(ref):
+            assert torch.equal(outs[k], fst[k])
+            got = outs[k].cpu().numpy()
+            assert np.all(np.abs(got - r) <= 1e-6 * S), text[:30]
+    off = be.Batch(ctx, items, be.make_config(split=0))
+    assert [off.instance_kind(k) for k in range(len(items))] == ["factored"] * len(items)
+    off.run()
+    torch.cuda.synchronize()
+    for (e, _, outs), ref, (text, _) in zip(items, refs, meta):
+        for k, (r, S) in enumerate(ref):
+            assert np.all(np.abs(outs[k].cpu().numpy() - r) <= 1e-12 * S), text[:30]
+    with pytest.raises(be.BEError):
+        b.instance_kind(len(items))
