@@ -1443,13 +1443,17 @@ int be_batch_create(be_ctx *x, int32_t n, const be_einsum *const *es, const be_b
       }
       for (int q = 0; q < NDN && c1 == cudaSuccess; ++q) c1 = launch_dn(q, b->branch[1 + q]);
     }
-    if (c1 == cudaSuccess) c1 = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), b->cap);
-    if (c1 == cudaSuccess && b->d_done)
-      c1 = cudaMemsetAsync(b->d_done, 0, sizeof(unsigned int) * b->rows.size(), b->cap);
-    // one persistent launch; factored steps wait in it for the steps they read
-    if (c1 == cudaSuccess)
-      c1 = launch_persistent(b->d_rows, b->d_tiles, (int64_t)b->tiles.size(), b->d_counter, b->d_done,
-                             b->d_done ? b->status : nullptr, wl, b->grid, b->block, b->cap);
+    // one persistent launch; factored steps wait in it for the steps they
+    // read (left out, with its counter resets, when there are no generic
+    // tiles and the branches hold all the work)
+    if (!b->tiles.empty() || !side) {
+      if (c1 == cudaSuccess) c1 = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), b->cap);
+      if (c1 == cudaSuccess && b->d_done)
+        c1 = cudaMemsetAsync(b->d_done, 0, sizeof(unsigned int) * b->rows.size(), b->cap);
+      if (c1 == cudaSuccess)
+        c1 = launch_persistent(b->d_rows, b->d_tiles, (int64_t)b->tiles.size(), b->d_counter, b->d_done,
+                               b->d_done ? b->status : nullptr, wl, b->grid, b->block, b->cap);
+    }
     if (side) {
       for (int q = 0; q < 1 + NDN && c1 == cudaSuccess; ++q) c1 = cudaEventRecord(b->ev[1 + q], b->branch[q]);
       for (int q = 0; q < 1 + NDN && c1 == cudaSuccess; ++q) c1 = cudaStreamWaitEvent(b->cap, b->ev[1 + q], 0);
