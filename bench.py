@@ -1234,6 +1234,12 @@ def other_configs(args):
         "chem_dense_v128_o32_b4": sub(run_chem, steps=5, warmup=3),
         "uneven_mix_512": sub(run_mix, steps=6, warmup=3),
         "serving_poisson_20k": sub(run_serving, serve_seconds=3.0, serve_sweep=""),
+        # the rows built beyond the five configurations, on the same run
+        "dg_divergence_p4_b1": sub(run_stacked, workload="dg_divergence", order=4, rows=1, steps=10, warmup=3,
+                                   element_variant=0),
+        "face_mass_p4_b1": sub(run_stacked, workload="face_mass", order=4, rows=1, steps=10, warmup=3,
+                               element_variant=0),
+        "dense_affine_n96": sub(run_affine, affine_n=96, steps=5, warmup=3),
     }
 
 
